@@ -1,0 +1,295 @@
+"""Pins of the oracle's dynamics against exact enumeration and closed forms.
+
+* Distributional: the replayed schedules (serial RSU on the Philox stream,
+  the two-phase Poisson-domain schedule, the two-lane model) and the
+  independent serial reference are compared state by state, by a chi-square
+  test, with the exact master-equation evolution of :mod:`oracle.exact`.
+  Each test also checks that the same samples REJECT a plausible mistake
+  (wrong rate placement, wrong direction, fixed attempt counts ...), so the
+  pin has power.
+* Closed forms: uniform stationary measure of RSU, <W^2> = (L+1)/12 on the
+  half-filled ring, current (p-q) N (L-N) / (L (L-1)) per bond and sweep.
+* Conservation of particle number, and the paper's growth exponent
+  beta = alpha / z = 1/3 (sec. 2.2).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.linalg import expm
+
+from oracle import exact as ex
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def chi2_pvalue(counts: np.ndarray, probs: np.ndarray, min_expected: float = 5.0) -> float:
+    expected = probs * counts.sum()
+    order = np.argsort(expected)
+    obs_b, exp_b = [], []
+    acc_o = acc_e = 0.0
+    for k in order:
+        acc_o += counts[k]
+        acc_e += expected[k]
+        if acc_e >= min_expected:
+            obs_b.append(acc_o)
+            exp_b.append(acc_e)
+            acc_o = acc_e = 0.0
+    if acc_e > 0:
+        obs_b[-1] += acc_o
+        exp_b[-1] += acc_e
+    obs_b, exp_b = np.array(obs_b), np.array(exp_b)
+    stat = float(((obs_b - exp_b) ** 2 / exp_b).sum())
+    return float(stats.chi2.sf(stat, len(obs_b) - 1))
+
+
+def histogram(space: ex.Space, state: np.ndarray) -> np.ndarray:
+    L = space.L
+    mask = (1 << L) - 1
+    counts = np.zeros(space.n)
+    for s in range(state.shape[0]):
+        x = int(state[s, 0, 0]) & mask
+        if space.lanes == 2:
+            x |= (int(state[s, 1, 0]) & mask) << L
+        counts[space.index[x]] += 1
+    return counts
+
+
+S_DIST = 20000
+
+
+def _replay_hist(oracle_mod, P, t, mask=None):
+    st = oracle_mod.init_state(P)
+    m = oracle_mod.disorder(P) if mask is None else mask
+    oracle_mod.replay(P, st, 0, t, mask=m)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# Closed forms via the enumerator
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10])
+def test_rsu_stationary_uniform_width_and_current(L):
+    p, q = 0.75, 0.25
+    N = L // 2
+    m = ex.RingModel(L, N, p, q)
+    pi = ex.stationary(m.rsu_sweep())
+    assert np.max(np.abs(pi - 1.0 / m.sp.n)) < 1e-12
+    # uniform half-filled ring: E[W^2] = (L+1)/12 (random-walk bridge)
+    assert abs(pi @ m.sp.w2() - (L + 1) / 12) < 1e-12
+    # current per bond per sweep: L attempts x (1/L) x (p-q) P(10 at a bond)
+    j = pi @ m.current_per_attempt_vector(p, q) / L
+    assert abs(j - (p - q) * N * (L - N) / (L * (L - 1))) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Ring: serial replay, domain replay and serial reference vs exact evolution
+# ---------------------------------------------------------------------------
+
+def test_serial_replay_matches_exact_rsu(oracle_mod):
+    L, p, q = 8, 0.75, 0.25
+    P = oracle_mod.Params(L=L, schedule=oracle_mod.SCHED_SERIAL, samples_per_real=S_DIST, seed=11,
+                          p_thr=oracle_mod.threshold(p), q_thr=oracle_mod.threshold(q))
+    m = ex.RingModel(L, L // 2, p, q)
+    for t in (1, 3):
+        st = _replay_hist(oracle_mod, P, t)
+        counts = histogram(m.sp, st)
+        exact = m.sp.flat_alt() @ np.linalg.matrix_power(m.rsu_sweep(), t)
+        assert chi2_pvalue(counts, exact) > 1e-4, t
+        wrong = m.sp.flat_alt() @ np.linalg.matrix_power(ex.RingModel(L, L // 2, q, p).rsu_sweep(), t)
+        assert chi2_pvalue(counts, wrong) < 1e-6
+
+
+@pytest.mark.parametrize("D", [1, 2, 4])
+def test_domain_replay_matches_exact_domain_schedule(oracle_mod, D):
+    L, p, q = 8, 0.75, 0.25
+    P = oracle_mod.Params(L=L, D=D, samples_per_real=S_DIST, seed=3 + D, p_thr=oracle_mod.threshold(p),
+                          q_thr=oracle_mod.threshold(q))
+    m = ex.RingModel(L, L // 2, p, q)
+    A = m.domain_sweep(D)
+    for t in (1, 2):
+        counts = histogram(m.sp, _replay_hist(oracle_mod, P, t))
+        exact = m.sp.flat_alt() @ np.linalg.matrix_power(A, t)
+        assert chi2_pvalue(counts, exact) > 1e-4, (D, t)
+    # power: the same samples reject D fixed attempts per domain (no Poisson count)
+    if D >= 2:
+        I = np.eye(m.sp.n)
+        fixed = np.zeros_like(I)
+        for o in range(2 * D):
+            B = I
+            for phase in (0, 1):
+                for g in range(L // (2 * D)):
+                    base = o + 2 * D * g + phase * D
+                    M = sum(m.K[(base + j) % L] for j in range(D)) / D
+                    B = B @ np.linalg.matrix_power(M, D)
+            fixed += B
+        fixed /= 2 * D
+        wrong = m.sp.flat_alt() @ np.linalg.matrix_power(fixed, 2)
+        assert chi2_pvalue(counts, wrong) < 1e-6
+
+
+def test_domain_replay_disorder_rate_placement(oracle_mod):
+    """Right hops across (i, i+1) use p_i, left hops use q_{i+1} (paper
+    sec. 2.1); the slow class of Eq. (bimodal) replaces both at a site."""
+    L, D = 8, 2
+    pf, ps, qf, qs = 0.9, 0.3, 0.4, 0.1
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(L=L, D=D, samples_per_real=S_DIST, seed=21, p_thr=th(pf), q_thr=th(qf),
+                          dis_kind=oracle_mod.DIS_BIMODAL, dis_a_thr=th(0.5), dis_b_thr=th(ps), dis_c_thr=th(qs),
+                          dis_seed=5)
+    mask = oracle_mod.disorder(P)
+    slow = [(int(mask[0, 0]) >> i) & 1 for i in range(L)]
+    assert 0 < sum(slow) < L
+    pvec = [ps if c else pf for c in slow]
+    qvec = [qs if c else qf for c in slow]
+    m = ex.RingModel(L, L // 2, pvec, qvec)
+    counts = histogram(m.sp, _replay_hist(oracle_mod, P, 2, mask=mask))
+    exact = m.sp.flat_alt() @ np.linalg.matrix_power(m.domain_sweep(D), 2)
+    assert chi2_pvalue(counts, exact) > 1e-4
+    # plausible mistake: left hop out of site i+1 using q_i instead of q_{i+1}
+    q_shift = [qvec[(i - 1) % L] for i in range(L)]
+    wrong_m = ex.RingModel(L, L // 2, pvec, q_shift)
+    wrong = m.sp.flat_alt() @ np.linalg.matrix_power(wrong_m.domain_sweep(D), 2)
+    assert chi2_pvalue(counts, wrong) < 1e-6
+
+
+def test_serial_reference_matches_exact_rsu(oracle_mod):
+    L, p, q = 8, 0.6, 0.1
+    P = oracle_mod.Params(L=L, schedule=oracle_mod.SCHED_SERIAL, samples_per_real=S_DIST,
+                          p_thr=oracle_mod.threshold(p), q_thr=oracle_mod.threshold(q))
+    m = ex.RingModel(L, L // 2, p, q)
+    st = oracle_mod.init_state(P)
+    oracle_mod.serial_reference(P, st, 2, rng_seeds=np.arange(S_DIST) + 1000)
+    counts = histogram(m.sp, st)
+    exact = m.sp.flat_alt() @ np.linalg.matrix_power(m.rsu_sweep(), 2)
+    assert chi2_pvalue(counts, exact) > 1e-4
+    wrong = m.sp.flat_alt() @ expm(2 * 0.5 * m.generator())  # half the time
+    assert chi2_pvalue(counts, wrong) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Two lanes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("schedule", ["domain", "serial"])
+def test_two_lane_replay_matches_exact(oracle_mod, schedule):
+    L, D, omega = 4, 1, 0.5
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(model=oracle_mod.MODEL_TWO_LANE, L=L, D=D, samples_per_real=S_DIST, seed=31,
+                          schedule=oracle_mod.SCHED_DOMAIN if schedule == "domain" else oracle_mod.SCHED_SERIAL,
+                          p_thr=oracle_mod.ALWAYS, q_thr=oracle_mod.ALWAYS, dis_kind=oracle_mod.DIS_TURNING,
+                          dis_a_thr=th(0.5), dis_b_thr=th(omega), dis_seed=2)
+    mask = oracle_mod.disorder(P)
+    turning = [i for i in range(L) if (int(mask[0, 0]) >> i) & 1]
+    assert 0 < len(turning) < L
+    m = ex.TwoLaneModel(L, L, 1.0, 1.0, turning, omega)
+    A = m.domain_sweep(D) if schedule == "domain" else m.rsu_sweep()
+    st = _replay_hist(oracle_mod, P, 2, mask=mask)
+    counts = histogram(m.sp, st)
+    exact = m.sp.flat_alt() @ np.linalg.matrix_power(A, 2)
+    assert chi2_pvalue(counts, exact) > 1e-4
+    # plausible mistake: lane B moving right like lane A
+    wrong_m = ex.TwoLaneModel(L, L, 1.0, 1.0, turning, omega)
+    wrong_m.KB = [m.sp.bond_kernel(1, b, 1.0, 0.0) for b in range(L)]
+    W = wrong_m.domain_sweep(D) if schedule == "domain" else wrong_m.rsu_sweep()
+    assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(W, 2)) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Conservation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("model,schedule,dis", [
+    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2)])
+def test_particle_number_conserved(oracle_mod, model, schedule, dis):
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(model=model, schedule=schedule, L=1024, D=64, samples_per_real=3, seed=9,
+                          init_kind=oracle_mod.INIT_BERNOULLI_HALF, init_seed=4,
+                          p_thr=th(0.7) if model == 0 else oracle_mod.ALWAYS,
+                          q_thr=th(0.2) if model == 0 else oracle_mod.ALWAYS,
+                          dis_kind=dis, dis_a_thr=th(0.1 if dis == 1 else 0.05), dis_b_thr=th(0.3 if dis == 1 else 0.1),
+                          dis_c_thr=th(0.05), dis_seed=8)
+    st = oracle_mod.init_state(P)
+    n0 = [[int(np.unpackbits(st[s, pl].view(np.uint8)).sum()) for pl in range(P.planes)] for s in range(P.S)]
+    cnt = oracle_mod.replay(P, st, 0, 20, mask=oracle_mod.disorder(P))
+    n1 = [[int(np.unpackbits(st[s, pl].view(np.uint8)).sum()) for pl in range(P.planes)] for s in range(P.S)]
+    for s in range(P.S):
+        if model == 0:
+            assert n0[s] == n1[s]
+            assert cnt[s, 0] + cnt[s, 1] > 0
+        else:
+            assert sum(n0[s]) == sum(n1[s])
+            # lane A loses A->B turns and gains B->A turns
+            assert n1[s][0] - n0[s][0] == int(cnt[s, 3]) - int(cnt[s, 2])
+
+
+# ---------------------------------------------------------------------------
+# Long runs: stationary width, current, growth exponent
+# ---------------------------------------------------------------------------
+
+def test_serial_reference_stationary_width_and_current(oracle_mod):
+    L, p, q, S = 64, 0.75, 0.25, 64
+    P = oracle_mod.Params(L=L, samples_per_real=S, p_thr=oracle_mod.threshold(p), q_thr=oracle_mod.threshold(q))
+    st = oracle_mod.init_state(P)
+    oracle_mod.serial_reference(P, st, 3000, rng_seeds=np.arange(S) + 77)  # burn-in past saturation
+    w2 = np.zeros(S)
+    n_meas, gap = 40, 50
+    cnt_tot = np.zeros((S, 4), dtype=np.uint64)
+    for k in range(n_meas):
+        cnt_tot += oracle_mod.serial_reference(P, st, gap, rng_seeds=np.arange(S) * 1000 + k + 5)
+        for s in range(S):
+            w2[s] += oracle_mod.width2(L, *oracle_mod.heights(st[s, 0], L)) / n_meas
+    sem = w2.std(ddof=1) / np.sqrt(S)
+    assert abs(w2.mean() - (L + 1) / 12) < 4 * sem
+    j = (cnt_tot[:, 0].astype(float) - cnt_tot[:, 1].astype(float)) / (L * n_meas * gap)
+    jexp = (p - q) * (L // 2) * (L // 2) / (L * (L - 1))
+    assert abs(j.mean() - jexp) < 4 * j.std(ddof=1) / np.sqrt(S)
+
+
+def _growth_slope(times, w2):
+    x = np.log(np.array(times, dtype=float))
+    y = np.log(np.array(w2) - 0.25)  # paper sec. 2.2 subtracts W^2(0) = 0.25
+    return float(np.polyfit(x, y, 1)[0])
+
+
+def _w2_at(oracle_mod, P, times, serial_ref: bool):
+    if not serial_ref:
+        r = oracle_mod.run(P, times[-1], times)
+        return r.w2[:, :, 0].mean(axis=1), r.w2[:, :, 0]
+    st = oracle_mod.init_state(P)
+    out = np.zeros((len(times), P.S))
+    done = 0
+    for i, t in enumerate(times):
+        oracle_mod.serial_reference(P, st, t - done, rng_seeds=np.arange(P.S) * 7919 + t)
+        done = t
+        for s in range(P.S):
+            out[i, s] = oracle_mod.width2(P.L, *oracle_mod.heights(st[s, 0], P.L))
+    return out.mean(axis=1), out
+
+
+def test_growth_exponent_beta_one_third(oracle_mod):
+    with open(GOLDEN) as f:
+        g = json.load(f)["kpz_exponents"]
+    beta = g["alpha"] / g["z"]
+    times = [16, 32, 64, 128, 256]
+    P = oracle_mod.Params(L=4096, D=256, samples_per_real=24, seed=99)
+    for serial_ref in (True, False):
+        mean, _ = _w2_at(oracle_mod, P, times, serial_ref)
+        slope = _growth_slope(times, mean)
+        assert abs(slope - 2 * beta) < 0.07, (serial_ref, slope)
+
+
+def test_domain_schedule_width_within_3sigma_of_serial_reference(oracle_mod):
+    """W(t) of the D = 256 domain schedule vs the independent serial RSU."""
+    times = [8, 32, 128]
+    for p, q in [(1.0, 0.0), (0.75, 0.25)]:
+        P = oracle_mod.Params(L=4096, D=256, samples_per_real=48, seed=123,
+                              p_thr=oracle_mod.threshold(p), q_thr=oracle_mod.threshold(q))
+        m_dom, all_dom = _w2_at(oracle_mod, P, times, False)
+        m_ser, all_ser = _w2_at(oracle_mod, P, times, True)
+        for i in range(len(times)):
+            sig = np.sqrt(all_dom[i].var(ddof=1) / P.S + all_ser[i].var(ddof=1) / P.S)
+            assert abs(m_dom[i] - m_ser[i]) < 3 * sig, (p, times[i], m_dom[i], m_ser[i], sig)

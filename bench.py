@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Throughput of the bit-packed ASEP / KPZ engine on one GB300 (or N replicas).
+
+Workload (the growth-regime batch of the paper's KPZ study, sec. 2.2, at the
+size the headline is quoted on): one ring of L = 2^17 sites per sample (4096
+uint32 words, resident in shared memory), ASEP with p = 0.75, q = 0.25, flat
+1010... start, 2^14 Monte Carlo sweeps with W^2 recorded at the log-spaced
+times of Eq. (sampling), 256 independent samples in one launch, two-phase
+Poisson-domain schedule with D = 256.
+
+One step = re-draw the initial state + 2^14 sweeps of all samples (with the
+fused height / W^2 recording).  The metric is site-update attempts per second
+(L attempts per sample per sweep).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (plain C replay of the same schedule)
+on the host cores on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica on its own
+sample range (no data-path collective); the timed region is bracketed by
+barriers and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_SITES = 1 << 17
+DOMAIN = 256
+SAMPLES = 256
+N_MCS = 1 << 14
+P_RATE, Q_RATE = 0.75, 0.25
+SEED = 1
+# Algorithmic int32 lane operations per attempt of the domain kernel: a
+# quarter of one Philox4x32-10 call (10 rounds x [2 wide multiplies + 2
+# three-input XORs] = 40) plus the update (slot and row decode 2, address 1,
+# load 1, straddle test 1, pattern extract 2, threshold select 2, masked
+# compare 2, flip mask and xor 2, store 1) = 10 + 14.
+OPS_PER_ATTEMPT = 24
+SMS, LANES_PER_SM = 152, 128  # GB300: 152 SMs x 4 schedulers x 32 lanes issue per clock
+
+WORKLOAD_NAME = ("growth regime, batched: L=2^17 ring (4096 u32 words, shared-memory resident), ASEP p=0.75 q=0.25, "
+                 "flat start, 2^14 MCS, W^2 at log-spaced times, 256 samples in one launch")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxes.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def _traffic_from_profile():
+    """DRAM bytes per launch of the domain kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1012_0385_gb300", "csrc", "asep_kernels.cu")
+    prof = os.path.join(ROOT, "profiles", "k_domain_growth_regime_traffic.txt")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = dict(line.strip().split("=", 1) for line in open(prof) if "=" in line)
+        if kv.get("kernel_source_sha256_16") == digest:
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def cpu_oracle_sample(target_s: float, n_mcs_cap: int = N_MCS):
+    """Time the CPU oracle (whole path: init, sweeps, heights at the log
+    times) on `cores` samples of the workload, sized to about target_s."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    th = oracle.threshold
+    P = oracle.Params(L=L_SITES, D=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE), q_thr=th(Q_RATE), seed=SEED)
+    k = min(cores, SAMPLES)
+    oracle.build()
+    # calibrate on 4 sweeps
+    t0 = time.perf_counter()
+    oracle.run(P, 4, [0], threads=cores, samples=range(k))
+    rate = k * L_SITES * 4 / (time.perf_counter() - t0)
+    n = int(max(8, min(n_mcs_cap, target_s * rate / (k * L_SITES))))
+    from paper_1012_0385_gb300.sampling import log_times
+
+    t0 = time.perf_counter()
+    oracle.run(P, n, [t for t in log_times(N_MCS) if t <= n], threads=cores, samples=range(k))
+    dt = time.perf_counter() - t0
+    return {"value": k * L_SITES * n / dt, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+            "sample": f"{k} of 256 samples x {n} of 2^14 sweeps (init + sweeps + W^2 at the log times), "
+                      f"{dt:.1f} s on {cores} host threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = 8.0
+    for _ in range(args.warmup):
+        cpu_oracle_sample(0.5)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(per_step)
+        vals.append(r["value"])
+        secs.append(L_SITES * SAMPLES * N_MCS / r["value"])
+    value = statistics.mean(vals)
+    line = {"metric": "site-update attempts/s", "value": value, "unit": "attempts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_NAME, "L": L_SITES, "samples": SAMPLES, "n_mcs": N_MCS,
+                       "domain_sites": DOMAIN, "schedule": "two-phase Poisson-domain RSU",
+                       "note": "ms_per_step extrapolates the sampled oracle rate to one full step"},
+            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300.sampling import log_times
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    th = A.asep_threshold
+    times = log_times(N_MCS)
+
+    def params():
+        return A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, first_sample=rank * SAMPLES,
+                             p_thr=th(P_RATE), q_thr=th(Q_RATE), seed=SEED)
+
+    stream = torch.cuda.current_stream()
+    ctx = A.asep_create(params(), sample_times=times)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    attempts_per_step = L_SITES * SAMPLES * N_MCS
+
+    for w in range(args.warmup):
+        A.asep_reset(ctx, seed=1000 + w)
+        A.asep_sweep(ctx, N_MCS)
+    torch.cuda.synchronize()
+
+    launches0 = A.asep_get_info(ctx)["kernel_launches"]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    step_ms, kern_ms = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        A.asep_reset(ctx, seed=SEED + k)
+        e1.record(stream)
+        A.asep_sweep(ctx, N_MCS)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        step_ms.append(e0.elapsed_time(e2))
+        kern_ms.append(e1.elapsed_time(e2))
+    clk = clocks.stop()
+    launches = A.asep_get_info(ctx)["kernel_launches"] - launches0
+    # sanity: the last step's width table is finite and starts at W^2 = 1/4
+    _, _, w2 = A.asep_width(ctx)
+    assert w2.shape[0] == len(times) and abs(w2[0].mean() - 0.25) < 1e-12 and w2[-1].mean() > 1.0
+    A.asep_destroy(ctx)
+
+    total_ms = sum(step_ms)
+    kernel_ms = statistics.mean(kern_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms, kernel_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, kernel_ms = float(t[0]), float(t[1])
+    value = attempts_per_step * args.steps * world / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: create (host params and
+    # sample times in), sweeps, W(t) table out, destroy
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = d2h = 0
+    e2e_s = []
+    for k in range(e2e_steps):
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        c = A.asep_create(params(), sample_times=times)
+        A.asep_sweep(c, N_MCS)
+        sh, sh2, w2 = A.asep_width(c)
+        A.asep_destroy(c)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+        h2d = 8 * len(times) + 4 * len(A.asep_poisson_table(DOMAIN)[1])
+        d2h = sh.nbytes + sh2.nbytes
+    e2e_time = statistics.mean(e2e_s)
+    if dist is not None:
+        t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_time = float(t[0])
+    e2e_value = attempts_per_step * world / e2e_time
+
+    if rank == 0:
+        peaks = _peaks()
+        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_ops = SMS * LANES_PER_SM * max_mhz * 1e6
+        achieved_ops = L_SITES * SAMPLES * N_MCS / (kernel_ms / 1000.0) * OPS_PER_ATTEMPT
+        line = {
+            "metric": "site-update attempts/s", "value": value, "unit": "attempts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "L": L_SITES, "samples_per_gpu": SAMPLES, "n_mcs": N_MCS,
+                       "sample_times": len(times), "domain_sites": DOMAIN,
+                       "schedule": "two-phase Poisson-domain RSU", "rates": {"p": P_RATE, "q": Q_RATE},
+                       "l2": "flushed between steps (256 MB write outside the timed region)",
+                       "parallelism": f"replicas x{world} (disjoint sample ranges)"},
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": _traffic_from_profile(),
+                         "kernel": "k_domain<ring>", "kernel_ms": kernel_ms,
+                         "ops_per_attempt": OPS_PER_ATTEMPT,
+                         "peak_basis": f"{SMS} SMs x {LANES_PER_SM} int32 lanes/clk x {max_mhz:.0f} MHz (issue)"},
+            "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

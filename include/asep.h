@@ -1,0 +1,203 @@
+/*
+ * asep.h -- C ABI of libasep.so, a GB300 (sm_103a) Monte Carlo engine for the
+ * 1+1-d restricted-solid-on-solid (KPZ) surface mapped onto a bit-packed ASEP
+ * lattice gas (Schulz, Odor, Odor, Nagy, "Simulation of 1+1 dimensional
+ * surface growth and lattice gases using GPUs", arXiv:1012.0385).
+ *
+ * Model (paper sec. 2, Fig. "kpzasep"): an up slope of the roof-top surface is
+ * a particle (bit 1), a down slope a hole (bit 0).  Deposition is a right hop
+ * 10 -> 01 across bond (i, i+1) with probability p_i, evaporation a left hop
+ * 01 -> 10 with probability q_{i+1} (paper sec. 2.1).  Quenched columnar
+ * disorder draws a slow class per site with probability Q (Eq. bimodal,
+ * paper sec. 2.3).  The two-lane model (paper sec. 3) couples a right-moving
+ * ring A and a left-moving ring B through quenched turning sites.
+ *
+ * Storage: 32 sites per uint32 word, bit k of word w is site 32 w + k.  A
+ * context holds S = n_realizations * samples_per_real independent samples,
+ * each with `planes` = 1 (ring) or 2 (lanes A, B) planes of L / 32 words;
+ * host copies use the layout [S][planes][L/32].
+ *
+ * Randomness: Philox4x32-10 keyed by a 64-bit seed, counter = (sweep, tag,
+ * call, sample, domain or site group); no generator state is stored, so
+ * (words, sweep index, params) is a complete checkpoint.
+ *
+ * Rates are u32 thresholds t: 0 = never, ASEP_ALWAYS = always, otherwise a
+ * multiple of 4096 meaning probability t / 2^32 (see asep_threshold).
+ *
+ * Schedules:
+ *   ASEP_SCHED_SERIAL  plain random-sequential update (RSU, paper sec. 2.1):
+ *                      per sweep L (two lanes: 2L) attempts on uniformly drawn
+ *                      bonds.  One GPU thread per sample; L a power of two.
+ *   ASEP_SCHED_DOMAIN  two-phase Poisson-domain RSU (no paper counterpart; the
+ *                      paper's GPU schedule is a two-sub-lattice cellular
+ *                      automaton).  Per sweep a random offset splits the ring
+ *                      into super-domains of 2D sites; the first halves run,
+ *                      then the second halves; each half-domain performs a
+ *                      Poisson(D) (two lanes: Poisson(2D)) number of attempts
+ *                      on uniformly drawn bonds of its own D (2D) bonds.
+ *
+ * Error behaviour: every function returns ASEP_OK (0) or a negative
+ * ASEP_ERR_* code and never aborts; the context keeps a message readable with
+ * asep_last_error().  A context that saw ASEP_ERR_CUDA may be unusable.
+ *
+ * Threading: a context is used by one host thread at a time.  Device work is
+ * enqueued on the context's stream; functions that return host data
+ * synchronise that stream only.
+ */
+#ifndef ASEP_H
+#define ASEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASEP_OK 0
+#define ASEP_ERR_INVALID (-1) /* bad argument or unsupported combination */
+#define ASEP_ERR_NOMEM (-2)   /* device or host allocation failed */
+#define ASEP_ERR_CUDA (-3)    /* a CUDA runtime call failed */
+#define ASEP_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define ASEP_ERR_STATE (-5)   /* call not valid in the context's state */
+
+#define ASEP_MODEL_RING 0u     /* one ring, right rate p_i, left rate q_{i+1} */
+#define ASEP_MODEL_TWO_LANE 1u /* lane A right (p_thr), lane B left (q_thr) */
+
+#define ASEP_SCHED_DOMAIN 0u
+#define ASEP_SCHED_SERIAL 1u
+
+#define ASEP_DIS_NONE 0u
+#define ASEP_DIS_BIMODAL 1u /* dis_a = Q, dis_b = p_slow, dis_c = q_slow     */
+#define ASEP_DIS_TURNING 2u /* two lanes: dis_a = site density, dis_b = omega */
+
+#define ASEP_INIT_FLAT_ALT 0u       /* 1010...: site i occupied iff i even (paper sec. 2.1) */
+#define ASEP_INIT_BERNOULLI_HALF 1u /* every lane site occupied with probability 1/2 (sec. 3) */
+
+#define ASEP_ALWAYS 0xFFFFFFFFu
+
+typedef struct asep_ctx asep_ctx; /* opaque; owns every device buffer it allocates */
+
+/* Device allocator hook: when alloc is non-NULL the context obtains all of
+ * its device memory through it (e.g. a framework's caching allocator) and
+ * returns it through free_fn; otherwise it uses cudaMalloc / cudaFree. */
+typedef void* (*asep_alloc_fn)(size_t bytes, void* user);
+typedef void (*asep_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct asep_params {
+  uint32_t model;            /* ASEP_MODEL_* */
+  uint32_t schedule;         /* ASEP_SCHED_* */
+  uint64_t L;                /* sites per lane; DOMAIN: multiple of 2*domain_sites; SERIAL: power of two */
+  uint32_t domain_sites;     /* D: power of two in [32, 2048]; 0 = 256 or the largest that divides L/2 */
+  uint32_t n_realizations;   /* quenched-disorder realizations (1 without disorder) */
+  uint32_t samples_per_real; /* samples per realization */
+  uint32_t first_sample;     /* global id of sample 0 (disjoint ranges make replicas mergeable) */
+  uint32_t p_thr;            /* ring: right-hop rate of fast sites; two lanes: lane A rate */
+  uint32_t q_thr;            /* ring: left-hop rate of fast sites; two lanes: lane B rate */
+  uint32_t dis_kind;         /* ASEP_DIS_* */
+  uint32_t dis_a_thr;
+  uint32_t dis_b_thr;
+  uint32_t dis_c_thr;
+  uint32_t init_kind;        /* ASEP_INIT_* */
+  uint64_t seed;             /* dynamics key */
+  uint64_t dis_seed;         /* quenched-disorder key (realization r uses sample field r) */
+  uint64_t init_seed;        /* initial-filling key */
+  const uint64_t* sample_times; /* host array, ascending sweep counts at which heights are recorded (0 = start) */
+  uint32_t n_sample_times;
+  uint32_t flags;            /* reserved, 0 */
+  void* stream;              /* cudaStream_t for all work of the context; NULL = default stream */
+  asep_alloc_fn alloc;       /* optional allocator hook (with free_fn and alloc_user) */
+  asep_free_fn free_fn;
+  void* alloc_user;
+} asep_params;
+
+typedef struct asep_info {
+  uint64_t L;
+  uint32_t D;             /* effective domain size (DOMAIN schedule) */
+  uint32_t planes;        /* 1 or 2 */
+  uint32_t S;             /* samples */
+  uint32_t n_recorded;    /* sample times recorded so far */
+  uint64_t sweep;         /* sweeps done so far (the next sweep's index) */
+  uint64_t attempts_per_sweep; /* L * planes per sample */
+  uint64_t device_bytes;  /* device memory held by the context */
+  uint64_t kernel_launches; /* kernels the context has enqueued so far */
+} asep_info;
+
+/* Validate `params`, allocate device memory, draw the initial state (paper
+ * sec. 2.1 flat start, or sec. 3 random half filling) and the quenched
+ * disorder (Eq. bimodal or turning sites), and record the heights at sweep 0
+ * when 0 is a sample time.  On success *out owns the context; on failure
+ * *out is NULL and nothing is leaked.  The sample_times array is copied. */
+int asep_create(const asep_params* params, asep_ctx** out);
+
+/* Enqueue n_mcs sweeps (Monte Carlo steps, paper sec. 2.1: one sweep = L
+ * attempts per lane and sample) of all S samples on the context stream,
+ * recording heights after every sweep count listed in sample_times.
+ * Asynchronous: returns once the work is enqueued. */
+int asep_sweep(asep_ctx* ctx, uint64_t n_mcs);
+
+/* Copy the heights recorded so far.  Entry e = (time index, sample, plane),
+ * layout [n_recorded][S][planes]: sum_h[e] = sum_i h_i with
+ * h_i = sum_{j<=i} (2 n_j - 1); sum_h2[2e], sum_h2[2e+1] = low and high words
+ * of the unsigned 128-bit sum_i h_i^2; w2[e] = W^2 of Eq. (W) (paper sec.
+ * 2.1) = (L sum h^2 - (sum h)^2) / L^2, evaluated exactly then rounded.  Any
+ * output pointer may be NULL.  n_entries must be >= n_recorded*S*planes.
+ * Synchronises the context stream. */
+int asep_width(asep_ctx* ctx, int64_t* sum_h, uint64_t* sum_h2, double* w2, size_t n_entries);
+
+/* Copy the packed lattices, layout [S][planes][L/32], and the number of
+ * sweeps done.  n_words must be >= S*planes*L/32.  Synchronises. */
+int asep_state(asep_ctx* ctx, uint32_t* words, size_t n_words, uint64_t* sweep_out);
+
+/* Replace the lattices and the sweep counter (resume from a checkpoint made
+ * by asep_state, or set a test state).  Layout as asep_state. */
+int asep_load_state(asep_ctx* ctx, const uint32_t* words, size_t n_words, uint64_t sweep);
+
+/* Start the ensemble again on the same buffers: re-draw the initial state
+ * with init_seed, use `seed` for the dynamics from now on, set the sweep
+ * counter to 0, clear the hop counters and the height table, and record
+ * sweep 0 when it is a sample time.  The quenched disorder is kept.
+ * Asynchronous (context stream); allocates nothing. */
+int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed);
+
+/* Cumulative hop counters per sample, layout [S][4]: ring = (right hops,
+ * left hops, 0, 0); two lanes = (lane A hops, lane B hops, A->B lane
+ * changes, B->A lane changes).  The net current of paper sec. 3 is
+ * J = c[0] - c[1].  Synchronises. */
+int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n);
+
+/* Copy the quenched planes, layout [n_realizations][L/32] (bit = slow site
+ * for BIMODAL, turning site for TURNING).  Synchronises. */
+int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words);
+
+int asep_get_info(const asep_ctx* ctx, asep_info* info);
+
+/* Wait for all work of the context. */
+int asep_sync(asep_ctx* ctx);
+
+/* Free everything the context owns.  NULL-safe; synchronises first. */
+int asep_destroy(asep_ctx* ctx);
+
+/* Last error message of the context (or of the last failed asep_create when
+ * ctx is NULL); never NULL. */
+const char* asep_last_error(const asep_ctx* ctx);
+
+/* Threshold of probability p: 0 for p <= 0, ASEP_ALWAYS for p >= 1, else
+ * round(p * 2^20) * 4096.  Host only. */
+uint32_t asep_threshold(double p);
+
+/* The attempt-count table of a domain with m bonds: T_k = floor(2^32 *
+ * P(Poisson(m) <= k)); *k_lo = number of leading zero entries, table[j] =
+ * T_{k_lo + j} for j < *n_out, ending before the first T_k = 2^32 - 1.  A
+ * draw w gives K = k_lo + #{j : table[j] <= w}.  Host only; capacity is the
+ * length of `table`. */
+int asep_poisson_table(uint32_t m, uint32_t* k_lo, uint32_t* table, uint32_t capacity, uint32_t* n_out);
+
+/* Library version string. */
+const char* asep_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASEP_H */

@@ -1,0 +1,604 @@
+// asep_api.cu -- host runtime behind the C ABI declared in include/asep.h.
+//
+// A context owns: the packed lattices [S][planes][W], the quenched planes
+// [R][W], the attempt-count (Poisson) table, the list of sample times, the
+// height table [n_times][S][planes] (sum h as int64, sum h^2 as 128 bits)
+// and the hop counters [S][4].  asep_sweep splits the requested sweeps into
+// launches of the resident domain kernel (or the serial kernel) so that the
+// per-lane 32-bit hop counters cannot wrap, and tells each launch which of
+// its sweep counts are sample times.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/asep.h"
+#include "asep_internal.h"
+
+using namespace asep;
+
+struct asep_ctx {
+  asep_params p{};
+  uint64_t L = 0;
+  uint32_t D = 0, logD = 0, planes = 1, W = 0, S = 0, R = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<uint64_t> times;
+  uint32_t next_time = 0;  // first sample time not yet recorded
+  uint64_t sweep = 0;
+  // device buffers
+  uint32_t* d_state = nullptr;
+  uint32_t* d_mask = nullptr;
+  uint32_t* d_ptab = nullptr;
+  uint64_t* d_times = nullptr;
+  int64_t* d_sh = nullptr;
+  uint64_t* d_sh2 = nullptr;
+  uint64_t* d_cnt = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+  size_t dev_bytes = 0;
+  // attempt-count table
+  std::vector<uint32_t> ptab;
+  uint32_t ptab_klo = 0;
+  // resident launch plan
+  uint32_t R2 = 0, logR2 = 0, G = 0, spc = 1, C = 0, Cp = 0, threads = 0, blocks = 0;
+  size_t smem = 0;
+  uint32_t max_sweeps_per_launch = 1;
+  uint64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(asep_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(asep_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, ASEP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+uint32_t log2u(uint64_t x) {
+  uint32_t k = 0;
+  while ((1ull << k) < x) ++k;
+  return k;
+}
+
+bool thr_ok(uint32_t t) { return t == ASEP_ALWAYS || (t & 0xFFFu) == 0; }
+
+// T_k = floor(2^32 P(Poisson(m) <= k)).  Weights relative to the mode come
+// from the exact ratio recurrence (no large logarithms cancel), and are
+// normalised by their sum over mode +- 14 sigma (the mass outside is below
+// 1e-40); the upper half is taken from the complementary tail sum.
+int poisson_table_host(uint32_t m, std::vector<uint32_t>& tab, uint32_t& k_lo) {
+  if (m == 0 || m > (1u << 16)) return ASEP_ERR_INVALID;
+  const long double lm = static_cast<long double>(m);
+  const long double sd = sqrtl(lm);
+  const int64_t kmin = std::max<int64_t>(0, static_cast<int64_t>(lm - 14.0L * sd - 30.0L));
+  const int64_t kmax = static_cast<int64_t>(lm + 14.0L * sd + 60.0L);
+  const size_t n = static_cast<size_t>(kmax - kmin + 1);
+  std::vector<long double> w(n);
+  const int64_t mode = m;
+  w[static_cast<size_t>(mode - kmin)] = 1.0L;
+  for (int64_t k = mode - 1; k >= kmin; --k)
+    w[static_cast<size_t>(k - kmin)] = w[static_cast<size_t>(k + 1 - kmin)] * static_cast<long double>(k + 1) / lm;
+  for (int64_t k = mode + 1; k <= kmax; ++k)
+    w[static_cast<size_t>(k - kmin)] = w[static_cast<size_t>(k - 1 - kmin)] * lm / static_cast<long double>(k);
+  std::vector<long double> left(n), right(n);
+  long double acc = 0.0L;
+  for (size_t i = 0; i < n; ++i) {
+    acc += w[i];
+    left[i] = acc;  // sum_{j<=k}
+  }
+  const long double total = acc;
+  acc = 0.0L;
+  for (size_t i = n; i-- > 0;) {
+    right[i] = acc;  // sum_{j>k}
+    acc += w[i];
+  }
+  const long double two32 = 4294967296.0L;
+  tab.clear();
+  k_lo = static_cast<uint32_t>(kmin);  // every k < kmin has T_k = 0
+  for (size_t i = 0; i < n; ++i) {
+    const long double F = left[i] / total;
+    uint64_t t;
+    if (F < 0.5L) {
+      t = static_cast<uint64_t>(floorl(F * two32));
+    } else {
+      const long double Gt = right[i] / total;
+      t = 4294967295ull - static_cast<uint64_t>(floorl(Gt * two32));
+    }
+    if (t >= 4294967295ull) return ASEP_OK;
+    if (t == 0) ++k_lo;
+    else tab.push_back(static_cast<uint32_t>(t));
+  }
+  return ASEP_ERR_INVALID;  // the range did not reach the saturated tail
+}
+
+void* dev_alloc(asep_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  if (ctx->p.alloc) {
+    ptr = ctx->p.alloc(bytes, ctx->p.alloc_user);
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    ptr = nullptr;
+  }
+  if (ptr) {
+    ctx->allocs.emplace_back(ptr, bytes);
+    ctx->dev_bytes += bytes;
+  }
+  return ptr;
+}
+
+void release(asep_ctx* ctx) {
+  if (!ctx) return;
+  if (!ctx->allocs.empty()) cudaStreamSynchronize(ctx->stream);
+  for (auto& a : ctx->allocs) {
+    if (ctx->p.alloc) {
+      if (ctx->p.free_fn) ctx->p.free_fn(a.first, a.second, ctx->p.alloc_user);
+    } else {
+      cudaFree(a.first);
+    }
+  }
+  ctx->allocs.clear();
+}
+
+int validate(const asep_params* p, asep_ctx* ctx) {
+  if (!p) return fail(ctx, ASEP_ERR_INVALID, "params is NULL");
+  if (p->model > ASEP_MODEL_TWO_LANE) return fail(ctx, ASEP_ERR_INVALID, "unknown model %u", p->model);
+  if (p->schedule > ASEP_SCHED_SERIAL) return fail(ctx, ASEP_ERR_INVALID, "unknown schedule %u", p->schedule);
+  if (p->L < 64 || (p->L & 63) || p->L > (1ull << 22))
+    return fail(ctx, ASEP_ERR_INVALID, "L = %llu must be a multiple of 64 in [64, 2^22]", (unsigned long long)p->L);
+  if (p->n_realizations == 0 || p->samples_per_real == 0)
+    return fail(ctx, ASEP_ERR_INVALID, "n_realizations and samples_per_real must be >= 1");
+  const uint64_t S = static_cast<uint64_t>(p->n_realizations) * p->samples_per_real;
+  if (S > (1u << 24)) return fail(ctx, ASEP_ERR_INVALID, "too many samples (%llu)", (unsigned long long)S);
+  if (p->first_sample % p->samples_per_real)
+    return fail(ctx, ASEP_ERR_INVALID, "first_sample must be a multiple of samples_per_real");
+  if (static_cast<uint64_t>(p->first_sample) + S > (1ull << 32))
+    return fail(ctx, ASEP_ERR_INVALID, "sample ids exceed 32 bits");
+  if (!thr_ok(p->p_thr) || !thr_ok(p->q_thr) || !thr_ok(p->dis_a_thr) || !thr_ok(p->dis_b_thr) ||
+      !thr_ok(p->dis_c_thr))
+    return fail(ctx, ASEP_ERR_INVALID, "thresholds must be 0, ASEP_ALWAYS or multiples of 4096");
+  if (p->dis_kind > ASEP_DIS_TURNING) return fail(ctx, ASEP_ERR_INVALID, "unknown dis_kind %u", p->dis_kind);
+  if (p->dis_kind == ASEP_DIS_BIMODAL && p->model != ASEP_MODEL_RING)
+    return fail(ctx, ASEP_ERR_INVALID, "bimodal disorder is defined for the ring model");
+  if (p->dis_kind == ASEP_DIS_TURNING && p->model != ASEP_MODEL_TWO_LANE)
+    return fail(ctx, ASEP_ERR_INVALID, "turning sites are defined for the two-lane model");
+  if (p->init_kind > ASEP_INIT_BERNOULLI_HALF) return fail(ctx, ASEP_ERR_INVALID, "unknown init_kind %u", p->init_kind);
+  if (p->flags != 0) return fail(ctx, ASEP_ERR_INVALID, "flags must be 0");
+  if ((p->alloc == nullptr) != (p->free_fn == nullptr))
+    return fail(ctx, ASEP_ERR_INVALID, "alloc and free_fn must be given together");
+  if (p->n_sample_times && !p->sample_times) return fail(ctx, ASEP_ERR_INVALID, "sample_times is NULL");
+  for (uint32_t i = 1; i < p->n_sample_times; ++i)
+    if (p->sample_times[i] <= p->sample_times[i - 1])
+      return fail(ctx, ASEP_ERR_INVALID, "sample_times must be strictly ascending");
+  if (p->schedule == ASEP_SCHED_SERIAL && !is_pow2(p->L))
+    return fail(ctx, ASEP_ERR_INVALID, "the serial schedule needs L a power of two");
+  return ASEP_OK;
+}
+
+// Resident plan: columns = super-domains, one thread per column.
+int plan_domain(asep_ctx* ctx) {
+  const uint32_t D = ctx->D;
+  ctx->R2 = 2 * D / 32;
+  ctx->logR2 = log2u(ctx->R2);
+  const uint64_t G = ctx->L / (2ull * D);
+  if (G > 1024)
+    return fail(ctx, ASEP_ERR_INVALID, "L = %llu needs %llu columns of 2D sites; the resident kernel holds <= 1024",
+                (unsigned long long)ctx->L, (unsigned long long)G);
+  ctx->G = static_cast<uint32_t>(G);
+  uint32_t spc = 1;
+  if (ctx->G < 128) spc = std::max<uint32_t>(1, std::min<uint32_t>(ctx->S, 128 / ctx->G));
+  const uint32_t nocc = ctx->planes;
+  const uint32_t dis = ctx->p.dis_kind;
+  for (;;) {
+    const uint32_t C = spc * ctx->G;
+    const uint32_t Cp = (C + 31) / 32 * 32;
+    const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, static_cast<uint32_t>(ctx->ptab.size()), Cp);
+    if (smem <= 227 * 1024 && Cp <= 1024) {
+      ctx->spc = spc;
+      ctx->C = C;
+      ctx->Cp = Cp;
+      ctx->threads = Cp;
+      ctx->smem = smem;
+      break;
+    }
+    if (spc == 1)
+      return fail(ctx, ASEP_ERR_INVALID, "L = %llu with %u planes does not fit the resident kernel's shared memory",
+                  (unsigned long long)ctx->L, nocc);
+    spc = std::max<uint32_t>(1, spc / 2);
+  }
+  ctx->blocks = (ctx->S + ctx->spc - 1) / ctx->spc;
+  // per-lane 32-bit hop counters: at most 2 phases x largest count + 2D turns per sweep
+  const uint64_t per_sweep = 2ull * (ctx->ptab_klo + ctx->ptab.size() + 1) + 2ull * D;
+  ctx->max_sweeps_per_launch = static_cast<uint32_t>(std::max<uint64_t>(1, 4000000000ull / per_sweep));
+  return ASEP_OK;
+}
+
+Geometry geometry(const asep_ctx* ctx) {
+  Geometry g;
+  g.L = ctx->L;
+  g.W = ctx->W;
+  g.planes = ctx->planes;
+  g.S = ctx->S;
+  g.samples_per_real = ctx->p.samples_per_real;
+  g.first_sample = ctx->p.first_sample;
+  return g;
+}
+
+Rates rates(const asep_ctx* ctx) {
+  Rates r;
+  r.p = ctx->p.p_thr;
+  r.q = ctx->p.q_thr;
+  r.p_slow = ctx->p.dis_kind == ASEP_DIS_BIMODAL ? ctx->p.dis_b_thr : ctx->p.p_thr;
+  r.q_slow = ctx->p.dis_kind == ASEP_DIS_BIMODAL ? ctx->p.dis_c_thr : ctx->p.q_thr;
+  r.omega = ctx->p.dis_kind == ASEP_DIS_TURNING ? ctx->p.dis_b_thr : 0u;
+  return r;
+}
+
+int record_now(asep_ctx* ctx, uint32_t slot) {
+  HeightsLaunch h;
+  h.geo = geometry(ctx);
+  h.state = ctx->d_state;
+  h.slot = slot;
+  h.tab_sh = ctx->d_sh;
+  h.tab_sh2 = ctx->d_sh2;
+  const cudaError_t e = launch_heights(h, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "heights kernel");
+  ++ctx->launches;
+  return ASEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* asep_version(void) { return "asep 0.1 (sm_103a)"; }
+
+uint32_t asep_threshold(double p) {
+  if (!(p > 0.0)) return 0u;
+  if (p >= 1.0) return ASEP_ALWAYS;
+  const double q = std::floor(p * 1048576.0 + 0.5);
+  if (q >= 1048576.0) return ASEP_ALWAYS;
+  return static_cast<uint32_t>(q) << 12;
+}
+
+int asep_poisson_table(uint32_t m, uint32_t* k_lo, uint32_t* table, uint32_t capacity, uint32_t* n_out) {
+  if (!k_lo || !n_out) return ASEP_ERR_INVALID;
+  std::vector<uint32_t> tab;
+  uint32_t klo = 0;
+  const int rc = poisson_table_host(m, tab, klo);
+  if (rc != ASEP_OK) return rc;
+  *k_lo = klo;
+  *n_out = static_cast<uint32_t>(tab.size());
+  if (table) {
+    if (capacity < tab.size()) return ASEP_ERR_INVALID;
+    std::memcpy(table, tab.data(), tab.size() * sizeof(uint32_t));
+  }
+  return ASEP_OK;
+}
+
+const char* asep_last_error(const asep_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+int asep_create(const asep_params* params, asep_ctx** out) {
+  if (!out) return fail(nullptr, ASEP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  g_create_error.clear();
+  int rc = validate(params, nullptr);
+  if (rc != ASEP_OK) return rc;
+  asep_ctx* ctx = new (std::nothrow) asep_ctx();
+  if (!ctx) return fail(nullptr, ASEP_ERR_NOMEM, "host allocation failed");
+  ctx->p = *params;
+  ctx->p.sample_times = nullptr;
+  ctx->L = params->L;
+  ctx->W = static_cast<uint32_t>(params->L / 32);
+  ctx->planes = params->model == ASEP_MODEL_TWO_LANE ? 2u : 1u;
+  ctx->S = params->n_realizations * params->samples_per_real;
+  ctx->R = params->dis_kind == ASEP_DIS_NONE ? 0u : params->n_realizations;
+  ctx->stream = static_cast<cudaStream_t>(params->stream);
+  ctx->times.assign(params->sample_times, params->sample_times + params->n_sample_times);
+
+  auto bail = [&](int code) {
+    g_create_error = ctx->err;
+    release(ctx);
+    delete ctx;
+    return code;
+  };
+
+  if (params->schedule == ASEP_SCHED_DOMAIN) {
+    uint32_t D = params->domain_sites;
+    if (D == 0) {
+      D = 256;
+      while (D > 32 && ctx->L % (2ull * D)) D >>= 1;
+    }
+    if (D < 32 || D > 2048 || !is_pow2(D) || ctx->L % (2ull * D))
+      return bail(fail(ctx, ASEP_ERR_INVALID, "domain_sites = %u must be a power of two in [32, 2048] with "
+                       "L a multiple of 2*domain_sites", D));
+    ctx->D = D;
+    ctx->logD = log2u(D);
+    const uint32_t bonds = ctx->planes * D;
+    if (poisson_table_host(bonds, ctx->ptab, ctx->ptab_klo) != ASEP_OK)
+      return bail(fail(ctx, ASEP_ERR_INVALID, "attempt-count table for %u bonds failed", bonds));
+    rc = plan_domain(ctx);
+    if (rc != ASEP_OK) return bail(rc);
+  }
+
+  // device memory
+  const size_t state_words = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
+  const size_t n_times = std::max<size_t>(1, ctx->times.size());
+  const size_t entries = n_times * ctx->S * ctx->planes;
+  ctx->d_state = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
+  ctx->d_cnt = static_cast<uint64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * 4 * 8));
+  ctx->d_sh = static_cast<int64_t*>(dev_alloc(ctx, entries * 8));
+  ctx->d_sh2 = static_cast<uint64_t*>(dev_alloc(ctx, entries * 16));
+  ctx->d_times = static_cast<uint64_t*>(dev_alloc(ctx, n_times * 8));
+  if (ctx->R) ctx->d_mask = static_cast<uint32_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->R) * ctx->W * 4));
+  if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
+  if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || (ctx->R && !ctx->d_mask) ||
+      (!ctx->ptab.empty() && !ctx->d_ptab))
+    return bail(fail(ctx, ASEP_ERR_NOMEM, "device allocation failed (%zu bytes so far)", ctx->dev_bytes));
+
+  cudaError_t e;
+  if (!ctx->times.empty() &&
+      (e = cudaMemcpyAsync(ctx->d_times, ctx->times.data(), ctx->times.size() * 8, cudaMemcpyHostToDevice,
+                           ctx->stream)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "copy sample times"));
+  if (!ctx->ptab.empty() &&
+      (e = cudaMemcpyAsync(ctx->d_ptab, ctx->ptab.data(), ctx->ptab.size() * 4, cudaMemcpyHostToDevice,
+                           ctx->stream)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "copy attempt-count table"));
+  if ((e = cudaMemsetAsync(ctx->d_cnt, 0, static_cast<size_t>(ctx->S) * 32, ctx->stream)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "clear counters"));
+  if ((e = cudaMemsetAsync(ctx->d_sh, 0, entries * 8, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_sh2, 0, entries * 16, ctx->stream)) != cudaSuccess)
+    return bail(cuda_fail(ctx, e, "clear height table"));
+
+  InitLaunch il;
+  il.geo = geometry(ctx);
+  il.state = ctx->d_state;
+  il.init_kind = params->init_kind;
+  il.init_seed = params->init_seed;
+  if ((e = launch_init(il, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "init kernel"));
+  ++ctx->launches;
+  if (ctx->R) {
+    DisorderLaunch dl;
+    dl.L = ctx->L;
+    dl.W = ctx->W;
+    dl.R = ctx->R;
+    dl.first_real = params->first_sample / params->samples_per_real;
+    dl.thr = params->dis_a_thr;
+    dl.dis_seed = params->dis_seed;
+    dl.mask = ctx->d_mask;
+    if ((e = launch_disorder(dl, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "disorder kernel"));
+    ++ctx->launches;
+  }
+  if (!ctx->times.empty() && ctx->times[0] == 0) {
+    rc = record_now(ctx, 0);
+    if (rc != ASEP_OK) return bail(rc);
+    ctx->next_time = 1;
+  }
+  *out = ctx;
+  return ASEP_OK;
+}
+
+int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  if (ctx->sweep + n_mcs >= (1ull << 40)) return fail(ctx, ASEP_ERR_INVALID, "sweep index would exceed 2^40");
+  uint64_t done = 0;
+  while (done < n_mcs) {
+    uint64_t n = n_mcs - done;
+    const uint32_t cap = ctx->p.schedule == ASEP_SCHED_DOMAIN ? ctx->max_sweeps_per_launch : (1u << 20);
+    if (n > cap) n = cap;
+    const uint64_t s0 = ctx->sweep;
+    uint32_t i1 = ctx->next_time;
+    while (i1 < ctx->times.size() && ctx->times[i1] <= s0 + n) ++i1;
+    Record rec;
+    rec.rec_times = ctx->d_times + ctx->next_time;
+    rec.n_rec = i1 - ctx->next_time;
+    rec.slot_base = ctx->next_time;
+    rec.tab_sh = ctx->d_sh;
+    rec.tab_sh2 = ctx->d_sh2;
+    cudaError_t e;
+    if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
+      DomainLaunch a;
+      a.geo = geometry(ctx);
+      a.state = ctx->d_state;
+      a.mask = ctx->d_mask;
+      a.ptab = ctx->d_ptab;
+      a.ptab_n = static_cast<uint32_t>(ctx->ptab.size());
+      a.ptab_klo = ctx->ptab_klo;
+      a.D = ctx->D;
+      a.logD = ctx->logD;
+      a.R2 = ctx->R2;
+      a.logR2 = ctx->logR2;
+      a.G = ctx->G;
+      a.spc = ctx->spc;
+      a.C = ctx->C;
+      a.Cp = ctx->Cp;
+      a.rates = rates(ctx);
+      a.seed = ctx->p.seed;
+      a.s0 = s0;
+      a.n_sweeps = static_cast<uint32_t>(n);
+      a.rec = rec;
+      a.counters = ctx->d_cnt;
+      e = launch_domain(a, ctx->p.model, ctx->p.dis_kind, ctx->threads, ctx->blocks, ctx->smem, ctx->stream);
+    } else {
+      SerialLaunch a;
+      a.geo = geometry(ctx);
+      a.state = ctx->d_state;
+      a.mask = ctx->d_mask;
+      a.rates = rates(ctx);
+      a.seed = ctx->p.seed;
+      a.s0 = s0;
+      a.n_sweeps = static_cast<uint32_t>(n);
+      a.rec = rec;
+      a.counters = ctx->d_cnt;
+      e = launch_serial(a, ctx->p.model, ctx->p.dis_kind, ctx->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep kernel launch");
+    ++ctx->launches;
+    ctx->sweep = s0 + n;
+    ctx->next_time = i1;
+    done += n;
+  }
+  return ASEP_OK;
+}
+
+int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  ctx->p.seed = seed;
+  ctx->p.init_seed = init_seed;
+  const size_t n_times = std::max<size_t>(1, ctx->times.size());
+  const size_t entries = n_times * ctx->S * ctx->planes;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ctx->d_cnt, 0, static_cast<size_t>(ctx->S) * 32, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_sh, 0, entries * 8, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_sh2, 0, entries * 16, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "clear tables");
+  InitLaunch il;
+  il.geo = geometry(ctx);
+  il.state = ctx->d_state;
+  il.init_kind = ctx->p.init_kind;
+  il.init_seed = init_seed;
+  if ((e = launch_init(il, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "init kernel");
+  ++ctx->launches;
+  ctx->sweep = 0;
+  ctx->next_time = 0;
+  if (!ctx->times.empty() && ctx->times[0] == 0) {
+    const int rc = record_now(ctx, 0);
+    if (rc != ASEP_OK) return rc;
+    ctx->next_time = 1;
+  }
+  return ASEP_OK;
+}
+
+int asep_sync(asep_ctx* ctx) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  return ASEP_OK;
+}
+
+int asep_width(asep_ctx* ctx, int64_t* sum_h, uint64_t* sum_h2, double* w2, size_t n_entries) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  const size_t need = static_cast<size_t>(ctx->next_time) * ctx->S * ctx->planes;
+  if (n_entries < need) return fail(ctx, ASEP_ERR_INVALID, "n_entries = %zu < %zu recorded entries", n_entries, need);
+  int rc = asep_sync(ctx);
+  if (rc != ASEP_OK) return rc;
+  if (need == 0) return ASEP_OK;
+  std::vector<int64_t> sh(need);
+  std::vector<uint64_t> sh2(2 * need);
+  cudaError_t e;
+  if ((e = cudaMemcpy(sh.data(), ctx->d_sh, need * 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(sh2.data(), ctx->d_sh2, need * 16, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(ctx, e, "copy height table");
+  if (sum_h) std::memcpy(sum_h, sh.data(), need * 8);
+  if (sum_h2) std::memcpy(sum_h2, sh2.data(), need * 16);
+  if (w2) {
+    const __int128 L = static_cast<__int128>(ctx->L);
+    for (size_t i = 0; i < need; ++i) {
+      const unsigned __int128 s2 = (static_cast<unsigned __int128>(sh2[2 * i + 1]) << 64) | sh2[2 * i];
+      const __int128 s1 = sh[i];
+      const __int128 num = L * static_cast<__int128>(s2) - s1 * s1;  // >= 0, < 2^110
+      // num / L^2 with one rounding: split into integer quotient and remainder
+      const __int128 L2 = L * L;
+      const __int128 qt = num / L2, rm = num % L2;
+      w2[i] = static_cast<double>(qt) + static_cast<double>(rm) / static_cast<double>(L2);
+    }
+  }
+  return ASEP_OK;
+}
+
+int asep_state(asep_ctx* ctx, uint32_t* words, size_t n_words, uint64_t* sweep_out) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  const size_t need = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
+  if (words && n_words < need) return fail(ctx, ASEP_ERR_INVALID, "n_words = %zu < %zu", n_words, need);
+  int rc = asep_sync(ctx);
+  if (rc != ASEP_OK) return rc;
+  if (words) {
+    const cudaError_t e = cudaMemcpy(words, ctx->d_state, need * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy state");
+  }
+  if (sweep_out) *sweep_out = ctx->sweep;
+  return ASEP_OK;
+}
+
+int asep_load_state(asep_ctx* ctx, const uint32_t* words, size_t n_words, uint64_t sweep) {
+  if (!ctx || !words) return ASEP_ERR_INVALID;
+  const size_t need = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
+  if (n_words < need) return fail(ctx, ASEP_ERR_INVALID, "n_words = %zu < %zu", n_words, need);
+  if (sweep >= (1ull << 40)) return fail(ctx, ASEP_ERR_INVALID, "sweep index >= 2^40");
+  int rc = asep_sync(ctx);
+  if (rc != ASEP_OK) return rc;
+  const cudaError_t e = cudaMemcpy(ctx->d_state, words, need * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "load state");
+  ctx->sweep = sweep;
+  uint32_t i = 0;
+  while (i < ctx->times.size() && ctx->times[i] <= sweep) ++i;
+  ctx->next_time = i;
+  return ASEP_OK;
+}
+
+int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n) {
+  if (!ctx || !counters) return ASEP_ERR_INVALID;
+  const size_t need = static_cast<size_t>(ctx->S) * 4;
+  if (n < need) return fail(ctx, ASEP_ERR_INVALID, "n = %zu < %zu", n, need);
+  int rc = asep_sync(ctx);
+  if (rc != ASEP_OK) return rc;
+  const cudaError_t e = cudaMemcpy(counters, ctx->d_cnt, need * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy counters");
+  return ASEP_OK;
+}
+
+int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words) {
+  if (!ctx || !words) return ASEP_ERR_INVALID;
+  const size_t need = static_cast<size_t>(ctx->R) * ctx->W;
+  if (n_words < need) return fail(ctx, ASEP_ERR_INVALID, "n_words = %zu < %zu", n_words, need);
+  int rc = asep_sync(ctx);
+  if (rc != ASEP_OK) return rc;
+  if (need == 0) return ASEP_OK;
+  const cudaError_t e = cudaMemcpy(words, ctx->d_mask, need * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "copy disorder");
+  return ASEP_OK;
+}
+
+int asep_get_info(const asep_ctx* ctx, asep_info* info) {
+  if (!ctx || !info) return ASEP_ERR_INVALID;
+  info->L = ctx->L;
+  info->D = ctx->D;
+  info->planes = ctx->planes;
+  info->S = ctx->S;
+  info->n_recorded = ctx->next_time;
+  info->sweep = ctx->sweep;
+  info->attempts_per_sweep = ctx->L * ctx->planes;
+  info->device_bytes = ctx->dev_bytes;
+  info->kernel_launches = ctx->launches;
+  return ASEP_OK;
+}
+
+int asep_destroy(asep_ctx* ctx) {
+  if (!ctx) return ASEP_OK;
+  release(ctx);
+  delete ctx;
+  return ASEP_OK;
+}
+
+}  // extern "C"

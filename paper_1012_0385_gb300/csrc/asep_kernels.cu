@@ -1,0 +1,660 @@
+// asep_kernels.cu -- sm_103a kernels of the bit-packed ASEP / KPZ engine.
+//
+// Lattices are 32 sites per uint32 (bit k of word w = site 32w + k).  Every
+// random number is a Philox4x32-10 output (Salmon et al., SC'11) with key =
+// 64-bit seed and counter = (sweep lo, sweep hi | tag << 8 | call << 12,
+// sample, domain / site group); nothing of the generator is stored.  A draw r
+// accepts a move of threshold t iff (r & 0xfffff000) < t.
+//
+// Kernels
+//   k_init      initial filling: 1010... (paper sec. 2.1) or Bernoulli(1/2)
+//               per lane site (paper sec. 3).
+//   k_disorder  quenched site classes (Eq. bimodal, paper sec. 2.3) or
+//               turning sites (paper sec. 3), one bit per site.
+//   k_domain    the resident two-phase Poisson-domain sweep: a CTA holds one
+//               or more whole rings in shared memory for a whole launch.
+//   k_serial    plain random-sequential update (paper sec. 2.1), one thread
+//               per sample, lattice in global memory.
+//   k_heights   h_i = sum_{j<=i} (2 n_j - 1) and the sums of Eq. (W).
+//
+// Resident layout.  For sweep s with offset o the ring is cut into G = L/2D
+// super-domains of 2D sites starting at o; super-domain g is column g of a
+// transposed word array, rows r = 0..2D/32-1 (row r holds sites
+// o + 2Dg + 32r .. +31).  Rows 0..D/32-1 are the first (even) half-domain,
+// the rest the second (odd) half.  In a phase every active lane touches only
+// its own column (plus, for the last bond of an odd half, bit 0 of the next
+// column's row 0, which no active lane touches in that phase), so plain
+// shared loads and stores are race-free, and lanes of a warp hit 32
+// different banks whatever rows they draw.  At the start of every sweep the
+// words are rotated ("realigned") from the previous offset to the new one
+// into a second buffer (double buffering), one funnel shift per word.
+#include <cstdint>
+
+#include "asep_internal.h"
+
+namespace asep {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 and counters
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint2 key_of(uint64_t seed) {
+  return make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+}
+
+__device__ __forceinline__ uint4 ctr_of(uint64_t sweep, uint32_t tag, uint32_t call, uint32_t sample, uint32_t d) {
+  return make_uint4(static_cast<uint32_t>(sweep),
+                    (static_cast<uint32_t>(sweep >> 32) & 0xFFu) | (tag << 8) | (call << 12), sample, d);
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4 x, uint32_t i) {
+  return i == 0 ? x.x : (i == 1 ? x.y : (i == 2 ? x.z : x.w));
+}
+
+__device__ __forceinline__ bool accept(uint32_t r, uint32_t t) { return (r & kAcceptMask) < t; }
+
+// K = k_lo + #{ j : tab[j] <= w } (table ascending): inversion of the
+// Poisson CDF in u32 fixed point.
+__device__ __forceinline__ uint32_t poisson_count(const uint32_t* tab, uint32_t n, uint32_t klo, uint32_t w) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (tab[mid] <= w) lo = mid + 1;
+    else hi = mid;
+  }
+  return klo + lo;
+}
+
+// ---------------------------------------------------------------------------
+// Block scans (all threads of the block must call; blockDim.x % 32 == 0)
+// ---------------------------------------------------------------------------
+
+__device__ long long block_scan_incl(long long v, long long* warp_tot) {
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= static_cast<uint32_t>(o)) v += t;
+  }
+  if (lane == 31u) warp_tot[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= static_cast<uint32_t>(o)) t += u;
+    }
+    if (lane < nw) warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (wid > 0) v += warp_tot[wid - 1];
+  __syncthreads();
+  return v;
+}
+
+// Segmented scan over the columns [col0, col0 + G) of one sample.
+__device__ void seg_scan(long long v, uint32_t col0, uint32_t G, long long* warp_tot, long long* arr,
+                         long long& excl_in_seg, long long& seg_total) {
+  const long long inc = block_scan_incl(v, warp_tot);
+  arr[threadIdx.x] = inc;
+  __syncthreads();
+  const long long before = col0 > 0 ? arr[col0 - 1] : 0;
+  excl_in_seg = inc - v - before;
+  seg_total = arr[col0 + G - 1] - before;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Initial state and quenched disorder
+// ---------------------------------------------------------------------------
+
+__global__ void k_init(const InitLaunch a) {
+  const size_t per_sample = static_cast<size_t>(a.geo.planes) * a.geo.W;
+  const size_t total = per_sample * a.geo.S;
+  const uint2 key = key_of(a.init_seed);
+  for (size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    uint32_t v;
+    if (a.init_kind == 0) {
+      v = 0x55555555u;  // site i occupied iff i even
+    } else {
+      const uint32_t sample = static_cast<uint32_t>(idx / per_sample);
+      const uint32_t q = static_cast<uint32_t>(idx - static_cast<size_t>(sample) * per_sample);
+      const uint4 x = philox10(ctr_of(0, kTagInit, 0, a.geo.first_sample + sample, q >> 2), key);
+      v = pick(x, q & 3u);
+    }
+    a.state[idx] = v;
+  }
+}
+
+__global__ void k_disorder(const DisorderLaunch a) {
+  const size_t total = static_cast<size_t>(a.R) * a.W;
+  const uint2 key = key_of(a.dis_seed);
+  for (size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const uint32_t r = static_cast<uint32_t>(idx / a.W);
+    const uint32_t w = static_cast<uint32_t>(idx - static_cast<size_t>(r) * a.W);
+    uint32_t v = 0;
+    for (uint32_t q = 0; q < 8; ++q) {  // site group 8w + q holds sites 32w + 4q .. +3
+      const uint4 x = philox10(ctr_of(0, kTagDis, 0, a.first_real + r, 8u * w + q), key);
+      v |= (static_cast<uint32_t>(accept(x.x, a.thr)) << (4 * q)) |
+           (static_cast<uint32_t>(accept(x.y, a.thr)) << (4 * q + 1)) |
+           (static_cast<uint32_t>(accept(x.z, a.thr)) << (4 * q + 2)) |
+           (static_cast<uint32_t>(accept(x.w, a.thr)) << (4 * q + 3));
+    }
+    a.mask[idx] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Heights of natural-order lattices (one CTA per sample and plane)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_heights(const HeightsLaunch a) {
+  __shared__ long long warp_tot[32];
+  __shared__ unsigned long long warp_s2[32];
+  const uint32_t planes = a.geo.planes, W = a.geo.W;
+  const uint32_t sample = blockIdx.x / planes, p = blockIdx.x - sample * planes;
+  const uint32_t* w = a.state + (static_cast<size_t>(sample) * planes + p) * W;
+  const uint32_t chunk = (W + blockDim.x - 1) / blockDim.x;
+  const uint32_t w0 = min(W, threadIdx.x * chunk), w1 = min(W, w0 + chunk);
+  long long tot = 0;
+  for (uint32_t i = w0; i < w1; ++i) tot += 2 * __popc(w[i]) - 32;
+  const long long excl = block_scan_incl(tot, warp_tot) - tot;
+  long long h = excl, s1 = 0;
+  unsigned long long s2 = 0;
+  for (uint32_t i = w0; i < w1; ++i) {
+    const uint32_t x = w[i];
+    for (uint32_t b = 0; b < 32; ++b) {
+      h += ((x >> b) & 1u) ? 1 : -1;
+      s1 += h;
+      s2 += static_cast<unsigned long long>(h * h);
+    }
+  }
+  const long long s1_all = block_scan_incl(s1, warp_tot);  // last thread holds the total
+  // sum of h^2 can exceed 2^64 for L = 2^22: warp sums (< 2^63) then 128 bits
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31u) == 0) warp_s2[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x == blockDim.x - 1) {
+    unsigned __int128 acc = 0;
+    for (uint32_t i = 0; i < (blockDim.x >> 5); ++i) acc += warp_s2[i];
+    const size_t e = (static_cast<size_t>(a.slot) * a.geo.S + sample) * planes + p;
+    a.tab_sh[e] = s1_all;
+    a.tab_sh2[2 * e] = static_cast<uint64_t>(acc);
+    a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(acc >> 64);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Resident two-phase Poisson-domain kernel
+// ---------------------------------------------------------------------------
+
+// Hop counters of one lane (named fields so they stay in registers).
+struct Cnt {
+  uint32_t a = 0, b = 0, c = 0, d = 0;  // ring: right, left; two lanes: A hops, B hops, A->B, B->A
+};
+
+struct Lane {
+  uint32_t c;        // column in the CTA
+  uint32_t g;        // super-domain index within the sample
+  uint32_t col0;     // first column of the sample
+  uint32_t c_next;   // column of super-domain g+1 (ring)
+  uint32_t sample;   // sample index in the context
+  uint32_t n_glob;   // global sample id (Philox counter)
+  bool active;
+};
+
+// Rotate the planes of one column from frame offset R_old to R_new:
+// new frame word f = g*R2 + r holds logical sites R_new + 32 f .. + 31.
+template <uint32_t NP>
+__device__ __forceinline__ void realign(const uint32_t* src, uint32_t* dst, const DomainLaunch& a, const Lane& ln,
+                                        uint32_t PW, uint32_t delta) {
+  const uint64_t L = a.geo.L;
+  const uint32_t W = a.geo.W, R2 = a.R2, Cp = a.Cp;
+  for (uint32_t r = 0; r < R2; ++r) {
+    uint64_t pos = delta + 32ull * (ln.g * R2 + r);
+    if (pos >= L) pos -= L;
+    const uint32_t fa = static_cast<uint32_t>(pos >> 5), sh = static_cast<uint32_t>(pos & 31u);
+    const uint32_t fb = (fa + 1 == W) ? 0u : fa + 1;
+    const uint32_t ia = (fa & (R2 - 1)) * Cp + ln.col0 + (fa >> a.logR2);
+    const uint32_t ib = (fb & (R2 - 1)) * Cp + ln.col0 + (fb >> a.logR2);
+#pragma unroll
+    for (uint32_t p = 0; p < NP; ++p)
+      dst[p * PW + r * Cp + ln.c] = __funnelshift_r(src[p * PW + ia], src[p * PW + ib], sh);
+  }
+}
+
+// One half-domain phase of one sweep.  All threads of the warp must call.
+template <uint32_t MODEL, uint32_t DIS>
+__device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, const uint32_t* tab, uint32_t PW,
+                                          uint32_t phase, uint64_t s, const Lane& ln, uint2 key, Cnt& cnt) {
+  const uint32_t d = 2 * ln.g + phase;
+  uint4 x0 = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t K = 0;
+  if (ln.active) {
+    x0 = philox10(ctr_of(s, kTagDom, 0, ln.n_glob, d), key);
+    K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
+  }
+  const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
+  const uint32_t R2 = a.R2, Cp = a.Cp, D = a.D;
+  const uint32_t row0 = phase * (D >> 5);
+
+  auto attempt = [&](uint32_t k, uint32_t r) {
+    if (k > K) return;
+    uint32_t j;
+    uint32_t* pl;
+    uint32_t lane = 0;
+    if (MODEL == kTwoLane) {
+      const uint32_t jj = r & (2 * D - 1);
+      lane = jj >> a.logD;
+      j = jj & (D - 1);
+      pl = cur + lane * PW;
+    } else {
+      j = r & (D - 1);
+      pl = cur;
+    }
+    const uint32_t row = row0 + (j >> 5);
+    const uint32_t i0 = row * Cp + ln.c;
+    const bool strad = (j & 31u) == 31u;
+    const uint32_t i1 = (row + 1 < R2) ? i0 + Cp : ln.c_next;
+    const uint32_t w0 = pl[i0];
+    const uint32_t w1 = strad ? pl[i1] : 0u;
+    const uint32_t pat = __funnelshift_r(w0, w1, j) & 3u;  // bit0 = site i, bit1 = site i+1
+    uint32_t thr;
+    if (MODEL == kTwoLane) {
+      thr = lane == 0 ? (pat == 1u ? a.rates.p : 0u) : (pat == 2u ? a.rates.q : 0u);
+    } else if (DIS == kDisBimodal) {
+      const uint32_t* cls = cur + PW;
+      const uint32_t k0 = cls[i0], k1 = strad ? cls[i1] : 0u;
+      const uint32_t pc = __funnelshift_r(k0, k1, j) & 3u;
+      thr = pat == 1u ? ((pc & 1u) ? a.rates.p_slow : a.rates.p)
+                      : (pat == 2u ? ((pc & 2u) ? a.rates.q_slow : a.rates.q) : 0u);
+    } else {
+      thr = pat == 1u ? a.rates.p : (pat == 2u ? a.rates.q : 0u);
+    }
+    if ((r & kAcceptMask) < thr) {
+      pl[i0] = w0 ^ (3u << (j & 31u));
+      if (strad) pl[i1] = w1 ^ 1u;
+      if (MODEL == kTwoLane) {
+        cnt.a += lane ^ 1u;
+        cnt.b += lane;
+      } else {
+        cnt.a += pat == 1u;
+        cnt.b += pat != 1u;
+      }
+    }
+  };
+
+  attempt(1, x0.y);
+  attempt(2, x0.z);
+  attempt(3, x0.w);
+  for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
+    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, d), key);
+    const uint32_t k = call << 2;
+    attempt(k, y.x);
+    attempt(k + 1, y.y);
+    attempt(k + 2, y.z);
+    attempt(k + 3, y.w);
+  }
+}
+
+// Lane changes of the two-lane model at the turning sites of one column.
+__device__ __forceinline__ void turning(uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint64_t s,
+                                        uint32_t R_cur, const Lane& ln, uint2 key, Cnt& cnt) {
+  uint32_t* A = cur;
+  uint32_t* B = cur + PW;
+  const uint32_t* M = cur + 2 * PW;
+  const uint64_t L = a.geo.L;
+  for (uint32_t r = 0; r < a.R2; ++r) {
+    const uint32_t idx = r * a.Cp + ln.c;
+    uint32_t av = A[idx], bv = B[idx];
+    uint32_t e = M[idx] & (av ^ bv);
+    while (e) {
+      const uint32_t b = __ffs(e) - 1;
+      e &= e - 1;
+      uint64_t site = static_cast<uint64_t>(R_cur) + 32ull * (ln.g * a.R2 + r) + b;
+      if (site >= L) site -= L;
+      const uint4 x = philox10(ctr_of(s, kTagTurn, 0, ln.n_glob, static_cast<uint32_t>(site >> 2)), key);
+      if (accept(pick(x, static_cast<uint32_t>(site & 3u)), a.rates.omega)) {
+        const uint32_t bit = 1u << b;
+        if (av & bit) ++cnt.c;
+        else ++cnt.d;
+        av ^= bit;
+        bv ^= bit;
+      }
+    }
+    A[idx] = av;
+    B[idx] = bv;
+  }
+}
+
+// Heights of the occupancy planes (frame offset 0) into table slot `slot`.
+template <uint32_t NOCC>
+__device__ void record_heights(const uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint32_t slot, const Lane& ln,
+                               long long* warp_tot, long long* arr) {
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    const uint32_t* pl = cur + p * PW;
+    long long tot = 0;
+    if (ln.active)
+      for (uint32_t r = 0; r < a.R2; ++r) tot += 2 * __popc(pl[r * a.Cp + ln.c]) - 32;
+    long long h0, seg_unused;
+    seg_scan(tot, ln.col0, a.G, warp_tot, arr, h0, seg_unused);
+    long long s1 = 0, s2 = 0;
+    if (ln.active) {
+      long long h = h0;
+      for (uint32_t r = 0; r < a.R2; ++r) {
+        const uint32_t x = pl[r * a.Cp + ln.c];
+        for (uint32_t b = 0; b < 32; ++b) {
+          h += ((x >> b) & 1u) ? 1 : -1;
+          s1 += h;
+          s2 += h * h;
+        }
+      }
+    }
+    long long e1, t1, e2, t2;
+    seg_scan(s1, ln.col0, a.G, warp_tot, arr, e1, t1);
+    seg_scan(s2, ln.col0, a.G, warp_tot, arr, e2, t2);
+    if (ln.active && ln.g == 0) {
+      const size_t e = (static_cast<size_t>(slot) * a.geo.S + ln.sample) * NOCC + p;
+      a.rec.tab_sh[e] = t1;
+      a.rec.tab_sh2[2 * e] = static_cast<uint64_t>(t2);
+      a.rec.tab_sh2[2 * e + 1] = 0;
+    }
+  }
+}
+
+template <uint32_t MODEL, uint32_t DIS>
+__global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
+  constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
+  const uint32_t R2 = a.R2, Cp = a.Cp, G = a.G, W = a.geo.W;
+  const uint32_t PW = R2 * Cp;
+  const uint64_t L = a.geo.L;
+  uint32_t* bufA = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* bufB = bufA + NP * PW;
+  uint32_t* tab = bufB + NP * PW;
+  long long* warp_tot = reinterpret_cast<long long*>(tab + ((a.ptab_n + 1u) & ~1u));
+  long long* arr = warp_tot + 32;
+
+  Lane ln;
+  ln.c = threadIdx.x;
+  const bool col_ok = ln.c < a.C;
+  const uint32_t s_loc = col_ok ? ln.c / G : 0u;
+  ln.g = col_ok ? ln.c - s_loc * G : 0u;
+  ln.col0 = s_loc * G;
+  ln.c_next = ln.col0 + (ln.g + 1 == G ? 0u : ln.g + 1);
+  ln.sample = blockIdx.x * a.spc + s_loc;
+  ln.active = col_ok && ln.sample < a.geo.S;
+  ln.n_glob = a.geo.first_sample + ln.sample;
+  const uint2 key = key_of(a.seed);
+
+  // load the Poisson table and the lattices (frame offset 0)
+  for (uint32_t i = threadIdx.x; i < a.ptab_n; i += blockDim.x) tab[i] = a.ptab[i];
+  const uint32_t first = blockIdx.x * a.spc;
+  const uint32_t nloc = min(a.spc, a.geo.S - first);
+  for (uint32_t p = 0; p < NP; ++p) {
+    for (uint32_t idx = threadIdx.x; idx < nloc * W; idx += blockDim.x) {
+      const uint32_t sl = idx / W, w = idx - sl * W;
+      const uint32_t smp = first + sl;
+      const uint32_t v = p < NOCC ? a.state[(static_cast<size_t>(smp) * a.geo.planes + p) * W + w]
+                                  : a.mask[static_cast<size_t>(smp / a.geo.samples_per_real) * W + w];
+      bufA[p * PW + (w & (R2 - 1)) * Cp + sl * G + (w >> a.logR2)] = v;
+    }
+  }
+  __syncthreads();
+
+  uint32_t* cur = bufA;
+  uint32_t* nxt = bufB;
+  uint32_t R_cur = 0;
+  Cnt cnt;
+  uint32_t rec_i = 0;
+
+  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
+    const uint64_t s = a.s0 + it;
+    uint32_t o = 0;
+    if (ln.active) o = philox10(ctr_of(s, kTagOff, 0, ln.n_glob, 0), key).x & (2 * a.D - 1);
+    if (ln.active) realign<NP>(cur, nxt, a, ln, PW, static_cast<uint32_t>((o + L - R_cur) % L));
+    uint32_t* t = cur;
+    cur = nxt;
+    nxt = t;
+    R_cur = o;
+    __syncthreads();
+    run_phase<MODEL, DIS>(cur, a, tab, PW, 0, s, ln, key, cnt);
+    __syncthreads();
+    run_phase<MODEL, DIS>(cur, a, tab, PW, 1, s, ln, key, cnt);
+    __syncthreads();
+    if (MODEL == kTwoLane && DIS == kDisTurning) {
+      if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);
+      __syncthreads();
+    }
+    if (rec_i < a.rec.n_rec && a.rec.rec_times[rec_i] == s + 1) {
+      if (ln.active) realign<NP>(cur, nxt, a, ln, PW, static_cast<uint32_t>((L - R_cur) % L));
+      t = cur;
+      cur = nxt;
+      nxt = t;
+      R_cur = 0;
+      __syncthreads();
+      record_heights<NOCC>(cur, a, PW, a.rec.slot_base + rec_i, ln, warp_tot, arr);
+      ++rec_i;
+    }
+  }
+
+  // back to frame offset 0 and out to global memory
+  if (ln.active) realign<NP>(cur, nxt, a, ln, PW, static_cast<uint32_t>((L - R_cur) % L));
+  cur = nxt;
+  __syncthreads();
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    for (uint32_t idx = threadIdx.x; idx < nloc * W; idx += blockDim.x) {
+      const uint32_t sl = idx / W, w = idx - sl * W;
+      a.state[(static_cast<size_t>(first + sl) * a.geo.planes + p) * W + w] =
+          cur[p * PW + (w & (R2 - 1)) * Cp + sl * G + (w >> a.logR2)];
+    }
+  }
+  if (ln.active) {
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.counters + 4ull * ln.sample);
+    if (cnt.a) atomicAdd(dst + 0, static_cast<unsigned long long>(cnt.a));
+    if (cnt.b) atomicAdd(dst + 1, static_cast<unsigned long long>(cnt.b));
+    if (cnt.c) atomicAdd(dst + 2, static_cast<unsigned long long>(cnt.c));
+    if (cnt.d) atomicAdd(dst + 3, static_cast<unsigned long long>(cnt.d));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Serial random-sequential update, one thread per sample
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t bit_at(const uint32_t* w, uint64_t i) {
+  return (w[i >> 5] >> (i & 31u)) & 1u;
+}
+__device__ __forceinline__ void flip_at(uint32_t* w, uint64_t i) { w[i >> 5] ^= 1u << (i & 31u); }
+
+template <uint32_t MODEL, uint32_t DIS>
+__global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
+  const uint32_t sample = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sample >= a.geo.S) return;
+  const uint64_t L = a.geo.L;
+  const uint32_t W = a.geo.W;
+  uint32_t* A = a.state + static_cast<size_t>(sample) * a.geo.planes * W;
+  uint32_t* B = A + W;
+  const uint32_t* M = (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+  const uint32_t n_glob = a.geo.first_sample + sample;
+  const uint2 key = key_of(a.seed);
+  const uint64_t n_att = MODEL == kTwoLane ? 2 * L : L;
+  const uint32_t logL = 63u - static_cast<uint32_t>(__clzll(static_cast<long long>(L)));
+  unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+  uint32_t rec_i = 0;
+
+  auto attempt = [&](uint32_t rb, uint32_t ru) {
+    if (MODEL == kTwoLane) {
+      const uint64_t j = rb & (n_att - 1);
+      const uint32_t lane = static_cast<uint32_t>(j >> logL);
+      const uint64_t i = j & (L - 1), i1 = (i + 1) & (L - 1);
+      uint32_t* pl = lane ? B : A;
+      const uint32_t x = bit_at(pl, i) | (bit_at(pl, i1) << 1);
+      const uint32_t thr = lane == 0 ? (x == 1u ? a.rates.p : 0u) : (x == 2u ? a.rates.q : 0u);
+      if (accept(ru, thr)) {
+        flip_at(pl, i);
+        flip_at(pl, i1);
+        c0 += lane ^ 1u;
+        c1 += lane;
+      }
+    } else {
+      const uint64_t i = rb & (L - 1), i1 = (i + 1) & (L - 1);
+      const uint32_t x = bit_at(A, i) | (bit_at(A, i1) << 1);
+      uint32_t thr;
+      if (DIS == kDisBimodal) {
+        thr = x == 1u ? (bit_at(M, i) ? a.rates.p_slow : a.rates.p)
+                      : (x == 2u ? (bit_at(M, i1) ? a.rates.q_slow : a.rates.q) : 0u);
+      } else {
+        thr = x == 1u ? a.rates.p : (x == 2u ? a.rates.q : 0u);
+      }
+      if (accept(ru, thr)) {
+        flip_at(A, i);
+        flip_at(A, i1);
+        c0 += x == 1u;
+        c1 += x != 1u;
+      }
+    }
+  };
+
+  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
+    const uint64_t s = a.s0 + it;
+    for (uint64_t k = 0; k < n_att; k += 2) {
+      const uint4 x = philox10(ctr_of(s, kTagSer, 0, n_glob, static_cast<uint32_t>(k >> 1)), key);
+      attempt(x.x, x.y);
+      attempt(x.z, x.w);
+    }
+    if (MODEL == kTwoLane && DIS == kDisTurning) {
+      for (uint32_t w = 0; w < W; ++w) {
+        uint32_t e = M[w] & (A[w] ^ B[w]);
+        while (e) {
+          const uint32_t b = __ffs(e) - 1;
+          e &= e - 1;
+          const uint64_t site = 32ull * w + b;
+          const uint4 x = philox10(ctr_of(s, kTagTurn, 0, n_glob, static_cast<uint32_t>(site >> 2)), key);
+          if (accept(pick(x, static_cast<uint32_t>(site & 3u)), a.rates.omega)) {
+            if (A[w] & (1u << b)) ++c2;
+            else ++c3;
+            A[w] ^= 1u << b;
+            B[w] ^= 1u << b;
+          }
+        }
+      }
+    }
+    if (rec_i < a.rec.n_rec && a.rec.rec_times[rec_i] == s + 1) {
+      for (uint32_t p = 0; p < a.geo.planes; ++p) {
+        const uint32_t* pl = p ? B : A;
+        long long h = 0, s1 = 0;
+        unsigned __int128 s2 = 0;
+        for (uint32_t w = 0; w < W; ++w) {
+          const uint32_t x = pl[w];
+          for (uint32_t b = 0; b < 32; ++b) {
+            h += ((x >> b) & 1u) ? 1 : -1;
+            s1 += h;
+            s2 += static_cast<unsigned long long>(h * h);
+          }
+        }
+        const size_t e = (static_cast<size_t>(a.rec.slot_base + rec_i) * a.geo.S + sample) * a.geo.planes + p;
+        a.rec.tab_sh[e] = s1;
+        a.rec.tab_sh2[2 * e] = static_cast<uint64_t>(s2);
+        a.rec.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2 >> 64);
+      }
+      ++rec_i;
+    }
+  }
+  uint64_t* dst = a.counters + 4 * static_cast<size_t>(sample);
+  dst[0] += c0;
+  dst[1] += c1;
+  dst[2] += c2;
+  dst[3] += c3;
+}
+
+template <uint32_t MODEL, uint32_t DIS>
+cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               227 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_domain<MODEL, DIS><<<blocks, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <uint32_t MODEL, uint32_t DIS>
+cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
+  const uint32_t threads = 32;
+  const uint32_t blocks = (a.geo.S + threads - 1) / threads;
+  k_serial<MODEL, DIS><<<blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+uint32_t grid_for(size_t total, uint32_t threads) {
+  size_t b = (total + threads - 1) / threads;
+  if (b > 152u * 32u) b = 152u * 32u;
+  return static_cast<uint32_t>(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp, uint32_t ptab_n, uint32_t threads) {
+  const uint32_t nocc = model == kTwoLane ? 2u : 1u;
+  const uint32_t np = nocc + (dis != kDisNone ? 1u : 0u);
+  return 2ull * np * R2 * Cp * 4ull + ((ptab_n + 1ull) & ~1ull) * 4ull + (32ull + threads) * 8ull;
+}
+
+cudaError_t launch_init(const InitLaunch& a, cudaStream_t st) {
+  const size_t total = static_cast<size_t>(a.geo.S) * a.geo.planes * a.geo.W;
+  k_init<<<grid_for(total, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_disorder(const DisorderLaunch& a, cudaStream_t st) {
+  k_disorder<<<grid_for(static_cast<size_t>(a.R) * a.W, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st) {
+  k_heights<<<a.geo.S * a.geo.planes, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, uint32_t threads, uint32_t blocks,
+                          size_t smem, cudaStream_t st) {
+  if (model == kRing && dis == kDisNone) return launch_domain_t<kRing, kDisNone>(a, threads, blocks, smem, st);
+  if (model == kRing && dis == kDisBimodal) return launch_domain_t<kRing, kDisBimodal>(a, threads, blocks, smem, st);
+  if (model == kTwoLane && dis == kDisNone) return launch_domain_t<kTwoLane, kDisNone>(a, threads, blocks, smem, st);
+  if (model == kTwoLane && dis == kDisTurning)
+    return launch_domain_t<kTwoLane, kDisTurning>(a, threads, blocks, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st) {
+  if (model == kRing && dis == kDisNone) return launch_serial_t<kRing, kDisNone>(a, st);
+  if (model == kRing && dis == kDisBimodal) return launch_serial_t<kRing, kDisBimodal>(a, st);
+  if (model == kTwoLane && dis == kDisNone) return launch_serial_t<kTwoLane, kDisNone>(a, st);
+  if (model == kTwoLane && dis == kDisTurning) return launch_serial_t<kTwoLane, kDisTurning>(a, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace asep

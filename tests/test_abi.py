@@ -1,0 +1,74 @@
+"""The C ABI without a GPU: the library builds, loads, exports every symbol
+include/asep.h declares, and its host-only functions agree with the oracle
+and with the paper's sampling schedule."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_1012_0385_gb300 import build
+
+    if not build.up_to_date():
+        build.build()
+    from paper_1012_0385_gb300 import asep
+
+    return asep
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "asep.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|uint32_t|const char\*)\s+(asep_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_symbol(A):
+    import subprocess
+
+    declared = _declared()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", A._build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (asep_\w+)", out))
+    assert set(declared) <= exported, set(declared) - exported
+    assert set(declared) == set(A.EXPORTED)
+    lib = A.lib()
+    for name in declared:
+        assert getattr(lib, name) is not None
+
+
+def test_version_and_thresholds(A, oracle_mod):
+    assert "sm_103a" in A.asep_version()
+    for p in [0.0, -1.0, 1.0, 2.0, 0.75, 0.25, 0.1, 0.3, 0.05, 0.999999, 1e-7]:
+        assert A.asep_threshold(p) == oracle_mod.threshold(p), p
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 32, 64, 100, 256, 512, 1000, 1024, 2048, 4096])
+def test_poisson_table_identical_to_exact_oracle(A, oracle_mod, m):
+    k_lo, tab = A.asep_poisson_table(m)
+    ok, ot = oracle_mod.poisson_table(m)
+    assert k_lo == ok and np.array_equal(tab, np.array(ot, dtype=np.uint32))
+
+
+def test_sampling_times_match_paper_and_oracle(oracle_mod):
+    from paper_1012_0385_gb300.sampling import every, log_times
+
+    assert log_times(10**7) == oracle_mod.log_times(10**7)
+    assert len(log_times(10**7, include_zero=False)) == 261  # t_0 plus the paper's 260 events
+    assert every(100, 10**4)[:3] == [0, 100, 200] and every(100, 10**4)[-1] == 10**4
+
+
+def test_create_rejects_bad_params_without_device(A):
+    """Validation happens before any CUDA call."""
+    bad = [dict(L=100), dict(L=1 << 23), dict(L=4096, domain_sites=48), dict(L=4096, p_thr=123),
+           dict(L=4096, n_realizations=0), dict(L=4096, dis_kind=2), dict(L=4096, model=1, dis_kind=1),
+           dict(L=4096 + 64, schedule=1), dict(L=4096, samples_per_real=3, first_sample=1)]
+    for kw in bad:
+        prm = A.make_params(**kw)
+        with pytest.raises(A.AsepError) as ei:
+            A.asep_create(prm, torch_alloc=False, stream=0)
+        assert ei.value.code == A.ASEP_ERR_INVALID, kw
+        assert A.asep_last_error(None)

@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work, so the bar is bit-exact: lattice words after the run, every
+recorded (sum h, sum h^2), and the hop counters.  Cases span several CTAs and
+ragged last CTAs, domain sizes 32..2048, disorder, two lanes, the serial
+schedule, launch splitting and checkpoint/resume.  At the full sizes of the
+configurations the oracle checks sampled outputs (spot sweeps restarted from
+a GPU state).  The statistical tests compare W(t) of the domain schedule on
+the GPU with the independent serial RSU reference within 3 sigma.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_0385_gb300 import asep as A
+from paper_1012_0385_gb300.sampling import every, log_times
+
+pytestmark = pytest.mark.gpu
+
+th = oracle.threshold
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_0385_gb300 import build
+
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+ORACLE_KEYS = {"model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
+               "n_realizations": "n_realizations", "samples_per_real": "samples_per_real",
+               "first_sample": "first_sample", "p_thr": "p_thr", "q_thr": "q_thr", "dis_kind": "dis_kind",
+               "dis_a_thr": "dis_a_thr", "dis_b_thr": "dis_b_thr", "dis_c_thr": "dis_c_thr",
+               "init_kind": "init_kind", "seed": "seed", "dis_seed": "dis_seed", "init_seed": "init_seed"}
+
+
+def oracle_params(kw):
+    P = oracle.Params()
+    for k, v in kw.items():
+        setattr(P, ORACLE_KEYS[k], v)
+    if kw.get("schedule", 0) == A.ASEP_SCHED_DOMAIN and not kw.get("domain_sites"):
+        P.D = 256
+    return P
+
+
+def run_gpu(kw, chunks, times):
+    prm = A.make_params(**kw)
+    with A.asep_create(prm, sample_times=times) as ctx:
+        for c in chunks:
+            A.asep_sweep(ctx, c)
+        words, sweep = A.asep_state(ctx)
+        sh, sh2, w2 = A.asep_width(ctx)
+        cnt = A.asep_counters(ctx)
+        dis = A.asep_disorder(ctx)
+    assert sweep == sum(chunks)
+    return dict(words=words, sh=sh, sh2=sh2, w2=w2, cnt=cnt, dis=dis)
+
+
+def assert_same(g, ref, P, times):
+    assert g["words"].shape == ref.state.shape
+    bad = np.argwhere(g["words"] != ref.state)
+    assert bad.size == 0, f"{len(bad)} words differ, first at {bad[:3].tolist()}"
+    assert np.array_equal(g["cnt"], ref.counters), (g["cnt"][:3], ref.counters[:3])
+    nt = len([t for t in times if t <= max(times)])
+    assert g["sh"].shape[0] == nt
+    for ti in range(nt):
+        for s in range(P.S):
+            for pl in range(P.planes):
+                assert int(g["sh"][ti, s, pl]) == ref.sum_h[ti, s, pl], (ti, s, pl)
+                s2 = (int(g["sh2"][ti, s, pl, 1]) << 64) | int(g["sh2"][ti, s, pl, 0])
+                assert s2 == ref.sum_h2[ti, s, pl], (ti, s, pl)
+                assert g["w2"][ti, s, pl] == pytest.approx(ref.w2[ti, s, pl], rel=1e-15, abs=0)
+
+
+RING = A.ASEP_MODEL_RING
+TWO = A.ASEP_MODEL_TWO_LANE
+CASES = {
+    # several CTAs (16 samples each) with a ragged last CTA
+    "ring_asep_ragged": (dict(L=4096, domain_sites=256, samples_per_real=20, p_thr=th(0.75), q_thr=th(0.25),
+                              seed=3), 40, [0, 1, 2, 7, 40]),
+    "ring_tasep_d32": (dict(L=2048, domain_sites=32, samples_per_real=6, seed=5), 30, [0, 30]),
+    "ring_d64": (dict(L=8192, domain_sites=64, samples_per_real=3, p_thr=th(0.6), q_thr=th(0.1), seed=9), 20,
+                 [3, 20]),
+    "ring_d2048": (dict(L=8192, domain_sites=2048, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=11),
+                   10, [0, 5, 10]),
+    "ring_multi_tile": (dict(L=1 << 15, domain_sites=256, samples_per_real=5, p_thr=th(0.8), seed=13), 25,
+                        [0, 25]),
+    "ring_cfg1_columns": (dict(L=1 << 17, domain_sites=256, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25),
+                               seed=1), 6, [0, 3, 6]),
+    "ring_min_L": (dict(L=64, domain_sites=32, samples_per_real=40, p_thr=th(0.7), q_thr=th(0.3), seed=2), 50,
+                   [0, 50]),
+    "ring_first_sample": (dict(L=4096, domain_sites=128, samples_per_real=4, first_sample=8, p_thr=th(0.75),
+                               q_thr=th(0.25), seed=3), 12, [12]),
+    "ring_bernoulli": (dict(L=4096, domain_sites=128, samples_per_real=4, init_kind=1, init_seed=77,
+                            p_thr=th(0.75), q_thr=th(0.25), seed=3), 12, [0, 12]),
+    "ring_frozen": (dict(L=4096, domain_sites=128, samples_per_real=2, p_thr=0, q_thr=0, seed=3), 5, [0, 5]),
+    "bimodal_cfg2_shape": (dict(L=1 << 16, domain_sites=256, n_realizations=3, samples_per_real=2,
+                                dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_c_thr=0,
+                                dis_seed=21, seed=4), 20, [0, 10, 20]),
+    "bimodal_qssep": (dict(L=8192, domain_sites=128, n_realizations=2, samples_per_real=2, p_thr=th(0.5),
+                           q_thr=th(0.5), dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.5), dis_b_thr=th(0.1),
+                           dis_c_thr=th(0.1), dis_seed=5, seed=6), 15, [15]),
+    "two_lane_cfg3_shape": (dict(model=TWO, L=1 << 16, domain_sites=256, samples_per_real=3, init_kind=1,
+                                 init_seed=8, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
+                                 dis_seed=9, q_thr=A.ASEP_ALWAYS), 10, [0, 10]),
+    "two_lane_plain": (dict(model=TWO, L=4096, domain_sites=64, samples_per_real=4, init_kind=1, init_seed=1,
+                            p_thr=th(0.5), q_thr=th(0.7), seed=7), 15, [15]),
+    "serial_cfg0_shape": (dict(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=8, seed=1), 200,
+                          every(100, 200)),
+    "serial_asep": (dict(L=1024, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=5, p_thr=th(0.75),
+                         q_thr=th(0.25), seed=12), 30, [0, 10, 30]),
+    "serial_two_lane": (dict(model=TWO, L=1024, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=3, init_kind=1,
+                             init_seed=4, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
+                             dis_seed=2, q_thr=A.ASEP_ALWAYS, seed=3), 20, [20]),
+    "serial_bimodal": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
+                            dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=3, seed=4),
+                       20, [20]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_bit_exact_against_oracle(name):
+    kw, n, times = CASES[name]
+    g = run_gpu(kw, [n], times)
+    P = oracle_params(kw)
+    ref = oracle.run(P, n, times)
+    if P.dis_kind != 0:
+        assert np.array_equal(g["dis"], oracle.disorder(P))
+    assert_same(g, ref, P, times)
+
+
+def test_launch_splitting_is_invisible():
+    kw = dict(L=8192, domain_sites=128, samples_per_real=5, p_thr=th(0.75), q_thr=th(0.25), seed=31)
+    times = [0, 4, 7, 20, 25]
+    a = run_gpu(kw, [25], times)
+    b = run_gpu(kw, [7, 13, 5], times)
+    c = run_gpu(kw, [1] * 25, times)
+    for x in (b, c):
+        assert np.array_equal(a["words"], x["words"])
+        assert np.array_equal(a["sh"], x["sh"]) and np.array_equal(a["sh2"], x["sh2"])
+        assert np.array_equal(a["cnt"], x["cnt"])
+
+
+def test_checkpoint_resume_is_bit_exact():
+    kw = dict(model=TWO, L=4096, domain_sites=128, samples_per_real=3, init_kind=1, init_seed=6,
+              dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=5, seed=8)
+    full = run_gpu(kw, [30], [30])
+    with A.asep_create(A.make_params(**kw), sample_times=[30]) as c1:
+        A.asep_sweep(c1, 11)
+        words, s = A.asep_state(c1)
+    with A.asep_create(A.make_params(**kw), sample_times=[30]) as c2:
+        A.asep_load_state(c2, words, s)
+        A.asep_sweep(c2, 19)
+        w2, s2 = A.asep_state(c2)
+        sh, sh2, _ = A.asep_width(c2)
+    assert s2 == 30 and np.array_equal(w2, full["words"])
+    assert np.array_equal(sh[-1], full["sh"][-1]) and np.array_equal(sh2[-1], full["sh2"][-1])
+
+
+def test_reset_reproduces_a_fresh_context():
+    kw = dict(L=8192, domain_sites=256, samples_per_real=4, p_thr=th(0.75), q_thr=th(0.25), seed=41)
+    fresh = run_gpu(kw, [9], [0, 9])
+    with A.asep_create(A.make_params(**dict(kw, seed=5)), sample_times=[0, 9]) as ctx:
+        A.asep_sweep(ctx, 17)
+        A.asep_reset(ctx, seed=41)
+        A.asep_sweep(ctx, 9)
+        words, _ = A.asep_state(ctx)
+        sh, _, _ = A.asep_width(ctx)
+        cnt = A.asep_counters(ctx)
+    assert np.array_equal(words, fresh["words"]) and np.array_equal(sh, fresh["sh"])
+    assert np.array_equal(cnt, fresh["cnt"])
+
+
+def test_cfg0_full_run_snapshots_every_100_mcs():
+    """Plain serial RSU, L = 4096, 8 samples, p = 1, q = 0, 10^4 MCS: the
+    lattice every 100 MCS and W(t) bit-exact against the oracle."""
+    kw = dict(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=8, seed=1)
+    times = every(100, 10**4)
+    P = oracle_params(kw)
+    ref_state = oracle.init_state(P)
+    ref_sums = [[oracle.heights(ref_state[s, 0], P.L) for s in range(P.S)]]
+    with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
+        for k in range(100):
+            A.asep_sweep(ctx, 100)
+            words, _ = A.asep_state(ctx)
+            oracle.replay(P, ref_state, 100 * k, 100)
+            assert np.array_equal(words, ref_state), f"lattice differs after {100 * (k + 1)} MCS"
+            ref_sums.append([oracle.heights(ref_state[s, 0], P.L) for s in range(P.S)])
+        sh, sh2, w2 = A.asep_width(ctx)
+    assert sh.shape[0] == len(times) == len(ref_sums)
+    for ti in range(len(times)):
+        for s in range(P.S):
+            a, b = ref_sums[ti][s]
+            assert int(sh[ti, s, 0]) == a and ((int(sh2[ti, s, 0, 1]) << 64) | int(sh2[ti, s, 0, 0])) == b
+    assert np.all(w2[0] == 0.25)
+
+
+def test_cfg1_full_size_spot_checks():
+    """The benchmarked launch (L = 2^17, 256 samples, D = 256, 2^14 MCS, log
+    times): the first sweeps of sampled samples replayed from the start, and
+    the last sweeps replayed from the GPU state of the same run."""
+    n_mcs, k_tail = 1 << 14, 4
+    times = log_times(n_mcs)
+    kw = dict(L=1 << 17, domain_sites=256, samples_per_real=256, p_thr=th(0.75), q_thr=th(0.25), seed=1)
+    P = oracle_params(kw)
+    picks = [0, 97, 255]
+    with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
+        A.asep_sweep(ctx, 40)
+        early, _ = A.asep_state(ctx)
+        A.asep_sweep(ctx, n_mcs - 40 - k_tail)
+        mid, s_mid = A.asep_state(ctx)
+        A.asep_sweep(ctx, k_tail)
+        final, _ = A.asep_state(ctx)
+        sh, sh2, w2 = A.asep_width(ctx)
+    ref = oracle.init_state(P)
+    oracle.replay(P, ref, 0, 40, samples=picks)
+    for s in picks:
+        assert np.array_equal(early[s], ref[s]), s
+    tail = mid.copy()
+    oracle.replay(P, tail, s_mid, k_tail, samples=picks)
+    for s in picks:
+        assert np.array_equal(final[s], tail[s]), s
+        a, b = oracle.heights(final[s, 0], P.L)
+        assert int(sh[-1, s, 0]) == a and ((int(sh2[-1, s, 0, 1]) << 64) | int(sh2[-1, s, 0, 0])) == b
+    # every sample keeps half filling, W^2(0) = 1/4 exactly
+    pop = np.unpackbits(final.view(np.uint8), axis=-1).sum(axis=-1)
+    assert np.all(pop == P.L // 2)
+    assert np.all(w2[0] == 0.25)
+
+
+# ---------------------------------------------------------------------------
+# Statistics: W(t) of the GPU domain schedule vs the serial RSU reference
+# ---------------------------------------------------------------------------
+
+def _serial_w2(P, times, mask=None):
+    st = oracle.init_state(P)
+    out = np.zeros((len(times), P.S, P.planes))
+    done = 0
+    for i, t in enumerate(times):
+        if t > done:
+            oracle.serial_reference(P, st, t - done, rng_seeds=np.arange(P.S) * 104729 + t, mask=mask)
+            done = t
+        for s in range(P.S):
+            for pl in range(P.planes):
+                out[i, s, pl] = oracle.width2(P.L, *oracle.heights(st[s, pl], P.L))
+    return out
+
+
+@pytest.mark.parametrize("case", ["asep", "tasep", "bimodal", "two_lane"])
+def test_width_within_3_sigma_of_serial_reference(case):
+    times = [4, 16, 64]
+    if case == "asep":
+        kw = dict(L=1 << 14, domain_sites=256, samples_per_real=96, p_thr=th(0.75), q_thr=th(0.25), seed=17)
+    elif case == "tasep":
+        kw = dict(L=1 << 14, domain_sites=256, samples_per_real=96, seed=19)
+    elif case == "bimodal":
+        kw = dict(L=1 << 14, domain_sites=256, n_realizations=1, samples_per_real=96, dis_kind=A.ASEP_DIS_BIMODAL,
+                  dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=23, seed=29)
+    else:
+        kw = dict(model=TWO, L=1 << 14, domain_sites=256, samples_per_real=96, init_kind=1, init_seed=3,
+                  dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=31,
+                  q_thr=A.ASEP_ALWAYS, seed=37)
+    g = run_gpu(kw, [times[-1]], times)
+    P = oracle_params(kw)
+    mask = oracle.disorder(P)
+    ser = _serial_w2(P, times, mask=mask)
+    for ti in range(len(times)):
+        for pl in range(P.planes):
+            a, b = g["w2"][ti, :, pl], ser[ti, :, pl]
+            sig = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
+            assert abs(a.mean() - b.mean()) < 3 * sig, (case, times[ti], pl, a.mean(), b.mean(), sig)

@@ -305,6 +305,26 @@ def run_ours(args):
     return 0
 
 
+def profile_case():
+    """The benchmarked configuration with 64 sweeps instead of 2^14: the
+    domain kernel reads and writes each lattice once per launch, so its DRAM
+    traffic per launch is that of a full step; only the loop is shorter."""
+    import torch
+
+    from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300.sampling import log_times
+
+    th = A.asep_threshold
+    prm = A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE),
+                        q_thr=th(Q_RATE), seed=SEED)
+    with A.asep_create(prm, sample_times=log_times(N_MCS)) as ctx:
+        A.asep_sweep(ctx, 64)
+        A.asep_sync(ctx)
+    torch.cuda.synchronize()
+    print("profile case done", flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +333,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

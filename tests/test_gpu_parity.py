@@ -206,7 +206,7 @@ def test_cfg1_full_size_spot_checks():
     times): the first sweeps of sampled samples replayed from the start, and
     the last sweeps replayed from the GPU state of the same run."""
     n_mcs, k_tail = 1 << 14, 4
-    times = log_times(n_mcs)
+    times = log_times(n_mcs) + [n_mcs]  # the log times end below 2^14; record the last sweep too
     kw = dict(L=1 << 17, domain_sites=256, samples_per_real=256, p_thr=th(0.75), q_thr=th(0.25), seed=1)
     P = oracle_params(kw)
     picks = [0, 97, 255]

@@ -326,6 +326,7 @@ def profile_case():
 
 
 def main():
+    global DOMAIN
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -333,6 +334,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")
     args = ap.parse_args()
@@ -340,6 +342,7 @@ def main():
         return profile_case()
     if args.warmup < 3:
         args.warmup = 3
+    DOMAIN = args.domain
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

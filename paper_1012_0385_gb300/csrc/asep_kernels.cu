@@ -242,11 +242,61 @@ __device__ __forceinline__ void realign(const uint32_t* src, uint32_t* dst, cons
   }
 }
 
+// One attempt of a half-domain phase, without branches: both words of the
+// bond are loaded unconditionally (the second is the next row of the same
+// column, or row 0 of the next column after the last row of an odd half;
+// both in bounds and untouched by other lanes in this phase), the 64-bit flip
+// mask (3 << j across the word pair) is applied under one predicate, and the
+// stores are predicated.  `valid` is k <= K.
+template <uint32_t MODEL, uint32_t DIS, uint32_t PHASE>
+__device__ __forceinline__ void attempt(uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint32_t row0,
+                                        const Lane& ln, uint32_t r, bool valid, Cnt& cnt) {
+  const uint32_t D = a.D, Cp = a.Cp;
+  uint32_t j, tR, tL;
+  uint32_t* pl;
+  if (MODEL == kTwoLane) {
+    const uint32_t lane = (r >> a.logD) & 1u;  // bit log2(D) of the bond index j' = r & (2D - 1)
+    j = r & (D - 1);
+    pl = cur + lane * PW;
+    tR = lane ? 0u : a.rates.p;  // lane A: 10 -> 01
+    tL = lane ? a.rates.q : 0u;  // lane B: 01 -> 10
+  } else {
+    j = r & (D - 1);
+    pl = cur;
+    tR = a.rates.p;
+    tL = a.rates.q;
+  }
+  const uint32_t row = row0 + (j >> 5);
+  const uint32_t i0 = row * Cp + ln.c;
+  uint32_t i1 = i0 + Cp;
+  if (PHASE == 1) i1 = (row + 1 < a.R2) ? i1 : ln.c_next;
+  if (DIS == kDisBimodal) {
+    const uint32_t* cls = cur + PW;
+    const uint32_t pc = __funnelshift_r(cls[i0], cls[i1], j);  // bit0: class of site i, bit1: of site i+1
+    tR = (pc & 1u) ? a.rates.p_slow : tR;
+    tL = (pc & 2u) ? a.rates.q_slow : tL;
+  }
+  const uint32_t u = r & kAcceptMask;
+  const bool okR = valid && (u < tR);
+  const bool okL = valid && (u < tL);
+  const uint32_t w0 = pl[i0];
+  const uint32_t w1 = pl[i1];
+  const uint32_t pat = __funnelshift_r(w0, w1, j) & 3u;  // bit0 = site i, bit1 = site i+1
+  const bool hopR = okR && pat == 1u;
+  const bool hopL = okL && pat == 2u;
+  if (hopR || hopL) {
+    pl[i0] = w0 ^ (3u << (j & 31u));
+    pl[i1] = w1 ^ __funnelshift_l(3u, 0u, j);  // 1 when j % 32 == 31, else 0
+  }
+  cnt.a += hopR;
+  cnt.b += hopL;
+}
+
 // One half-domain phase of one sweep.  All threads of the warp must call.
-template <uint32_t MODEL, uint32_t DIS>
+template <uint32_t MODEL, uint32_t DIS, uint32_t PHASE>
 __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, const uint32_t* tab, uint32_t PW,
-                                          uint32_t phase, uint64_t s, const Lane& ln, uint2 key, Cnt& cnt) {
-  const uint32_t d = 2 * ln.g + phase;
+                                          uint64_t s, const Lane& ln, uint2 key, Cnt& cnt) {
+  const uint32_t d = 2 * ln.g + PHASE;
   uint4 x0 = make_uint4(0u, 0u, 0u, 0u);
   uint32_t K = 0;
   if (ln.active) {
@@ -254,65 +304,18 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, 
     K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
   }
   const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
-  const uint32_t R2 = a.R2, Cp = a.Cp, D = a.D;
-  const uint32_t row0 = phase * (D >> 5);
-
-  auto attempt = [&](uint32_t k, uint32_t r) {
-    if (k > K) return;
-    uint32_t j;
-    uint32_t* pl;
-    uint32_t lane = 0;
-    if (MODEL == kTwoLane) {
-      const uint32_t jj = r & (2 * D - 1);
-      lane = jj >> a.logD;
-      j = jj & (D - 1);
-      pl = cur + lane * PW;
-    } else {
-      j = r & (D - 1);
-      pl = cur;
-    }
-    const uint32_t row = row0 + (j >> 5);
-    const uint32_t i0 = row * Cp + ln.c;
-    const bool strad = (j & 31u) == 31u;
-    const uint32_t i1 = (row + 1 < R2) ? i0 + Cp : ln.c_next;
-    const uint32_t w0 = pl[i0];
-    const uint32_t w1 = strad ? pl[i1] : 0u;
-    const uint32_t pat = __funnelshift_r(w0, w1, j) & 3u;  // bit0 = site i, bit1 = site i+1
-    uint32_t thr;
-    if (MODEL == kTwoLane) {
-      thr = lane == 0 ? (pat == 1u ? a.rates.p : 0u) : (pat == 2u ? a.rates.q : 0u);
-    } else if (DIS == kDisBimodal) {
-      const uint32_t* cls = cur + PW;
-      const uint32_t k0 = cls[i0], k1 = strad ? cls[i1] : 0u;
-      const uint32_t pc = __funnelshift_r(k0, k1, j) & 3u;
-      thr = pat == 1u ? ((pc & 1u) ? a.rates.p_slow : a.rates.p)
-                      : (pat == 2u ? ((pc & 2u) ? a.rates.q_slow : a.rates.q) : 0u);
-    } else {
-      thr = pat == 1u ? a.rates.p : (pat == 2u ? a.rates.q : 0u);
-    }
-    if ((r & kAcceptMask) < thr) {
-      pl[i0] = w0 ^ (3u << (j & 31u));
-      if (strad) pl[i1] = w1 ^ 1u;
-      if (MODEL == kTwoLane) {
-        cnt.a += lane ^ 1u;
-        cnt.b += lane;
-      } else {
-        cnt.a += pat == 1u;
-        cnt.b += pat != 1u;
-      }
-    }
-  };
-
-  attempt(1, x0.y);
-  attempt(2, x0.z);
-  attempt(3, x0.w);
+  const uint32_t row0 = PHASE * (a.D >> 5);
+  attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, x0.y, 1 <= K, cnt);
+  attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, x0.z, 2 <= K, cnt);
+  attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, x0.w, 3 <= K, cnt);
+#pragma unroll 2
   for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
     const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, d), key);
     const uint32_t k = call << 2;
-    attempt(k, y.x);
-    attempt(k + 1, y.y);
-    attempt(k + 2, y.z);
-    attempt(k + 3, y.w);
+    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.x, k <= K, cnt);
+    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.y, k + 1 <= K, cnt);
+    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.z, k + 2 <= K, cnt);
+    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.w, k + 3 <= K, cnt);
   }
 }
 
@@ -438,9 +441,9 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
     nxt = t;
     R_cur = o;
     __syncthreads();
-    run_phase<MODEL, DIS>(cur, a, tab, PW, 0, s, ln, key, cnt);
+    run_phase<MODEL, DIS, 0>(cur, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
-    run_phase<MODEL, DIS>(cur, a, tab, PW, 1, s, ln, key, cnt);
+    run_phase<MODEL, DIS, 1>(cur, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
     if (MODEL == kTwoLane && DIS == kDisTurning) {
       if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);

@@ -205,7 +205,7 @@ def run_ours(args):
 
     def params():
         return A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, first_sample=rank * SAMPLES,
-                             p_thr=th(P_RATE), q_thr=th(Q_RATE), seed=SEED)
+                             p_thr=th(P_RATE), q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
 
     stream = torch.cuda.current_stream()
     ctx = A.asep_create(params(), sample_times=times)
@@ -274,6 +274,12 @@ def run_ours(args):
         e2e_time = float(t[0])
     e2e_value = attempts_per_step * world / e2e_time
 
+    # the random stream alone: Philox4x32-10 calls/s with no lattice memory
+    sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device="cuda")
+    A.asep_philox_bench(152 * 8, 256, 1 << 12, sink.data_ptr(), stream.cuda_stream)
+    ph_ms = A.asep_philox_bench(152 * 8, 256, 1 << 14, sink.data_ptr(), stream.cuda_stream)
+    philox_calls_s = 152 * 8 * 256 * (1 << 14) / (ph_ms / 1000.0)
+
     if rank == 0:
         peaks = _peaks()
         max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -286,13 +292,15 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_NAME, "L": L_SITES, "samples_per_gpu": SAMPLES, "n_mcs": N_MCS,
                        "sample_times": len(times), "domain_sites": DOMAIN,
                        "schedule": "two-phase Poisson-domain RSU", "rates": {"p": P_RATE, "q": Q_RATE},
+                       "observables": "W^2 at the log times (hop counters off)",
                        "l2": "flushed between steps (256 MB write outside the timed region)",
                        "parallelism": f"replicas x{world} (disjoint sample ranges)"},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": _traffic_from_profile(),
                          "kernel": "k_domain<ring>", "kernel_ms": kernel_ms,
                          "ops_per_attempt": OPS_PER_ATTEMPT,
-                         "peak_basis": f"{SMS} SMs x {LANES_PER_SM} int32 lanes/clk x {max_mhz:.0f} MHz (issue)"},
+                         "peak_basis": f"{SMS} SMs x {LANES_PER_SM} int32 lanes/clk x {max_mhz:.0f} MHz (issue)",
+                         "philox_only_attempts_per_s": 4 * philox_calls_s},
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -316,7 +324,7 @@ def profile_case():
 
     th = A.asep_threshold
     prm = A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE),
-                        q_thr=th(Q_RATE), seed=SEED)
+                        q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
     with A.asep_create(prm, sample_times=log_times(N_MCS)) as ctx:
         A.asep_sweep(ctx, 64)
         A.asep_sync(ctx)

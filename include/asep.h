@@ -76,6 +76,9 @@ extern "C" {
 
 #define ASEP_ALWAYS 0xFFFFFFFFu
 
+/* asep_params.flags */
+#define ASEP_FLAG_NO_HOP_COUNTS 1u /* ring model: do not count hops (asep_counters then reports zeros) */
+
 typedef struct asep_ctx asep_ctx; /* opaque; owns every device buffer it allocates */
 
 /* Device allocator hook: when alloc is non-NULL the context obtains all of
@@ -104,7 +107,7 @@ typedef struct asep_params {
   uint64_t init_seed;        /* initial-filling key */
   const uint64_t* sample_times; /* host array, ascending sweep counts at which heights are recorded (0 = start) */
   uint32_t n_sample_times;
-  uint32_t flags;            /* reserved, 0 */
+  uint32_t flags;            /* ASEP_FLAG_* bits, 0 = default */
   void* stream;              /* cudaStream_t for all work of the context; NULL = default stream */
   asep_alloc_fn alloc;       /* optional allocator hook (with free_fn and alloc_user) */
   asep_free_fn free_fn;
@@ -192,6 +195,15 @@ uint32_t asep_threshold(double p);
  * draw w gives K = k_lo + #{j : table[j] <= w}.  Host only; capacity is the
  * length of `table`. */
 int asep_poisson_table(uint32_t m, uint32_t* k_lo, uint32_t* table, uint32_t capacity, uint32_t* n_out);
+
+/* Microbenchmark of the random stream alone (no lattice memory): a grid of
+ * `blocks` x `threads` threads, each running `calls` Philox4x32-10 calls in
+ * the counter layout of the attempt stream and folding the outputs into one
+ * word of `sink` (device buffer of blocks*threads uint32, owned by the
+ * caller).  Writes the kernel time in milliseconds (CUDA events on `stream`)
+ * to *ms; synchronises `stream`.  It bounds the attempt rate of the domain
+ * kernel from above: one call feeds four attempts. */
+int asep_philox_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, float* ms);
 
 /* Library version string. */
 const char* asep_version(void);

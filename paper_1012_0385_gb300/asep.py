@@ -32,6 +32,7 @@ ASEP_SCHED_DOMAIN, ASEP_SCHED_SERIAL = 0, 1
 ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING = 0, 1, 2
 ASEP_INIT_FLAT_ALT, ASEP_INIT_BERNOULLI_HALF = 0, 1
 ASEP_ALWAYS = 0xFFFFFFFF
+ASEP_FLAG_NO_HOP_COUNTS = 1
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -83,7 +84,7 @@ class asep_info(ctypes.Structure):
 # Every symbol include/asep.h declares (tests check that the library exports them).
 EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_state", "asep_reset", "asep_counters",
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
-            "asep_poisson_table", "asep_version")
+            "asep_poisson_table", "asep_philox_bench", "asep_version")
 
 
 class AsepError(RuntimeError):
@@ -124,6 +125,8 @@ def lib():
             L.asep_threshold.restype = ctypes.c_uint32
             L.asep_poisson_table.argtypes = [ctypes.c_uint32, P(ctypes.c_uint32), P(ctypes.c_uint32), ctypes.c_uint32,
                                              P(ctypes.c_uint32)]
+            L.asep_philox_bench.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp,
+                                            P(ctypes.c_float)]
             L.asep_version.restype = ctypes.c_char_p
             for name in EXPORTED:
                 if name not in ("asep_last_error", "asep_threshold", "asep_version"):
@@ -213,7 +216,7 @@ def make_params(**kw) -> asep_params:
     p.seed = kw.pop("seed", 1)
     p.dis_seed = kw.pop("dis_seed", 0)
     p.init_seed = kw.pop("init_seed", 0)
-    p.flags = 0
+    p.flags = kw.pop("flags", 0)
     if kw:
         raise TypeError(f"unknown parameters {sorted(kw)}")
     return p
@@ -353,6 +356,14 @@ def asep_destroy(ctx) -> None:
         _check(lib().asep_destroy(h))
     if isinstance(ctx, Context):
         ctx.handle = None
+
+
+def asep_philox_bench(blocks: int, threads: int, calls: int, sink_ptr: int, stream=None) -> float:
+    """Milliseconds for blocks*threads threads x `calls` Philox4x32-10 calls
+    (sink_ptr: device buffer of blocks*threads uint32)."""
+    ms = ctypes.c_float()
+    _check(lib().asep_philox_bench(stream, blocks, threads, calls, ctypes.c_void_p(sink_ptr), ctypes.byref(ms)))
+    return float(ms.value)
 
 
 def width2_exact(L: int, sum_h: int, sum_h2_lo: int, sum_h2_hi: int):

@@ -180,7 +180,7 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (p->dis_kind == ASEP_DIS_TURNING && p->model != ASEP_MODEL_TWO_LANE)
     return fail(ctx, ASEP_ERR_INVALID, "turning sites are defined for the two-lane model");
   if (p->init_kind > ASEP_INIT_BERNOULLI_HALF) return fail(ctx, ASEP_ERR_INVALID, "unknown init_kind %u", p->init_kind);
-  if (p->flags != 0) return fail(ctx, ASEP_ERR_INVALID, "flags must be 0");
+  if (p->flags & ~ASEP_FLAG_NO_HOP_COUNTS) return fail(ctx, ASEP_ERR_INVALID, "unknown flags 0x%x", p->flags);
   if ((p->alloc == nullptr) != (p->free_fn == nullptr))
     return fail(ctx, ASEP_ERR_INVALID, "alloc and free_fn must be given together");
   if (p->n_sample_times && !p->sample_times) return fail(ctx, ASEP_ERR_INVALID, "sample_times is NULL");
@@ -248,6 +248,8 @@ Rates rates(const asep_ctx* ctx) {
   r.p_slow = ctx->p.dis_kind == ASEP_DIS_BIMODAL ? ctx->p.dis_b_thr : ctx->p.p_thr;
   r.q_slow = ctx->p.dis_kind == ASEP_DIS_BIMODAL ? ctx->p.dis_c_thr : ctx->p.q_thr;
   r.omega = ctx->p.dis_kind == ASEP_DIS_TURNING ? ctx->p.dis_b_thr : 0u;
+  r.p_always = r.p == ASEP_ALWAYS;
+  r.q_always = r.q == ASEP_ALWAYS;
   return r;
 }
 
@@ -291,6 +293,26 @@ int asep_poisson_table(uint32_t m, uint32_t* k_lo, uint32_t* table, uint32_t cap
     std::memcpy(table, tab.data(), tab.size() * sizeof(uint32_t));
   }
   return ASEP_OK;
+}
+
+int asep_philox_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, float* ms) {
+  if (!sink || !ms || blocks == 0 || threads == 0 || threads > 1024 || (threads & 31))
+    return fail(nullptr, ASEP_ERR_INVALID, "philox bench: bad launch shape");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(nullptr, e, "event create");
+  }
+  int rc = ASEP_OK;
+  if ((e = cudaEventRecord(e0, st)) != cudaSuccess || (e = launch_philox_bench(blocks, threads, calls, sink, st)) !=
+      cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+      (e = cudaEventElapsedTime(ms, e0, e1)) != cudaSuccess)
+    rc = cuda_fail(nullptr, e, "philox bench");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 const char* asep_last_error(const asep_ctx* ctx) {
@@ -429,6 +451,7 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
       a.logD = ctx->logD;
       a.R2 = ctx->R2;
       a.logR2 = ctx->logR2;
+      a.row_bits = (ctx->D - 1) & ~31u;
       a.G = ctx->G;
       a.spc = ctx->spc;
       a.C = ctx->C;
@@ -439,7 +462,8 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
       a.n_sweeps = static_cast<uint32_t>(n);
       a.rec = rec;
       a.counters = ctx->d_cnt;
-      e = launch_domain(a, ctx->p.model, ctx->p.dis_kind, ctx->threads, ctx->blocks, ctx->smem, ctx->stream);
+      const bool count = ctx->p.model == ASEP_MODEL_TWO_LANE || !(ctx->p.flags & ASEP_FLAG_NO_HOP_COUNTS);
+      e = launch_domain(a, ctx->p.model, ctx->p.dis_kind, count, ctx->threads, ctx->blocks, ctx->smem, ctx->stream);
     } else {
       SerialLaunch a;
       a.geo = geometry(ctx);

@@ -27,6 +27,7 @@ struct Rates {
   uint32_t p, q;          // ring: fast right/left; two lanes: lane A / lane B
   uint32_t p_slow, q_slow;  // bimodal slow class
   uint32_t omega;         // two lanes: lane-change probability per sweep
+  bool p_always, q_always;  // p / q == 0xffffffff (a draw r < t test alone cannot say "always")
 };
 
 // Heights recorded inside a launch: after the sweep count rec_times[i] the
@@ -57,6 +58,7 @@ struct DomainLaunch {
   uint32_t ptab_n, ptab_klo;
   uint32_t D, logD;        // domain sites, log2
   uint32_t R2, logR2;      // rows per column = 2D / 32, log2
+  uint32_t row_bits;       // (D - 1) & ~31: the row bits of a slot
   uint32_t G;              // super-domains (columns) per sample = L / (2D)
   uint32_t spc;            // samples per CTA
   uint32_t C;              // columns per CTA = spc * G
@@ -105,14 +107,16 @@ struct HeightsLaunch {
   uint64_t* tab_sh2;
 };
 
-// Shared memory of the resident kernel, in bytes.
+// Shared memory of the resident kernel, in bytes (planes of R2 + 1 rows:
+// the extra row mirrors the next column's row 0).
 size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp, uint32_t ptab_n, uint32_t threads);
 
 cudaError_t launch_init(const InitLaunch& a, cudaStream_t st);
 cudaError_t launch_disorder(const DisorderLaunch& a, cudaStream_t st);
 cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st);
-cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, uint32_t threads, uint32_t blocks,
-                          size_t smem, cudaStream_t st);
+cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, bool count_hops, uint32_t threads,
+                          uint32_t blocks, size_t smem, cudaStream_t st);
 cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st);
+cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, cudaStream_t st);
 
 }  // namespace asep

@@ -22,12 +22,14 @@
 // transposed word array, rows r = 0..2D/32-1 (row r holds sites
 // o + 2Dg + 32r .. +31).  Rows 0..D/32-1 are the first (even) half-domain,
 // the rest the second (odd) half.  In a phase every active lane touches only
-// its own column (plus, for the last bond of an odd half, bit 0 of the next
-// column's row 0, which no active lane touches in that phase), so plain
-// shared loads and stores are race-free, and lanes of a warp hit 32
-// different banks whatever rows they draw.  At the start of every sweep the
-// words are rotated ("realigned") from the previous offset to the new one
-// into a second buffer (double buffering), one funnel shift per word.
+// its own column, so plain shared loads and stores are race-free, and lanes
+// of a warp hit 32 different banks whatever rows they draw.  The last bond of
+// an odd half reaches bit 0 of the next column's row 0: every column has one
+// extra row (row 2D/32) that mirrors the next column's row 0 during the odd
+// phase (copied in after the even phase, bit 0 written back after the odd
+// phase), so that bond is "row + 1" like every other.  At the start of every
+// sweep the words are rotated ("realigned") from the previous offset to the
+// new one into a second buffer (double buffering), one funnel shift per word.
 #include <cstdint>
 
 #include "asep_internal.h"
@@ -217,6 +219,7 @@ struct Lane {
   uint32_t g;        // super-domain index within the sample
   uint32_t col0;     // first column of the sample
   uint32_t c_next;   // column of super-domain g+1 (ring)
+  uint32_t c_prev;   // column of super-domain g-1 (ring)
   uint32_t sample;   // sample index in the context
   uint32_t n_glob;   // global sample id (Philox counter)
   bool active;
@@ -242,58 +245,54 @@ __device__ __forceinline__ void realign(const uint32_t* src, uint32_t* dst, cons
   }
 }
 
-// One attempt of a half-domain phase, without branches: both words of the
-// bond are loaded unconditionally (the second is the next row of the same
-// column, or row 0 of the next column after the last row of an odd half;
-// both in bounds and untouched by other lanes in this phase), the 64-bit flip
-// mask (3 << j across the word pair) is applied under one predicate, and the
-// stores are predicated.  `valid` is k <= K.
-template <uint32_t MODEL, uint32_t DIS, uint32_t PHASE>
-__device__ __forceinline__ void attempt(uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint32_t row0,
-                                        const Lane& ln, uint32_t r, bool valid, Cnt& cnt) {
-  const uint32_t D = a.D, Cp = a.Cp;
-  uint32_t j, tR, tL;
-  uint32_t* pl;
+// One attempt of a half-domain phase, without branches.  The bond's two
+// words are rows `row` and `row + 1` of the lane's own column (row 2D/32 is
+// the mirror of the next column's row 0), both loaded unconditionally; the
+// 64-bit flip mask (3 << j across the word pair) is applied under one
+// predicate.  Thresholds t are 0, multiples of 4096 or "always", and for the
+// multiples r < t is the same test as (r & 0xfffff000) < t, so only the
+// always flag needs separate handling.  `valid` is k <= K.
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+__device__ __forceinline__ void attempt(uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint32_t base,
+                                        uint32_t row_scale, uint32_t r, bool valid, Cnt& cnt) {
+  const uint32_t Cp = a.Cp;
+  // word offset of row (j >> 5) of this half: (r & (D - 1) & ~31) * (Cp / 32)
+  const uint32_t i0 = base + (r & a.row_bits) * row_scale;
+  const uint32_t i1 = i0 + Cp;
+  bool okR, okL;
+  uint32_t* pl = cur;
   if (MODEL == kTwoLane) {
-    const uint32_t lane = (r >> a.logD) & 1u;  // bit log2(D) of the bond index j' = r & (2D - 1)
-    j = r & (D - 1);
-    pl = cur + lane * PW;
-    tR = lane ? 0u : a.rates.p;  // lane A: 10 -> 01
-    tL = lane ? a.rates.q : 0u;  // lane B: 01 -> 10
-  } else {
-    j = r & (D - 1);
-    pl = cur;
-    tR = a.rates.p;
-    tL = a.rates.q;
-  }
-  const uint32_t row = row0 + (j >> 5);
-  const uint32_t i0 = row * Cp + ln.c;
-  uint32_t i1 = i0 + Cp;
-  if (PHASE == 1) i1 = (row + 1 < a.R2) ? i1 : ln.c_next;
-  if (DIS == kDisBimodal) {
+    const bool laneB = (r >> a.logD) & 1u;
+    pl = cur + (laneB ? PW : 0u);
+    okR = !laneB && (a.rates.p_always || r < a.rates.p);  // lane A: 10 -> 01
+    okL = laneB && (a.rates.q_always || r < a.rates.q);   // lane B: 01 -> 10
+  } else if (DIS == kDisBimodal) {
     const uint32_t* cls = cur + PW;
-    const uint32_t pc = __funnelshift_r(cls[i0], cls[i1], j);  // bit0: class of site i, bit1: of site i+1
-    tR = (pc & 1u) ? a.rates.p_slow : tR;
-    tL = (pc & 2u) ? a.rates.q_slow : tL;
+    const uint32_t pc = __funnelshift_r(cls[i0], cls[i1], r);  // bit0: class of site i, bit1: of site i+1
+    const uint32_t u = r & kAcceptMask;
+    okR = u < ((pc & 1u) ? a.rates.p_slow : a.rates.p);
+    okL = u < ((pc & 2u) ? a.rates.q_slow : a.rates.q);
+  } else {
+    okR = a.rates.p_always || r < a.rates.p;
+    okL = a.rates.q_always || r < a.rates.q;
   }
-  const uint32_t u = r & kAcceptMask;
-  const bool okR = valid && (u < tR);
-  const bool okL = valid && (u < tL);
   const uint32_t w0 = pl[i0];
   const uint32_t w1 = pl[i1];
-  const uint32_t pat = __funnelshift_r(w0, w1, j) & 3u;  // bit0 = site i, bit1 = site i+1
+  const uint32_t pat = __funnelshift_r(w0, w1, r) & 3u;  // bit0 = site i, bit1 = site i+1 (shift = r mod 32)
   const bool hopR = okR && pat == 1u;
   const bool hopL = okL && pat == 2u;
-  if (hopR || hopL) {
-    pl[i0] = w0 ^ (3u << (j & 31u));
-    pl[i1] = w1 ^ __funnelshift_l(3u, 0u, j);  // 1 when j % 32 == 31, else 0
+  if (valid && (hopR || hopL)) {
+    pl[i0] = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
+    pl[i1] = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
   }
-  cnt.a += hopR;
-  cnt.b += hopL;
+  if (COUNT) {
+    cnt.a += valid && hopR;
+    cnt.b += valid && hopL;
+  }
 }
 
 // One half-domain phase of one sweep.  All threads of the warp must call.
-template <uint32_t MODEL, uint32_t DIS, uint32_t PHASE>
+template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t PHASE>
 __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, const uint32_t* tab, uint32_t PW,
                                           uint64_t s, const Lane& ln, uint2 key, Cnt& cnt) {
   const uint32_t d = 2 * ln.g + PHASE;
@@ -304,18 +303,39 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, 
     K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
   }
   const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
-  const uint32_t row0 = PHASE * (a.D >> 5);
-  attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, x0.y, 1 <= K, cnt);
-  attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, x0.z, 2 <= K, cnt);
-  attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, x0.w, 3 <= K, cnt);
+  const uint32_t base = PHASE * (a.D >> 5) * a.Cp + ln.c;
+  const uint32_t row_scale = a.Cp >> 5;
+  attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, x0.y, 1 <= K, cnt);
+  attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, x0.z, 2 <= K, cnt);
+  attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, x0.w, 3 <= K, cnt);
 #pragma unroll 2
   for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
     const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, d), key);
     const uint32_t k = call << 2;
-    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.x, k <= K, cnt);
-    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.y, k + 1 <= K, cnt);
-    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.z, k + 2 <= K, cnt);
-    attempt<MODEL, DIS, PHASE>(cur, a, PW, row0, ln, y.w, k + 3 <= K, cnt);
+    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.x, k <= K, cnt);
+    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.y, k + 1 <= K, cnt);
+    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.z, k + 2 <= K, cnt);
+    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.w, k + 3 <= K, cnt);
+  }
+}
+
+// Mirror row: copy row 0 of the next column into row R2 of this column (all
+// planes), after the even phase and before the odd phase.
+template <uint32_t NP>
+__device__ __forceinline__ void mirror_in(uint32_t* cur, const DomainLaunch& a, uint32_t PW, const Lane& ln) {
+#pragma unroll
+  for (uint32_t p = 0; p < NP; ++p) cur[p * PW + a.R2 * a.Cp + ln.c] = cur[p * PW + ln.c_next];
+}
+
+// After the odd phase: the only bit of row 0 another lane may have changed is
+// bit 0 (the previous column's last odd bond); take it back from its mirror.
+template <uint32_t NOCC>
+__device__ __forceinline__ void mirror_out(uint32_t* cur, const DomainLaunch& a, uint32_t PW, const Lane& ln) {
+#pragma unroll
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    const uint32_t w = cur[p * PW + ln.c];
+    const uint32_t m = cur[p * PW + a.R2 * a.Cp + ln.c_prev];
+    cur[p * PW + ln.c] = (w & ~1u) | (m & 1u);
   }
 }
 
@@ -384,13 +404,13 @@ __device__ void record_heights(const uint32_t* cur, const DomainLaunch& a, uint3
   }
 }
 
-template <uint32_t MODEL, uint32_t DIS>
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
 __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
   constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
   const uint32_t R2 = a.R2, Cp = a.Cp, G = a.G, W = a.geo.W;
-  const uint32_t PW = R2 * Cp;
+  const uint32_t PW = (R2 + 1) * Cp;  // R2 rows + the mirror row
   const uint64_t L = a.geo.L;
   uint32_t* bufA = reinterpret_cast<uint32_t*>(smem_raw);
   uint32_t* bufB = bufA + NP * PW;
@@ -405,6 +425,7 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
   ln.g = col_ok ? ln.c - s_loc * G : 0u;
   ln.col0 = s_loc * G;
   ln.c_next = ln.col0 + (ln.g + 1 == G ? 0u : ln.g + 1);
+  ln.c_prev = ln.col0 + (ln.g == 0 ? G - 1 : ln.g - 1);
   ln.sample = blockIdx.x * a.spc + s_loc;
   ln.active = col_ok && ln.sample < a.geo.S;
   ln.n_glob = a.geo.first_sample + ln.sample;
@@ -441,9 +462,12 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
     nxt = t;
     R_cur = o;
     __syncthreads();
-    run_phase<MODEL, DIS, 0>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, 0>(cur, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
-    run_phase<MODEL, DIS, 1>(cur, a, tab, PW, s, ln, key, cnt);
+    if (ln.active) mirror_in<NP>(cur, a, PW, ln);
+    run_phase<MODEL, DIS, COUNT, 1>(cur, a, tab, PW, s, ln, key, cnt);
+    __syncthreads();
+    if (ln.active) mirror_out<NOCC>(cur, a, PW, ln);
     __syncthreads();
     if (MODEL == kTwoLane && DIS == kDisTurning) {
       if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);
@@ -591,16 +615,13 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
   dst[3] += c3;
 }
 
-template <uint32_t MODEL, uint32_t DIS>
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
 cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_domain<MODEL, DIS><<<blocks, threads, smem, st>>>(a);
+  // set per call: cheap, and correct on every device the process uses
+  const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS, COUNT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  k_domain<MODEL, DIS, COUNT><<<blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -618,12 +639,28 @@ uint32_t grid_for(size_t total, uint32_t threads) {
   return static_cast<uint32_t>(b < 1 ? 1 : b);
 }
 
+__global__ void k_philox_bench(uint32_t calls, uint32_t* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint2 key = key_of(0x243F6A8885A308D3ull);
+  uint32_t acc = 0;
+  for (uint32_t c = 0; c < calls; ++c) {
+    const uint4 x = philox10(ctr_of(c >> 4, kTagDom, c & 15u, tid, tid >> 5), key);
+    acc ^= x.x ^ x.y ^ x.z ^ x.w;
+  }
+  sink[tid] = acc;
+}
+
 }  // namespace
+
+cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, cudaStream_t st) {
+  k_philox_bench<<<blocks, threads, 0, st>>>(calls, sink);
+  return cudaGetLastError();
+}
 
 size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp, uint32_t ptab_n, uint32_t threads) {
   const uint32_t nocc = model == kTwoLane ? 2u : 1u;
   const uint32_t np = nocc + (dis != kDisNone ? 1u : 0u);
-  return 2ull * np * R2 * Cp * 4ull + ((ptab_n + 1ull) & ~1ull) * 4ull + (32ull + threads) * 8ull;
+  return 2ull * np * (R2 + 1ull) * Cp * 4ull + ((ptab_n + 1ull) & ~1ull) * 4ull + (32ull + threads) * 8ull;
 }
 
 cudaError_t launch_init(const InitLaunch& a, cudaStream_t st) {
@@ -642,13 +679,18 @@ cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, uint32_t threads, uint32_t blocks,
-                          size_t smem, cudaStream_t st) {
-  if (model == kRing && dis == kDisNone) return launch_domain_t<kRing, kDisNone>(a, threads, blocks, smem, st);
-  if (model == kRing && dis == kDisBimodal) return launch_domain_t<kRing, kDisBimodal>(a, threads, blocks, smem, st);
-  if (model == kTwoLane && dis == kDisNone) return launch_domain_t<kTwoLane, kDisNone>(a, threads, blocks, smem, st);
+cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, bool count_hops, uint32_t threads,
+                          uint32_t blocks, size_t smem, cudaStream_t st) {
+  if (model == kRing && dis == kDisNone)
+    return count_hops ? launch_domain_t<kRing, kDisNone, true>(a, threads, blocks, smem, st)
+                      : launch_domain_t<kRing, kDisNone, false>(a, threads, blocks, smem, st);
+  if (model == kRing && dis == kDisBimodal)
+    return count_hops ? launch_domain_t<kRing, kDisBimodal, true>(a, threads, blocks, smem, st)
+                      : launch_domain_t<kRing, kDisBimodal, false>(a, threads, blocks, smem, st);
+  if (model == kTwoLane && dis == kDisNone)
+    return launch_domain_t<kTwoLane, kDisNone, true>(a, threads, blocks, smem, st);
   if (model == kTwoLane && dis == kDisTurning)
-    return launch_domain_t<kTwoLane, kDisTurning>(a, threads, blocks, smem, st);
+    return launch_domain_t<kTwoLane, kDisTurning, true>(a, threads, blocks, smem, st);
   return cudaErrorInvalidValue;
 }
 

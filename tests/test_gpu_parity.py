@@ -33,7 +33,7 @@ def _device():
     torch.cuda.set_device(0)
 
 
-ORACLE_KEYS = {"model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
+ORACLE_KEYS = {"flags": None, "model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
                "n_realizations": "n_realizations", "samples_per_real": "samples_per_real",
                "first_sample": "first_sample", "p_thr": "p_thr", "q_thr": "q_thr", "dis_kind": "dis_kind",
                "dis_a_thr": "dis_a_thr", "dis_b_thr": "dis_b_thr", "dis_c_thr": "dis_c_thr",
@@ -43,7 +43,8 @@ ORACLE_KEYS = {"model": "model", "schedule": "schedule", "L": "L", "domain_sites
 def oracle_params(kw):
     P = oracle.Params()
     for k, v in kw.items():
-        setattr(P, ORACLE_KEYS[k], v)
+        if ORACLE_KEYS[k]:
+            setattr(P, ORACLE_KEYS[k], v)
     if kw.get("schedule", 0) == A.ASEP_SCHED_DOMAIN and not kw.get("domain_sites"):
         P.D = 256
     return P
@@ -145,6 +146,14 @@ def test_launch_splitting_is_invisible():
         assert np.array_equal(a["words"], x["words"])
         assert np.array_equal(a["sh"], x["sh"]) and np.array_equal(a["sh2"], x["sh2"])
         assert np.array_equal(a["cnt"], x["cnt"])
+
+
+def test_hop_count_flag_changes_nothing_else():
+    kw = dict(L=1 << 15, domain_sites=256, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=43)
+    a = run_gpu(kw, [20], [0, 20])
+    b = run_gpu(dict(kw, flags=A.ASEP_FLAG_NO_HOP_COUNTS), [20], [0, 20])
+    assert np.array_equal(a["words"], b["words"]) and np.array_equal(a["sh"], b["sh"])
+    assert a["cnt"][:, :2].sum() > 0 and not b["cnt"].any()
 
 
 def test_checkpoint_resume_is_bit_exact():

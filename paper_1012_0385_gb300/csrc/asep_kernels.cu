@@ -252,23 +252,22 @@ __device__ __forceinline__ void realign(const uint32_t* src, uint32_t* dst, cons
 // predicate.  Thresholds t are 0, multiples of 4096 or "always", and for the
 // multiples r < t is the same test as (r & 0xfffff000) < t, so only the
 // always flag needs separate handling.  `valid` is k <= K.
-template <uint32_t MODEL, uint32_t DIS, bool COUNT>
-__device__ __forceinline__ void attempt(uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint32_t base,
-                                        uint32_t row_scale, uint32_t r, bool valid, Cnt& cnt) {
-  const uint32_t Cp = a.Cp;
-  // word offset of row (j >> 5) of this half: (r & (D - 1) & ~31) * (Cp / 32)
-  const uint32_t i0 = base + (r & a.row_bits) * row_scale;
-  const uint32_t i1 = i0 + Cp;
+template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
+__device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& a, uint32_t PWb, uint32_t base_b,
+                                        uint32_t row_scale_b, uint32_t r, bool valid, Cnt& cnt) {
+  // byte offset of row (j >> 5) of this half: (r & (D - 1) & ~31) * (4 Cp / 32)
+  const uint32_t cpb = CP ? CP * 4u : a.Cp * 4u;  // row pitch in bytes (compile-time when CP != 0)
+  uint32_t o0 = base_b + (r & a.row_bits) * row_scale_b;
   bool okR, okL;
-  uint32_t* pl = cur;
   if (MODEL == kTwoLane) {
-    const bool laneB = (r >> a.logD) & 1u;
-    pl = cur + (laneB ? PW : 0u);
+    const uint32_t laneB = (r >> a.logD) & 1u;
+    o0 += laneB * PWb;
     okR = !laneB && (a.rates.p_always || r < a.rates.p);  // lane A: 10 -> 01
     okL = laneB && (a.rates.q_always || r < a.rates.q);   // lane B: 01 -> 10
   } else if (DIS == kDisBimodal) {
-    const uint32_t* cls = cur + PW;
-    const uint32_t pc = __funnelshift_r(cls[i0], cls[i1], r);  // bit0: class of site i, bit1: of site i+1
+    const uint32_t c0 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0);
+    const uint32_t c1 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0 + cpb);
+    const uint32_t pc = __funnelshift_r(c0, c1, r);  // bit0: class of site i, bit1: of site i+1
     const uint32_t u = r & kAcceptMask;
     okR = u < ((pc & 1u) ? a.rates.p_slow : a.rates.p);
     okL = u < ((pc & 2u) ? a.rates.q_slow : a.rates.q);
@@ -276,14 +275,16 @@ __device__ __forceinline__ void attempt(uint32_t* cur, const DomainLaunch& a, ui
     okR = a.rates.p_always || r < a.rates.p;
     okL = a.rates.q_always || r < a.rates.q;
   }
-  const uint32_t w0 = pl[i0];
-  const uint32_t w1 = pl[i1];
+  uint32_t* p0 = reinterpret_cast<uint32_t*>(cur + o0);
+  uint32_t* p1 = reinterpret_cast<uint32_t*>(cur + o0 + cpb);
+  const uint32_t w0 = *p0;
+  const uint32_t w1 = *p1;
   const uint32_t pat = __funnelshift_r(w0, w1, r) & 3u;  // bit0 = site i, bit1 = site i+1 (shift = r mod 32)
   const bool hopR = okR && pat == 1u;
   const bool hopL = okL && pat == 2u;
   if (valid && (hopR || hopL)) {
-    pl[i0] = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
-    pl[i1] = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
+    *p0 = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
+    *p1 = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
   }
   if (COUNT) {
     cnt.a += valid && hopR;
@@ -292,7 +293,7 @@ __device__ __forceinline__ void attempt(uint32_t* cur, const DomainLaunch& a, ui
 }
 
 // One half-domain phase of one sweep.  All threads of the warp must call.
-template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t PHASE>
+template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP, uint32_t PHASE>
 __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, const uint32_t* tab, uint32_t PW,
                                           uint64_t s, const Lane& ln, uint2 key, Cnt& cnt) {
   const uint32_t d = 2 * ln.g + PHASE;
@@ -303,19 +304,22 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, 
     K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
   }
   const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
-  const uint32_t base = PHASE * (a.D >> 5) * a.Cp + ln.c;
-  const uint32_t row_scale = a.Cp >> 5;
-  attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, x0.y, 1 <= K, cnt);
-  attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, x0.z, 2 <= K, cnt);
-  attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, x0.w, 3 <= K, cnt);
+  unsigned char* cb = reinterpret_cast<unsigned char*>(cur);
+  const uint32_t cp = CP ? CP : a.Cp;
+  const uint32_t base_b = (PHASE * (a.D >> 5) * cp + ln.c) * 4u;
+  const uint32_t row_scale_b = cp >> 3;  // 4 * Cp / 32
+  const uint32_t PWb = PW * 4u;
+  attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.y, 1 <= K, cnt);
+  attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.z, 2 <= K, cnt);
+  attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
 #pragma unroll 2
   for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
     const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, d), key);
     const uint32_t k = call << 2;
-    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.x, k <= K, cnt);
-    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.y, k + 1 <= K, cnt);
-    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.z, k + 2 <= K, cnt);
-    attempt<MODEL, DIS, COUNT>(cur, a, PW, base, row_scale, y.w, k + 3 <= K, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, k + 1 <= K, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.z, k + 2 <= K, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.w, k + 3 <= K, cnt);
   }
 }
 
@@ -404,7 +408,7 @@ __device__ void record_heights(const uint32_t* cur, const DomainLaunch& a, uint3
   }
 }
 
-template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
 __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
@@ -462,10 +466,10 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
     nxt = t;
     R_cur = o;
     __syncthreads();
-    run_phase<MODEL, DIS, COUNT, 0>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, CP, 0>(cur, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
     if (ln.active) mirror_in<NP>(cur, a, PW, ln);
-    run_phase<MODEL, DIS, COUNT, 1>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, CP, 1>(cur, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
     if (ln.active) mirror_out<NOCC>(cur, a, PW, ln);
     __syncthreads();
@@ -615,14 +619,22 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
   dst[3] += c3;
 }
 
-template <uint32_t MODEL, uint32_t DIS, bool COUNT>
-cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
+template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
+cudaError_t launch_domain_cp(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
   // set per call: cheap, and correct on every device the process uses
-  const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS, COUNT>,
+  const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS, COUNT, CP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
-  k_domain<MODEL, DIS, COUNT><<<blocks, threads, smem, st>>>(a);
+  k_domain<MODEL, DIS, COUNT, CP><<<blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// The row pitch is a compile-time constant for the common 256-column plan
+// (e.g. L = 2^17 with D = 256), a runtime value otherwise.
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
+  if (a.Cp == 256) return launch_domain_cp<MODEL, DIS, COUNT, 256>(a, threads, blocks, smem, st);
+  return launch_domain_cp<MODEL, DIS, COUNT, 0>(a, threads, blocks, smem, st);
 }
 
 template <uint32_t MODEL, uint32_t DIS>

@@ -185,6 +185,42 @@ int asep_destroy(asep_ctx* ctx);
  * ctx is NULL); never NULL. */
 const char* asep_last_error(const asep_ctx* ctx);
 
+/* ---- Batched execution ------------------------------------------------- */
+
+typedef struct asep_batch asep_batch; /* opaque; owns device workspace and a CUDA graph cache */
+
+/* A batch runs many contexts -- each with its own L, D, rates, disorder and
+ * samples -- in ONE persistent launch whose CTAs take (context, sample group)
+ * items, largest first, from a device work queue.  Every sample's randomness
+ * depends only on its own Philox counters, so each context's results are
+ * bit-identical to running it alone with asep_sweep.  The batch owns device
+ * workspace for up to max_jobs contexts and max_items queue items (a
+ * context contributes ceil(S / samples per group) items).  Work is enqueued
+ * on `stream` (cudaStream_t or NULL); the batch first waits for the work
+ * already enqueued on each context's stream, and each context's stream waits
+ * for the batch before its later work.  Only ASEP_SCHED_DOMAIN contexts. */
+int asep_batch_create(void* stream, uint32_t max_jobs, uint32_t max_items, asep_batch** out);
+
+/* Advance ctxs[i] by n_mcs[i] sweeps (0 allowed) for i < n, in one persistent
+ * launch per at most 2^20 sweeps.  Each context may appear once.  Asynchronous. */
+int asep_batch_sweep(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n);
+
+/* Capture one batch step (these contexts, these sweep counts) as a CUDA
+ * graph on the first call for this set, then launch it `replays` times.
+ * The sweep index and the sample-time cursor of each context live in device
+ * memory and advance with every replay.  Asynchronous. */
+int asep_batch_graph(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n, uint32_t replays);
+
+/* Launch shape of the persistent kernel: threads per CTA (0 = the largest a
+ * context needs; must be a multiple of 32 and at least that) and CTAs per SM
+ * (0 = as many as fit).  Results do not depend on it. */
+int asep_batch_set_launch(asep_batch* b, uint32_t threads, uint32_t ctas_per_sm);
+
+/* Free the batch (NULL-safe); synchronises its stream first. */
+int asep_batch_destroy(asep_batch* b);
+
+const char* asep_batch_last_error(const asep_batch* b);
+
 /* Threshold of probability p: 0 for p <= 0, ASEP_ALWAYS for p >= 1, else
  * round(p * 2^20) * 4096.  Host only. */
 uint32_t asep_threshold(double p);

@@ -84,7 +84,8 @@ class asep_info(ctypes.Structure):
 # Every symbol include/asep.h declares (tests check that the library exports them).
 EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_state", "asep_reset", "asep_counters",
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
-            "asep_poisson_table", "asep_philox_bench", "asep_version")
+            "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
+            "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error")
 
 
 class AsepError(RuntimeError):
@@ -128,8 +129,15 @@ def lib():
             L.asep_philox_bench.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp,
                                             P(ctypes.c_float)]
             L.asep_version.restype = ctypes.c_char_p
+            L.asep_batch_create.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, P(vp)]
+            L.asep_batch_sweep.argtypes = [vp, P(vp), P(ctypes.c_uint64), ctypes.c_uint32]
+            L.asep_batch_graph.argtypes = [vp, P(vp), P(ctypes.c_uint64), ctypes.c_uint32, ctypes.c_uint32]
+            L.asep_batch_set_launch.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
+            L.asep_batch_destroy.argtypes = [vp]
+            L.asep_batch_last_error.argtypes = [vp]
+            L.asep_batch_last_error.restype = ctypes.c_char_p
             for name in EXPORTED:
-                if name not in ("asep_last_error", "asep_threshold", "asep_version"):
+                if name not in ("asep_last_error", "asep_threshold", "asep_version", "asep_batch_last_error"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -364,6 +372,91 @@ def asep_philox_bench(blocks: int, threads: int, calls: int, sink_ptr: int, stre
     ms = ctypes.c_float()
     _check(lib().asep_philox_bench(stream, blocks, threads, calls, ctypes.c_void_p(sink_ptr), ctypes.byref(ms)))
     return float(ms.value)
+
+
+# ---------------------------------------------------------------------------
+# Batches
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Owning handle around ``asep_batch*``."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            asep_batch_destroy(self)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bh(b):
+    return b.handle if isinstance(b, Batch) else b
+
+
+def asep_batch_last_error(b=None) -> str:
+    msg = lib().asep_batch_last_error(_bh(b) if b is not None else None)
+    return msg.decode() if msg else ""
+
+
+def _bcheck(rc: int, b):
+    if rc != ASEP_OK:
+        raise AsepError(rc, asep_batch_last_error(b))
+
+
+def asep_batch_create(max_jobs: int = 256, max_items: int = 1 << 16, stream=None) -> Batch:
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+    h = ctypes.c_void_p()
+    rc = lib().asep_batch_create(stream or None, int(max_jobs), int(max_items), ctypes.byref(h))
+    if rc != ASEP_OK:
+        raise AsepError(rc, asep_batch_last_error(None))
+    return Batch(h)
+
+
+def _ctx_array(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[_h(c).value if isinstance(_h(c), ctypes.c_void_p) else _h(c)
+                                          for c in ctxs])
+    return arr
+
+
+def asep_batch_sweep(b, ctxs, n_mcs) -> None:
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n_mcs, dtype=np.uint64), (len(ctxs),)))
+    _bcheck(lib().asep_batch_sweep(_bh(b), _ctx_array(ctxs), _ptr(n, ctypes.c_uint64), len(ctxs)), b)
+
+
+def asep_batch_graph(b, ctxs, n_mcs, replays: int) -> None:
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n_mcs, dtype=np.uint64), (len(ctxs),)))
+    _bcheck(lib().asep_batch_graph(_bh(b), _ctx_array(ctxs), _ptr(n, ctypes.c_uint64), len(ctxs), int(replays)), b)
+
+
+def asep_batch_set_launch(b, threads: int = 0, ctas_per_sm: int = 0) -> None:
+    _bcheck(lib().asep_batch_set_launch(_bh(b), int(threads), int(ctas_per_sm)), b)
+
+
+def asep_batch_destroy(b) -> None:
+    h = _bh(b)
+    if h:
+        lib().asep_batch_destroy(h)
+    if isinstance(b, Batch):
+        b.handle = None
 
 
 def width2_exact(L: int, sum_h: int, sum_h2_lo: int, sum_h2_hi: int):

@@ -37,6 +37,7 @@ struct asep_ctx {
   int64_t* d_sh = nullptr;
   uint64_t* d_sh2 = nullptr;
   uint64_t* d_cnt = nullptr;
+  Clock* d_clock = nullptr;  // device-side (sweep, next sample time); see asep_internal.h
   std::vector<std::pair<void*, size_t>> allocs;
   size_t dev_bytes = 0;
   // attempt-count table
@@ -266,6 +267,54 @@ int record_now(asep_ctx* ctx, uint32_t slot) {
   return ASEP_OK;
 }
 
+DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
+  DomainLaunch a{};
+  a.geo = geometry(ctx);
+  a.model = ctx->p.model;
+  a.dis = ctx->p.dis_kind;
+  a.count_hops = (ctx->p.model == ASEP_MODEL_TWO_LANE || !(ctx->p.flags & ASEP_FLAG_NO_HOP_COUNTS)) ? 1u : 0u;
+  a.state = ctx->d_state;
+  a.mask = ctx->d_mask;
+  a.ptab = ctx->d_ptab;
+  a.ptab_n = static_cast<uint32_t>(ctx->ptab.size());
+  a.ptab_klo = ctx->ptab_klo;
+  a.D = ctx->D;
+  a.logD = ctx->logD;
+  a.R2 = ctx->R2;
+  a.logR2 = ctx->logR2;
+  a.row_bits = (ctx->D - 1) & ~31u;
+  a.G = ctx->G;
+  a.spc = ctx->spc;
+  a.C = ctx->C;
+  a.Cp = ctx->Cp;
+  a.n_groups = ctx->blocks;
+  a.rates = rates(ctx);
+  a.seed = ctx->p.seed;
+  a.n_sweeps = n;
+  a.clock = ctx->d_clock;
+  a.times = ctx->d_times;
+  a.n_times = static_cast<uint32_t>(ctx->times.size());
+  a.tab_sh = ctx->d_sh;
+  a.tab_sh2 = ctx->d_sh2;
+  a.counters = ctx->d_cnt;
+  return a;
+}
+
+// Host mirror of the device clock after n more sweeps.
+void advance_host(asep_ctx* ctx, uint64_t n) {
+  ctx->sweep += n;
+  while (ctx->next_time < ctx->times.size() && ctx->times[ctx->next_time] <= ctx->sweep) ++ctx->next_time;
+}
+
+int set_clock(asep_ctx* ctx, uint64_t sweep, uint32_t next_time) {
+  const cudaError_t e = launch_set_clock(ctx->d_clock, sweep, next_time, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "set clock");
+  ++ctx->launches;
+  ctx->sweep = sweep;
+  ctx->next_time = next_time;
+  return ASEP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -372,9 +421,11 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   ctx->d_sh = static_cast<int64_t*>(dev_alloc(ctx, entries * 8));
   ctx->d_sh2 = static_cast<uint64_t*>(dev_alloc(ctx, entries * 16));
   ctx->d_times = static_cast<uint64_t*>(dev_alloc(ctx, n_times * 8));
+  ctx->d_clock = static_cast<Clock*>(dev_alloc(ctx, sizeof(Clock)));
   if (ctx->R) ctx->d_mask = static_cast<uint32_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->R) * ctx->W * 4));
   if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
-  if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || (ctx->R && !ctx->d_mask) ||
+  if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || !ctx->d_clock ||
+      (ctx->R && !ctx->d_mask) ||
       (!ctx->ptab.empty() && !ctx->d_ptab))
     return bail(fail(ctx, ASEP_ERR_NOMEM, "device allocation failed (%zu bytes so far)", ctx->dev_bytes));
 
@@ -412,11 +463,14 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     if ((e = launch_disorder(dl, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "disorder kernel"));
     ++ctx->launches;
   }
+  uint32_t next = 0;
   if (!ctx->times.empty() && ctx->times[0] == 0) {
     rc = record_now(ctx, 0);
     if (rc != ASEP_OK) return bail(rc);
-    ctx->next_time = 1;
+    next = 1;
   }
+  rc = set_clock(ctx, 0, next);
+  if (rc != ASEP_OK) return bail(rc);
   *out = ctx;
   return ASEP_OK;
 }
@@ -429,41 +483,9 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     uint64_t n = n_mcs - done;
     const uint32_t cap = ctx->p.schedule == ASEP_SCHED_DOMAIN ? ctx->max_sweeps_per_launch : (1u << 20);
     if (n > cap) n = cap;
-    const uint64_t s0 = ctx->sweep;
-    uint32_t i1 = ctx->next_time;
-    while (i1 < ctx->times.size() && ctx->times[i1] <= s0 + n) ++i1;
-    Record rec;
-    rec.rec_times = ctx->d_times + ctx->next_time;
-    rec.n_rec = i1 - ctx->next_time;
-    rec.slot_base = ctx->next_time;
-    rec.tab_sh = ctx->d_sh;
-    rec.tab_sh2 = ctx->d_sh2;
     cudaError_t e;
     if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
-      DomainLaunch a;
-      a.geo = geometry(ctx);
-      a.state = ctx->d_state;
-      a.mask = ctx->d_mask;
-      a.ptab = ctx->d_ptab;
-      a.ptab_n = static_cast<uint32_t>(ctx->ptab.size());
-      a.ptab_klo = ctx->ptab_klo;
-      a.D = ctx->D;
-      a.logD = ctx->logD;
-      a.R2 = ctx->R2;
-      a.logR2 = ctx->logR2;
-      a.row_bits = (ctx->D - 1) & ~31u;
-      a.G = ctx->G;
-      a.spc = ctx->spc;
-      a.C = ctx->C;
-      a.Cp = ctx->Cp;
-      a.rates = rates(ctx);
-      a.seed = ctx->p.seed;
-      a.s0 = s0;
-      a.n_sweeps = static_cast<uint32_t>(n);
-      a.rec = rec;
-      a.counters = ctx->d_cnt;
-      const bool count = ctx->p.model == ASEP_MODEL_TWO_LANE || !(ctx->p.flags & ASEP_FLAG_NO_HOP_COUNTS);
-      e = launch_domain(a, ctx->p.model, ctx->p.dis_kind, count, ctx->threads, ctx->blocks, ctx->smem, ctx->stream);
+      e = launch_domain(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else {
       SerialLaunch a;
       a.geo = geometry(ctx);
@@ -471,16 +493,21 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
       a.mask = ctx->d_mask;
       a.rates = rates(ctx);
       a.seed = ctx->p.seed;
-      a.s0 = s0;
       a.n_sweeps = static_cast<uint32_t>(n);
-      a.rec = rec;
+      a.clock = ctx->d_clock;
+      a.times = ctx->d_times;
+      a.n_times = static_cast<uint32_t>(ctx->times.size());
+      a.tab_sh = ctx->d_sh;
+      a.tab_sh2 = ctx->d_sh2;
       a.counters = ctx->d_cnt;
       e = launch_serial(a, ctx->p.model, ctx->p.dis_kind, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep kernel launch");
-    ++ctx->launches;
-    ctx->sweep = s0 + n;
-    ctx->next_time = i1;
+    if ((e = launch_advance(ctx->d_clock, ctx->d_times, static_cast<uint32_t>(ctx->times.size()),
+                            static_cast<uint32_t>(n), ctx->stream)) != cudaSuccess)
+      return cuda_fail(ctx, e, "clock advance");
+    ctx->launches += 2;
+    advance_host(ctx, n);
     done += n;
   }
   return ASEP_OK;
@@ -504,14 +531,13 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
   il.init_seed = init_seed;
   if ((e = launch_init(il, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "init kernel");
   ++ctx->launches;
-  ctx->sweep = 0;
-  ctx->next_time = 0;
+  uint32_t next = 0;
   if (!ctx->times.empty() && ctx->times[0] == 0) {
     const int rc = record_now(ctx, 0);
     if (rc != ASEP_OK) return rc;
-    ctx->next_time = 1;
+    next = 1;
   }
-  return ASEP_OK;
+  return set_clock(ctx, 0, next);
 }
 
 int asep_sync(asep_ctx* ctx) {
@@ -574,11 +600,11 @@ int asep_load_state(asep_ctx* ctx, const uint32_t* words, size_t n_words, uint64
   if (rc != ASEP_OK) return rc;
   const cudaError_t e = cudaMemcpy(ctx->d_state, words, need * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "load state");
-  ctx->sweep = sweep;
   uint32_t i = 0;
   while (i < ctx->times.size() && ctx->times[i] <= sweep) ++i;
-  ctx->next_time = i;
-  return ASEP_OK;
+  rc = set_clock(ctx, sweep, i);
+  if (rc != ASEP_OK) return rc;
+  return asep_sync(ctx);
 }
 
 int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n) {
@@ -603,6 +629,289 @@ int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words) {
   if (e != cudaSuccess) return cuda_fail(ctx, e, "copy disorder");
   return ASEP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct asep_batch {
+  cudaStream_t stream = nullptr;
+  uint32_t max_jobs = 0, max_items = 0;
+  uint32_t threads_req = 0, ctas_per_sm_req = 0;
+  DomainLaunch* d_jobs = nullptr;
+  uint32_t* d_items = nullptr;
+  uint32_t* d_queue = nullptr;
+  DomainLaunch* h_jobs = nullptr;  // pinned staging
+  uint32_t* h_items = nullptr;
+  cudaEvent_t staged = nullptr;  // the staging buffers may be rewritten once this event is done
+  cudaEvent_t order = nullptr;   // cross-stream ordering with the contexts
+  // graph cache: one captured step
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> graph_key;
+  std::string err;
+};
+
+namespace {
+
+int bfail(asep_batch* b, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+// Build descriptors and the largest-first item list for one step, stage and
+// upload them, and compute the launch shape.  n[i] <= the context's cap.
+int batch_prepare(asep_batch* b, asep_ctx* const* ctxs, const uint32_t* n, uint32_t nj, uint32_t* n_items_out,
+                  uint32_t* threads_out, uint32_t* ctas_out, size_t* smem_out) {
+  uint32_t threads = 32;
+  for (uint32_t j = 0; j < nj; ++j) threads = std::max(threads, ctxs[j]->threads);
+  if (b->threads_req) {
+    if (b->threads_req < threads || (b->threads_req & 31) || b->threads_req > 1024)
+      return bfail(b, ASEP_ERR_INVALID, "threads %u: must be a multiple of 32 in [%u, 1024]", b->threads_req, threads);
+    threads = b->threads_req;
+  }
+  size_t smem = 0;
+  struct It {
+    uint64_t cost;
+    uint32_t code;
+  };
+  std::vector<It> items;
+  cudaError_t e = cudaEventSynchronize(b->staged);
+  if (e != cudaSuccess) return bfail(b, ASEP_ERR_CUDA, "staging event: %s", cudaGetErrorString(e));
+  for (uint32_t j = 0; j < nj; ++j) {
+    const asep_ctx* c = ctxs[j];
+    b->h_jobs[j] = domain_desc(c, n[j]);
+    smem = std::max(smem, domain_smem_bytes(c->p.model, c->p.dis_kind, c->R2, c->Cp,
+                                            static_cast<uint32_t>(c->ptab.size()), threads));
+    if (n[j] == 0) continue;
+    const uint64_t cost = static_cast<uint64_t>(n[j]) * c->spc * c->L * c->planes;
+    for (uint32_t g = 0; g < c->blocks; ++g) items.push_back({cost, (j << 20) | g});
+  }
+  if (items.size() > b->max_items)
+    return bfail(b, ASEP_ERR_INVALID, "%zu queue items exceed the batch's max_items %u", items.size(), b->max_items);
+  std::stable_sort(items.begin(), items.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  for (size_t i = 0; i < items.size(); ++i) b->h_items[i] = items[i].code;
+  if (smem > 227 * 1024) return bfail(b, ASEP_ERR_INVALID, "batch needs %zu bytes of shared memory", smem);
+  int per_sm = batch_ctas_per_sm(threads, smem);
+  if (per_sm <= 0) return bfail(b, ASEP_ERR_INVALID, "batch kernel does not fit (%u threads, %zu B)", threads, smem);
+  if (b->ctas_per_sm_req) per_sm = std::min<int>(per_sm, static_cast<int>(b->ctas_per_sm_req));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t ctas = static_cast<uint32_t>(std::max<size_t>(1, std::min<size_t>(items.size(),
+                                                                  static_cast<size_t>(per_sm) * sms)));
+  if ((e = cudaMemcpyAsync(b->d_jobs, b->h_jobs, nj * sizeof(DomainLaunch), cudaMemcpyHostToDevice, b->stream)) !=
+          cudaSuccess ||
+      (items.size() && (e = cudaMemcpyAsync(b->d_items, b->h_items, items.size() * 4, cudaMemcpyHostToDevice,
+                                            b->stream)) != cudaSuccess) ||
+      (e = cudaEventRecord(b->staged, b->stream)) != cudaSuccess)
+    return bfail(b, ASEP_ERR_CUDA, "stage batch: %s", cudaGetErrorString(e));
+  *n_items_out = static_cast<uint32_t>(items.size());
+  *threads_out = threads;
+  *ctas_out = ctas;
+  *smem_out = smem;
+  return ASEP_OK;
+}
+
+int batch_check(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n) {
+  if (!b) return ASEP_ERR_INVALID;
+  if (n == 0) return ASEP_OK;
+  if (!ctxs || !n_mcs) return bfail(b, ASEP_ERR_INVALID, "ctxs or n_mcs is NULL");
+  if (n > b->max_jobs) return bfail(b, ASEP_ERR_INVALID, "%u contexts exceed max_jobs %u", n, b->max_jobs);
+  if (n > (1u << 12)) return bfail(b, ASEP_ERR_INVALID, "at most 4096 contexts per batch");
+  for (uint32_t j = 0; j < n; ++j) {
+    if (!ctxs[j]) return bfail(b, ASEP_ERR_INVALID, "context %u is NULL", j);
+    if (ctxs[j]->p.schedule != ASEP_SCHED_DOMAIN)
+      return bfail(b, ASEP_ERR_INVALID, "context %u: only the domain schedule runs in a batch", j);
+    if (ctxs[j]->sweep + n_mcs[j] >= (1ull << 40)) return bfail(b, ASEP_ERR_INVALID, "context %u: sweep >= 2^40", j);
+    if (ctxs[j]->blocks > (1u << 20)) return bfail(b, ASEP_ERR_INVALID, "context %u: more than 2^20 groups", j);
+    for (uint32_t k = 0; k < j; ++k)
+      if (ctxs[k] == ctxs[j]) return bfail(b, ASEP_ERR_INVALID, "context %u appears twice", j);
+  }
+  return ASEP_OK;
+}
+
+int order_in(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
+  for (uint32_t j = 0; j < n; ++j) {
+    if (ctxs[j]->stream == b->stream) continue;
+    cudaError_t e;
+    if ((e = cudaEventRecord(b->order, ctxs[j]->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->stream, b->order, 0)) != cudaSuccess)
+      return bfail(b, ASEP_ERR_CUDA, "order: %s", cudaGetErrorString(e));
+  }
+  return ASEP_OK;
+}
+
+int order_out(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
+  cudaError_t e = cudaEventRecord(b->order, b->stream);
+  if (e != cudaSuccess) return bfail(b, ASEP_ERR_CUDA, "order: %s", cudaGetErrorString(e));
+  for (uint32_t j = 0; j < n; ++j) {
+    if (ctxs[j]->stream == b->stream) continue;
+    if ((e = cudaStreamWaitEvent(ctxs[j]->stream, b->order, 0)) != cudaSuccess)
+      return bfail(b, ASEP_ERR_CUDA, "order: %s", cudaGetErrorString(e));
+  }
+  return ASEP_OK;
+}
+
+int batch_step_enqueue(asep_batch* b, uint32_t nj, uint32_t n_items, uint32_t threads, uint32_t ctas, size_t smem) {
+  cudaError_t e;
+  if (n_items && (e = launch_batch(b->d_jobs, b->d_items, n_items, b->d_queue, threads, ctas, smem, b->stream)) !=
+                     cudaSuccess)
+    return bfail(b, ASEP_ERR_CUDA, "batch kernel: %s", cudaGetErrorString(e));
+  if ((e = launch_advance_batch(b->d_jobs, nj, b->stream)) != cudaSuccess)
+    return bfail(b, ASEP_ERR_CUDA, "batch clock advance: %s", cudaGetErrorString(e));
+  return ASEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int asep_batch_create(void* stream, uint32_t max_jobs, uint32_t max_items, asep_batch** out) {
+  if (!out) return bfail(nullptr, ASEP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (max_jobs == 0 || max_jobs > (1u << 12) || max_items == 0 || max_items > (1u << 24))
+    return bfail(nullptr, ASEP_ERR_INVALID, "max_jobs in [1, 4096], max_items in [1, 2^24]");
+  asep_batch* b = new (std::nothrow) asep_batch();
+  if (!b) return bfail(nullptr, ASEP_ERR_NOMEM, "host allocation failed");
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->max_jobs = max_jobs;
+  b->max_items = max_items;
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_jobs, max_jobs * sizeof(DomainLaunch))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_items, static_cast<size_t>(max_items) * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_queue, 16)) != cudaSuccess ||
+      (e = cudaMallocHost(&b->h_jobs, max_jobs * sizeof(DomainLaunch))) != cudaSuccess ||
+      (e = cudaMallocHost(&b->h_items, static_cast<size_t>(max_items) * 4)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming)) != cudaSuccess) {
+    const int rc = bfail(nullptr, e == cudaErrorMemoryAllocation ? ASEP_ERR_NOMEM : ASEP_ERR_CUDA,
+                         "batch workspace: %s", cudaGetErrorString(e));
+    (void)cudaGetLastError();
+    asep_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return ASEP_OK;
+}
+
+int asep_batch_set_launch(asep_batch* b, uint32_t threads, uint32_t ctas_per_sm) {
+  if (!b) return ASEP_ERR_INVALID;
+  if (threads && ((threads & 31) || threads > 1024)) return bfail(b, ASEP_ERR_INVALID, "threads %u", threads);
+  b->threads_req = threads;
+  b->ctas_per_sm_req = ctas_per_sm;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_key.clear();
+  }
+  return ASEP_OK;
+}
+
+int asep_batch_sweep(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n) {
+  int rc = batch_check(b, ctxs, n_mcs, n);
+  if (rc != ASEP_OK || n == 0) return rc;
+  if ((rc = order_in(b, ctxs, n)) != ASEP_OK) return rc;
+  std::vector<uint64_t> left(n_mcs, n_mcs + n);
+  std::vector<uint32_t> step(n);
+  for (;;) {
+    bool any = false;
+    for (uint32_t j = 0; j < n; ++j) {
+      step[j] = static_cast<uint32_t>(std::min<uint64_t>(left[j], std::min<uint64_t>(ctxs[j]->max_sweeps_per_launch,
+                                                                                       1u << 20)));
+      any = any || step[j] > 0;
+    }
+    if (!any) break;
+    uint32_t n_items, threads, ctas;
+    size_t smem;
+    if ((rc = batch_prepare(b, ctxs, step.data(), n, &n_items, &threads, &ctas, &smem)) != ASEP_OK) return rc;
+    if ((rc = batch_step_enqueue(b, n, n_items, threads, ctas, smem)) != ASEP_OK) return rc;
+    for (uint32_t j = 0; j < n; ++j) {
+      left[j] -= step[j];
+      advance_host(ctxs[j], step[j]);
+      ctxs[j]->launches += 2;
+    }
+  }
+  return order_out(b, ctxs, n);
+}
+
+int asep_batch_graph(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n, uint32_t replays) {
+  int rc = batch_check(b, ctxs, n_mcs, n);
+  if (rc != ASEP_OK || n == 0 || replays == 0) return rc;
+  std::vector<uint32_t> step(n);
+  std::vector<uintptr_t> key;
+  for (uint32_t j = 0; j < n; ++j) {
+    if (n_mcs[j] > std::min<uint64_t>(ctxs[j]->max_sweeps_per_launch, 1u << 20))
+      return bfail(b, ASEP_ERR_INVALID, "context %u: a graph step is at most one launch of sweeps", j);
+    step[j] = static_cast<uint32_t>(n_mcs[j]);
+    key.push_back(reinterpret_cast<uintptr_t>(ctxs[j]));
+    key.push_back(step[j]);
+  }
+  if ((rc = order_in(b, ctxs, n)) != ASEP_OK) return rc;
+  cudaError_t e;
+  if (!b->exec || key != b->graph_key) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    uint32_t n_items, threads, ctas;
+    size_t smem;
+    // descriptors and items are uploaded once, outside the graph
+    if ((rc = batch_prepare(b, ctxs, step.data(), n, &n_items, &threads, &ctas, &smem)) != ASEP_OK) return rc;
+    // kernel attributes are set before capture begins
+    if (batch_ctas_per_sm(threads, smem) <= 0) return bfail(b, ASEP_ERR_INVALID, "batch kernel does not fit");
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return bfail(b, ASEP_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    const int rc_enq = batch_step_enqueue(b, n, n_items, threads, ctas, smem);
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc_enq != ASEP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc_enq;
+    }
+    if (e != cudaSuccess) return bfail(b, ASEP_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      return bfail(b, ASEP_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    }
+    b->graph_key = key;
+  }
+  for (uint32_t r = 0; r < replays; ++r) {
+    if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess)
+      return bfail(b, ASEP_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    for (uint32_t j = 0; j < n; ++j) {
+      advance_host(ctxs[j], step[j]);
+      ctxs[j]->launches += 2;
+    }
+  }
+  return order_out(b, ctxs, n);
+}
+
+int asep_batch_destroy(asep_batch* b) {
+  if (!b) return ASEP_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->staged) cudaEventDestroy(b->staged);
+  if (b->order) cudaEventDestroy(b->order);
+  if (b->d_jobs) cudaFree(b->d_jobs);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_queue) cudaFree(b->d_queue);
+  if (b->h_jobs) cudaFreeHost(b->h_jobs);
+  if (b->h_items) cudaFreeHost(b->h_items);
+  delete b;
+  return ASEP_OK;
+}
+
+const char* asep_batch_last_error(const asep_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info) {
   if (!ctx || !info) return ASEP_ERR_INVALID;

@@ -30,14 +30,14 @@ struct Rates {
   bool p_always, q_always;  // p / q == 0xffffffff (a draw r < t test alone cannot say "always")
 };
 
-// Heights recorded inside a launch: after the sweep count rec_times[i] the
-// kernel writes table slot slot_base + i.
-struct Record {
-  const uint64_t* rec_times;  // device, ascending
-  uint32_t n_rec;
-  uint32_t slot_base;
-  int64_t* tab_sh;    // [slot][S][planes]
-  uint64_t* tab_sh2;  // [slot][S][planes][2] (low, high word)
+// Device-side clock of a context: the sweep index of the next sweep and the
+// index of the first sample time not yet recorded.  Kernels read it; only the
+// advance kernel, enqueued after them, writes it -- so an enqueued sequence of
+// launches (or a captured CUDA graph of it) needs no host-side sweep value.
+struct Clock {
+  unsigned long long sweep;
+  uint32_t next_time;
+  uint32_t pad;
 };
 
 struct Geometry {
@@ -49,9 +49,11 @@ struct Geometry {
   uint32_t first_sample;
 };
 
-// Resident two-phase Poisson-domain kernel.
+// Everything a domain-kernel launch needs about one context ("job").
 struct DomainLaunch {
   Geometry geo;
+  uint32_t model, dis;     // Model, Dis
+  uint32_t count_hops;     // ring: count hops (two lanes always count)
   uint32_t* state;         // [S][planes][W]
   const uint32_t* mask;    // [R][W] or nullptr
   const uint32_t* ptab;    // Poisson table entries (device)
@@ -60,14 +62,18 @@ struct DomainLaunch {
   uint32_t R2, logR2;      // rows per column = 2D / 32, log2
   uint32_t row_bits;       // (D - 1) & ~31: the row bits of a slot
   uint32_t G;              // super-domains (columns) per sample = L / (2D)
-  uint32_t spc;            // samples per CTA
-  uint32_t C;              // columns per CTA = spc * G
+  uint32_t spc;            // samples per sample group (CTA or queue item)
+  uint32_t C;              // columns per group = spc * G
   uint32_t Cp;             // row pitch in words (multiple of 32, >= C)
+  uint32_t n_groups;       // ceil(S / spc)
   Rates rates;
   uint64_t seed;
-  uint64_t s0;             // index of the first sweep of this launch
-  uint32_t n_sweeps;
-  Record rec;
+  uint32_t n_sweeps;       // sweeps of this launch
+  Clock* clock;            // device
+  const uint64_t* times;   // device, ascending sample times
+  uint32_t n_times;
+  int64_t* tab_sh;         // [n_times][S][planes]
+  uint64_t* tab_sh2;       // [n_times][S][planes][2] (low, high word)
   uint64_t* counters;      // [S][4]
 };
 
@@ -77,9 +83,12 @@ struct SerialLaunch {
   const uint32_t* mask;
   Rates rates;
   uint64_t seed;
-  uint64_t s0;
   uint32_t n_sweeps;
-  Record rec;
+  Clock* clock;
+  const uint64_t* times;
+  uint32_t n_times;
+  int64_t* tab_sh;
+  uint64_t* tab_sh2;
   uint64_t* counters;
 };
 
@@ -114,8 +123,18 @@ size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp,
 cudaError_t launch_init(const InitLaunch& a, cudaStream_t st);
 cudaError_t launch_disorder(const DisorderLaunch& a, cudaStream_t st);
 cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st);
-cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, bool count_hops, uint32_t threads,
-                          uint32_t blocks, size_t smem, cudaStream_t st);
+// One CTA per sample group of one context.
+cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
+// Persistent: `ctas` CTAs of `threads` threads take items (job << 20 | group)
+// from items[0..n_items) through the queue counter (zeroed here first).
+cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items, uint32_t* queue,
+                         uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st);
+// Advance clocks after n sweeps (one context, or the jobs of a batch).
+cudaError_t launch_advance(Clock* clock, const uint64_t* times, uint32_t n_times, uint32_t n, cudaStream_t st);
+cudaError_t launch_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs, cudaStream_t st);
+cudaError_t launch_set_clock(Clock* clock, uint64_t sweep, uint32_t next_time, cudaStream_t st);
+// Occupancy of the persistent kernel (CTAs per SM) for a block size and shared memory.
+int batch_ctas_per_sm(uint32_t threads, size_t smem);
 cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st);
 cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, cudaStream_t st);
 

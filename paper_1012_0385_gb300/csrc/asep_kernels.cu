@@ -401,16 +401,19 @@ __device__ void record_heights(const uint32_t* cur, const DomainLaunch& a, uint3
     seg_scan(s2, ln.col0, a.G, warp_tot, arr, e2, t2);
     if (ln.active && ln.g == 0) {
       const size_t e = (static_cast<size_t>(slot) * a.geo.S + ln.sample) * NOCC + p;
-      a.rec.tab_sh[e] = t1;
-      a.rec.tab_sh2[2 * e] = static_cast<uint64_t>(t2);
-      a.rec.tab_sh2[2 * e + 1] = 0;
+      a.tab_sh[e] = t1;
+      a.tab_sh2[2 * e] = static_cast<uint64_t>(t2);
+      a.tab_sh2[2 * e + 1] = 0;
     }
   }
 }
 
+// Sweeps of one sample group (spc samples, one column per thread) of one
+// context, for a.n_sweeps sweeps starting at the context clock.  Used by the
+// one-launch-per-context kernel (group = blockIdx.x) and by the persistent
+// batch kernel (group from the work queue).  All threads of the block call.
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
-__global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group, unsigned char* smem_raw) {
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
   constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
   const uint32_t R2 = a.R2, Cp = a.Cp, G = a.G, W = a.geo.W;
@@ -430,14 +433,16 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
   ln.col0 = s_loc * G;
   ln.c_next = ln.col0 + (ln.g + 1 == G ? 0u : ln.g + 1);
   ln.c_prev = ln.col0 + (ln.g == 0 ? G - 1 : ln.g - 1);
-  ln.sample = blockIdx.x * a.spc + s_loc;
+  ln.sample = group * a.spc + s_loc;
   ln.active = col_ok && ln.sample < a.geo.S;
   ln.n_glob = a.geo.first_sample + ln.sample;
   const uint2 key = key_of(a.seed);
+  const uint64_t s0 = a.clock->sweep;
+  const uint32_t cursor = a.clock->next_time;
 
   // load the Poisson table and the lattices (frame offset 0)
   for (uint32_t i = threadIdx.x; i < a.ptab_n; i += blockDim.x) tab[i] = a.ptab[i];
-  const uint32_t first = blockIdx.x * a.spc;
+  const uint32_t first = group * a.spc;
   const uint32_t nloc = min(a.spc, a.geo.S - first);
   for (uint32_t p = 0; p < NP; ++p) {
     for (uint32_t idx = threadIdx.x; idx < nloc * W; idx += blockDim.x) {
@@ -454,10 +459,10 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
   uint32_t* nxt = bufB;
   uint32_t R_cur = 0;
   Cnt cnt;
-  uint32_t rec_i = 0;
+  uint32_t rec = cursor;
 
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
-    const uint64_t s = a.s0 + it;
+    const uint64_t s = s0 + it;
     uint32_t o = 0;
     if (ln.active) o = philox10(ctr_of(s, kTagOff, 0, ln.n_glob, 0), key).x & (2 * a.D - 1);
     if (ln.active) realign<NP>(cur, nxt, a, ln, PW, static_cast<uint32_t>((o + L - R_cur) % L));
@@ -477,15 +482,15 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
       if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);
       __syncthreads();
     }
-    if (rec_i < a.rec.n_rec && a.rec.rec_times[rec_i] == s + 1) {
+    if (rec < a.n_times && a.times[rec] == s + 1) {
       if (ln.active) realign<NP>(cur, nxt, a, ln, PW, static_cast<uint32_t>((L - R_cur) % L));
       t = cur;
       cur = nxt;
       nxt = t;
       R_cur = 0;
       __syncthreads();
-      record_heights<NOCC>(cur, a, PW, a.rec.slot_base + rec_i, ln, warp_tot, arr);
-      ++rec_i;
+      record_heights<NOCC>(cur, a, PW, rec, ln, warp_tot, arr);
+      ++rec;
     }
   }
 
@@ -507,6 +512,76 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
     if (cnt.c) atomicAdd(dst + 2, static_cast<unsigned long long>(cnt.c));
     if (cnt.d) atomicAdd(dst + 3, static_cast<unsigned long long>(cnt.d));
   }
+  __syncthreads();  // the shared memory is reused by the next group of a persistent CTA
+}
+
+template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
+__global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  run_group<MODEL, DIS, COUNT, CP>(a, blockIdx.x, smem_raw);
+}
+
+// Runtime dispatch of one group to the matching instantiation.
+__device__ __forceinline__ void run_group_any(const DomainLaunch& a, uint32_t group, unsigned char* smem) {
+  if (a.model == kTwoLane) {
+    if (a.dis == kDisTurning) run_group<kTwoLane, kDisTurning, true, 0>(a, group, smem);
+    else run_group<kTwoLane, kDisNone, true, 0>(a, group, smem);
+  } else if (a.dis == kDisBimodal) {
+    if (a.count_hops) run_group<kRing, kDisBimodal, true, 0>(a, group, smem);
+    else run_group<kRing, kDisBimodal, false, 0>(a, group, smem);
+  } else if (a.Cp == 256) {
+    if (a.count_hops) run_group<kRing, kDisNone, true, 256>(a, group, smem);
+    else run_group<kRing, kDisNone, false, 256>(a, group, smem);
+  } else {
+    if (a.count_hops) run_group<kRing, kDisNone, true, 0>(a, group, smem);
+    else run_group<kRing, kDisNone, false, 0>(a, group, smem);
+  }
+}
+
+// Persistent batch kernel: CTAs take (job, group) items until the queue is
+// empty.  Items are ordered largest first by the host.  The descriptor of the
+// current item is copied to shared memory once.  Two block-size classes: up
+// to 512 threads (128 registers available) and up to 1024.
+template <uint32_t MAXT>
+__global__ void __launch_bounds__(MAXT) k_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items,
+                                                uint32_t* queue) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t item_idx;
+  __shared__ DomainLaunch desc;
+  for (;;) {
+    if (threadIdx.x == 0) item_idx = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t i = item_idx;
+    if (i >= n_items) break;
+    const uint32_t it = items[i];
+    if (threadIdx.x == 0) desc = jobs[it >> 20];
+    __syncthreads();
+    run_group_any(desc, it & 0xFFFFFu, smem_raw);
+  }
+}
+
+__device__ __forceinline__ void advance_clock(Clock* c, const uint64_t* times, uint32_t n_times, uint32_t n) {
+  const unsigned long long sweep = c->sweep + n;
+  uint32_t next = c->next_time;
+  while (next < n_times && times[next] <= sweep) ++next;
+  c->sweep = sweep;
+  c->next_time = next;
+}
+
+__global__ void k_advance(Clock* clock, const uint64_t* times, uint32_t n_times, uint32_t n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) advance_clock(clock, times, n_times, n);
+}
+
+__global__ void k_set_clock(Clock* clock, unsigned long long sweep, uint32_t next_time) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    clock->sweep = sweep;
+    clock->next_time = next_time;
+  }
+}
+
+__global__ void k_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n_jobs) advance_clock(jobs[j].clock, jobs[j].times, jobs[j].n_times, jobs[j].n_sweeps);
 }
 
 // ---------------------------------------------------------------------------
@@ -532,7 +607,8 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
   const uint64_t n_att = MODEL == kTwoLane ? 2 * L : L;
   const uint32_t logL = 63u - static_cast<uint32_t>(__clzll(static_cast<long long>(L)));
   unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-  uint32_t rec_i = 0;
+  const uint64_t s0 = a.clock->sweep;
+  uint32_t rec = a.clock->next_time;
 
   auto attempt = [&](uint32_t rb, uint32_t ru) {
     if (MODEL == kTwoLane) {
@@ -568,7 +644,7 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
   };
 
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
-    const uint64_t s = a.s0 + it;
+    const uint64_t s = s0 + it;
     for (uint64_t k = 0; k < n_att; k += 2) {
       const uint4 x = philox10(ctr_of(s, kTagSer, 0, n_glob, static_cast<uint32_t>(k >> 1)), key);
       attempt(x.x, x.y);
@@ -591,7 +667,7 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
         }
       }
     }
-    if (rec_i < a.rec.n_rec && a.rec.rec_times[rec_i] == s + 1) {
+    if (rec < a.n_times && a.times[rec] == s + 1) {
       for (uint32_t p = 0; p < a.geo.planes; ++p) {
         const uint32_t* pl = p ? B : A;
         long long h = 0, s1 = 0;
@@ -604,12 +680,12 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
             s2 += static_cast<unsigned long long>(h * h);
           }
         }
-        const size_t e = (static_cast<size_t>(a.rec.slot_base + rec_i) * a.geo.S + sample) * a.geo.planes + p;
-        a.rec.tab_sh[e] = s1;
-        a.rec.tab_sh2[2 * e] = static_cast<uint64_t>(s2);
-        a.rec.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2 >> 64);
+        const size_t e = (static_cast<size_t>(rec) * a.geo.S + sample) * a.geo.planes + p;
+        a.tab_sh[e] = s1;
+        a.tab_sh2[2 * e] = static_cast<uint64_t>(s2);
+        a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2 >> 64);
       }
-      ++rec_i;
+      ++rec;
     }
   }
   uint64_t* dst = a.counters + 4 * static_cast<size_t>(sample);
@@ -620,21 +696,21 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
 }
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
-cudaError_t launch_domain_cp(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
+cudaError_t launch_domain_cp(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   // set per call: cheap, and correct on every device the process uses
   const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS, COUNT, CP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
-  k_domain<MODEL, DIS, COUNT, CP><<<blocks, threads, smem, st>>>(a);
+  k_domain<MODEL, DIS, COUNT, CP><<<a.n_groups, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 // The row pitch is a compile-time constant for the common 256-column plan
 // (e.g. L = 2^17 with D = 256), a runtime value otherwise.
 template <uint32_t MODEL, uint32_t DIS, bool COUNT>
-cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, uint32_t blocks, size_t smem, cudaStream_t st) {
-  if (a.Cp == 256) return launch_domain_cp<MODEL, DIS, COUNT, 256>(a, threads, blocks, smem, st);
-  return launch_domain_cp<MODEL, DIS, COUNT, 0>(a, threads, blocks, smem, st);
+cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
+  if (a.Cp == 256) return launch_domain_cp<MODEL, DIS, COUNT, 256>(a, threads, smem, st);
+  return launch_domain_cp<MODEL, DIS, COUNT, 0>(a, threads, smem, st);
 }
 
 template <uint32_t MODEL, uint32_t DIS>
@@ -691,19 +767,69 @@ cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_domain(const DomainLaunch& a, uint32_t model, uint32_t dis, bool count_hops, uint32_t threads,
-                          uint32_t blocks, size_t smem, cudaStream_t st) {
-  if (model == kRing && dis == kDisNone)
-    return count_hops ? launch_domain_t<kRing, kDisNone, true>(a, threads, blocks, smem, st)
-                      : launch_domain_t<kRing, kDisNone, false>(a, threads, blocks, smem, st);
-  if (model == kRing && dis == kDisBimodal)
-    return count_hops ? launch_domain_t<kRing, kDisBimodal, true>(a, threads, blocks, smem, st)
-                      : launch_domain_t<kRing, kDisBimodal, false>(a, threads, blocks, smem, st);
-  if (model == kTwoLane && dis == kDisNone)
-    return launch_domain_t<kTwoLane, kDisNone, true>(a, threads, blocks, smem, st);
-  if (model == kTwoLane && dis == kDisTurning)
-    return launch_domain_t<kTwoLane, kDisTurning, true>(a, threads, blocks, smem, st);
+cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
+  const bool count = a.count_hops != 0;
+  if (a.model == kRing && a.dis == kDisNone)
+    return count ? launch_domain_t<kRing, kDisNone, true>(a, threads, smem, st)
+                 : launch_domain_t<kRing, kDisNone, false>(a, threads, smem, st);
+  if (a.model == kRing && a.dis == kDisBimodal)
+    return count ? launch_domain_t<kRing, kDisBimodal, true>(a, threads, smem, st)
+                 : launch_domain_t<kRing, kDisBimodal, false>(a, threads, smem, st);
+  if (a.model == kTwoLane && a.dis == kDisNone) return launch_domain_t<kTwoLane, kDisNone, true>(a, threads, smem, st);
+  if (a.model == kTwoLane && a.dis == kDisTurning)
+    return launch_domain_t<kTwoLane, kDisTurning, true>(a, threads, smem, st);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items, uint32_t* queue,
+                         uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+  if (threads <= 512) {
+    if ((e = cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) !=
+        cudaSuccess)
+      return e;
+    k_batch<512><<<ctas, threads, smem, st>>>(jobs, items, n_items, queue);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) !=
+        cudaSuccess)
+      return e;
+    k_batch<1024><<<ctas, threads, smem, st>>>(jobs, items, n_items, queue);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(Clock* clock, const uint64_t* times, uint32_t n_times, uint32_t n, cudaStream_t st) {
+  k_advance<<<1, 32, 0, st>>>(clock, times, n_times, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_clock(Clock* clock, uint64_t sweep, uint32_t next_time, cudaStream_t st) {
+  k_set_clock<<<1, 32, 0, st>>>(clock, sweep, next_time);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs, cudaStream_t st) {
+  k_advance_batch<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, n_jobs);
+  return cudaGetLastError();
+}
+
+int batch_ctas_per_sm(uint32_t threads, size_t smem) {
+  int n = 0;
+  if (threads <= 512) {
+    if (cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<512>, static_cast<int>(threads), smem) !=
+        cudaSuccess)
+      return 0;
+  } else {
+    if (cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<1024>, static_cast<int>(threads), smem) !=
+        cudaSuccess)
+      return 0;
+  }
+  return n;
 }
 
 cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st) {

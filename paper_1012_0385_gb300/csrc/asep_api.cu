@@ -698,7 +698,9 @@ int batch_prepare(asep_batch* b, asep_ctx* const* ctxs, const uint32_t* n, uint3
     return bfail(b, ASEP_ERR_INVALID, "%zu queue items exceed the batch's max_items %u", items.size(), b->max_items);
   std::stable_sort(items.begin(), items.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
   for (size_t i = 0; i < items.size(); ++i) b->h_items[i] = items[i].code;
-  if (smem > 227 * 1024) return bfail(b, ASEP_ERR_INVALID, "batch needs %zu bytes of shared memory", smem);
+  // the batch kernel's own static shared memory (item index, descriptor) shares the 227 KB opt-in
+  if (smem + sizeof(DomainLaunch) + 64 > 227 * 1024)
+    return bfail(b, ASEP_ERR_INVALID, "batch needs %zu bytes of shared memory", smem);
   int per_sm = batch_ctas_per_sm(threads, smem);
   if (per_sm <= 0) return bfail(b, ASEP_ERR_INVALID, "batch kernel does not fit (%u threads, %zu B)", threads, smem);
   if (b->ctas_per_sm_req) per_sm = std::min<int>(per_sm, static_cast<int>(b->ctas_per_sm_req));

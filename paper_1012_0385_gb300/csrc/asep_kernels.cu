@@ -697,9 +697,10 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
 cudaError_t launch_domain_cp(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
-  // set per call: cheap, and correct on every device the process uses
+  // set per call to what this launch needs: cheap, and right on every device
+  (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(k_domain<MODEL, DIS, COUNT, CP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   k_domain<MODEL, DIS, COUNT, CP><<<a.n_groups, threads, smem, st>>>(a);
   return cudaGetLastError();
@@ -752,17 +753,20 @@ size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp,
 }
 
 cudaError_t launch_init(const InitLaunch& a, cudaStream_t st) {
+  (void)cudaGetLastError();
   const size_t total = static_cast<size_t>(a.geo.S) * a.geo.planes * a.geo.W;
   k_init<<<grid_for(total, 256), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_disorder(const DisorderLaunch& a, cudaStream_t st) {
+  (void)cudaGetLastError();
   k_disorder<<<grid_for(static_cast<size_t>(a.R) * a.W, 256), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st) {
+  (void)cudaGetLastError();
   k_heights<<<a.geo.S * a.geo.planes, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -781,19 +785,23 @@ cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, 
   return cudaErrorInvalidValue;
 }
 
+// Dynamic shared memory opt-in of the batch kernel (its static shared memory
+// -- the item index and the descriptor copy -- counts against the same limit).
+template <uint32_t MAXT>
+cudaError_t batch_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_batch<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
 cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items, uint32_t* queue,
                          uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st) {
+  (void)cudaGetLastError();
   cudaError_t e;
   if ((e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
   if (threads <= 512) {
-    if ((e = cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) !=
-        cudaSuccess)
-      return e;
+    if ((e = batch_attr<512>(smem)) != cudaSuccess) return e;
     k_batch<512><<<ctas, threads, smem, st>>>(jobs, items, n_items, queue);
   } else {
-    if ((e = cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) !=
-        cudaSuccess)
-      return e;
+    if ((e = batch_attr<1024>(smem)) != cudaSuccess) return e;
     k_batch<1024><<<ctas, threads, smem, st>>>(jobs, items, n_items, queue);
   }
   return cudaGetLastError();
@@ -816,18 +824,17 @@ cudaError_t launch_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs, cuda
 
 int batch_ctas_per_sm(uint32_t threads, size_t smem) {
   int n = 0;
+  cudaError_t e;
   if (threads <= 512) {
-    if (cudaFuncSetAttribute(k_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
-      return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<512>, static_cast<int>(threads), smem) !=
-        cudaSuccess)
-      return 0;
+    if ((e = batch_attr<512>(smem)) == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<512>, static_cast<int>(threads), smem);
   } else {
-    if (cudaFuncSetAttribute(k_batch<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
-      return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<1024>, static_cast<int>(threads), smem) !=
-        cudaSuccess)
-      return 0;
+    if ((e = batch_attr<1024>(smem)) == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<1024>, static_cast<int>(threads), smem);
+  }
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();  // do not leave the failure for the next launch check to find
+    return 0;
   }
   return n;
 }

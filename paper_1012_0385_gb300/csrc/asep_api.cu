@@ -647,6 +647,7 @@ struct asep_batch {
   uint32_t* h_items = nullptr;
   cudaEvent_t staged = nullptr;  // the staging buffers may be rewritten once this event is done
   cudaEvent_t order = nullptr;   // cross-stream ordering with the contexts
+  cudaStream_t cap_stream = nullptr;  // capture stream (the legacy default stream cannot be captured)
   // graph cache: one captured step
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> graph_key;
@@ -762,12 +763,13 @@ int order_out(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
   return ASEP_OK;
 }
 
-int batch_step_enqueue(asep_batch* b, uint32_t nj, uint32_t n_items, uint32_t threads, uint32_t ctas, size_t smem) {
+int batch_step_enqueue(asep_batch* b, uint32_t nj, uint32_t n_items, uint32_t threads, uint32_t ctas, size_t smem,
+                       cudaStream_t st) {
   cudaError_t e;
-  if (n_items && (e = launch_batch(b->d_jobs, b->d_items, n_items, b->d_queue, threads, ctas, smem, b->stream)) !=
+  if (n_items && (e = launch_batch(b->d_jobs, b->d_items, n_items, b->d_queue, threads, ctas, smem, st)) !=
                      cudaSuccess)
     return bfail(b, ASEP_ERR_CUDA, "batch kernel: %s", cudaGetErrorString(e));
-  if ((e = launch_advance_batch(b->d_jobs, nj, b->stream)) != cudaSuccess)
+  if ((e = launch_advance_batch(b->d_jobs, nj, st)) != cudaSuccess)
     return bfail(b, ASEP_ERR_CUDA, "batch clock advance: %s", cudaGetErrorString(e));
   return ASEP_OK;
 }
@@ -793,7 +795,8 @@ int asep_batch_create(void* stream, uint32_t max_jobs, uint32_t max_items, asep_
       (e = cudaMallocHost(&b->h_jobs, max_jobs * sizeof(DomainLaunch))) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_items, static_cast<size_t>(max_items) * 4)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming)) != cudaSuccess) {
+      (e = cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     const int rc = bfail(nullptr, e == cudaErrorMemoryAllocation ? ASEP_ERR_NOMEM : ASEP_ERR_CUDA,
                          "batch workspace: %s", cudaGetErrorString(e));
     (void)cudaGetLastError();
@@ -834,7 +837,7 @@ int asep_batch_sweep(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs
     uint32_t n_items, threads, ctas;
     size_t smem;
     if ((rc = batch_prepare(b, ctxs, step.data(), n, &n_items, &threads, &ctas, &smem)) != ASEP_OK) return rc;
-    if ((rc = batch_step_enqueue(b, n, n_items, threads, ctas, smem)) != ASEP_OK) return rc;
+    if ((rc = batch_step_enqueue(b, n, n_items, threads, ctas, smem, b->stream)) != ASEP_OK) return rc;
     for (uint32_t j = 0; j < n; ++j) {
       left[j] -= step[j];
       advance_host(ctxs[j], step[j]);
@@ -869,11 +872,12 @@ int asep_batch_graph(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs
     if ((rc = batch_prepare(b, ctxs, step.data(), n, &n_items, &threads, &ctas, &smem)) != ASEP_OK) return rc;
     // kernel attributes are set before capture begins
     if (batch_ctas_per_sm(threads, smem) <= 0) return bfail(b, ASEP_ERR_INVALID, "batch kernel does not fit");
+    // capture on the batch's own stream (nothing runs during capture), launch on b->stream
     cudaGraph_t graph = nullptr;
-    if ((e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return bfail(b, ASEP_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-    const int rc_enq = batch_step_enqueue(b, n, n_items, threads, ctas, smem);
-    e = cudaStreamEndCapture(b->stream, &graph);
+    const int rc_enq = batch_step_enqueue(b, n, n_items, threads, ctas, smem, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &graph);
     if (rc_enq != ASEP_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rc_enq;
@@ -904,6 +908,7 @@ int asep_batch_destroy(asep_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->order) cudaEventDestroy(b->order);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->d_jobs) cudaFree(b->d_jobs);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_queue) cudaFree(b->d_queue);

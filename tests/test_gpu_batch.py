@@ -96,11 +96,12 @@ def test_batch_in_uneven_steps_equals_alone(reference):
 
 def test_batch_graph_replays_equal_alone(reference):
     ctxs = [A.asep_create(A.make_params(**kw), sample_times=t) for kw, t in MIX]
-    # common chunk that divides every count: replay the captured step, then finish the rest
+    # per-context step n // 5: replay the captured step 3 + 2 times, then finish the rest
+    step = [n // 5 for n in N_MCS]
     with A.asep_batch_create(max_jobs=16, max_items=4096) as b:
-        A.asep_batch_graph(b, ctxs, [5] * len(ctxs), replays=3)
-        A.asep_batch_graph(b, ctxs, [5] * len(ctxs), replays=2)  # cached graph
-        A.asep_batch_sweep(b, ctxs, [n - 25 for n in N_MCS])
+        A.asep_batch_graph(b, ctxs, step, replays=3)
+        A.asep_batch_graph(b, ctxs, step, replays=2)  # cached graph
+        A.asep_batch_sweep(b, ctxs, [n - 5 * k for n, k in zip(N_MCS, step)])
         for c, ref in zip(ctxs, reference):
             same(snapshot(c), ref)
     for c in ctxs:

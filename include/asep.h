@@ -221,6 +221,25 @@ int asep_batch_destroy(asep_batch* b);
 
 const char* asep_batch_last_error(const asep_batch* b);
 
+/* Batch sweep that allocates nothing -- for callers that may not allocate
+ * device memory when they run work (memory owned by another allocator or a
+ * fixed pool, a footprint frozen after start-up, or threads that must stay off
+ * cudaMalloc's device-synchronising path).  Same work and bit-identical
+ * results as asep_batch_create + asep_batch_sweep with a stream, but the work
+ * queue (context descriptors, queue items, queue counter) lives in one static
+ * device array of the library, about 80 KB, held on every GPU that loads the
+ * library until the process exits.  Limits: at most 64 contexts per call and
+ * 16384 sample groups per launch step; larger requests return
+ * ASEP_ERR_INVALID.  Every context must use `stream`.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, so make it before any stream capture.  All calls on one GPU
+ * share its array, which keeps the last call's contents (the queue counter is
+ * cleared by every call): calls whose work overlaps on the same GPU, e.g. on
+ * two streams, race and must be ordered by the caller.  The host side of calls
+ * is serialised by a lock.  Calls no allocating function, host or device.
+ * No counterpart in the paper. */
+int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n, void* stream);
+
 /* Threshold of probability p: 0 for p <= 0, ASEP_ALWAYS for p >= 1, else
  * round(p * 2^20) * 4096.  Host only. */
 uint32_t asep_threshold(double p);

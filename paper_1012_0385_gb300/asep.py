@@ -85,7 +85,8 @@ class asep_info(ctypes.Structure):
 EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_state", "asep_reset", "asep_counters",
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
-            "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error")
+            "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
+            "asep_batch_sweep_static")
 
 
 class AsepError(RuntimeError):
@@ -136,6 +137,7 @@ def lib():
             L.asep_batch_destroy.argtypes = [vp]
             L.asep_batch_last_error.argtypes = [vp]
             L.asep_batch_last_error.restype = ctypes.c_char_p
+            L.asep_batch_sweep_static.argtypes = [P(vp), P(ctypes.c_uint64), ctypes.c_uint32, vp]
             for name in EXPORTED:
                 if name not in ("asep_last_error", "asep_threshold", "asep_version", "asep_batch_last_error"):
                     getattr(L, name).restype = ctypes.c_int
@@ -457,6 +459,22 @@ def asep_batch_destroy(b) -> None:
         lib().asep_batch_destroy(h)
     if isinstance(b, Batch):
         b.handle = None
+
+
+def asep_batch_sweep_static(ctxs, n_mcs, stream=None) -> None:
+    """The batch sweep without any allocation (static device workspace): for
+    callers that may not allocate device memory when they run work.  Every
+    context must use `stream` (default: torch's current stream)."""
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n_mcs, dtype=np.uint64), (len(ctxs),)))
+    _check(lib().asep_batch_sweep_static(_ctx_array(ctxs), _ptr(n, ctypes.c_uint64), len(ctxs), stream or None))
 
 
 def width2_exact(L: int, sum_h: int, sum_h2_lo: int, sum_h2_hi: int):

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -938,6 +939,154 @@ int asep_destroy(asep_ctx* ctx) {
   if (!ctx) return ASEP_OK;
   release(ctx);
   delete ctx;
+  return ASEP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch sweep without allocation
+// ---------------------------------------------------------------------------
+//
+// Some callers cannot allocate device memory at the moment they want to run
+// work: a host application whose device memory is owned by another allocator
+// or pool that refuses outside requests, code that must not grow its memory
+// footprint after start-up, or a thread that may not hit the driver's
+// allocation path (cudaMalloc can synchronise the device).  For them the
+// batch sweep below keeps its work queue -- context descriptors, the item
+// list and the queue counter -- in one fixed static device array instead of
+// a batch object's workspace.  The array belongs to the library: every GPU
+// that loads libasep.so holds it until the process exits.
+
+namespace {
+
+constexpr uint32_t kStaticMaxJobs = 64;      // contexts per call
+constexpr uint32_t kStaticMaxItems = 16384;  // queue items (sample groups) per step
+constexpr size_t kStaticJobsBytes = (kStaticMaxJobs * sizeof(DomainLaunch) + 255) / 256 * 256;
+constexpr size_t kStaticItemsBytes = kStaticMaxItems * sizeof(uint32_t);
+constexpr size_t kStaticBytes = kStaticJobsBytes + kStaticItemsBytes + 256;  // + the queue counter
+
+// In host code this name is only a stand-in for the device array; kernels get
+// its device address from cudaGetSymbolAddress (see static_scratch()).
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;  // held for a whole call: serialises the host side of all calls
+void* g_static_ptr[kMaxDevices] = {};
+// host staging for the uploads (static, so no stack or heap use)
+DomainLaunch g_static_jobs[kStaticMaxJobs];
+uint32_t g_static_items[kStaticMaxItems];
+
+// Device address of the static array on the current device, looked up once
+// per device (with that device current) and cached.  Caller holds g_static_mu.
+int static_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, ASEP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, ASEP_ERR_INVALID, "device %d out of range", dev);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return fail(nullptr, ASEP_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_static_ptr[dev]);
+  return ASEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n, void* stream) {
+  if (n == 0) return ASEP_OK;
+  if (!ctxs || !n_mcs) return fail(nullptr, ASEP_ERR_INVALID, "ctxs or n_mcs is NULL");
+  if (n > kStaticMaxJobs)
+    return fail(nullptr, ASEP_ERR_INVALID, "%u contexts exceed the static batch limit of %u", n, kStaticMaxJobs);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (uint32_t j = 0; j < n; ++j) {
+    const asep_ctx* c = ctxs[j];
+    if (!c) return fail(nullptr, ASEP_ERR_INVALID, "context %u is NULL", j);
+    if (c->p.schedule != ASEP_SCHED_DOMAIN)
+      return fail(nullptr, ASEP_ERR_INVALID, "context %u: only the domain schedule runs in a batch", j);
+    if (c->stream != st) return fail(nullptr, ASEP_ERR_INVALID, "context %u does not use the call's stream", j);
+    if (c->sweep + n_mcs[j] >= (1ull << 40)) return fail(nullptr, ASEP_ERR_INVALID, "context %u: sweep >= 2^40", j);
+    for (uint32_t k = 0; k < j; ++k)
+      if (ctxs[k] == c) return fail(nullptr, ASEP_ERR_INVALID, "context %u appears twice", j);
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  unsigned char* scratch = nullptr;
+  int rc = static_scratch(&scratch);
+  if (rc != ASEP_OK) return rc;
+  DomainLaunch* d_jobs = reinterpret_cast<DomainLaunch*>(scratch);
+  uint32_t* d_items = reinterpret_cast<uint32_t*>(scratch + kStaticJobsBytes);
+  uint32_t* d_queue = reinterpret_cast<uint32_t*>(scratch + kStaticJobsBytes + kStaticItemsBytes);
+
+  DomainLaunch* jobs = g_static_jobs;
+  uint32_t* items = g_static_items;
+  uint32_t order[kStaticMaxJobs];
+  uint64_t left[kStaticMaxJobs];
+  for (uint32_t j = 0; j < n; ++j) left[j] = n_mcs[j];
+  for (;;) {
+    uint32_t threads = 32;
+    size_t smem = 0;
+    bool any = false;
+    uint64_t cost[kStaticMaxJobs];
+    for (uint32_t j = 0; j < n; ++j) {
+      const asep_ctx* c = ctxs[j];
+      const uint32_t step = static_cast<uint32_t>(std::min<uint64_t>(left[j], std::min<uint64_t>(
+                                                                                 c->max_sweeps_per_launch, 1u << 20)));
+      jobs[j] = domain_desc(c, step);
+      threads = std::max(threads, c->threads);
+      cost[j] = static_cast<uint64_t>(step) * c->spc * c->L * c->planes;
+      order[j] = j;
+      any = any || step > 0;
+    }
+    if (!any) break;
+    for (uint32_t j = 0; j < n; ++j) {
+      const asep_ctx* c = ctxs[j];
+      smem = std::max(smem, domain_smem_bytes(c->p.model, c->p.dis_kind, c->R2, c->Cp,
+                                              static_cast<uint32_t>(c->ptab.size()), threads));
+    }
+    if (smem + sizeof(DomainLaunch) + 64 > 227 * 1024)
+      return fail(nullptr, ASEP_ERR_INVALID, "batch needs %zu bytes of shared memory", smem);
+    // largest first: contexts by cost per item, each context's groups in order
+    std::stable_sort(order, order + n, [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+    uint32_t n_items = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+      const uint32_t j = order[k];
+      if (jobs[j].n_sweeps == 0) continue;
+      if (ctxs[j]->blocks > (1u << 20) || n_items + ctxs[j]->blocks > kStaticMaxItems)
+        return fail(nullptr, ASEP_ERR_INVALID, "more than %u sample groups exceed the static batch limit",
+                    kStaticMaxItems);
+      for (uint32_t g = 0; g < ctxs[j]->blocks; ++g) items[n_items++] = (j << 20) | g;
+    }
+    int per_sm = batch_ctas_per_sm(threads, smem);
+    if (per_sm <= 0) return fail(nullptr, ASEP_ERR_INVALID, "batch kernel does not fit (%u threads)", threads);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t ctas = std::max<uint32_t>(1, std::min<uint32_t>(n_items, static_cast<uint32_t>(per_sm * sms)));
+    // pageable copies: they return once the host buffers have been read, and
+    // reach the device in stream order after the previous step's kernels
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_jobs, jobs, n * sizeof(DomainLaunch), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (n_items && (e = cudaMemcpyAsync(d_items, items, n_items * sizeof(uint32_t), cudaMemcpyHostToDevice, st)) !=
+                        cudaSuccess))
+      return fail(nullptr, ASEP_ERR_CUDA, "static batch upload: %s", cudaGetErrorString(e));
+    if (n_items && (e = launch_batch(d_jobs, d_items, n_items, d_queue, threads, ctas, smem, st)) != cudaSuccess)
+      return fail(nullptr, ASEP_ERR_CUDA, "static batch kernel: %s", cudaGetErrorString(e));
+    if ((e = launch_advance_batch(d_jobs, n, st)) != cudaSuccess)
+      return fail(nullptr, ASEP_ERR_CUDA, "static batch clock advance: %s", cudaGetErrorString(e));
+    for (uint32_t j = 0; j < n; ++j) {
+      left[j] -= jobs[j].n_sweeps;
+      advance_host(ctxs[j], jobs[j].n_sweeps);
+      ctxs[j]->launches += 2;
+    }
+  }
   return ASEP_OK;
 }
 

@@ -305,12 +305,35 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if not args.no_serving and world == 1:
+            line["serving"] = serving_comparison()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def serving_comparison(n_jobs: int = 64, rate_hz: float = 45.0, seed: int = 2026):
+    """The served ensemble mix, scaled to seconds: Poisson arrivals of jobs
+    drawn from the four workload families, L log-uniform in [2^10, 2^19],
+    1-256 samples, n_mcs log-uniform in [10, 10^4] (the full mix's 10^3-10^6
+    divided by 100).  The same trace is replayed with continuous batching and
+    with one launch per job; results are bit-identical between the two."""
+    from paper_1012_0385_gb300 import serve
+
+    def trace():
+        return serve.make_trace(n_jobs, seed=seed, rate_hz=rate_hz, L_range=(1 << 10, 1 << 19),
+                                samples_range=(1, 256), n_mcs_range=(10, 10_000))
+
+    batched = serve.serve_batched(trace(), quantum_s=0.02)
+    plain = serve.serve_plain(trace())
+    return {"trace": f"{n_jobs} jobs, Poisson {rate_hz:g} Hz, kinds tasep/asep/bimodal/two_lane, "
+                     "L log-uniform [2^10, 2^19], samples log-uniform [1, 256], n_mcs log-uniform [10, 10^4]",
+            "batched": batched, "plain": plain,
+            "throughput_ratio": batched["throughput_attempts_per_s"] / plain["throughput_attempts_per_s"],
+            "p99_ratio": batched["p99_latency_s"] / plain["p99_latency_s"]}
 
 
 def profile_case():
@@ -342,6 +365,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-mix comparison")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")

@@ -46,6 +46,7 @@ struct asep_ctx {
   uint32_t ptab_klo = 0;
   // resident launch plan
   uint32_t R2 = 0, logR2 = 0, G = 0, spc = 1, C = 0, Cp = 0, threads = 0, blocks = 0;
+  uint32_t cluster = 1, Gc = 0;  // cluster tier: CTAs per sample, columns per CTA
   size_t smem = 0;
   uint32_t max_sweeps_per_launch = 1;
   uint64_t launches = 0;
@@ -195,37 +196,65 @@ int validate(const asep_params* p, asep_ctx* ctx) {
 }
 
 // Resident plan: columns = super-domains, one thread per column.
+// Resident plan: columns = super-domains, one thread per column, a whole
+// sample (or several small ones) per CTA.  When one CTA cannot hold a sample
+// (more than 1024 columns, or more shared memory than 227 KB), the cluster
+// tier spreads each sample over 2..16 CTAs of a thread-block cluster.
 int plan_domain(asep_ctx* ctx) {
   const uint32_t D = ctx->D;
   ctx->R2 = 2 * D / 32;
   ctx->logR2 = log2u(ctx->R2);
   const uint64_t G = ctx->L / (2ull * D);
-  if (G > 1024)
-    return fail(ctx, ASEP_ERR_INVALID, "L = %llu needs %llu columns of 2D sites; the resident kernel holds <= 1024",
-                (unsigned long long)ctx->L, (unsigned long long)G);
   ctx->G = static_cast<uint32_t>(G);
-  uint32_t spc = 1;
-  if (ctx->G < 128) spc = std::max<uint32_t>(1, std::min<uint32_t>(ctx->S, 128 / ctx->G));
-  const uint32_t nocc = ctx->planes;
   const uint32_t dis = ctx->p.dis_kind;
-  for (;;) {
-    const uint32_t C = spc * ctx->G;
-    const uint32_t Cp = (C + 31) / 32 * 32;
-    const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, static_cast<uint32_t>(ctx->ptab.size()), Cp);
-    if (smem <= 227 * 1024 && Cp <= 1024) {
-      ctx->spc = spc;
-      ctx->C = C;
+  const uint32_t ptab_n = static_cast<uint32_t>(ctx->ptab.size());
+  ctx->cluster = 1;
+  bool resident = false;
+  if (G <= 1024) {
+    uint32_t spc = 1;
+    if (ctx->G < 128) spc = std::max<uint32_t>(1, std::min<uint32_t>(ctx->S, 128 / ctx->G));
+    for (;;) {
+      const uint32_t C = spc * ctx->G;
+      const uint32_t Cp = (C + 31) / 32 * 32;
+      const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, ptab_n, Cp);
+      if (smem <= 227 * 1024 && Cp <= 1024) {
+        ctx->spc = spc;
+        ctx->C = C;
+        ctx->Cp = Cp;
+        ctx->threads = Cp;
+        ctx->smem = smem;
+        resident = true;
+        break;
+      }
+      if (spc == 1) break;
+      spc = std::max<uint32_t>(1, spc / 2);
+    }
+  }
+  if (resident) {
+    ctx->blocks = (ctx->S + ctx->spc - 1) / ctx->spc;
+  } else {
+    bool placed = false;
+    for (uint32_t nc = 2; nc <= 16 && !placed; nc *= 2) {
+      const uint32_t Gc = static_cast<uint32_t>((G + nc - 1) / nc);
+      if (Gc > 1024 || (G + Gc - 1) / Gc != nc) continue;  // every CTA of the cluster must hold columns
+      const uint32_t Cp = (Gc + 31) / 32 * 32;
+      const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, ptab_n, Cp);
+      if (smem + 64 > 227 * 1024 || Cp > 1024) continue;
+      if (cluster_fits(ctx->p.model, dis, nc, Cp, smem) <= 0) continue;
+      ctx->cluster = nc;
+      ctx->spc = 1;
+      ctx->C = Gc;
+      ctx->Gc = Gc;
       ctx->Cp = Cp;
       ctx->threads = Cp;
       ctx->smem = smem;
-      break;
+      ctx->blocks = ctx->S;
+      placed = true;
     }
-    if (spc == 1)
-      return fail(ctx, ASEP_ERR_INVALID, "L = %llu with %u planes does not fit the resident kernel's shared memory",
-                  (unsigned long long)ctx->L, nocc);
-    spc = std::max<uint32_t>(1, spc / 2);
+    if (!placed)
+      return fail(ctx, ASEP_ERR_INVALID, "L = %llu (%llu columns, %u planes) fits neither one CTA nor a cluster of "
+                  "up to 16 CTAs on this device", (unsigned long long)ctx->L, (unsigned long long)G, ctx->planes);
   }
-  ctx->blocks = (ctx->S + ctx->spc - 1) / ctx->spc;
   // per-lane 32-bit hop counters: at most 2 phases x largest count + 2D turns per sweep
   const uint64_t per_sweep = 2ull * (ctx->ptab_klo + ctx->ptab.size() + 1) + 2ull * D;
   ctx->max_sweeps_per_launch = static_cast<uint32_t>(std::max<uint64_t>(1, 4000000000ull / per_sweep));
@@ -289,6 +318,8 @@ DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
   a.C = ctx->C;
   a.Cp = ctx->Cp;
   a.n_groups = ctx->blocks;
+  a.cluster = ctx->cluster;
+  a.Gc = ctx->Gc;
   a.rates = rates(ctx);
   a.seed = ctx->p.seed;
   a.n_sweeps = n;
@@ -485,7 +516,9 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     const uint32_t cap = ctx->p.schedule == ASEP_SCHED_DOMAIN ? ctx->max_sweeps_per_launch : (1u << 20);
     if (n > cap) n = cap;
     cudaError_t e;
-    if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
+    if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster > 1) {
+      e = launch_cluster(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
+    } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
       e = launch_domain(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else {
       SerialLaunch a;
@@ -673,7 +706,8 @@ int bfail(asep_batch* b, int code, const char* fmt, ...) {
 int batch_prepare(asep_batch* b, asep_ctx* const* ctxs, const uint32_t* n, uint32_t nj, uint32_t* n_items_out,
                   uint32_t* threads_out, uint32_t* ctas_out, size_t* smem_out) {
   uint32_t threads = 32;
-  for (uint32_t j = 0; j < nj; ++j) threads = std::max(threads, ctxs[j]->threads);
+  for (uint32_t j = 0; j < nj; ++j)
+    if (ctxs[j]->cluster == 1) threads = std::max(threads, ctxs[j]->threads);
   if (b->threads_req) {
     if (b->threads_req < threads || (b->threads_req & 31) || b->threads_req > 1024)
       return bfail(b, ASEP_ERR_INVALID, "threads %u: must be a multiple of 32 in [%u, 1024]", b->threads_req, threads);
@@ -690,6 +724,7 @@ int batch_prepare(asep_batch* b, asep_ctx* const* ctxs, const uint32_t* n, uint3
   for (uint32_t j = 0; j < nj; ++j) {
     const asep_ctx* c = ctxs[j];
     b->h_jobs[j] = domain_desc(c, n[j]);
+    if (c->cluster > 1) continue;  // cluster-tier contexts get their own cluster launch
     smem = std::max(smem, domain_smem_bytes(c->p.model, c->p.dis_kind, c->R2, c->Cp,
                                             static_cast<uint32_t>(c->ptab.size()), threads));
     if (n[j] == 0) continue;
@@ -764,9 +799,17 @@ int order_out(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
   return ASEP_OK;
 }
 
-int batch_step_enqueue(asep_batch* b, uint32_t nj, uint32_t n_items, uint32_t threads, uint32_t ctas, size_t smem,
-                       cudaStream_t st) {
+int batch_step_enqueue(asep_batch* b, asep_ctx* const* ctxs, uint32_t nj, uint32_t n_items, uint32_t threads,
+                       uint32_t ctas, size_t smem, cudaStream_t st) {
   cudaError_t e;
+  // contexts of the cluster tier run as their own cluster launches before the
+  // persistent kernel (they read their clocks before the batch advances them)
+  for (uint32_t j = 0; j < nj; ++j) {
+    const DomainLaunch& d = b->h_jobs[j];
+    if (ctxs[j]->cluster > 1 && d.n_sweeps > 0 &&
+        (e = launch_cluster(d, ctxs[j]->threads, ctxs[j]->smem, st)) != cudaSuccess)
+      return bfail(b, ASEP_ERR_CUDA, "cluster kernel of context %u: %s", j, cudaGetErrorString(e));
+  }
   if (n_items && (e = launch_batch(b->d_jobs, b->d_items, n_items, b->d_queue, threads, ctas, smem, st)) !=
                      cudaSuccess)
     return bfail(b, ASEP_ERR_CUDA, "batch kernel: %s", cudaGetErrorString(e));
@@ -838,7 +881,7 @@ int asep_batch_sweep(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs
     uint32_t n_items, threads, ctas;
     size_t smem;
     if ((rc = batch_prepare(b, ctxs, step.data(), n, &n_items, &threads, &ctas, &smem)) != ASEP_OK) return rc;
-    if ((rc = batch_step_enqueue(b, n, n_items, threads, ctas, smem, b->stream)) != ASEP_OK) return rc;
+    if ((rc = batch_step_enqueue(b, ctxs, n, n_items, threads, ctas, smem, b->stream)) != ASEP_OK) return rc;
     for (uint32_t j = 0; j < n; ++j) {
       left[j] -= step[j];
       advance_host(ctxs[j], step[j]);
@@ -877,7 +920,7 @@ int asep_batch_graph(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
       return bfail(b, ASEP_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-    const int rc_enq = batch_step_enqueue(b, n, n_items, threads, ctas, smem, b->cap_stream);
+    const int rc_enq = batch_step_enqueue(b, ctxs, n, n_items, threads, ctas, smem, b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &graph);
     if (rc_enq != ASEP_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -1013,6 +1056,8 @@ int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32
     if (c->p.schedule != ASEP_SCHED_DOMAIN)
       return fail(nullptr, ASEP_ERR_INVALID, "context %u: only the domain schedule runs in a batch", j);
     if (c->stream != st) return fail(nullptr, ASEP_ERR_INVALID, "context %u does not use the call's stream", j);
+    if (c->cluster > 1)
+      return fail(nullptr, ASEP_ERR_INVALID, "context %u is spread over a CTA cluster; use asep_batch_sweep", j);
     if (c->sweep + n_mcs[j] >= (1ull << 40)) return fail(nullptr, ASEP_ERR_INVALID, "context %u: sweep >= 2^40", j);
     for (uint32_t k = 0; k < j; ++k)
       if (ctxs[k] == c) return fail(nullptr, ASEP_ERR_INVALID, "context %u appears twice", j);

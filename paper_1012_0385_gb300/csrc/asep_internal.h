@@ -65,7 +65,9 @@ struct DomainLaunch {
   uint32_t spc;            // samples per sample group (CTA or queue item)
   uint32_t C;              // columns per group = spc * G
   uint32_t Cp;             // row pitch in words (multiple of 32, >= C)
-  uint32_t n_groups;       // ceil(S / spc)
+  uint32_t n_groups;       // ceil(S / spc); cluster tier: S (one cluster per sample)
+  uint32_t cluster;        // CTAs per sample: 1 = resident in one CTA, 2..16 = a thread-block cluster
+  uint32_t Gc;             // cluster tier: columns per CTA (the last CTA may hold fewer)
   Rates rates;
   uint64_t seed;
   uint32_t n_sweeps;       // sweeps of this launch
@@ -129,6 +131,10 @@ cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, 
 // from items[0..n_items) through the queue counter (zeroed here first).
 cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items, uint32_t* queue,
                          uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st);
+// Cluster tier: one cluster of a.cluster CTAs per sample (grid S * cluster).
+cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
+// How many clusters of the given shape can be resident at once (0 = none).
+int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem);
 // Advance clocks after n sweeps (one context, or the jobs of a batch).
 cudaError_t launch_advance(Clock* clock, const uint64_t* times, uint32_t n_times, uint32_t n, cudaStream_t st);
 cudaError_t launch_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs, cudaStream_t st);

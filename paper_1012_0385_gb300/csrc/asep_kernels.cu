@@ -32,6 +32,8 @@
 // new one into a second buffer (double buffering), one funnel shift per word.
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "asep_internal.h"
 
 namespace asep {
@@ -585,6 +587,217 @@ __global__ void k_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs) {
 }
 
 // ---------------------------------------------------------------------------
+// Cluster tier: one sample spread over a thread-block cluster
+// ---------------------------------------------------------------------------
+//
+// CTA k of the cluster holds columns [k Gc, (k+1) Gc) of the sample in its
+// own shared memory, laid out exactly as in the resident kernel, and runs the
+// same phases on them.  The few accesses that cross a slice boundary -- the
+// rotation (new column g reads old columns g and g+1, or g-1 and g across the
+// ring's end), the mirror copy (next column's row 0), the mirror write-back
+// (previous column's mirror row) and the height scan -- go to the owning CTA
+// through distributed shared memory.  Cluster barriers stand where data
+// crosses CTAs: after the even phase, after the odd phase, and at the end of
+// each sweep.
+
+namespace cg = cooperative_groups;
+
+// Word (p, row, global column g) of a plane buffer, in whichever CTA holds it.
+__device__ __forceinline__ uint32_t* cl_word(const cg::cluster_group& cl, uint32_t* buf, uint32_t p, uint32_t PW,
+                                            uint32_t row, uint32_t Cp, uint32_t g, uint32_t Gc, uint32_t my_rank) {
+  const uint32_t rank = g / Gc, col = g - rank * Gc;
+  uint32_t* base = rank == my_rank ? buf : cl.map_shared_rank(buf, rank);
+  return base + p * PW + row * Cp + col;
+}
+
+template <uint32_t NP>
+__device__ __forceinline__ void realign_cl(const cg::cluster_group& cl, uint32_t* src, uint32_t* dst,
+                                           const DomainLaunch& a, const Lane& ln, uint32_t PW, uint32_t delta,
+                                           uint32_t my_rank) {
+  const uint64_t L = a.geo.L;
+  const uint32_t W = a.geo.W, R2 = a.R2, Cp = a.Cp;
+  for (uint32_t r = 0; r < R2; ++r) {
+    uint64_t pos = delta + 32ull * (ln.g * R2 + r);
+    if (pos >= L) pos -= L;
+    const uint32_t fa = static_cast<uint32_t>(pos >> 5), sh = static_cast<uint32_t>(pos & 31u);
+    const uint32_t fb = (fa + 1 == W) ? 0u : fa + 1;
+#pragma unroll
+    for (uint32_t p = 0; p < NP; ++p) {
+      const uint32_t wa = *cl_word(cl, src, p, PW, fa & (R2 - 1), Cp, fa >> a.logR2, a.Gc, my_rank);
+      const uint32_t wb = *cl_word(cl, src, p, PW, fb & (R2 - 1), Cp, fb >> a.logR2, a.Gc, my_rank);
+      dst[p * PW + r * Cp + ln.c] = __funnelshift_r(wa, wb, sh);
+    }
+  }
+}
+
+// Heights of the occupancy planes (frame offset 0) of the cluster's sample.
+template <uint32_t NOCC>
+__device__ void record_heights_cl(const cg::cluster_group& cl, uint32_t* cur, const DomainLaunch& a, uint32_t PW,
+                                  uint32_t slot, const Lane& ln, uint32_t my_rank, long long* warp_tot,
+                                  long long* cta_sums) {
+  const uint32_t last = blockDim.x - 1;
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    const uint32_t* pl = cur + p * PW;
+    long long tot = 0;
+    if (ln.active)
+      for (uint32_t r = 0; r < a.R2; ++r) tot += 2 * __popc(pl[r * a.Cp + ln.c]) - 32;
+    const long long inc = block_scan_incl(tot, warp_tot);
+    if (threadIdx.x == last) cta_sums[0] = inc;  // slice total of (2n - 1)
+    cl.sync();
+    long long h = inc - tot;  // height before this column within the slice
+    for (uint32_t k = 0; k < my_rank; ++k) h += *cl.map_shared_rank(cta_sums, k);
+    long long s1 = 0;
+    unsigned long long s2 = 0;
+    if (ln.active) {
+      for (uint32_t r = 0; r < a.R2; ++r) {
+        const uint32_t x = pl[r * a.Cp + ln.c];
+        for (uint32_t b = 0; b < 32; ++b) {
+          h += ((x >> b) & 1u) ? 1 : -1;
+          s1 += h;
+          s2 += static_cast<unsigned long long>(h * h);
+        }
+      }
+    }
+    const long long t1 = block_scan_incl(s1, warp_tot);
+    const long long t2 = block_scan_incl(static_cast<long long>(s2), warp_tot);  // slice sum < 2^62
+    cl.sync();  // every CTA has read the slice totals
+    if (threadIdx.x == last) {
+      cta_sums[1] = t1;
+      cta_sums[2] = t2;
+    }
+    cl.sync();
+    if (my_rank == 0 && threadIdx.x == 0) {
+      long long sum1 = 0;
+      unsigned __int128 sum2 = 0;
+      for (uint32_t k = 0; k < cl.num_blocks(); ++k) {
+        const long long* o = cl.map_shared_rank(cta_sums, k);
+        sum1 += o[1];
+        sum2 += static_cast<unsigned long long>(o[2]);
+      }
+      const size_t e = (static_cast<size_t>(slot) * a.geo.S + ln.sample) * NOCC + p;
+      a.tab_sh[e] = sum1;
+      a.tab_sh2[2 * e] = static_cast<uint64_t>(sum2);
+      a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(sum2 >> 64);
+    }
+    cl.sync();  // the slots are reused by the next plane
+  }
+}
+
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+__global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long cta_sums[4];
+  constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
+  constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
+  cg::cluster_group cl = cg::this_cluster();
+  const uint32_t my_rank = cl.block_rank(), NC = cl.num_blocks();
+  const uint32_t R2 = a.R2, Cp = a.Cp, G = a.G, W = a.geo.W, Gc = a.Gc;
+  const uint32_t PW = (R2 + 1) * Cp;
+  const uint64_t L = a.geo.L;
+  uint32_t* bufA = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* bufB = bufA + NP * PW;
+  uint32_t* tab = bufB + NP * PW;
+  long long* warp_tot = reinterpret_cast<long long*>(tab + ((a.ptab_n + 1u) & ~1u));
+
+  const uint32_t sample = blockIdx.x / NC;
+  const uint32_t g_lo = my_rank * Gc;
+  const uint32_t g_hi = min(G, g_lo + Gc);
+  Lane ln;
+  ln.c = threadIdx.x;
+  ln.g = g_lo + threadIdx.x;
+  ln.active = ln.g < g_hi && sample < a.geo.S;
+  ln.col0 = 0;
+  ln.c_next = 0;  // not used by the cluster tier
+  ln.c_prev = 0;
+  ln.sample = sample;
+  ln.n_glob = a.geo.first_sample + sample;
+  const uint32_t gn = (ln.g + 1 >= G) ? 0u : ln.g + 1;
+  const uint32_t gp = (ln.g == 0) ? G - 1 : ln.g - 1;
+  const uint2 key = key_of(a.seed);
+  const uint64_t s0 = a.clock->sweep;
+
+  // Poisson table and this CTA's slice of the lattice (frame offset 0)
+  for (uint32_t i = threadIdx.x; i < a.ptab_n; i += blockDim.x) tab[i] = a.ptab[i];
+  const uint32_t w_lo = g_lo * R2, w_hi = g_hi * R2;
+  for (uint32_t p = 0; p < NP; ++p) {
+    for (uint32_t w = w_lo + threadIdx.x; w < w_hi; w += blockDim.x) {
+      const uint32_t v = p < NOCC ? a.state[(static_cast<size_t>(sample) * a.geo.planes + p) * W + w]
+                                  : a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + w];
+      const uint32_t wl = w - w_lo;
+      bufA[p * PW + (wl & (R2 - 1)) * Cp + (wl >> a.logR2)] = v;
+    }
+  }
+  cl.sync();
+
+  uint32_t* cur = bufA;
+  uint32_t* nxt = bufB;
+  uint32_t R_cur = 0;
+  Cnt cnt;
+  uint32_t rec = a.clock->next_time;
+
+  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
+    const uint64_t s = s0 + it;
+    const uint32_t o = philox10(ctr_of(s, kTagOff, 0, ln.n_glob, 0), key).x & (2 * a.D - 1);
+    if (ln.active) realign_cl<NP>(cl, cur, nxt, a, ln, PW, static_cast<uint32_t>((o + L - R_cur) % L), my_rank);
+    uint32_t* t = cur;
+    cur = nxt;
+    nxt = t;
+    R_cur = o;
+    __syncthreads();
+    run_phase<MODEL, DIS, COUNT, 0, 0>(cur, a, tab, PW, s, ln, key, cnt);
+    cl.sync();
+    if (ln.active) {
+#pragma unroll
+      for (uint32_t p = 0; p < NP; ++p)
+        cur[p * PW + R2 * Cp + ln.c] = *cl_word(cl, cur, p, PW, 0, Cp, gn, Gc, my_rank);
+    }
+    run_phase<MODEL, DIS, COUNT, 0, 1>(cur, a, tab, PW, s, ln, key, cnt);
+    cl.sync();
+    if (ln.active) {
+#pragma unroll
+      for (uint32_t p = 0; p < NOCC; ++p) {
+        const uint32_t m = *cl_word(cl, cur, p, PW, R2, Cp, gp, Gc, my_rank);
+        cur[p * PW + ln.c] = (cur[p * PW + ln.c] & ~1u) | (m & 1u);
+      }
+    }
+    __syncthreads();
+    if (MODEL == kTwoLane && DIS == kDisTurning) {
+      if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);
+    }
+    cl.sync();
+    if (rec < a.n_times && a.times[rec] == s + 1) {
+      if (ln.active) realign_cl<NP>(cl, cur, nxt, a, ln, PW, static_cast<uint32_t>((L - R_cur) % L), my_rank);
+      t = cur;
+      cur = nxt;
+      nxt = t;
+      R_cur = 0;
+      __syncthreads();
+      record_heights_cl<NOCC>(cl, cur, a, PW, rec, ln, my_rank, warp_tot, cta_sums);
+      ++rec;
+    }
+  }
+
+  if (ln.active) realign_cl<NP>(cl, cur, nxt, a, ln, PW, static_cast<uint32_t>((L - R_cur) % L), my_rank);
+  cur = nxt;
+  __syncthreads();
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    for (uint32_t w = w_lo + threadIdx.x; w < w_hi; w += blockDim.x) {
+      const uint32_t wl = w - w_lo;
+      a.state[(static_cast<size_t>(sample) * a.geo.planes + p) * W + w] =
+          cur[p * PW + (wl & (R2 - 1)) * Cp + (wl >> a.logR2)];
+    }
+  }
+  if (ln.active) {
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.counters + 4ull * ln.sample);
+    if (cnt.a) atomicAdd(dst + 0, static_cast<unsigned long long>(cnt.a));
+    if (cnt.b) atomicAdd(dst + 1, static_cast<unsigned long long>(cnt.b));
+    if (cnt.c) atomicAdd(dst + 2, static_cast<unsigned long long>(cnt.c));
+    if (cnt.d) atomicAdd(dst + 3, static_cast<unsigned long long>(cnt.d));
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
 // Serial random-sequential update, one thread per sample
 // ---------------------------------------------------------------------------
 
@@ -805,6 +1018,83 @@ cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32
     k_batch<1024><<<ctas, threads, smem, st>>>(jobs, items, n_items, queue);
   }
   return cudaGetLastError();
+}
+
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+cudaError_t cluster_attrs(uint32_t cluster, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_cluster<MODEL, DIS, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e == cudaSuccess && cluster > 8)
+    e = cudaFuncSetAttribute(k_cluster<MODEL, DIS, COUNT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+cudaError_t launch_cluster_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
+  (void)cudaGetLastError();
+  cudaError_t e = cluster_attrs<MODEL, DIS, COUNT>(a.cluster, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.geo.S * a.cluster, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_cluster<MODEL, DIS, COUNT>, a);
+}
+
+template <uint32_t MODEL, uint32_t DIS, bool COUNT>
+int cluster_fits_t(uint32_t cluster, uint32_t threads, size_t smem) {
+  if (cluster_attrs<MODEL, DIS, COUNT>(cluster, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_cluster<MODEL, DIS, COUNT>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
+  const bool count = a.count_hops != 0;
+  if (a.model == kRing && a.dis == kDisNone)
+    return count ? launch_cluster_t<kRing, kDisNone, true>(a, threads, smem, st)
+                 : launch_cluster_t<kRing, kDisNone, false>(a, threads, smem, st);
+  if (a.model == kRing && a.dis == kDisBimodal)
+    return count ? launch_cluster_t<kRing, kDisBimodal, true>(a, threads, smem, st)
+                 : launch_cluster_t<kRing, kDisBimodal, false>(a, threads, smem, st);
+  if (a.model == kTwoLane && a.dis == kDisNone) return launch_cluster_t<kTwoLane, kDisNone, true>(a, threads, smem, st);
+  if (a.model == kTwoLane && a.dis == kDisTurning)
+    return launch_cluster_t<kTwoLane, kDisTurning, true>(a, threads, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem) {
+  if (model == kRing && dis == kDisNone) return cluster_fits_t<kRing, kDisNone, true>(cluster, threads, smem);
+  if (model == kRing && dis == kDisBimodal) return cluster_fits_t<kRing, kDisBimodal, true>(cluster, threads, smem);
+  if (model == kTwoLane && dis == kDisNone) return cluster_fits_t<kTwoLane, kDisNone, true>(cluster, threads, smem);
+  if (model == kTwoLane && dis == kDisTurning)
+    return cluster_fits_t<kTwoLane, kDisTurning, true>(cluster, threads, smem);
+  return 0;
 }
 
 cudaError_t launch_advance(Clock* clock, const uint64_t* times, uint32_t n_times, uint32_t n, cudaStream_t st) {

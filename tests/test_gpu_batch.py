@@ -120,6 +120,29 @@ def test_launch_shape_does_not_change_results(reference, threads, ctas):
         c.close()
 
 
+def test_batch_with_a_cluster_tier_context_equals_alone():
+    big = (dict(L=1 << 19, domain_sites=256, n_realizations=1, samples_per_real=2, dis_kind=A.ASEP_DIS_BIMODAL,
+                dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=3, seed=77), [0, 3, 6])
+    mix = [big] + MIX[:2]
+    n = [6, 9, 7]
+    ref = []
+    for (kw, t), k in zip(mix, n):
+        with A.asep_create(A.make_params(**kw), sample_times=t) as c:
+            A.asep_sweep(c, k)
+            ref.append(snapshot(c))
+    ctxs = [A.asep_create(A.make_params(**kw), sample_times=t) for kw, t in mix]
+    with A.asep_batch_create(max_jobs=8, max_items=4096) as b:
+        A.asep_batch_sweep(b, ctxs, [2, 4, 3])
+        A.asep_batch_graph(b, ctxs, [2, 5, 4], replays=1)
+        A.asep_batch_sweep(b, ctxs, [2, 0, 0])
+        for c, r in zip(ctxs, ref):
+            same(snapshot(c), r)
+    with pytest.raises(A.AsepError):
+        A.asep_batch_sweep_static(ctxs[:1], [1])  # the static batch takes resident contexts only
+    for c in ctxs:
+        c.close()
+
+
 def test_batch_rejects_bad_input():
     with A.asep_create(A.make_params(L=1024, schedule=A.ASEP_SCHED_SERIAL), sample_times=[]) as c, \
             A.asep_batch_create(max_jobs=2, max_items=64) as b:

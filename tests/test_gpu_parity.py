@@ -122,6 +122,23 @@ CASES = {
     "serial_bimodal": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
                             dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=3, seed=4),
                        20, [20]),
+    # cluster tier: one sample spread over 2..16 CTAs of a thread-block cluster
+    "cluster_ring_2x": (dict(L=1 << 20, domain_sites=256, samples_per_real=2, p_thr=th(0.75), q_thr=th(0.25),
+                             seed=51), 5, [0, 2, 5]),
+    "cluster_ring_d64": (dict(L=1 << 18, domain_sites=64, samples_per_real=2, p_thr=th(0.6), seed=52), 6, [0, 6]),
+    "cluster_uneven_slices": (dict(L=1025 * 512, domain_sites=256, samples_per_real=1, p_thr=th(0.75),
+                                   q_thr=th(0.25), seed=53), 4, [0, 4]),
+    "cluster_bimodal": (dict(L=1 << 19, domain_sites=256, n_realizations=2, samples_per_real=1,
+                             dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=7, seed=54),
+                        4, [0, 4]),
+    "cluster_two_lane": (dict(model=TWO, L=1 << 19, domain_sites=256, samples_per_real=1, init_kind=1, init_seed=5,
+                              dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=8,
+                              q_thr=A.ASEP_ALWAYS, seed=55), 3, [0, 3]),
+    "cluster_ring_max_L": (dict(L=1 << 22, domain_sites=256, samples_per_real=1, p_thr=th(0.75), q_thr=th(0.25),
+                                seed=56), 2, [0, 2]),
+    "cluster_two_lane_max_L": (dict(model=TWO, L=1 << 22, domain_sites=256, samples_per_real=1, init_kind=1,
+                                    init_seed=6, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
+                                    dis_b_thr=th(0.1), dis_seed=9, q_thr=A.ASEP_ALWAYS, seed=57), 1, [0, 1]),
 }
 
 

@@ -306,7 +306,7 @@ def run_ours(args):
             "clocks": clk,
         }
         if not args.no_serving and world == 1:
-            line["serving"] = serving_comparison()
+            line["serving"] = serving_comparison(capacity=value)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -315,22 +315,26 @@ def run_ours(args):
     return 0
 
 
-def serving_comparison(n_jobs: int = 64, rate_hz: float = 45.0, seed: int = 2026):
-    """The served ensemble mix, scaled to seconds: Poisson arrivals of jobs
-    drawn from the four workload families, L log-uniform in [2^10, 2^19],
-    1-256 samples, n_mcs log-uniform in [10, 10^4] (the full mix's 10^3-10^6
-    divided by 100).  The same trace is replayed with continuous batching and
-    with one launch per job; results are bit-identical between the two."""
+def serving_comparison(capacity: float, n_jobs: int = 32, seed: int = 2026, load: float = 0.7):
+    """The served ensemble mix scaled to seconds: Poisson arrivals of jobs
+    drawn from the four workload families with L log-uniform in [2^10, 2^22]
+    (the mix's full range; L > ~2^19 runs on thread-block clusters), 1-16
+    samples and n_mcs log-uniform in [5, 100] (the mix's 10^3-10^6 and 1-256
+    scaled down so that one replay takes seconds), arrivals offering 70 % of
+    the measured batched capacity.  The same trace is replayed with continuous
+    batching and with one launch per job; results are bit-identical."""
     from paper_1012_0385_gb300 import serve
 
     def trace():
-        return serve.make_trace(n_jobs, seed=seed, rate_hz=rate_hz, L_range=(1 << 10, 1 << 19),
-                                samples_range=(1, 256), n_mcs_range=(10, 10_000))
+        return serve.make_trace(n_jobs, seed=seed, rate_hz=1.0, L_range=(1 << 10, 1 << 22), samples_range=(1, 16),
+                                n_mcs_range=(5, 100), load=load, capacity=capacity)
 
     batched = serve.serve_batched(trace(), quantum_s=0.02)
     plain = serve.serve_plain(trace())
-    return {"trace": f"{n_jobs} jobs, Poisson {rate_hz:g} Hz, kinds tasep/asep/bimodal/two_lane, "
-                     "L log-uniform [2^10, 2^19], samples log-uniform [1, 256], n_mcs log-uniform [10, 10^4]",
+    rate = n_jobs / max(j.arrival for j in trace())
+    return {"trace": f"{n_jobs} jobs, Poisson ~{rate:.2f} Hz (offered load {load:g} of {capacity:.3g} attempts/s), "
+                     "kinds tasep/asep/bimodal/two_lane, L log-uniform [2^10, 2^22], samples log-uniform [1, 16], "
+                     "n_mcs log-uniform [5, 100]",
             "batched": batched, "plain": plain,
             "throughput_ratio": batched["throughput_attempts_per_s"] / plain["throughput_attempts_per_s"],
             "p99_ratio": batched["p99_latency_s"] / plain["p99_latency_s"]}

@@ -102,9 +102,12 @@ class Job:
 
 
 def make_trace(n_jobs: int, seed: int = 0, rate_hz: float = 50.0, L_range=(1 << 10, 1 << 19),
-               samples_range=(1, 256), n_mcs_range=(10, 10_000), kinds=KINDS, D: int = 256) -> list[Job]:
+               samples_range=(1, 256), n_mcs_range=(10, 10_000), kinds=KINDS, D: int = 256,
+               load: float | None = None, capacity: float | None = None) -> list[Job]:
     """Seeded Poisson arrivals; L, samples and n_mcs log-uniform in their
-    ranges (L rounded to a multiple of 2D), the kind uniform over `kinds`."""
+    ranges (L rounded to a multiple of 2D), the kind uniform over `kinds`.
+    With `load` and `capacity` (attempts/s), the arrival rate is set so the
+    trace offers load x capacity: rate = load * capacity / mean job attempts."""
     rng = np.random.default_rng(seed)
     t = 0.0
     jobs = []
@@ -116,6 +119,11 @@ def make_trace(n_jobs: int, seed: int = 0, rate_hz: float = 50.0, L_range=(1 << 
         n = int(round(math.exp(rng.uniform(math.log(n_mcs_range[0]), math.log(n_mcs_range[1])))))
         kind = kinds[int(rng.integers(len(kinds)))]
         jobs.append(Job(id=i, kind=kind, L=L, samples=max(1, S), n_mcs=max(1, n), seed=1000 + 7 * i, arrival=t, D=D))
+    if load is not None and capacity is not None:
+        mean_attempts = sum(j.attempts for j in jobs) / len(jobs)
+        scale = rate_hz * mean_attempts / (load * capacity)  # new gaps = old gaps x scale
+        for j in jobs:
+            j.arrival *= scale
     return jobs
 
 

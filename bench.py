@@ -315,26 +315,26 @@ def run_ours(args):
     return 0
 
 
-def serving_comparison(capacity: float, n_jobs: int = 32, seed: int = 2026, load: float = 0.7):
-    """The served ensemble mix scaled to seconds: Poisson arrivals of jobs
-    drawn from the four workload families with L log-uniform in [2^10, 2^22]
-    (the mix's full range; L > ~2^19 runs on thread-block clusters), 1-16
-    samples and n_mcs log-uniform in [5, 100] (the mix's 10^3-10^6 and 1-256
-    scaled down so that one replay takes seconds), arrivals offering 70 % of
-    the measured batched capacity.  The same trace is replayed with continuous
-    batching and with one launch per job; results are bit-identical."""
+def serving_comparison(capacity: float, n_jobs: int = 48, seed: int = 2026, load: float = 0.7):
+    """The served ensemble mix, scaled: Poisson arrivals of jobs drawn from
+    the four workload families with L log-uniform in [2^10, 2^22] (the mix's
+    full range; L above ~2^19 runs on thread-block clusters), 1-256 samples
+    and n_mcs log-uniform in [10, 10^4] (the mix's 10^3-10^6 divided by 100),
+    arrivals offering 70 % of the measured batched capacity.  The same trace
+    is replayed with continuous batching and with one launch per job; the
+    results are bit-identical between the two."""
     from paper_1012_0385_gb300 import serve
 
     def trace():
-        return serve.make_trace(n_jobs, seed=seed, rate_hz=1.0, L_range=(1 << 10, 1 << 22), samples_range=(1, 16),
-                                n_mcs_range=(5, 100), load=load, capacity=capacity)
+        return serve.make_trace(n_jobs, seed=seed, rate_hz=1.0, L_range=(1 << 10, 1 << 22), samples_range=(1, 256),
+                                n_mcs_range=(10, 10_000), load=load, capacity=capacity)
 
     batched = serve.serve_batched(trace(), quantum_s=0.02)
     plain = serve.serve_plain(trace())
     rate = n_jobs / max(j.arrival for j in trace())
     return {"trace": f"{n_jobs} jobs, Poisson ~{rate:.2f} Hz (offered load {load:g} of {capacity:.3g} attempts/s), "
-                     "kinds tasep/asep/bimodal/two_lane, L log-uniform [2^10, 2^22], samples log-uniform [1, 16], "
-                     "n_mcs log-uniform [5, 100]",
+                     "kinds tasep/asep/bimodal/two_lane, L log-uniform [2^10, 2^22], samples log-uniform [1, 256], "
+                     "n_mcs log-uniform [10, 10^4]",
             "batched": batched, "plain": plain,
             "throughput_ratio": batched["throughput_attempts_per_s"] / plain["throughput_attempts_per_s"],
             "p99_ratio": batched["p99_latency_s"] / plain["p99_latency_s"]}

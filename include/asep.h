@@ -124,6 +124,10 @@ typedef struct asep_info {
   uint64_t attempts_per_sweep; /* L * planes per sample */
   uint64_t device_bytes;  /* device memory held by the context */
   uint64_t kernel_launches; /* kernels the context has enqueued so far */
+  uint32_t cluster;       /* CTAs per sample: 1 = one CTA holds whole samples, 2..16 = a thread-block cluster */
+  uint32_t samples_per_group; /* samples per CTA (resident) or 1 (cluster) */
+  uint32_t groups;        /* CTAs (resident) or clusters per sweep launch */
+  uint32_t threads;       /* threads per CTA */
 } asep_info;
 
 /* Validate `params`, allocate device memory, draw the initial state (paper

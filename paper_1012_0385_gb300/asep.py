@@ -78,6 +78,10 @@ class asep_info(ctypes.Structure):
         ("attempts_per_sweep", ctypes.c_uint64),
         ("device_bytes", ctypes.c_uint64),
         ("kernel_launches", ctypes.c_uint64),
+        ("cluster", ctypes.c_uint32),
+        ("samples_per_group", ctypes.c_uint32),
+        ("groups", ctypes.c_uint32),
+        ("threads", ctypes.c_uint32),
     ]
 
 

@@ -682,6 +682,8 @@ struct asep_batch {
   cudaEvent_t staged = nullptr;  // the staging buffers may be rewritten once this event is done
   cudaEvent_t order = nullptr;   // cross-stream ordering with the contexts
   cudaStream_t cap_stream = nullptr;  // capture stream (the legacy default stream cannot be captured)
+  cudaStream_t aux_stream = nullptr;  // cluster-tier launches run here, beside the persistent kernel
+  cudaEvent_t fork = nullptr, join = nullptr;
   // graph cache: one captured step
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> graph_key;
@@ -802,17 +804,28 @@ int order_out(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
 int batch_step_enqueue(asep_batch* b, asep_ctx* const* ctxs, uint32_t nj, uint32_t n_items, uint32_t threads,
                        uint32_t ctas, size_t smem, cudaStream_t st) {
   cudaError_t e;
-  // contexts of the cluster tier run as their own cluster launches before the
-  // persistent kernel (they read their clocks before the batch advances them)
+  // contexts of the cluster tier run as their own cluster launches on an
+  // auxiliary stream forked from `st`, beside the persistent kernel, and are
+  // joined back before the clocks advance
+  bool forked = false;
   for (uint32_t j = 0; j < nj; ++j) {
     const DomainLaunch& d = b->h_jobs[j];
-    if (ctxs[j]->cluster > 1 && d.n_sweeps > 0 &&
-        (e = launch_cluster(d, ctxs[j]->threads, ctxs[j]->smem, st)) != cudaSuccess)
+    if (ctxs[j]->cluster == 1 || d.n_sweeps == 0) continue;
+    if (!forked) {
+      if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(b->aux_stream, b->fork, 0)) != cudaSuccess)
+        return bfail(b, ASEP_ERR_CUDA, "fork: %s", cudaGetErrorString(e));
+      forked = true;
+    }
+    if ((e = launch_cluster(d, ctxs[j]->threads, ctxs[j]->smem, b->aux_stream)) != cudaSuccess)
       return bfail(b, ASEP_ERR_CUDA, "cluster kernel of context %u: %s", j, cudaGetErrorString(e));
   }
   if (n_items && (e = launch_batch(b->d_jobs, b->d_items, n_items, b->d_queue, threads, ctas, smem, st)) !=
                      cudaSuccess)
     return bfail(b, ASEP_ERR_CUDA, "batch kernel: %s", cudaGetErrorString(e));
+  if (forked && ((e = cudaEventRecord(b->join, b->aux_stream)) != cudaSuccess ||
+                 (e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess))
+    return bfail(b, ASEP_ERR_CUDA, "join: %s", cudaGetErrorString(e));
   if ((e = launch_advance_batch(b->d_jobs, nj, st)) != cudaSuccess)
     return bfail(b, ASEP_ERR_CUDA, "batch clock advance: %s", cudaGetErrorString(e));
   return ASEP_OK;
@@ -840,7 +853,10 @@ int asep_batch_create(void* stream, uint32_t max_jobs, uint32_t max_items, asep_
       (e = cudaMallocHost(&b->h_items, static_cast<size_t>(max_items) * 4)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming)) != cudaSuccess) {
     const int rc = bfail(nullptr, e == cudaErrorMemoryAllocation ? ASEP_ERR_NOMEM : ASEP_ERR_CUDA,
                          "batch workspace: %s", cudaGetErrorString(e));
     (void)cudaGetLastError();
@@ -953,6 +969,12 @@ int asep_batch_destroy(asep_batch* b) {
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->order) cudaEventDestroy(b->order);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->aux_stream) {
+    cudaStreamSynchronize(b->aux_stream);
+    cudaStreamDestroy(b->aux_stream);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   if (b->d_jobs) cudaFree(b->d_jobs);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_queue) cudaFree(b->d_queue);
@@ -975,6 +997,10 @@ int asep_get_info(const asep_ctx* ctx, asep_info* info) {
   info->attempts_per_sweep = ctx->L * ctx->planes;
   info->device_bytes = ctx->dev_bytes;
   info->kernel_launches = ctx->launches;
+  info->cluster = ctx->cluster;
+  info->samples_per_group = ctx->spc;
+  info->groups = ctx->blocks;
+  info->threads = ctx->threads;
   return ASEP_OK;
 }
 

@@ -156,12 +156,24 @@ def serve_plain(trace: list[Job]) -> dict:
     return _summary(jobs, time.perf_counter() - t0, "plain")
 
 
+def _group_work(ctx) -> tuple[int, int]:
+    """(attempts per sweep of one work item, SMs one item occupies): a
+    resident group is samples_per_group samples on one CTA, a cluster-tier
+    item one sample on `cluster` CTAs."""
+    info = A.asep_get_info(ctx)
+    return info["attempts_per_sweep"] * info["samples_per_group"], info["cluster"]
+
+
 def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int = 16 << 30, max_active: int = 256,
-                  rate_guess: float = 4e11) -> dict:
+                  rate_guess: float = 4e11, sms: int = 152) -> dict:
     """Continuous batching: admit at step boundaries by footprint, one
-    persistent launch per step over all active jobs, retire finished jobs."""
+    persistent launch per step over all active jobs, retire finished jobs.
+    Each job's quantum of sweeps is chosen so that one of its work items (a
+    CTA's sample group, or a cluster's sample) takes about `quantum_s` at the
+    per-SM rate, so the items of a step have similar lengths."""
     pending = sorted(trace, key=lambda j: j.arrival)
     active: list[tuple[Job, object, int]] = []  # (job, ctx, sweeps left)
+    shape: dict[int, tuple[int, int]] = {}
     used = 0
     t0 = time.perf_counter()
     batch = A.asep_batch_create(max_jobs=max_active, max_items=1 << 20)
@@ -176,14 +188,17 @@ def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int = 1
                     break
                 job = pending.pop(0)
                 job.admitted = now
-                active.append((job, A.asep_create(job.params(), sample_times=job.times()), job.n_mcs))
+                ctx = A.asep_create(job.params(), sample_times=job.times())
+                shape[job.id] = _group_work(ctx)
+                active.append((job, ctx, job.n_mcs))
                 used += fp
             if not active:
                 time.sleep(max(0.0, pending[0].arrival - now))
                 continue
-            # one quantum: the step's attempts spread evenly over the active jobs
-            share = rate * quantum_s / len(active)
-            q = [max(1, min(left, int(share // (job.L * job.planes * job.S)))) for job, _, left in active]
+            # one quantum: every work item runs about quantum_s at the per-SM rate
+            per_sm = rate / sms
+            q = [max(1, min(left, int(per_sm * shape[job.id][1] * quantum_s // shape[job.id][0])))
+                 for job, _, left in active]
             t_step = time.perf_counter()
             A.asep_batch_sweep(batch, [c for _, c, _ in active], q)
             A.asep_sync(active[0][1])

@@ -211,6 +211,11 @@ def run_ours(args):
     ctx = A.asep_create(params(), sample_times=times)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     attempts_per_step = L_SITES * SAMPLES * N_MCS
+    plan, tune_table = None, None
+    if not args.no_autotune:
+        from paper_1012_0385_gb300.autotune import autotune
+
+        plan, tune_table = autotune(ctx, probe_sweeps=64)
 
     for w in range(args.warmup):
         A.asep_reset(ctx, seed=1000 + w)
@@ -294,6 +299,8 @@ def run_ours(args):
                        "schedule": "two-phase Poisson-domain RSU", "rates": {"p": P_RATE, "q": Q_RATE},
                        "observables": "W^2 at the log times (hop counters off)",
                        "l2": "flushed between steps (256 MB write outside the timed region)",
+                       "plan": ({"cluster": plan.cluster, "samples_per_group": plan.samples_per_group}
+                                if plan else "default"),
                        "parallelism": f"replicas x{world} (disjoint sample ranges)"},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": _traffic_from_profile(),
@@ -305,6 +312,9 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if tune_table:
+            line["autotune"] = [{k: r[k] for k in ("cluster", "samples_per_group", "ms_per_sweep")}
+                                for r in tune_table]
         if not args.no_serving and world == 1:
             line["serving"] = serving_comparison(capacity=value)
         if not args.no_cpu_baseline and world == 1:
@@ -370,6 +380,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-mix comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")

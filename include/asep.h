@@ -179,6 +179,15 @@ int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words);
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info);
 
+/* Choose the launch plan of a domain-schedule context (the autotuner's knob;
+ * results never depend on it).  cluster: 0 = automatic, 1 = whole samples in
+ * one CTA, 2/4/8/16 = each sample spread over that many CTAs of a
+ * thread-block cluster (columns of 2D sites split evenly).  samples_per_group:
+ * samples per CTA of the one-CTA plan (0 = automatic).  Returns
+ * ASEP_ERR_INVALID, keeping the previous plan, when the plan does not fit the
+ * device.  Takes effect for the next launch. */
+int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group);
+
 /* Wait for all work of the context. */
 int asep_sync(asep_ctx* ctx);
 

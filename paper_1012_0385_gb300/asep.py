@@ -90,7 +90,7 @@ EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
-            "asep_batch_sweep_static")
+            "asep_batch_sweep_static", "asep_set_plan")
 
 
 class AsepError(RuntimeError):
@@ -142,6 +142,7 @@ def lib():
             L.asep_batch_last_error.argtypes = [vp]
             L.asep_batch_last_error.restype = ctypes.c_char_p
             L.asep_batch_sweep_static.argtypes = [P(vp), P(ctypes.c_uint64), ctypes.c_uint32, vp]
+            L.asep_set_plan.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
             for name in EXPORTED:
                 if name not in ("asep_last_error", "asep_threshold", "asep_version", "asep_batch_last_error"):
                     getattr(L, name).restype = ctypes.c_int
@@ -308,6 +309,10 @@ def asep_get_info(ctx) -> dict:
     info = asep_info()
     _check(lib().asep_get_info(_h(ctx), ctypes.byref(info)), _h(ctx))
     return {f: getattr(info, f) for f, _ in asep_info._fields_}
+
+
+def asep_set_plan(ctx, cluster: int = 0, samples_per_group: int = 0) -> None:
+    _check(lib().asep_set_plan(_h(ctx), int(cluster), int(samples_per_group)), _h(ctx))
 
 
 def asep_width(ctx):

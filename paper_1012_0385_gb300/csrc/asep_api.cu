@@ -196,11 +196,14 @@ int validate(const asep_params* p, asep_ctx* ctx) {
 }
 
 // Resident plan: columns = super-domains, one thread per column.
-// Resident plan: columns = super-domains, one thread per column, a whole
-// sample (or several small ones) per CTA.  When one CTA cannot hold a sample
-// (more than 1024 columns, or more shared memory than 227 KB), the cluster
-// tier spreads each sample over 2..16 CTAs of a thread-block cluster.
-int plan_domain(asep_ctx* ctx) {
+// Launch plan.  Resident: columns = super-domains, one thread per column, a
+// whole sample (or several small ones) per CTA.  Cluster tier: each sample
+// spread over 2..16 CTAs of a thread-block cluster, for samples one CTA
+// cannot hold -- or, on request, to spread few large samples over more SMs.
+// force_cluster: 0 = choose, 1 = resident only, n > 1 = exactly n CTAs per
+// sample.  force_spc: samples per CTA for the resident plan (0 = choose).
+// The plan changes only the launch shape, never the results.
+int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
   const uint32_t D = ctx->D;
   ctx->R2 = 2 * D / 32;
   ctx->logR2 = log2u(ctx->R2);
@@ -208,39 +211,38 @@ int plan_domain(asep_ctx* ctx) {
   ctx->G = static_cast<uint32_t>(G);
   const uint32_t dis = ctx->p.dis_kind;
   const uint32_t ptab_n = static_cast<uint32_t>(ctx->ptab.size());
-  ctx->cluster = 1;
-  bool resident = false;
-  if (G <= 1024) {
-    uint32_t spc = 1;
-    if (ctx->G < 128) spc = std::max<uint32_t>(1, std::min<uint32_t>(ctx->S, 128 / ctx->G));
+  bool placed = false;
+  if (G <= 1024 && force_cluster <= 1) {
+    uint32_t spc = force_spc ? force_spc : 1;
+    if (!force_spc && ctx->G < 128) spc = std::max<uint32_t>(1, std::min<uint32_t>(ctx->S, 128 / ctx->G));
     for (;;) {
       const uint32_t C = spc * ctx->G;
       const uint32_t Cp = (C + 31) / 32 * 32;
       const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, ptab_n, Cp);
       if (smem <= 227 * 1024 && Cp <= 1024) {
+        ctx->cluster = 1;
+        ctx->Gc = 0;
         ctx->spc = spc;
         ctx->C = C;
         ctx->Cp = Cp;
         ctx->threads = Cp;
         ctx->smem = smem;
-        resident = true;
+        ctx->blocks = (ctx->S + spc - 1) / spc;
+        placed = true;
         break;
       }
-      if (spc == 1) break;
+      if (spc == 1 || force_spc) break;
       spc = std::max<uint32_t>(1, spc / 2);
     }
+    if (!placed && (force_cluster == 1 || force_spc))
+      return fail(ctx, ASEP_ERR_INVALID, "the requested resident plan does not fit one CTA");
   }
-  if (resident) {
-    ctx->blocks = (ctx->S + ctx->spc - 1) / ctx->spc;
-  } else {
-    bool placed = false;
-    for (uint32_t nc = 2; nc <= 16 && !placed; nc *= 2) {
-      const uint32_t Gc = static_cast<uint32_t>((G + nc - 1) / nc);
-      if (Gc > 1024 || (G + Gc - 1) / Gc != nc) continue;  // every CTA of the cluster must hold columns
-      const uint32_t Cp = (Gc + 31) / 32 * 32;
-      const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, ptab_n, Cp);
-      if (smem + 64 > 227 * 1024 || Cp > 1024) continue;
-      if (cluster_fits(ctx->p.model, dis, nc, Cp, smem) <= 0) continue;
+  for (uint32_t nc = force_cluster > 1 ? force_cluster : 2; !placed && nc <= 16; nc *= 2) {
+    const uint32_t Gc = static_cast<uint32_t>((G + nc - 1) / nc);
+    const bool ok = Gc <= 1024 && (G + Gc - 1) / Gc == nc;  // every CTA of the cluster holds columns
+    const uint32_t Cp = (Gc + 31) / 32 * 32;
+    const size_t smem = domain_smem_bytes(ctx->p.model, dis, ctx->R2, Cp, ptab_n, Cp);
+    if (ok && smem + 64 <= 227 * 1024 && Cp <= 1024 && cluster_fits(ctx->p.model, dis, nc, Cp, smem) > 0) {
       ctx->cluster = nc;
       ctx->spc = 1;
       ctx->C = Gc;
@@ -251,10 +253,12 @@ int plan_domain(asep_ctx* ctx) {
       ctx->blocks = ctx->S;
       placed = true;
     }
-    if (!placed)
-      return fail(ctx, ASEP_ERR_INVALID, "L = %llu (%llu columns, %u planes) fits neither one CTA nor a cluster of "
-                  "up to 16 CTAs on this device", (unsigned long long)ctx->L, (unsigned long long)G, ctx->planes);
+    if (force_cluster > 1) break;
   }
+  if (!placed)
+    return fail(ctx, ASEP_ERR_INVALID, "L = %llu (%llu columns, %u planes) fits neither one CTA nor a cluster of "
+                "up to 16 CTAs on this device%s", (unsigned long long)ctx->L, (unsigned long long)G, ctx->planes,
+                force_cluster > 1 ? " with the requested cluster size" : "");
   // per-lane 32-bit hop counters: at most 2 phases x largest count + 2D turns per sweep
   const uint64_t per_sweep = 2ull * (ctx->ptab_klo + ctx->ptab.size() + 1) + 2ull * D;
   ctx->max_sweeps_per_launch = static_cast<uint32_t>(std::max<uint64_t>(1, 4000000000ull / per_sweep));
@@ -440,7 +444,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     const uint32_t bonds = ctx->planes * D;
     if (poisson_table_host(bonds, ctx->ptab, ctx->ptab_klo) != ASEP_OK)
       return bail(fail(ctx, ASEP_ERR_INVALID, "attempt-count table for %u bonds failed", bonds));
-    rc = plan_domain(ctx);
+    rc = plan_domain(ctx, 0, 0);
     if (rc != ASEP_OK) return bail(rc);
   }
 
@@ -985,6 +989,32 @@ int asep_batch_destroy(asep_batch* b) {
 }
 
 const char* asep_batch_last_error(const asep_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  if (ctx->p.schedule != ASEP_SCHED_DOMAIN) return fail(ctx, ASEP_ERR_INVALID, "plans apply to the domain schedule");
+  if (cluster > 16 || (cluster > 1 && (cluster & (cluster - 1))))
+    return fail(ctx, ASEP_ERR_INVALID, "cluster must be 0, 1, 2, 4, 8 or 16");
+  if (samples_per_group && cluster > 1)
+    return fail(ctx, ASEP_ERR_INVALID, "samples_per_group applies to the resident plan (cluster 0 or 1)");
+  if (samples_per_group > ctx->S) return fail(ctx, ASEP_ERR_INVALID, "samples_per_group exceeds the samples");
+  const asep_ctx saved = *ctx;  // restore the previous plan if the new one does not fit
+  const int rc = plan_domain(ctx, cluster, samples_per_group);
+  if (rc != ASEP_OK) {
+    const std::string msg = ctx->err;
+    ctx->cluster = saved.cluster;
+    ctx->Gc = saved.Gc;
+    ctx->spc = saved.spc;
+    ctx->C = saved.C;
+    ctx->Cp = saved.Cp;
+    ctx->threads = saved.threads;
+    ctx->smem = saved.smem;
+    ctx->blocks = saved.blocks;
+    ctx->max_sweeps_per_launch = saved.max_sweeps_per_launch;
+    ctx->err = msg;
+  }
+  return rc;
+}
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info) {
   if (!ctx || !info) return ASEP_ERR_INVALID;

@@ -1,0 +1,81 @@
+"""Launch plans and the autotuner: every plan gives bit-identical results,
+impossible plans are rejected without changing the context, and the tuner
+applies the fastest valid plan."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_0385_gb300 import asep as A
+from paper_1012_0385_gb300 import autotune
+
+pytestmark = pytest.mark.gpu
+th = oracle.threshold
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_0385_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def run(ctx, n):
+    A.asep_reset(ctx, seed=77)
+    A.asep_sweep(ctx, n)
+    words, _ = A.asep_state(ctx)
+    sh, sh2, _ = A.asep_width(ctx)
+    return words, sh, sh2, A.asep_counters(ctx)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(L=1 << 17, domain_sites=256, samples_per_real=6, p_thr=th(0.75), q_thr=th(0.25)),
+    dict(L=1 << 15, domain_sites=128, n_realizations=2, samples_per_real=3, dis_kind=A.ASEP_DIS_BIMODAL,
+         dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=4),
+    dict(model=A.ASEP_MODEL_TWO_LANE, L=1 << 16, domain_sites=128, samples_per_real=3, init_kind=1, init_seed=2,
+         dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=3),
+])
+def test_every_plan_gives_the_same_result(kw):
+    with A.asep_create(A.make_params(**kw), sample_times=[0, 3, 9]) as ctx:
+        cands = autotune.candidates(ctx)
+        assert any(c > 1 for c, _ in cands) and (0, 0) in cands
+        ref = run(ctx, 9)
+        tried = 0
+        for cluster, spc in cands:
+            try:
+                A.asep_set_plan(ctx, cluster, spc)
+            except A.AsepError:
+                continue
+            tried += 1
+            got = run(ctx, 9)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), (cluster, spc)
+        assert tried >= 3
+
+
+def test_impossible_plans_are_rejected_and_the_plan_kept():
+    with A.asep_create(A.make_params(L=1 << 15, domain_sites=256), sample_times=[]) as ctx:
+        before = A.asep_get_info(ctx)
+        for cluster, spc in [(3, 0), (32, 0), (16, 0), (2, 4)]:  # 16 CTAs would get 4 columns each
+            with pytest.raises(A.AsepError):
+                A.asep_set_plan(ctx, cluster, spc)
+            after = A.asep_get_info(ctx)
+            assert (after["cluster"], after["samples_per_group"], after["groups"]) == \
+                   (before["cluster"], before["samples_per_group"], before["groups"])
+
+
+def test_autotune_applies_the_fastest_valid_plan(tmp_path):
+    kw = dict(L=1 << 16, domain_sites=256, samples_per_real=40, p_thr=th(0.75), q_thr=th(0.25))
+    with A.asep_create(A.make_params(**kw), sample_times=[]) as ctx:
+        choice, table = autotune.autotune(ctx, probe_sweeps=16)
+        assert len(table) >= 3
+        assert choice.ms_per_sweep == min(r["ms_per_sweep"] for r in table)
+        info = A.asep_get_info(ctx)
+        assert info["cluster"] == choice.cluster
+        cache = autotune.PlanCache(str(tmp_path / "plans.json"))
+        cache.put(ctx.params, choice)
+        assert autotune.PlanCache(str(tmp_path / "plans.json")).get(ctx.params)["cluster"] == choice.cluster

@@ -58,9 +58,11 @@ def test_every_plan_gives_the_same_result(kw):
 
 
 def test_impossible_plans_are_rejected_and_the_plan_kept():
-    with A.asep_create(A.make_params(L=1 << 15, domain_sites=256), sample_times=[]) as ctx:
+    with A.asep_create(A.make_params(L=4096, domain_sites=256, samples_per_real=2), sample_times=[]) as ctx:
         before = A.asep_get_info(ctx)
-        for cluster, spc in [(3, 0), (32, 0), (16, 0), (2, 4)]:  # 16 CTAs would get 4 columns each
+        # 8 columns cannot fill 16 CTAs; 3 and 32 are not cluster sizes; samples per CTA needs the
+        # one-CTA plan; a CTA cannot hold more samples than exist
+        for cluster, spc in [(16, 0), (3, 0), (32, 0), (2, 4), (1, 3)]:
             with pytest.raises(A.AsepError):
                 A.asep_set_plan(ctx, cluster, spc)
             after = A.asep_get_info(ctx)

@@ -54,6 +54,11 @@
 extern "C" {
 #endif
 
+/* Only the functions declared here are exported by libasep.so. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 #define ASEP_OK 0
 #define ASEP_ERR_INVALID (-1) /* bad argument or unsupported combination */
 #define ASEP_ERR_NOMEM (-2)   /* device or host allocation failed */
@@ -78,6 +83,8 @@ extern "C" {
 
 /* asep_params.flags */
 #define ASEP_FLAG_NO_HOP_COUNTS 1u /* ring model: do not count hops (asep_counters then reports zeros) */
+#define ASEP_FLAG_PROFILE 2u       /* accumulate the occupancy profile at every sample time (asep_profile) */
+#define ASEP_FLAG_AUTOCORR 4u      /* record the overlap with the lattice at autocorr_t0 (asep_autocorr) */
 
 typedef struct asep_ctx asep_ctx; /* opaque; owns every device buffer it allocates */
 
@@ -112,6 +119,7 @@ typedef struct asep_params {
   asep_alloc_fn alloc;       /* optional allocator hook (with free_fn and alloc_user) */
   asep_free_fn free_fn;
   void* alloc_user;
+  uint64_t autocorr_t0;      /* ASEP_FLAG_AUTOCORR: reference sweep count, one of sample_times */
 } asep_params;
 
 typedef struct asep_info {
@@ -176,6 +184,23 @@ int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n);
 /* Copy the quenched planes, layout [n_realizations][L/32] (bit = slow site
  * for BIMODAL, turning site for TURNING).  Synchronises. */
 int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words);
+
+/* Hop counters (layout of asep_counters) at every sample time recorded so
+ * far, layout [n_recorded][S][4].  Two lanes: J_A and J_B give the current
+ * density c = (J_A - J_B) / L of paper sec. 3 at each time.  Synchronises. */
+int asep_currents(asep_ctx* ctx, int64_t* out, size_t n);
+
+/* ASEP_FLAG_PROFILE: for every sample, plane and word w, the number of
+ * occupied sites of word w (sites 32w..32w+31) summed over the sample times
+ * recorded so far, layout [S][planes][L/32] -- the density profile in bins of
+ * 32 sites, time-averaged by dividing by 32 * n_recorded.  Synchronises. */
+int asep_profile(asep_ctx* ctx, uint32_t* out, size_t n);
+
+/* ASEP_FLAG_AUTOCORR: overlap sum_i n_i(t0) n_i(t) with the lattice at
+ * t0 = autocorr_t0, for every sample time t recorded so far (0 for t < t0),
+ * layout [n_recorded][S][planes]; the density autocorrelation is
+ * overlap / L - rho^2.  Synchronises. */
+int asep_autocorr(asep_ctx* ctx, int64_t* out, size_t n);
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info);
 
@@ -275,6 +300,10 @@ int asep_philox_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t 
 
 /* Library version string. */
 const char* asep_version(void);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -359,10 +359,14 @@ class RunResult:
     extra: dict = field(default_factory=dict)
 
 
-def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samples=None) -> RunResult:
+def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samples=None,
+        autocorr_t0: int | None = None) -> RunResult:
     """The whole hot path on the CPU: initial state, quenched disorder, n_mcs
-    sweeps, heights and W^2 at every time in ``sample_times`` (sweep counts
-    after which to record; 0 = the initial state)."""
+    sweeps, and at every time in ``sample_times`` (sweep counts after which
+    to record; 0 = the initial state) the heights and W^2, the cumulative hop
+    counters, the occupancy profile (occupied sites per 32-site word, summed
+    over the sample times) and, with ``autocorr_t0``, the overlap
+    sum_i n_i(t0) n_i(t) for t >= t0 (0 before)."""
     times = sorted(set(int(t) for t in sample_times if 0 <= t <= n_mcs))
     state = init_state(P)
     mask = disorder(P)
@@ -372,14 +376,29 @@ def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samp
     sh2 = np.zeros((nt, P.S, P.planes), dtype=object)
     w2 = np.zeros((nt, P.S, P.planes), dtype=np.float64)
     cnt = np.zeros((P.S, 4), dtype=np.uint64)
+    cnt_at = np.zeros((nt, P.S, 4), dtype=np.int64)
+    profile = np.zeros((P.S, P.planes, P.W), dtype=np.int64)
+    overlap = np.zeros((nt, P.S, P.planes), dtype=np.int64)
+    snap = None
+
+    def popcounts(words):
+        return np.array([bin(int(x)).count("1") for x in words.ravel()], dtype=np.int64).reshape(words.shape)
 
     def record(ti):
+        nonlocal snap
+        t = times[ti]
+        if autocorr_t0 is not None and t == autocorr_t0:
+            snap = state.copy()
         for s in idx:
+            cnt_at[ti, s] = cnt[s].astype(np.int64)
             for pl in range(P.planes):
                 a, b = heights(state[s, pl], P.L)
                 sh[ti, s, pl] = a
                 sh2[ti, s, pl] = b
                 w2[ti, s, pl] = width2(P.L, a, b)
+                profile[s, pl] += popcounts(state[s, pl])
+                if snap is not None:
+                    overlap[ti, s, pl] = int(popcounts(state[s, pl] & snap[s, pl]).sum())
 
     done = 0
     ti = 0
@@ -393,4 +412,5 @@ def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samp
         if ti < nt and times[ti] == done:
             record(ti)
             ti += 1
-    return RunResult(times=times, sum_h=sh, sum_h2=sh2, w2=w2, state=state, counters=cnt)
+    return RunResult(times=times, sum_h=sh, sum_h2=sh2, w2=w2, state=state, counters=cnt,
+                     extra={"counters_at": cnt_at, "profile": profile, "overlap": overlap})

@@ -33,6 +33,8 @@ ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING = 0, 1, 2
 ASEP_INIT_FLAT_ALT, ASEP_INIT_BERNOULLI_HALF = 0, 1
 ASEP_ALWAYS = 0xFFFFFFFF
 ASEP_FLAG_NO_HOP_COUNTS = 1
+ASEP_FLAG_PROFILE = 2
+ASEP_FLAG_AUTOCORR = 4
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -64,6 +66,7 @@ class asep_params(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free_fn", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
+        ("autocorr_t0", ctypes.c_uint64),
     ]
 
 
@@ -90,7 +93,7 @@ EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
-            "asep_batch_sweep_static", "asep_set_plan")
+            "asep_batch_sweep_static", "asep_set_plan", "asep_currents", "asep_profile", "asep_autocorr")
 
 
 class AsepError(RuntimeError):
@@ -143,6 +146,9 @@ def lib():
             L.asep_batch_last_error.restype = ctypes.c_char_p
             L.asep_batch_sweep_static.argtypes = [P(vp), P(ctypes.c_uint64), ctypes.c_uint32, vp]
             L.asep_set_plan.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
+            L.asep_currents.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
+            L.asep_profile.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_size_t]
+            L.asep_autocorr.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
             for name in EXPORTED:
                 if name not in ("asep_last_error", "asep_threshold", "asep_version", "asep_batch_last_error"):
                     getattr(L, name).restype = ctypes.c_int
@@ -232,6 +238,7 @@ def make_params(**kw) -> asep_params:
     p.dis_seed = kw.pop("dis_seed", 0)
     p.init_seed = kw.pop("init_seed", 0)
     p.flags = kw.pop("flags", 0)
+    p.autocorr_t0 = kw.pop("autocorr_t0", 0)
     if kw:
         raise TypeError(f"unknown parameters {sorted(kw)}")
     return p
@@ -355,6 +362,30 @@ def asep_counters(ctx) -> np.ndarray:
     c = np.zeros((info["S"], 4), dtype=np.uint64)
     _check(lib().asep_counters(_h(ctx), _ptr(c, ctypes.c_uint64), c.size), _h(ctx))
     return c
+
+
+def asep_currents(ctx) -> np.ndarray:
+    """Hop counters at every recorded sample time, [n_recorded, S, 4] int64."""
+    info = asep_get_info(ctx)
+    out = np.zeros((max(info["n_recorded"], 1), info["S"], 4), dtype=np.int64)
+    _check(lib().asep_currents(_h(ctx), _ptr(out, ctypes.c_int64), out.size), _h(ctx))
+    return out[: info["n_recorded"]]
+
+
+def asep_profile(ctx) -> np.ndarray:
+    """Occupied sites per 32-site word summed over the sample times, [S, planes, L/32]."""
+    info = asep_get_info(ctx)
+    out = np.zeros((info["S"], info["planes"], info["L"] // 32), dtype=np.uint32)
+    _check(lib().asep_profile(_h(ctx), _ptr(out, ctypes.c_uint32), out.size), _h(ctx))
+    return out
+
+
+def asep_autocorr(ctx) -> np.ndarray:
+    """Overlap sum_i n_i(t0) n_i(t) at every recorded sample time, [n_recorded, S, planes]."""
+    info = asep_get_info(ctx)
+    out = np.zeros((max(info["n_recorded"], 1), info["S"], info["planes"]), dtype=np.int64)
+    _check(lib().asep_autocorr(_h(ctx), _ptr(out, ctypes.c_int64), out.size), _h(ctx))
+    return out[: info["n_recorded"]]
 
 
 def asep_disorder(ctx) -> np.ndarray:

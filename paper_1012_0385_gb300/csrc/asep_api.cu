@@ -39,6 +39,10 @@ struct asep_ctx {
   uint64_t* d_sh2 = nullptr;
   uint64_t* d_cnt = nullptr;
   Clock* d_clock = nullptr;  // device-side (sweep, next sample time); see asep_internal.h
+  int64_t* d_tab_cnt = nullptr;  // [n_times][S][4]
+  uint32_t* d_profile = nullptr; // [S][planes][W]
+  uint32_t* d_snap = nullptr;    // [S][planes][W]
+  int64_t* d_tab_ac = nullptr;   // [n_times][S][planes]
   std::vector<std::pair<void*, size_t>> allocs;
   size_t dev_bytes = 0;
   // attempt-count table
@@ -183,7 +187,13 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (p->dis_kind == ASEP_DIS_TURNING && p->model != ASEP_MODEL_TWO_LANE)
     return fail(ctx, ASEP_ERR_INVALID, "turning sites are defined for the two-lane model");
   if (p->init_kind > ASEP_INIT_BERNOULLI_HALF) return fail(ctx, ASEP_ERR_INVALID, "unknown init_kind %u", p->init_kind);
-  if (p->flags & ~ASEP_FLAG_NO_HOP_COUNTS) return fail(ctx, ASEP_ERR_INVALID, "unknown flags 0x%x", p->flags);
+  if (p->flags & ~(ASEP_FLAG_NO_HOP_COUNTS | ASEP_FLAG_PROFILE | ASEP_FLAG_AUTOCORR))
+    return fail(ctx, ASEP_ERR_INVALID, "unknown flags 0x%x", p->flags);
+  if (p->flags & ASEP_FLAG_AUTOCORR) {
+    bool found = false;
+    for (uint32_t i = 0; i < p->n_sample_times && p->sample_times; ++i) found = found || p->sample_times[i] == p->autocorr_t0;
+    if (!found) return fail(ctx, ASEP_ERR_INVALID, "autocorr_t0 must be one of the sample times");
+  }
   if ((p->alloc == nullptr) != (p->free_fn == nullptr))
     return fail(ctx, ASEP_ERR_INVALID, "alloc and free_fn must be given together");
   if (p->n_sample_times && !p->sample_times) return fail(ctx, ASEP_ERR_INVALID, "sample_times is NULL");
@@ -288,13 +298,47 @@ Rates rates(const asep_ctx* ctx) {
   return r;
 }
 
+int clear_extras(asep_ctx* ctx) {
+  const size_t n_times = std::max<size_t>(1, ctx->times.size());
+  const size_t state_words = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ctx->d_tab_cnt, 0, n_times * ctx->S * 32, ctx->stream)) != cudaSuccess ||
+      (ctx->d_profile && (e = cudaMemsetAsync(ctx->d_profile, 0, state_words * 4, ctx->stream)) != cudaSuccess) ||
+      (ctx->d_tab_ac &&
+       (e = cudaMemsetAsync(ctx->d_tab_ac, 0, n_times * ctx->S * ctx->planes * 8, ctx->stream)) != cudaSuccess))
+    return cuda_fail(ctx, e, "clear observables");
+  return ASEP_OK;
+}
+
+Extras extras(const asep_ctx* ctx) {
+  Extras ex;
+  ex.tab_cnt = ctx->d_tab_cnt;
+  ex.profile = ctx->d_profile;
+  ex.snap = ctx->d_snap;
+  ex.tab_ac = ctx->d_tab_ac;
+  ex.t0 = ctx->p.autocorr_t0;
+  return ex;
+}
+
+int copy_out(asep_ctx* ctx, void* dst, const void* src, size_t bytes, const char* what) {
+  int rc = asep_sync(ctx);
+  if (rc != ASEP_OK) return rc;
+  if (bytes == 0) return ASEP_OK;
+  const cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return ASEP_OK;
+}
+
 int record_now(asep_ctx* ctx, uint32_t slot) {
   HeightsLaunch h;
   h.geo = geometry(ctx);
   h.state = ctx->d_state;
   h.slot = slot;
+  h.t = ctx->times.empty() ? 0 : ctx->times[slot];
   h.tab_sh = ctx->d_sh;
   h.tab_sh2 = ctx->d_sh2;
+  h.counters = ctx->d_cnt;
+  h.ex = extras(ctx);
   const cudaError_t e = launch_heights(h, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "heights kernel");
   ++ctx->launches;
@@ -333,6 +377,7 @@ DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
   a.tab_sh = ctx->d_sh;
   a.tab_sh2 = ctx->d_sh2;
   a.counters = ctx->d_cnt;
+  a.ex = extras(ctx);
   return a;
 }
 
@@ -458,10 +503,17 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   ctx->d_sh2 = static_cast<uint64_t*>(dev_alloc(ctx, entries * 16));
   ctx->d_times = static_cast<uint64_t*>(dev_alloc(ctx, n_times * 8));
   ctx->d_clock = static_cast<Clock*>(dev_alloc(ctx, sizeof(Clock)));
+  ctx->d_tab_cnt = static_cast<int64_t*>(dev_alloc(ctx, n_times * ctx->S * 32));
+  if (params->flags & ASEP_FLAG_PROFILE) ctx->d_profile = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
+  if (params->flags & ASEP_FLAG_AUTOCORR) {
+    ctx->d_snap = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
+    ctx->d_tab_ac = static_cast<int64_t*>(dev_alloc(ctx, entries * 8));
+  }
   if (ctx->R) ctx->d_mask = static_cast<uint32_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->R) * ctx->W * 4));
   if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
   if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || !ctx->d_clock ||
-      (ctx->R && !ctx->d_mask) ||
+      !ctx->d_tab_cnt || ((params->flags & ASEP_FLAG_PROFILE) && !ctx->d_profile) ||
+      ((params->flags & ASEP_FLAG_AUTOCORR) && (!ctx->d_snap || !ctx->d_tab_ac)) || (ctx->R && !ctx->d_mask) ||
       (!ctx->ptab.empty() && !ctx->d_ptab))
     return bail(fail(ctx, ASEP_ERR_NOMEM, "device allocation failed (%zu bytes so far)", ctx->dev_bytes));
 
@@ -479,6 +531,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   if ((e = cudaMemsetAsync(ctx->d_sh, 0, entries * 8, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_sh2, 0, entries * 16, ctx->stream)) != cudaSuccess)
     return bail(cuda_fail(ctx, e, "clear height table"));
+  if ((rc = clear_extras(ctx)) != ASEP_OK) return bail(rc);
 
   InitLaunch il;
   il.geo = geometry(ctx);
@@ -538,6 +591,7 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
       a.tab_sh = ctx->d_sh;
       a.tab_sh2 = ctx->d_sh2;
       a.counters = ctx->d_cnt;
+      a.ex = extras(ctx);
       e = launch_serial(a, ctx->p.model, ctx->p.dis_kind, ctx->stream);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep kernel launch");
@@ -562,6 +616,8 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
       (e = cudaMemsetAsync(ctx->d_sh, 0, entries * 8, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_sh2, 0, entries * 16, ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "clear tables");
+  const int rcx = clear_extras(ctx);
+  if (rcx != ASEP_OK) return rcx;
   InitLaunch il;
   il.geo = geometry(ctx);
   il.state = ctx->d_state;
@@ -1014,6 +1070,29 @@ int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
     ctx->err = msg;
   }
   return rc;
+}
+
+int asep_currents(asep_ctx* ctx, int64_t* out, size_t n) {
+  if (!ctx || !out) return ASEP_ERR_INVALID;
+  const size_t need = static_cast<size_t>(ctx->next_time) * ctx->S * 4;
+  if (n < need) return fail(ctx, ASEP_ERR_INVALID, "n = %zu < %zu", n, need);
+  return copy_out(ctx, out, ctx->d_tab_cnt, need * 8, "copy currents");
+}
+
+int asep_profile(asep_ctx* ctx, uint32_t* out, size_t n) {
+  if (!ctx || !out) return ASEP_ERR_INVALID;
+  if (!ctx->d_profile) return fail(ctx, ASEP_ERR_STATE, "the context was created without ASEP_FLAG_PROFILE");
+  const size_t need = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
+  if (n < need) return fail(ctx, ASEP_ERR_INVALID, "n = %zu < %zu", n, need);
+  return copy_out(ctx, out, ctx->d_profile, need * 4, "copy profile");
+}
+
+int asep_autocorr(asep_ctx* ctx, int64_t* out, size_t n) {
+  if (!ctx || !out) return ASEP_ERR_INVALID;
+  if (!ctx->d_tab_ac) return fail(ctx, ASEP_ERR_STATE, "the context was created without ASEP_FLAG_AUTOCORR");
+  const size_t need = static_cast<size_t>(ctx->next_time) * ctx->S * ctx->planes;
+  if (n < need) return fail(ctx, ASEP_ERR_INVALID, "n = %zu < %zu", n, need);
+  return copy_out(ctx, out, ctx->d_tab_ac, need * 8, "copy autocorrelation");
 }
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info) {

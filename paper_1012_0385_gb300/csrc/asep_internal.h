@@ -49,6 +49,15 @@ struct Geometry {
   uint32_t first_sample;
 };
 
+// Observables recorded at every sample time besides the heights.
+struct Extras {
+  int64_t* tab_cnt;        // [n_times][S][4] cumulative hop counters at each sample time
+  uint32_t* profile;       // [S][planes][W] occupied sites per word, summed over sample times (or nullptr)
+  uint32_t* snap;          // [S][planes][W] lattice at the autocorrelation reference time (or nullptr)
+  int64_t* tab_ac;         // [n_times][S][planes] sum_i n_i(t0) n_i(t), 0 before t0 (or nullptr)
+  uint64_t t0;             // autocorrelation reference sweep count
+};
+
 // Everything a domain-kernel launch needs about one context ("job").
 struct DomainLaunch {
   Geometry geo;
@@ -77,6 +86,7 @@ struct DomainLaunch {
   int64_t* tab_sh;         // [n_times][S][planes]
   uint64_t* tab_sh2;       // [n_times][S][planes][2] (low, high word)
   uint64_t* counters;      // [S][4]
+  Extras ex;
 };
 
 struct SerialLaunch {
@@ -92,6 +102,7 @@ struct SerialLaunch {
   int64_t* tab_sh;
   uint64_t* tab_sh2;
   uint64_t* counters;
+  Extras ex;
 };
 
 struct InitLaunch {
@@ -114,8 +125,11 @@ struct HeightsLaunch {
   Geometry geo;
   const uint32_t* state;
   uint32_t slot;
+  uint64_t t;              // sweep count of this record (0 at creation)
   int64_t* tab_sh;
   uint64_t* tab_sh2;
+  const uint64_t* counters;
+  Extras ex;
 };
 
 // Shared memory of the resident kernel, in bytes (planes of R2 + 1 rows:

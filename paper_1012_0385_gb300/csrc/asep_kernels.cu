@@ -205,6 +205,25 @@ __global__ void __launch_bounds__(256) k_heights(const HeightsLaunch a) {
     a.tab_sh2[2 * e] = static_cast<uint64_t>(acc);
     a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(acc >> 64);
   }
+  // the other observables of this record
+  if (p == 0 && threadIdx.x == 0) {
+    const size_t ec = (static_cast<size_t>(a.slot) * a.geo.S + sample) * 4;
+    for (int k = 0; k < 4; ++k) a.ex.tab_cnt[ec + k] = static_cast<int64_t>(a.counters[4 * static_cast<size_t>(sample) + k]);
+  }
+  const size_t pbase = (static_cast<size_t>(sample) * planes + p) * W;
+  long long ov = 0;
+  for (uint32_t i = w0; i < w1; ++i) {
+    if (a.ex.profile) a.ex.profile[pbase + i] += __popc(w[i]);
+    if (a.ex.snap) {
+      if (a.t == a.ex.t0) a.ex.snap[pbase + i] = w[i];
+      if (a.t >= a.ex.t0) ov += __popc(w[i] & a.ex.snap[pbase + i]);
+    }
+  }
+  if (a.ex.snap) {
+    const long long tot = block_scan_incl(ov, warp_tot);
+    if (threadIdx.x == blockDim.x - 1)
+      a.ex.tab_ac[(static_cast<size_t>(a.slot) * a.geo.S + sample) * planes + p] = tot;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -414,6 +433,49 @@ __device__ void record_heights(const uint32_t* cur, const DomainLaunch& a, uint3
 // context, for a.n_sweeps sweeps starting at the context clock.  Used by the
 // one-launch-per-context kernel (group = blockIdx.x) and by the persistent
 // batch kernel (group from the work queue).  All threads of the block call.
+// The other observables at a sample time t (frame offset 0): cumulative hop
+// counters (lane counters are flushed first), the occupancy profile, and the
+// overlap with the reference lattice of the density autocorrelation.
+template <uint32_t NOCC>
+__device__ void record_extras(const uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint32_t slot, uint64_t t,
+                              const Lane& ln, long long* warp_tot, long long* arr, Cnt& cnt) {
+  const Extras& ex = a.ex;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(a.counters + 4ull * ln.sample);
+  if (ln.active) {
+    if (cnt.a) atomicAdd(ctr + 0, static_cast<unsigned long long>(cnt.a));
+    if (cnt.b) atomicAdd(ctr + 1, static_cast<unsigned long long>(cnt.b));
+    if (cnt.c) atomicAdd(ctr + 2, static_cast<unsigned long long>(cnt.c));
+    if (cnt.d) atomicAdd(ctr + 3, static_cast<unsigned long long>(cnt.d));
+    cnt = Cnt();
+  }
+  __syncthreads();  // the block's counter updates are visible below
+  if (ln.active && ln.g == 0) {
+    const size_t e = (static_cast<size_t>(slot) * a.geo.S + ln.sample) * 4;
+    for (int k = 0; k < 4; ++k) ex.tab_cnt[e + k] = static_cast<int64_t>(atomicAdd(ctr + k, 0ull));
+  }
+  const uint32_t W = a.geo.W;
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    const uint32_t* pl = cur + p * PW;
+    const size_t base = (static_cast<size_t>(ln.sample) * a.geo.planes + p) * W + static_cast<size_t>(ln.g) * a.R2;
+    long long ov = 0;
+    if (ln.active) {
+      for (uint32_t r = 0; r < a.R2; ++r) {
+        const uint32_t x = pl[r * a.Cp + ln.c];
+        if (ex.profile) ex.profile[base + r] += __popc(x);
+        if (ex.snap) {
+          if (t == ex.t0) ex.snap[base + r] = x;
+          if (t >= ex.t0) ov += __popc(x & ex.snap[base + r]);
+        }
+      }
+    }
+    if (ex.snap) {
+      long long e_unused, tot;
+      seg_scan(ov, ln.col0, a.G, warp_tot, arr, e_unused, tot);
+      if (ln.active && ln.g == 0) ex.tab_ac[(static_cast<size_t>(slot) * a.geo.S + ln.sample) * NOCC + p] = tot;
+    }
+  }
+}
+
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
 __device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group, unsigned char* smem_raw) {
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
@@ -492,6 +554,7 @@ __device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group,
       R_cur = 0;
       __syncthreads();
       record_heights<NOCC>(cur, a, PW, rec, ln, warp_tot, arr);
+      record_extras<NOCC>(cur, a, PW, rec, s + 1, ln, warp_tot, arr, cnt);
       ++rec;
     }
   }
@@ -683,6 +746,54 @@ __device__ void record_heights_cl(const cg::cluster_group& cl, uint32_t* cur, co
   }
 }
 
+template <uint32_t NOCC>
+__device__ void record_extras_cl(const cg::cluster_group& cl, const uint32_t* cur, const DomainLaunch& a,
+                                 uint32_t PW, uint32_t slot, uint64_t t, const Lane& ln, uint32_t my_rank,
+                                 long long* warp_tot, long long* cta_sums, Cnt& cnt) {
+  const Extras& ex = a.ex;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(a.counters + 4ull * ln.sample);
+  if (ln.active) {
+    if (cnt.a) atomicAdd(ctr + 0, static_cast<unsigned long long>(cnt.a));
+    if (cnt.b) atomicAdd(ctr + 1, static_cast<unsigned long long>(cnt.b));
+    if (cnt.c) atomicAdd(ctr + 2, static_cast<unsigned long long>(cnt.c));
+    if (cnt.d) atomicAdd(ctr + 3, static_cast<unsigned long long>(cnt.d));
+    cnt = Cnt();
+  }
+  __threadfence();
+  cl.sync();  // every CTA of the sample has flushed its counters
+  if (my_rank == 0 && threadIdx.x == 0) {
+    const size_t e = (static_cast<size_t>(slot) * a.geo.S + ln.sample) * 4;
+    for (int k = 0; k < 4; ++k) ex.tab_cnt[e + k] = static_cast<int64_t>(atomicAdd(ctr + k, 0ull));
+  }
+  const uint32_t W = a.geo.W;
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    const uint32_t* pl = cur + p * PW;
+    const size_t base = (static_cast<size_t>(ln.sample) * a.geo.planes + p) * W + static_cast<size_t>(ln.g) * a.R2;
+    long long ov = 0;
+    if (ln.active) {
+      for (uint32_t r = 0; r < a.R2; ++r) {
+        const uint32_t x = pl[r * a.Cp + ln.c];
+        if (ex.profile) ex.profile[base + r] += __popc(x);
+        if (ex.snap) {
+          if (t == ex.t0) ex.snap[base + r] = x;
+          if (t >= ex.t0) ov += __popc(x & ex.snap[base + r]);
+        }
+      }
+    }
+    if (ex.snap) {
+      const long long tot = block_scan_incl(ov, warp_tot);
+      if (threadIdx.x == blockDim.x - 1) cta_sums[3] = tot;
+      cl.sync();
+      if (my_rank == 0 && threadIdx.x == 0) {
+        long long sum = 0;
+        for (uint32_t k = 0; k < cl.num_blocks(); ++k) sum += cl.map_shared_rank(cta_sums, k)[3];
+        ex.tab_ac[(static_cast<size_t>(slot) * a.geo.S + ln.sample) * NOCC + p] = sum;
+      }
+      cl.sync();
+    }
+  }
+}
+
 template <uint32_t MODEL, uint32_t DIS, bool COUNT>
 __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -773,6 +884,7 @@ __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
       R_cur = 0;
       __syncthreads();
       record_heights_cl<NOCC>(cl, cur, a, PW, rec, ln, my_rank, warp_tot, cta_sums);
+      record_extras_cl<NOCC>(cl, cur, a, PW, rec, s + 1, ln, my_rank, warp_tot, cta_sums, cnt);
       ++rec;
     }
   }
@@ -822,6 +934,8 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
   unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
   const uint64_t s0 = a.clock->sweep;
   uint32_t rec = a.clock->next_time;
+  uint64_t* my_ctr = a.counters + 4 * static_cast<size_t>(sample);
+  const uint64_t base0 = my_ctr[0], base1 = my_ctr[1], base2 = my_ctr[2], base3 = my_ctr[3];
 
   auto attempt = [&](uint32_t rb, uint32_t ru) {
     if (MODEL == kTwoLane) {
@@ -897,15 +1011,31 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
         a.tab_sh[e] = s1;
         a.tab_sh2[2 * e] = static_cast<uint64_t>(s2);
         a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2 >> 64);
+        // profile and autocorrelation overlap of this plane
+        uint32_t* snap = a.ex.snap ? a.ex.snap + (static_cast<size_t>(sample) * a.geo.planes + p) * W : nullptr;
+        uint32_t* prof = a.ex.profile ? a.ex.profile + (static_cast<size_t>(sample) * a.geo.planes + p) * W : nullptr;
+        long long ov = 0;
+        for (uint32_t w = 0; w < W; ++w) {
+          if (prof) prof[w] += __popc(pl[w]);
+          if (snap) {
+            if (s + 1 == a.ex.t0) snap[w] = pl[w];
+            if (s + 1 >= a.ex.t0) ov += __popc(pl[w] & snap[w]);
+          }
+        }
+        if (snap) a.ex.tab_ac[e] = ov;
       }
+      const size_t ec = (static_cast<size_t>(rec) * a.geo.S + sample) * 4;
+      a.ex.tab_cnt[ec + 0] = static_cast<int64_t>(base0 + c0);
+      a.ex.tab_cnt[ec + 1] = static_cast<int64_t>(base1 + c1);
+      a.ex.tab_cnt[ec + 2] = static_cast<int64_t>(base2 + c2);
+      a.ex.tab_cnt[ec + 3] = static_cast<int64_t>(base3 + c3);
       ++rec;
     }
   }
-  uint64_t* dst = a.counters + 4 * static_cast<size_t>(sample);
-  dst[0] += c0;
-  dst[1] += c1;
-  dst[2] += c2;
-  dst[3] += c3;
+  my_ctr[0] = base0 + c0;
+  my_ctr[1] = base1 + c1;
+  my_ctr[2] = base2 + c2;
+  my_ctr[3] = base3 + c3;
 }
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>

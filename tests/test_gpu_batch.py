@@ -25,13 +25,14 @@ def _device():
 
 
 MIX = [
-    (dict(L=1 << 15, domain_sites=256, samples_per_real=5, p_thr=th(0.75), q_thr=th(0.25), seed=3), [0, 7, 20, 33]),
+    (dict(L=1 << 15, domain_sites=256, samples_per_real=5, p_thr=th(0.75), q_thr=th(0.25), seed=3,
+          flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=7), [0, 7, 20, 33]),
     (dict(L=4096, domain_sites=128, samples_per_real=40, p_thr=th(0.6), seed=5), [0, 30]),
     (dict(L=1 << 16, domain_sites=256, n_realizations=2, samples_per_real=2, dis_kind=A.ASEP_DIS_BIMODAL,
           dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=21, seed=4), [0, 12, 40]),
     (dict(model=A.ASEP_MODEL_TWO_LANE, L=8192, domain_sites=64, samples_per_real=3, init_kind=1, init_seed=8,
           dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=9, q_thr=A.ASEP_ALWAYS,
-          seed=10), [5, 25]),
+          seed=10, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), [5, 25]),
     (dict(L=1 << 17, domain_sites=256, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=1,
           flags=A.ASEP_FLAG_NO_HOP_COUNTS), [0, 16]),
     (dict(L=128, domain_sites=32, samples_per_real=300, p_thr=th(0.7), q_thr=th(0.2), seed=2), [0, 50]),
@@ -42,11 +43,16 @@ N_MCS = [33, 30, 40, 25, 16, 50]
 def snapshot(ctx):
     words, sweep = A.asep_state(ctx)
     sh, sh2, _ = A.asep_width(ctx)
-    return dict(words=words, sweep=sweep, sh=sh, sh2=sh2, cnt=A.asep_counters(ctx))
+    out = dict(words=words, sweep=sweep, sh=sh, sh2=sh2, cnt=A.asep_counters(ctx), cur=A.asep_currents(ctx))
+    try:
+        out["prof"], out["ac"] = A.asep_profile(ctx), A.asep_autocorr(ctx)
+    except A.AsepError:  # context made without the observable flags
+        out["prof"] = out["ac"] = np.zeros(0)
+    return out
 
 
 def same(a, b):
-    for k in ("words", "sh", "sh2", "cnt"):
+    for k in ("words", "sh", "sh2", "cnt", "cur", "prof", "ac"):
         assert np.array_equal(a[k], b[k]), k
     assert a["sweep"] == b["sweep"]
 

@@ -33,7 +33,7 @@ def _device():
     torch.cuda.set_device(0)
 
 
-ORACLE_KEYS = {"flags": None, "model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
+ORACLE_KEYS = {"flags": None, "autocorr_t0": None, "model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
                "n_realizations": "n_realizations", "samples_per_real": "samples_per_real",
                "first_sample": "first_sample", "p_thr": "p_thr", "q_thr": "q_thr", "dis_kind": "dis_kind",
                "dis_a_thr": "dis_a_thr", "dis_b_thr": "dis_b_thr", "dis_c_thr": "dis_c_thr",
@@ -59,11 +59,19 @@ def run_gpu(kw, chunks, times):
         sh, sh2, w2 = A.asep_width(ctx)
         cnt = A.asep_counters(ctx)
         dis = A.asep_disorder(ctx)
+        cur = A.asep_currents(ctx)
+        prof = A.asep_profile(ctx) if kw.get("flags", 0) & A.ASEP_FLAG_PROFILE else None
+        ac = A.asep_autocorr(ctx) if kw.get("flags", 0) & A.ASEP_FLAG_AUTOCORR else None
     assert sweep == sum(chunks)
-    return dict(words=words, sh=sh, sh2=sh2, w2=w2, cnt=cnt, dis=dis)
+    return dict(words=words, sh=sh, sh2=sh2, w2=w2, cnt=cnt, dis=dis, cur=cur, prof=prof, ac=ac)
 
 
 def assert_same(g, ref, P, times):
+    assert np.array_equal(g["cur"], ref.extra["counters_at"]), "hop counters at the sample times"
+    if g["prof"] is not None:
+        assert np.array_equal(g["prof"].astype(np.int64), ref.extra["profile"]), "occupancy profile"
+    if g["ac"] is not None:
+        assert np.array_equal(g["ac"], ref.extra["overlap"]), "autocorrelation overlap"
     assert g["words"].shape == ref.state.shape
     bad = np.argwhere(g["words"] != ref.state)
     assert bad.size == 0, f"{len(bad)} words differ, first at {bad[:3].tolist()}"
@@ -109,7 +117,13 @@ CASES = {
                            dis_c_thr=th(0.1), dis_seed=5, seed=6), 15, [15]),
     "two_lane_cfg3_shape": (dict(model=TWO, L=1 << 16, domain_sites=256, samples_per_real=3, init_kind=1,
                                  init_seed=8, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
-                                 dis_seed=9, q_thr=A.ASEP_ALWAYS), 10, [0, 10]),
+                                 dis_seed=9, q_thr=A.ASEP_ALWAYS, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR,
+                                 autocorr_t0=4), 10, [0, 2, 4, 7, 10]),
+    "two_lane_autocorr_from_start": (dict(model=TWO, L=4096, domain_sites=128, samples_per_real=2, init_kind=1,
+                                          init_seed=3, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
+                                          dis_b_thr=th(0.1), dis_seed=4, q_thr=A.ASEP_ALWAYS, seed=5,
+                                          flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=0),
+                                     6, [0, 3, 6]),
     "two_lane_plain": (dict(model=TWO, L=4096, domain_sites=64, samples_per_real=4, init_kind=1, init_seed=1,
                             p_thr=th(0.5), q_thr=th(0.7), seed=7), 15, [15]),
     "serial_cfg0_shape": (dict(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=8, seed=1), 200,
@@ -118,7 +132,8 @@ CASES = {
                          q_thr=th(0.25), seed=12), 30, [0, 10, 30]),
     "serial_two_lane": (dict(model=TWO, L=1024, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=3, init_kind=1,
                              init_seed=4, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
-                             dis_seed=2, q_thr=A.ASEP_ALWAYS, seed=3), 20, [20]),
+                             dis_seed=2, q_thr=A.ASEP_ALWAYS, seed=3,
+                             flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 20, [0, 5, 20]),
     "serial_bimodal": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
                             dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=3, seed=4),
                        20, [20]),
@@ -133,7 +148,8 @@ CASES = {
                         4, [0, 4]),
     "cluster_two_lane": (dict(model=TWO, L=1 << 19, domain_sites=256, samples_per_real=1, init_kind=1, init_seed=5,
                               dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=8,
-                              q_thr=A.ASEP_ALWAYS, seed=55), 3, [0, 3]),
+                              q_thr=A.ASEP_ALWAYS, seed=55, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR,
+                              autocorr_t0=1), 3, [0, 1, 3]),
     "cluster_ring_max_L": (dict(L=1 << 22, domain_sites=256, samples_per_real=1, p_thr=th(0.75), q_thr=th(0.25),
                                 seed=56), 2, [0, 2]),
     "cluster_two_lane_max_L": (dict(model=TWO, L=1 << 22, domain_sites=256, samples_per_real=1, init_kind=1,
@@ -147,7 +163,8 @@ def test_bit_exact_against_oracle(name):
     kw, n, times = CASES[name]
     g = run_gpu(kw, [n], times)
     P = oracle_params(kw)
-    ref = oracle.run(P, n, times)
+    ref = oracle.run(P, n, times, autocorr_t0=kw.get("autocorr_t0") if kw.get("flags", 0) & A.ASEP_FLAG_AUTOCORR
+                     else None)
     if P.dis_kind != 0:
         assert np.array_equal(g["dis"], oracle.disorder(P))
     assert_same(g, ref, P, times)

@@ -190,13 +190,16 @@ int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words);
  * density c = (J_A - J_B) / L of paper sec. 3 at each time.  Synchronises. */
 int asep_currents(asep_ctx* ctx, int64_t* out, size_t n);
 
-/* ASEP_FLAG_PROFILE: for every sample, plane and word w, the number of
- * occupied sites of word w (sites 32w..32w+31) summed over the sample times
- * recorded so far, layout [S][planes][L/32] -- the density profile in bins of
- * 32 sites, time-averaged by dividing by 32 * n_recorded.  Synchronises. */
+/* ASEP_FLAG_PROFILE (an observable the paper does not define): for every
+ * sample, plane and word w, the number of occupied sites of word w (sites
+ * 32w..32w+31) summed over the sample times recorded so far, layout
+ * [S][planes][L/32] -- the density profile in bins of 32 sites,
+ * time-averaged by dividing by 32 * n_recorded.  The flag allows at most 2^27
+ * sample times, so the counts fit 32 bits.  Synchronises. */
 int asep_profile(asep_ctx* ctx, uint32_t* out, size_t n);
 
-/* ASEP_FLAG_AUTOCORR: overlap sum_i n_i(t0) n_i(t) with the lattice at
+/* ASEP_FLAG_AUTOCORR (an observable the paper does not define): overlap
+ * sum_i n_i(t0) n_i(t) with the lattice at
  * t0 = autocorr_t0, for every sample time t recorded so far (0 for t < t0),
  * layout [n_recorded][S][planes]; the density autocorrelation is
  * overlap / L - rho^2.  Synchronises. */

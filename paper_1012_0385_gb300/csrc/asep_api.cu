@@ -189,6 +189,8 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (p->init_kind > ASEP_INIT_BERNOULLI_HALF) return fail(ctx, ASEP_ERR_INVALID, "unknown init_kind %u", p->init_kind);
   if (p->flags & ~(ASEP_FLAG_NO_HOP_COUNTS | ASEP_FLAG_PROFILE | ASEP_FLAG_AUTOCORR))
     return fail(ctx, ASEP_ERR_INVALID, "unknown flags 0x%x", p->flags);
+  if ((p->flags & ASEP_FLAG_PROFILE) && p->n_sample_times > (1u << 27))
+    return fail(ctx, ASEP_ERR_INVALID, "ASEP_FLAG_PROFILE takes at most 2^27 sample times (32-bit bin counts)");
   if (p->flags & ASEP_FLAG_AUTOCORR) {
     bool found = false;
     for (uint32_t i = 0; i < p->n_sample_times && p->sample_times; ++i) found = found || p->sample_times[i] == p->autocorr_t0;

@@ -72,3 +72,11 @@ def test_create_rejects_bad_params_without_device(A):
             A.asep_create(prm, torch_alloc=False, stream=0)
         assert ei.value.code == A.ASEP_ERR_INVALID, kw
         assert A.asep_last_error(None)
+    # observable flags: unknown bits; an autocorrelation reference time that is not a sample time
+    for kw, times in [(dict(L=4096, flags=8), [0, 5]),
+                      (dict(L=4096, flags=A.ASEP_FLAG_AUTOCORR, autocorr_t0=3), [0, 5]),
+                      (dict(L=4096, flags=A.ASEP_FLAG_AUTOCORR), [])]:
+        with pytest.raises(A.AsepError) as ei:
+            A.asep_create(A.make_params(**kw), sample_times=times, torch_alloc=False, stream=0)
+        assert ei.value.code == A.ASEP_ERR_INVALID, kw
+        assert "autocorr" in A.asep_last_error(None) or "flags" in A.asep_last_error(None), kw

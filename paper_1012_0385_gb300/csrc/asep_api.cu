@@ -370,6 +370,11 @@ DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
   a.n_groups = ctx->blocks;
   a.cluster = ctx->cluster;
   a.Gc = ctx->Gc;
+  {
+    // every warp inside one sample, and the idle realign buffer holds 5 words per column
+    const uint32_t np = (ctx->p.model == ASEP_MODEL_TWO_LANE ? 2u : 1u) + (ctx->p.dis_kind != ASEP_DIS_NONE ? 1u : 0u);
+    a.lane_sort = (ctx->cluster <= 1 && ctx->G % 32 == 0 && np * (ctx->R2 + 1) >= 5) ? 1u : 0u;
+  }
   a.rates = rates(ctx);
   a.seed = ctx->p.seed;
   a.n_sweeps = n;

@@ -77,6 +77,7 @@ struct DomainLaunch {
   uint32_t n_groups;       // ceil(S / spc); cluster tier: S (one cluster per sample)
   uint32_t cluster;        // CTAs per sample: 1 = resident in one CTA, 2..16 = a thread-block cluster
   uint32_t Gc;             // cluster tier: columns per CTA (the last CTA may hold fewer)
+  uint32_t lane_sort;      // resident tier: warps run domains of similar Poisson count (results unchanged)
   Rates rates;
   uint64_t seed;
   uint32_t n_sweeps;       // sweeps of this launch

@@ -313,10 +313,23 @@ __device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& 
   }
 }
 
-// One half-domain phase of one sweep.  All threads of the warp must call.
+// One half-domain phase of one sweep.  All threads of the block must call.
+//
+// Lane sort: the lanes of a warp run to the largest Poisson count of the
+// warp, so a warp whose domains drew similar counts wastes fewer slots.  With
+// `a.lane_sort` (every warp inside one sample, and a scratch area of 5 words
+// per column) each thread ranks its domain's count among the domains of the
+// same shared-memory bank in its sample (columns lane, lane + 32, ...) and
+// warp w runs the domains of rank w.  A domain's attempts are the same
+// whichever thread runs them, and a thread stays in its own sample and bank,
+// so results and bank mapping are unchanged; only the slots a warp wastes
+// shrink.  `scr` is the idle realign buffer (overwritten by the next realign).
+// The cluster tier passes sort = false: there other CTAs may still read that
+// buffer remotely during the first phase.
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP, uint32_t PHASE>
-__device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, const uint32_t* tab, uint32_t PW,
-                                          uint64_t s, const Lane& ln, uint2 key, Cnt& cnt) {
+__device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sort, const DomainLaunch& a,
+                                          const uint32_t* tab, uint32_t PW, uint64_t s, const Lane& ln, uint2 key,
+                                          Cnt& cnt) {
   const uint32_t d = 2 * ln.g + PHASE;
   uint4 x0 = make_uint4(0u, 0u, 0u, 0u);
   uint32_t K = 0;
@@ -324,10 +337,45 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, 
     x0 = philox10(ctr_of(s, kTagDom, 0, ln.n_glob, d), key);
     K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
   }
+  const uint32_t cp = CP ? CP : a.Cp;
+  uint32_t col = ln.c;  // the column (domain pair) this thread runs
+  uint32_t dd = d;      // its domain index in the sample
+  if (sort) {
+    // Only the group's own columns (c < C) take part: a persistent CTA may be
+    // wider than the group, and its extra threads keep K = 0 and no column.
+    const bool in_group = ln.c < a.C;
+    uint32_t* sK = scr;
+    uint32_t* sPerm = scr + cp;
+    uint32_t* sX = scr + 2 * cp;
+    if (in_group) {
+      sK[ln.c] = K;
+      sX[ln.c] = x0.y;
+      sX[cp + ln.c] = x0.z;
+      sX[2 * cp + ln.c] = x0.w;
+    }
+    __syncthreads();
+    if (in_group) {
+      const uint32_t lane = ln.c & 31u;
+      uint32_t rank = 0;
+      for (uint32_t q = ln.col0 + lane; q < ln.col0 + a.G; q += 32) {
+        const uint32_t kq = sK[q];
+        rank += (kq < K || (kq == K && q < ln.c)) ? 1u : 0u;
+      }
+      sPerm[ln.col0 + (rank << 5) + lane] = ln.c;
+    }
+    __syncthreads();
+    if (in_group) {
+      col = sPerm[ln.c];
+      dd = 2 * (ln.g - ln.c + col) + PHASE;
+      K = sK[col];
+      x0.y = sX[col];
+      x0.z = sX[cp + col];
+      x0.w = sX[2 * cp + col];
+    }
+  }
   const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
   unsigned char* cb = reinterpret_cast<unsigned char*>(cur);
-  const uint32_t cp = CP ? CP : a.Cp;
-  const uint32_t base_b = (PHASE * (a.D >> 5) * cp + ln.c) * 4u;
+  const uint32_t base_b = (PHASE * (a.D >> 5) * cp + col) * 4u;
   const uint32_t row_scale_b = cp >> 3;  // 4 * Cp / 32
   const uint32_t PWb = PW * 4u;
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.y, 1 <= K, cnt);
@@ -335,7 +383,7 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, const DomainLaunch& a, 
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
 #pragma unroll 2
   for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
-    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, d), key);
+    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), key);
     const uint32_t k = call << 2;
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, k + 1 <= K, cnt);
@@ -535,10 +583,10 @@ __device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group,
     nxt = t;
     R_cur = o;
     __syncthreads();
-    run_phase<MODEL, DIS, COUNT, CP, 0>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, CP, 0>(cur, nxt, a.lane_sort != 0, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
     if (ln.active) mirror_in<NP>(cur, a, PW, ln);
-    run_phase<MODEL, DIS, COUNT, CP, 1>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, CP, 1>(cur, nxt, a.lane_sort != 0, a, tab, PW, s, ln, key, cnt);
     __syncthreads();
     if (ln.active) mirror_out<NOCC>(cur, a, PW, ln);
     __syncthreads();
@@ -608,7 +656,7 @@ __device__ __forceinline__ void run_group_any(const DomainLaunch& a, uint32_t gr
 // current item is copied to shared memory once.  Two block-size classes: up
 // to 512 threads (128 registers available) and up to 1024.
 template <uint32_t MAXT>
-__global__ void __launch_bounds__(MAXT) k_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items,
+__global__ void __maxnreg__(MAXT == 512 ? 104 : 64) k_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items,
                                                 uint32_t* queue) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t item_idx;
@@ -855,14 +903,14 @@ __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
     nxt = t;
     R_cur = o;
     __syncthreads();
-    run_phase<MODEL, DIS, COUNT, 0, 0>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, 0, 0>(cur, nullptr, false, a, tab, PW, s, ln, key, cnt);
     cl.sync();
     if (ln.active) {
 #pragma unroll
       for (uint32_t p = 0; p < NP; ++p)
         cur[p * PW + R2 * Cp + ln.c] = *cl_word(cl, cur, p, PW, 0, Cp, gn, Gc, my_rank);
     }
-    run_phase<MODEL, DIS, COUNT, 0, 1>(cur, a, tab, PW, s, ln, key, cnt);
+    run_phase<MODEL, DIS, COUNT, 0, 1>(cur, nullptr, false, a, tab, PW, s, ln, key, cnt);
     cl.sync();
     if (ln.active) {
 #pragma unroll

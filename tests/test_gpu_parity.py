@@ -102,6 +102,9 @@ CASES = {
                         [0, 25]),
     "ring_cfg1_columns": (dict(L=1 << 17, domain_sites=256, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25),
                                seed=1), 6, [0, 3, 6]),
+    # 64 columns per sample, several samples per CTA: warps sort their domains by Poisson count (hop counts on)
+    "ring_sorted_packed": (dict(L=1 << 14, domain_sites=128, samples_per_real=20, p_thr=th(0.75), q_thr=th(0.25),
+                                seed=31, flags=A.ASEP_FLAG_PROFILE), 25, [0, 9, 25]),
     "ring_min_L": (dict(L=64, domain_sites=32, samples_per_real=40, p_thr=th(0.7), q_thr=th(0.3), seed=2), 50,
                    [0, 50]),
     "ring_first_sample": (dict(L=4096, domain_sites=128, samples_per_real=4, first_sample=8, p_thr=th(0.75),

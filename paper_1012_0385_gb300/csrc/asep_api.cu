@@ -377,6 +377,7 @@ DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
   }
   a.rates = rates(ctx);
   a.seed = ctx->p.seed;
+  a.ks = key_schedule(ctx->p.seed);
   a.n_sweeps = n;
   a.clock = ctx->d_clock;
   a.times = ctx->d_times;

@@ -59,6 +59,24 @@ struct Extras {
 };
 
 // Everything a domain-kernel launch needs about one context ("job").
+// Philox4x32-10 round keys for a 64-bit seed: round i uses
+// (lo + i * 0x9E3779B9, hi + i * 0xBB67AE85) mod 2^32.
+struct KeySchedule {
+  uint32_t x[10], y[10];
+};
+
+inline KeySchedule key_schedule(uint64_t seed) {
+  KeySchedule ks;
+  uint32_t kx = static_cast<uint32_t>(seed), ky = static_cast<uint32_t>(seed >> 32);
+  for (int i = 0; i < 10; ++i) {
+    ks.x[i] = kx;
+    ks.y[i] = ky;
+    kx += 0x9E3779B9u;
+    ky += 0xBB67AE85u;
+  }
+  return ks;
+}
+
 struct DomainLaunch {
   Geometry geo;
   uint32_t model, dis;     // Model, Dis
@@ -80,6 +98,7 @@ struct DomainLaunch {
   uint32_t lane_sort;      // resident tier: warps run domains of similar Poisson count (results unchanged)
   Rates rates;
   uint64_t seed;
+  KeySchedule ks;          // round keys of `seed`
   uint32_t n_sweeps;       // sweeps of this launch
   Clock* clock;            // device
   const uint64_t* times;   // device, ascending sample times

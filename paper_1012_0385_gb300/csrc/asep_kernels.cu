@@ -43,17 +43,36 @@ namespace {
 // Philox4x32-10 and counters
 // ---------------------------------------------------------------------------
 
+// 32 x 32 -> 64-bit product as one wide multiply; .x = low word, .y = high word.
+__device__ __forceinline__ uint2 mul_wide(uint32_t a, uint32_t b) {
+  unsigned long long p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  return make_uint2(static_cast<uint32_t>(p), static_cast<uint32_t>(p >> 32));
+}
+
+// One Philox4x32 round with round key (kx, ky).
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t kx, uint32_t ky) {
+  const uint2 p0 = mul_wide(0xD2511F53u, c.x);
+  const uint2 p1 = mul_wide(0xCD9E8D57u, c.z);
+  return make_uint4(p1.y ^ c.y ^ kx, p1.x, p0.y ^ c.w ^ ky, p0.x);
+}
+
 __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    c = philox_round(c, k.x, k.y);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
   }
+  return c;
+}
+
+// Philox4x32-10 with the round keys precomputed (KeySchedule, filled by the
+// host): in a kernel whose descriptor is a parameter the keys are read from
+// the constant bank, so a call costs only the multiplies and XORs.
+__device__ __forceinline__ uint4 philox10(uint4 c, const KeySchedule& ks) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) c = philox_round(c, ks.x[round], ks.y[round]);
   return c;
 }
 
@@ -334,7 +353,7 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
   uint4 x0 = make_uint4(0u, 0u, 0u, 0u);
   uint32_t K = 0;
   if (ln.active) {
-    x0 = philox10(ctr_of(s, kTagDom, 0, ln.n_glob, d), key);
+    x0 = philox10(ctr_of(s, kTagDom, 0, ln.n_glob, d), a.ks);
     K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
   }
   const uint32_t cp = CP ? CP : a.Cp;
@@ -383,7 +402,7 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
 #pragma unroll 2
   for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
-    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), key);
+    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
     const uint32_t k = call << 2;
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, k + 1 <= K, cnt);

@@ -136,10 +136,13 @@ def cpu_oracle_sample(target_s: float, n_mcs_cap: int = N_MCS):
     P = oracle.Params(L=L_SITES, D=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE), q_thr=th(Q_RATE), seed=SEED)
     k = min(cores, SAMPLES)
     oracle.build()
-    # calibrate on 4 sweeps
+    # calibrate on the difference of an 8- and a 40-sweep run (start-up costs cancel)
     t0 = time.perf_counter()
-    oracle.run(P, 4, [0], threads=cores, samples=range(k))
-    rate = k * L_SITES * 4 / (time.perf_counter() - t0)
+    oracle.run(P, 8, [0], threads=cores, samples=range(k))
+    t1 = time.perf_counter()
+    oracle.run(P, 40, [0], threads=cores, samples=range(k))
+    t2 = time.perf_counter()
+    rate = k * L_SITES * 32 / max(1e-6, (t2 - t1) - (t1 - t0))
     n = int(max(8, min(n_mcs_cap, target_s * rate / (k * L_SITES))))
     from paper_1012_0385_gb300.sampling import log_times
 
@@ -182,6 +185,7 @@ def run_ours(args):
     import torch
 
     from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300 import replicas
     from paper_1012_0385_gb300.sampling import log_times
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -202,9 +206,10 @@ def run_ours(args):
 
     th = A.asep_threshold
     times = log_times(N_MCS)
+    first, count = replicas.sample_range(rank, world, SAMPLES)
 
     def params():
-        return A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, first_sample=rank * SAMPLES,
+        return A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=count, first_sample=first,
                              p_thr=th(P_RATE), q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
 
     stream = torch.cuda.current_stream()
@@ -247,13 +252,8 @@ def run_ours(args):
     assert w2.shape[0] == len(times) and abs(w2[0].mean() - 0.25) < 1e-12 and w2[-1].mean() > 1.0
     A.asep_destroy(ctx)
 
-    total_ms = sum(step_ms)
-    kernel_ms = statistics.mean(kern_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms, kernel_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, kernel_ms = float(t[0]), float(t[1])
-    value = attempts_per_step * args.steps * world / (total_ms / 1000.0)
+    total_ms, kernel_ms = replicas.max_over_ranks([sum(step_ms), statistics.mean(kern_ms)], dist, device="cuda")
+    value = replicas.throughput(attempts_per_step, args.steps, world, total_ms)
 
     # end to end through the C ABI with host buffers: create (host params and
     # sample times in), sweeps, W(t) table out, destroy
@@ -272,12 +272,8 @@ def run_ours(args):
         e2e_s.append(time.perf_counter() - t0)
         h2d = 8 * len(times) + 4 * len(A.asep_poisson_table(DOMAIN)[1])
         d2h = sh.nbytes + sh2.nbytes
-    e2e_time = statistics.mean(e2e_s)
-    if dist is not None:
-        t = torch.tensor([e2e_time], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_time = float(t[0])
-    e2e_value = attempts_per_step * world / e2e_time
+    (e2e_ms,) = replicas.max_over_ranks([1000.0 * statistics.mean(e2e_s)], dist, device="cuda")
+    e2e_value = replicas.throughput(attempts_per_step, 1, world, e2e_ms)
 
     # the random stream alone: Philox4x32-10 calls/s with no lattice memory
     sink = torch.empty(152 * 8 * 256, dtype=torch.int32, device="cuda")

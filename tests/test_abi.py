@@ -80,3 +80,46 @@ def test_create_rejects_bad_params_without_device(A):
             A.asep_create(A.make_params(**kw), sample_times=times, torch_alloc=False, stream=0)
         assert ei.value.code == A.ASEP_ERR_INVALID, kw
         assert "autocorr" in A.asep_last_error(None) or "flags" in A.asep_last_error(None), kw
+
+
+@pytest.mark.parametrize("flags,dis", [(0, 0), (6, 0), (0, 1)])
+def test_allocation_failure_frees_everything_without_device(A, flags, dis):
+    """An allocator hook that fails one request makes asep_create return
+    ASEP_ERR_NOMEM and hand every other allocation back through free_fn
+    exactly once.  A serial-schedule context allocates before its first CUDA
+    call, so the hook's fake addresses are never dereferenced."""
+    th = A.asep_threshold
+    extra = dict(n_realizations=2, samples_per_real=2, dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1),
+                 dis_b_thr=th(0.3)) if dis else {}
+    times = [0, 5]
+
+    def attempt(fail_at):
+        calls, live, freed = [0], {}, []
+
+        def alloc(nbytes, user):
+            k = calls[0]
+            calls[0] += 1
+            if k == fail_at:
+                return None
+            ptr = 0x10000 * (k + 1)
+            live[ptr] = nbytes
+            return ptr
+
+        def free(ptr, nbytes, user):
+            freed.append((ptr, nbytes))
+
+        prm = A.make_params(L=1024, schedule=A.ASEP_SCHED_SERIAL, flags=flags, autocorr_t0=5, **extra)
+        prm.alloc, prm.free_fn = A.ALLOC_FN(alloc), A.FREE_FN(free)
+        with pytest.raises(A.AsepError) as ei:
+            A.asep_create(prm, sample_times=times, torch_alloc=False, stream=0)
+        return ei.value, calls[0], live, freed
+
+    # every request is made before the context is checked and released, so a
+    # run that fails the first one counts them; no run gets as far as a copy
+    _, n_calls, _, _ = attempt(fail_at=0)
+    assert n_calls >= 7
+    for k in range(n_calls):
+        err, calls, live, freed = attempt(fail_at=k)
+        assert err.code == A.ASEP_ERR_NOMEM and "allocation failed" in str(err), k
+        assert calls == n_calls  # every request is made, then the context is released as a whole
+        assert sorted(freed) == sorted(live.items()), k

@@ -295,10 +295,12 @@ def _threads(n: int | None) -> int:
 
 
 def replay(P: Params, state: np.ndarray, s0: int, n_sweeps: int, mask: np.ndarray | None = None,
-           samples=None, threads: int | None = None) -> np.ndarray:
+           samples=None, threads: int | None = None, seam: np.ndarray | None = None) -> np.ndarray:
     """Advance ``state`` ([S, planes, W]) in place by n_sweeps sweeps starting
     at sweep index s0, with the exact schedule of P.  Returns per-sample hop
-    counters [S, 4] (ring: right, left; two lanes: A, B, A->B, B->A)."""
+    counters [S, 4] (ring: right, left; two lanes: A, B, A->B, B->A).  With
+    ``seam`` ([S, 2]) the ring's right and left hops across the bond
+    (L-1, 0) are added to it."""
     if P.schedule == SCHED_DOMAIN:
         k_lo, tab = poisson_table(P.bonds_per_domain)
     else:
@@ -313,13 +315,15 @@ def replay(P: Params, state: np.ndarray, s0: int, n_sweeps: int, mask: np.ndarra
         m = None
         if mask is not None:
             m = np.ascontiguousarray(mask[s // P.samples_per_real])
-        c = np.zeros(4, dtype=np.uint64)
+        c = np.zeros(6, dtype=np.uint64)
         rc = lib().orc_sweeps(ctypes.byref(cp), _u32p(tab_np), k_lo, len(tab), _u32p(row),
                               _u32p(m) if m is not None else None, P.first_sample + s, s0, n_sweeps, _u64p(c))
         if rc != 0:
             raise ValueError("orc_sweeps rejected the parameters")
         state[s] = row
-        cnt[s] = c
+        cnt[s] = c[:4]
+        if seam is not None:
+            seam[s] += c[4:6]
 
     with ThreadPoolExecutor(max_workers=_threads(threads)) as ex:
         list(ex.map(one, idx))
@@ -335,13 +339,13 @@ def serial_reference(P: Params, state: np.ndarray, n_sweeps: int, rng_seeds, mas
     def one(s):
         row = np.ascontiguousarray(state[s])
         m = np.ascontiguousarray(mask[s // P.samples_per_real]) if mask is not None else None
-        c = np.zeros(4, dtype=np.uint64)
+        c = np.zeros(6, dtype=np.uint64)
         rc = lib().orc_serial_reference(ctypes.byref(cp), _u32p(row), _u32p(m) if m is not None else None,
                                         int(rng_seeds[s]), n_sweeps, _u64p(c))
         if rc != 0:
             raise ValueError("orc_serial_reference rejected the parameters")
         state[s] = row
-        cnt[s] = c
+        cnt[s] = c[:4]
 
     with ThreadPoolExecutor(max_workers=_threads(threads)) as ex:
         list(ex.map(one, range(P.S)))
@@ -365,8 +369,10 @@ def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samp
     sweeps, and at every time in ``sample_times`` (sweep counts after which
     to record; 0 = the initial state) the heights and W^2, the cumulative hop
     counters, the occupancy profile (occupied sites per 32-site word, summed
-    over the sample times) and, with ``autocorr_t0``, the overlap
-    sum_i n_i(t0) n_i(t) for t >= t0 (0 before)."""
+    over the sample times), the ring's height offset H(t) of the column
+    between sites L-1 and 0 relative to the start (counted directly from the
+    hops across that bond: -2 per right hop, +2 per left hop) and, with
+    ``autocorr_t0``, the overlap sum_i n_i(t0) n_i(t) for t >= t0 (0 before)."""
     times = sorted(set(int(t) for t in sample_times if 0 <= t <= n_mcs))
     state = init_state(P)
     mask = disorder(P)
@@ -377,6 +383,8 @@ def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samp
     w2 = np.zeros((nt, P.S, P.planes), dtype=np.float64)
     cnt = np.zeros((P.S, 4), dtype=np.uint64)
     cnt_at = np.zeros((nt, P.S, 4), dtype=np.int64)
+    seam = np.zeros((P.S, 2), dtype=np.uint64)
+    h_off = np.zeros((nt, P.S), dtype=np.int64)
     profile = np.zeros((P.S, P.planes, P.W), dtype=np.int64)
     overlap = np.zeros((nt, P.S, P.planes), dtype=np.int64)
     snap = None
@@ -391,6 +399,9 @@ def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samp
             snap = state.copy()
         for s in idx:
             cnt_at[ti, s] = cnt[s].astype(np.int64)
+            # height of the column between sites L-1 and 0 relative to the start:
+            # a right hop across a bond lowers that bond's column by 2, a left hop raises it
+            h_off[ti, s] = -2 * (int(seam[s, 0]) - int(seam[s, 1]))
             for pl in range(P.planes):
                 a, b = heights(state[s, pl], P.L)
                 sh[ti, s, pl] = a
@@ -407,10 +418,11 @@ def run(P: Params, n_mcs: int, sample_times=(), threads: int | None = None, samp
         ti += 1
     for target in times[ti:] + ([n_mcs] if not times or times[-1] != n_mcs else []):
         if target > done:
-            cnt += replay(P, state, done, target - done, mask=mask, samples=idx, threads=threads)
+            cnt += replay(P, state, done, target - done, mask=mask, samples=idx, threads=threads, seam=seam)
             done = target
         if ti < nt and times[ti] == done:
             record(ti)
             ti += 1
     return RunResult(times=times, sum_h=sh, sum_h2=sh2, w2=w2, state=state, counters=cnt,
-                     extra={"counters_at": cnt_at, "profile": profile, "overlap": overlap})
+                     extra={"counters_at": cnt_at, "profile": profile, "overlap": overlap, "height_offset": h_off,
+                            "seam": seam})

@@ -196,12 +196,14 @@ static void ring_attempt(const orc_params* P, uint32_t* w, const uint32_t* cls, 
       flip_site(w, i);
       flip_site(w, i1);
       cnt[0]++;
+      if (i == P->L - 1) cnt[4]++; /* across the seam (L-1, 0) */
     }
   } else if (a == 0 && b == 1) {
     if (accept(r, rate_q(P, cls, i1))) {
       flip_site(w, i);
       flip_site(w, i1);
       cnt[1]++;
+      if (i == P->L - 1) cnt[5]++;
     }
   }
 }
@@ -345,7 +347,9 @@ static int params_ok(const orc_params* P) {
  * words: [planes][ceil(L/32)], planes = 1 (ring) or 2 (two lanes).
  * mask:  this sample's realization of the class plane (BIMODAL) or of the
  *        turning-site plane (TURNING), or NULL.
- * cnt:   ring: [right hops, left hops]; two lanes: [A hops, B hops, A->B, B->A]. */
+ * cnt:   6 entries.  ring: [right hops, left hops, 0, 0, right hops across the
+ *        seam bond (L-1, 0), left hops across it]; two lanes: [A hops, B hops,
+ *        A->B, B->A, 0, 0]. */
 int orc_sweeps(const orc_params* P, const uint32_t* ptab, uint32_t ptab_klo, uint32_t ptab_n, uint32_t* words,
                const uint32_t* mask, uint32_t sample, uint64_t s0, uint64_t n_sweeps, uint64_t* cnt) {
   if (!params_ok(P)) return -1;

@@ -293,3 +293,49 @@ def test_domain_schedule_width_within_3sigma_of_serial_reference(oracle_mod):
         for i in range(len(times)):
             sig = np.sqrt(all_dom[i].var(ddof=1) / P.S + all_ser[i].var(ddof=1) / P.S)
             assert abs(m_dom[i] - m_ser[i]) < 3 * sig, (p, times[i], m_dom[i], m_ser[i], sig)
+
+
+# ---------------------------------------------------------------------------
+# Absolute height: hops across the seam bond (L-1, 0)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_seam_counter_closes_the_height_balance(oracle_mod, schedule):
+    """A right hop across bond (i, i+1) lowers h_i by 2 and leaves every other
+    h_k of the open prefix sum unchanged, except across the seam (L-1, 0),
+    where it raises h_0 ... h_{L-2} by 2.  Hence, exactly,
+    sum h(t) - sum h(0) = -2 (R - Lh) + 2 L (R_seam - Lh_seam): the seam
+    counter is pinned by the recorded heights and total hop counters."""
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(L=256, D=32, schedule=schedule, samples_per_real=6, p_thr=th(0.7), q_thr=th(0.4), seed=5)
+    times = [0, 3, 10, 40]
+    r = oracle_mod.run(P, 40, times)
+    seam_moves = 0
+    for ti in range(len(times)):
+        for s in range(P.S):
+            dsum = int(r.sum_h[ti, s, 0]) - int(r.sum_h[0, s, 0])
+            R, Lh = r.extra["counters_at"][ti, s, :2]
+            h_off = int(r.extra["height_offset"][ti, s])
+            assert dsum == -2 * int(R - Lh) - P.L * h_off, (ti, s)
+            seam_moves += abs(h_off)
+    assert seam_moves > 0  # the seam was crossed in both directions over the run
+
+
+def test_seam_current_equals_exact_rsu_current(oracle_mod):
+    """Stationary net hops across the seam per sweep (serial RSU replay) equal
+    the exact ring current (p - q) N (L - N) / (L (L - 1)) of the uniform
+    measure; the column height there falls at twice that rate."""
+    L, p, q, S = 64, 0.75, 0.25, 64
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(L=L, schedule=1, samples_per_real=S, p_thr=th(p), q_thr=th(q), seed=11)
+    st = oracle_mod.init_state(P)
+    oracle_mod.replay(P, st, 0, 1500)  # burn-in past saturation (L^(3/2) = 512 sweeps)
+    seam = np.zeros((S, 2), dtype=np.uint64)
+    T = 3000
+    oracle_mod.replay(P, st, 1500, T, seam=seam)
+    j = (seam[:, 0].astype(float) - seam[:, 1].astype(float)) / T
+    jexp = (p - q) * (L // 2) * (L // 2) / (L * (L - 1))
+    assert abs(j.mean() - jexp) < 4 * j.std(ddof=1) / np.sqrt(S)
+    # a seam counted at the wrong bond (0, 1) still sees the same mean current,
+    # but the balance test above fails for it; here check the sign convention
+    assert j.mean() > 0.5 * jexp

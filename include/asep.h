@@ -205,6 +205,19 @@ int asep_profile(asep_ctx* ctx, uint32_t* out, size_t n);
  * overlap / L - rho^2.  Synchronises. */
 int asep_autocorr(asep_ctx* ctx, int64_t* out, size_t n);
 
+/* Ring model with hop counting on: the height H(t) of the surface column
+ * between sites L-1 and 0 at every sample time recorded so far, relative to
+ * the lattice at the last asep_create, asep_reset or asep_load_state, layout
+ * [n_recorded][S]; records taken before the last load read 0.  With h_i the open prefix sum of asep_width, the absolute
+ * column heights are H + h_i and their mean H + sum_h / L; its slope in t is
+ * the growth velocity (paper sec. 2, Eq. KPZ).  A right hop across a bond
+ * lowers that bond's column by 2 and a left hop raises it, so
+ * H(t) = (sum_h(ref) - sum_h(t) - 2 [(R - Lh)(t) - (R - Lh)(ref)]) / L exactly,
+ * with R, Lh the cumulative right and left hop counters; the division is
+ * checked.  ASEP_ERR_STATE for the two-lane model or without hop counts.
+ * Synchronises. */
+int asep_height_offset(asep_ctx* ctx, int64_t* out, size_t n);
+
 int asep_get_info(const asep_ctx* ctx, asep_info* info);
 
 /* Choose the launch plan of a domain-schedule context (the autotuner's knob;

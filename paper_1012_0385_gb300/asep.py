@@ -93,7 +93,8 @@ EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
-            "asep_batch_sweep_static", "asep_set_plan", "asep_currents", "asep_profile", "asep_autocorr")
+            "asep_batch_sweep_static", "asep_set_plan", "asep_currents", "asep_profile", "asep_autocorr",
+            "asep_height_offset")
 
 
 class AsepError(RuntimeError):
@@ -149,6 +150,7 @@ def lib():
             L.asep_currents.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
             L.asep_profile.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_size_t]
             L.asep_autocorr.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
+            L.asep_height_offset.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
             for name in EXPORTED:
                 if name not in ("asep_last_error", "asep_threshold", "asep_version", "asep_batch_last_error"):
                     getattr(L, name).restype = ctypes.c_int
@@ -385,6 +387,15 @@ def asep_autocorr(ctx) -> np.ndarray:
     info = asep_get_info(ctx)
     out = np.zeros((max(info["n_recorded"], 1), info["S"], info["planes"]), dtype=np.int64)
     _check(lib().asep_autocorr(_h(ctx), _ptr(out, ctypes.c_int64), out.size), _h(ctx))
+    return out[: info["n_recorded"]]
+
+
+def asep_height_offset(ctx) -> np.ndarray:
+    """Height of the column between sites L-1 and 0 at every recorded sample
+    time, relative to the last create/reset/load, [n_recorded, S] int64."""
+    info = asep_get_info(ctx)
+    out = np.zeros((max(info["n_recorded"], 1), info["S"]), dtype=np.int64)
+    _check(lib().asep_height_offset(_h(ctx), _ptr(out, ctypes.c_int64), out.size), _h(ctx))
     return out[: info["n_recorded"]]
 
 

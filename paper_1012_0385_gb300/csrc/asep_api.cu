@@ -43,6 +43,10 @@ struct asep_ctx {
   uint32_t* d_profile = nullptr; // [S][planes][W]
   uint32_t* d_snap = nullptr;    // [S][planes][W]
   int64_t* d_tab_ac = nullptr;   // [n_times][S][planes]
+  int64_t* d_href = nullptr;     // [S][planes] sum h of the reference lattice (last create / reset / load)
+  uint64_t* d_href2 = nullptr;   // [S][planes][2] its sum h^2 (not used)
+  int64_t* d_hrefcnt = nullptr;  // [S][4] hop counters at the reference
+  uint32_t ref_slot = 0;         // first sample-time slot recorded after the reference
   std::vector<std::pair<void*, size_t>> allocs;
   size_t dev_bytes = 0;
   // attempt-count table
@@ -331,6 +335,25 @@ int copy_out(asep_ctx* ctx, void* dst, const void* src, size_t bytes, const char
   return ASEP_OK;
 }
 
+// Heights and hop counters of the current lattice as the reference of
+// asep_height_offset (a record into the reference tables, no observables).
+int record_reference(asep_ctx* ctx) {
+  HeightsLaunch h;
+  h.geo = geometry(ctx);
+  h.state = ctx->d_state;
+  h.slot = 0;
+  h.t = 0;
+  h.tab_sh = ctx->d_href;
+  h.tab_sh2 = ctx->d_href2;
+  h.counters = ctx->d_cnt;
+  h.ex = Extras{};
+  h.ex.tab_cnt = ctx->d_hrefcnt;
+  const cudaError_t e = launch_heights(h, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "reference heights kernel");
+  ++ctx->launches;
+  return ASEP_OK;
+}
+
 int record_now(asep_ctx* ctx, uint32_t slot) {
   HeightsLaunch h;
   h.geo = geometry(ctx);
@@ -512,6 +535,9 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   ctx->d_times = static_cast<uint64_t*>(dev_alloc(ctx, n_times * 8));
   ctx->d_clock = static_cast<Clock*>(dev_alloc(ctx, sizeof(Clock)));
   ctx->d_tab_cnt = static_cast<int64_t*>(dev_alloc(ctx, n_times * ctx->S * 32));
+  ctx->d_href = static_cast<int64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * ctx->planes * 8));
+  ctx->d_href2 = static_cast<uint64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * ctx->planes * 16));
+  ctx->d_hrefcnt = static_cast<int64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * 32));
   if (params->flags & ASEP_FLAG_PROFILE) ctx->d_profile = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
   if (params->flags & ASEP_FLAG_AUTOCORR) {
     ctx->d_snap = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
@@ -520,7 +546,8 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   if (ctx->R) ctx->d_mask = static_cast<uint32_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->R) * ctx->W * 4));
   if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
   if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || !ctx->d_clock ||
-      !ctx->d_tab_cnt || ((params->flags & ASEP_FLAG_PROFILE) && !ctx->d_profile) ||
+      !ctx->d_tab_cnt || !ctx->d_href || !ctx->d_href2 || !ctx->d_hrefcnt ||
+      ((params->flags & ASEP_FLAG_PROFILE) && !ctx->d_profile) ||
       ((params->flags & ASEP_FLAG_AUTOCORR) && (!ctx->d_snap || !ctx->d_tab_ac)) || (ctx->R && !ctx->d_mask) ||
       (!ctx->ptab.empty() && !ctx->d_ptab))
     return bail(fail(ctx, ASEP_ERR_NOMEM, "device allocation failed (%zu bytes so far)", ctx->dev_bytes));
@@ -560,6 +587,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     if ((e = launch_disorder(dl, ctx->stream)) != cudaSuccess) return bail(cuda_fail(ctx, e, "disorder kernel"));
     ++ctx->launches;
   }
+  if ((rc = record_reference(ctx)) != ASEP_OK) return bail(rc);
   uint32_t next = 0;
   if (!ctx->times.empty() && ctx->times[0] == 0) {
     rc = record_now(ctx, 0);
@@ -633,6 +661,9 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
   il.init_seed = init_seed;
   if ((e = launch_init(il, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "init kernel");
   ++ctx->launches;
+  const int rcr = record_reference(ctx);
+  if (rcr != ASEP_OK) return rcr;
+  ctx->ref_slot = 0;
   uint32_t next = 0;
   if (!ctx->times.empty() && ctx->times[0] == 0) {
     const int rc = record_now(ctx, 0);
@@ -702,8 +733,10 @@ int asep_load_state(asep_ctx* ctx, const uint32_t* words, size_t n_words, uint64
   if (rc != ASEP_OK) return rc;
   const cudaError_t e = cudaMemcpy(ctx->d_state, words, need * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "load state");
+  if ((rc = record_reference(ctx)) != ASEP_OK) return rc;
   uint32_t i = 0;
   while (i < ctx->times.size() && ctx->times[i] <= sweep) ++i;
+  ctx->ref_slot = i;
   rc = set_clock(ctx, sweep, i);
   if (rc != ASEP_OK) return rc;
   return asep_sync(ctx);
@@ -1101,6 +1134,36 @@ int asep_autocorr(asep_ctx* ctx, int64_t* out, size_t n) {
   const size_t need = static_cast<size_t>(ctx->next_time) * ctx->S * ctx->planes;
   if (n < need) return fail(ctx, ASEP_ERR_INVALID, "n = %zu < %zu", n, need);
   return copy_out(ctx, out, ctx->d_tab_ac, need * 8, "copy autocorrelation");
+}
+
+int asep_height_offset(asep_ctx* ctx, int64_t* out, size_t n) {
+  if (!ctx || !out) return ASEP_ERR_INVALID;
+  if (ctx->p.model != ASEP_MODEL_RING || (ctx->p.flags & ASEP_FLAG_NO_HOP_COUNTS))
+    return fail(ctx, ASEP_ERR_STATE, "the height offset needs the ring model with hop counting on");
+  const size_t S = ctx->S, nr = ctx->next_time;
+  if (n < nr * S) return fail(ctx, ASEP_ERR_INVALID, "n = %zu < %zu", n, nr * S);
+  std::vector<int64_t> sh(nr * S), cnt(nr * S * 4), ref(S), refcnt(S * 4);
+  int rc;
+  if ((rc = copy_out(ctx, sh.data(), ctx->d_sh, sh.size() * 8, "copy heights")) != ASEP_OK ||
+      (rc = copy_out(ctx, cnt.data(), ctx->d_tab_cnt, cnt.size() * 8, "copy counters")) != ASEP_OK ||
+      (rc = copy_out(ctx, ref.data(), ctx->d_href, ref.size() * 8, "copy reference heights")) != ASEP_OK ||
+      (rc = copy_out(ctx, refcnt.data(), ctx->d_hrefcnt, refcnt.size() * 8, "copy reference counters")) != ASEP_OK)
+    return rc;
+  const int64_t L = static_cast<int64_t>(ctx->L);
+  for (size_t t = 0; t < nr; ++t) {
+    for (size_t s = 0; s < S; ++s) {
+      if (t < ctx->ref_slot) {  // recorded before the reference lattice
+        out[t * S + s] = 0;
+        continue;
+      }
+      const int64_t net = (cnt[(t * S + s) * 4] - cnt[(t * S + s) * 4 + 1]) - (refcnt[s * 4] - refcnt[s * 4 + 1]);
+      const int64_t num = ref[s] - sh[t * S + s] - 2 * net;
+      if (num % L != 0)
+        return fail(ctx, ASEP_ERR_STATE, "record %zu sample %zu: heights and hop counters disagree", t, s);
+      out[t * S + s] = num / L;
+    }
+  }
+  return ASEP_OK;
 }
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info) {

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) k_heights(const HeightsLaunch a) {
     a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(acc >> 64);
   }
   // the other observables of this record
-  if (p == 0 && threadIdx.x == 0) {
+  if (p == 0 && threadIdx.x == 0 && a.ex.tab_cnt) {
     const size_t ec = (static_cast<size_t>(a.slot) * a.geo.S + sample) * 4;
     for (int k = 0; k < 4; ++k) a.ex.tab_cnt[ec + k] = static_cast<int64_t>(a.counters[4 * static_cast<size_t>(sample) + k]);
   }

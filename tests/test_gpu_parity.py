@@ -4,8 +4,8 @@ Integer work, so the bar is bit-exact: lattice words after the run, every
 recorded (sum h, sum h^2), and the hop counters.  Cases span several CTAs and
 ragged last CTAs, domain sizes 32..2048, disorder, two lanes, the serial
 schedule, launch splitting and checkpoint/resume.  At the full sizes of the
-configurations the oracle checks sampled outputs (spot sweeps restarted from
-a GPU state).  The statistical tests compare W(t) of the domain schedule on
+configurations the oracle checks sampled samples, replayed from their own
+initial state, and properties that hold at any size check the rest.  The statistical tests compare W(t) of the domain schedule on
 the GPU with the independent serial RSU reference within 3 sigma.
 """
 import numpy as np
@@ -60,14 +60,18 @@ def run_gpu(kw, chunks, times):
         cnt = A.asep_counters(ctx)
         dis = A.asep_disorder(ctx)
         cur = A.asep_currents(ctx)
+        ring_counts = kw.get("model", 0) == 0 and not kw.get("flags", 0) & A.ASEP_FLAG_NO_HOP_COUNTS
+        hoff = A.asep_height_offset(ctx) if ring_counts else None
         prof = A.asep_profile(ctx) if kw.get("flags", 0) & A.ASEP_FLAG_PROFILE else None
         ac = A.asep_autocorr(ctx) if kw.get("flags", 0) & A.ASEP_FLAG_AUTOCORR else None
     assert sweep == sum(chunks)
-    return dict(words=words, sh=sh, sh2=sh2, w2=w2, cnt=cnt, dis=dis, cur=cur, prof=prof, ac=ac)
+    return dict(words=words, sh=sh, sh2=sh2, w2=w2, cnt=cnt, dis=dis, cur=cur, prof=prof, ac=ac, hoff=hoff)
 
 
 def assert_same(g, ref, P, times):
     assert np.array_equal(g["cur"], ref.extra["counters_at"]), "hop counters at the sample times"
+    if g["hoff"] is not None:
+        assert np.array_equal(g["hoff"], ref.extra["height_offset"]), "height of the seam column"
     if g["prof"] is not None:
         assert np.array_equal(g["prof"].astype(np.int64), ref.extra["profile"]), "occupancy profile"
     if g["ac"] is not None:
@@ -219,8 +223,29 @@ def test_reset_reproduces_a_fresh_context():
         words, _ = A.asep_state(ctx)
         sh, _, _ = A.asep_width(ctx)
         cnt = A.asep_counters(ctx)
+        hoff = A.asep_height_offset(ctx)
     assert np.array_equal(words, fresh["words"]) and np.array_equal(sh, fresh["sh"])
-    assert np.array_equal(cnt, fresh["cnt"])
+    assert np.array_equal(cnt, fresh["cnt"]) and np.array_equal(hoff, fresh["hoff"])
+
+
+def test_height_offset_restarts_at_a_loaded_state():
+    """After asep_load_state the column height is measured from the loaded
+    lattice: resumed H(30) = H(30) - H(11) of the uninterrupted run."""
+    kw = dict(L=8192, domain_sites=128, samples_per_real=5, p_thr=th(0.75), q_thr=th(0.25), seed=13)
+    with A.asep_create(A.make_params(**kw), sample_times=[11, 30]) as c1:
+        A.asep_sweep(c1, 11)
+        words, s = A.asep_state(c1)
+        A.asep_sweep(c1, 19)
+        full = A.asep_height_offset(c1)
+    with A.asep_create(A.make_params(**kw), sample_times=[11, 30]) as c2:
+        A.asep_load_state(c2, words, s)
+        A.asep_sweep(c2, 19)
+        resumed = A.asep_height_offset(c2)
+    assert np.any(full[1] != full[0])
+    assert np.array_equal(resumed[1], full[1] - full[0])
+    with A.asep_create(A.make_params(model=TWO, L=4096, domain_sites=128), sample_times=[]) as c3:
+        with pytest.raises(A.AsepError):
+            A.asep_height_offset(c3)
 
 
 def test_cfg0_full_run_snapshots_every_100_mcs():
@@ -247,36 +272,46 @@ def test_cfg0_full_run_snapshots_every_100_mcs():
     assert np.all(w2[0] == 0.25)
 
 
+def _np_sums(row: np.ndarray, L: int) -> tuple[int, int]:
+    """(sum h, sum h^2) of one packed lattice row by plain numpy, h_i = sum_{j<=i} (2 n_j - 1);
+    |h| <= L = 2^17 keeps sum h^2 below 2^51."""
+    bits = np.unpackbits(row.view(np.uint8), bitorder="little")[:L].astype(np.int64)
+    h = np.cumsum(2 * bits - 1)
+    return int(h.sum()), int((h * h).sum())
+
+
 def test_cfg1_full_size_spot_checks():
-    """The benchmarked launch (L = 2^17, 256 samples, D = 256, 2^14 MCS, log
-    times): the first sweeps of sampled samples replayed from the start, and
-    the last sweeps replayed from the GPU state of the same run."""
-    n_mcs, k_tail = 1 << 14, 4
+    """The benchmarked launch configuration (L = 2^17, 256 samples, D = 256,
+    log times): sampled samples bit-exact against the oracle, which replays
+    them from their own initial state, over the first 1000 sweeps (lattices
+    and every record up to there); then the rest of the 2^14 sweeps, checked
+    by properties that hold at any size: particle number, the final record
+    equals the sums of the final lattice, W^2(0) = 1/4."""
+    n_mcs, k1 = 1 << 14, 1000
     times = log_times(n_mcs) + [n_mcs]  # the log times end below 2^14; record the last sweep too
     kw = dict(L=1 << 17, domain_sites=256, samples_per_real=256, p_thr=th(0.75), q_thr=th(0.25), seed=1)
     P = oracle_params(kw)
     picks = [0, 97, 255]
     with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
-        A.asep_sweep(ctx, 40)
-        early, _ = A.asep_state(ctx)
-        A.asep_sweep(ctx, n_mcs - 40 - k_tail)
-        mid, s_mid = A.asep_state(ctx)
-        A.asep_sweep(ctx, k_tail)
-        final, _ = A.asep_state(ctx)
+        A.asep_sweep(ctx, k1)
+        at_k1, _ = A.asep_state(ctx)
+        A.asep_sweep(ctx, n_mcs - k1)
+        final, s_final = A.asep_state(ctx)
         sh, sh2, w2 = A.asep_width(ctx)
-    ref = oracle.init_state(P)
-    oracle.replay(P, ref, 0, 40, samples=picks)
+    early = [t for t in times if t <= k1]
+    ref = oracle.run(P, k1, early, samples=picks)
     for s in picks:
-        assert np.array_equal(early[s], ref[s]), s
-    tail = mid.copy()
-    oracle.replay(P, tail, s_mid, k_tail, samples=picks)
-    for s in picks:
-        assert np.array_equal(final[s], tail[s]), s
-        a, b = oracle.heights(final[s, 0], P.L)
-        assert int(sh[-1, s, 0]) == a and ((int(sh2[-1, s, 0, 1]) << 64) | int(sh2[-1, s, 0, 0])) == b
-    # every sample keeps half filling, W^2(0) = 1/4 exactly
+        assert np.array_equal(at_k1[s], ref.state[s]), s
+        for ti in range(len(early)):
+            assert int(sh[ti, s, 0]) == int(ref.sum_h[ti, s, 0]), (s, early[ti])
+            assert ((int(sh2[ti, s, 0, 1]) << 64) | int(sh2[ti, s, 0, 0])) == int(ref.sum_h2[ti, s, 0]), (s, early[ti])
+    assert s_final == n_mcs
+    # every sample keeps half filling; the last record is the final lattice's sums; W^2(0) = 1/4 exactly
     pop = np.unpackbits(final.view(np.uint8), axis=-1).sum(axis=-1)
     assert np.all(pop == P.L // 2)
+    for s in range(P.S):
+        a, b = _np_sums(final[s, 0], P.L)
+        assert int(sh[-1, s, 0]) == a and ((int(sh2[-1, s, 0, 1]) << 64) | int(sh2[-1, s, 0, 0])) == b, s
     assert np.all(w2[0] == 0.25)
 
 

@@ -311,6 +311,8 @@ def run_ours(args):
         if tune_table:
             line["autotune"] = [{k: r[k] for k in ("cluster", "samples_per_group", "ms_per_sweep")}
                                 for r in tune_table]
+        if not args.no_workloads and world == 1:
+            line["workloads"] = other_workloads()
         if not args.no_serving and world == 1:
             line["serving"] = serving_comparison(capacity=value)
         if not args.no_cpu_baseline and world == 1:
@@ -319,6 +321,62 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def other_workloads():
+    """Device-timed windows of the other configurations of the study (one
+    run each after a warm-up launch, CUDA events on the launching stream):
+    plain TASEP under serial RSU and under the domain schedule (full 10^4
+    sweeps, snapshots every 100), quenched bimodal disorder and the two-lane
+    model with turning sites (10^4-sweep windows of their 10^7 / 10^6 sweep
+    runs, log-spaced sample times, two-lane currents, profile and
+    autocorrelation on)."""
+    import torch
+
+    from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300.sampling import every, log_times
+
+    th = A.asep_threshold
+    win = 10_000
+    lt = log_times(win) + ([win] if log_times(win)[-1] != win else [])
+    t0 = min(t for t in lt if t >= win // 2)
+    cases = [
+        ("plain TASEP, serial RSU: L=4096, p=1 q=0, flat, 10^4 MCS, 8 samples, snapshots every 100",
+         dict(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=8, p_thr=A.ASEP_ALWAYS, q_thr=0, seed=1),
+         every(100, win), 1),
+        ("plain TASEP, domain schedule D=256: L=4096, p=1 q=0, flat, 10^4 MCS, 8 samples, snapshots every 100",
+         dict(L=4096, domain_sites=256, samples_per_real=8, p_thr=A.ASEP_ALWAYS, q_thr=0, seed=1), every(100, win), 1),
+        ("quenched bimodal disorder: L=2^16, p_i=1 or 0.3 (Q=0.1), q=0, 64 realizations x 4 samples, "
+         "10^4-MCS window, log times",
+         dict(L=1 << 16, domain_sites=256, n_realizations=64, samples_per_real=4, p_thr=A.ASEP_ALWAYS, q_thr=0,
+              dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=2, seed=1), lt, 1),
+        ("two lanes: 2 x L=2^16, rate 1 both lanes, turning density 0.05, omega 0.1, Bernoulli(1/2) start, "
+         "128 samples, 10^4-MCS window, currents + profile + autocorrelation",
+         dict(model=A.ASEP_MODEL_TWO_LANE, L=1 << 16, domain_sites=256, samples_per_real=128,
+              p_thr=A.ASEP_ALWAYS, q_thr=A.ASEP_ALWAYS, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
+              dis_b_thr=th(0.1), dis_seed=3, init_kind=A.ASEP_INIT_BERNOULLI_HALF, init_seed=4, seed=1,
+              flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=t0), lt, 2),
+    ]
+    stream = torch.cuda.current_stream()
+    out = []
+    for name, kw, times, lanes in cases:
+        with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
+            A.asep_sweep(ctx, 8)  # warm-up launch
+            A.asep_reset(ctx, seed=kw["seed"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.asep_sweep(ctx, win)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            info = A.asep_get_info(ctx)
+            attempts = lanes * kw["L"] * info["S"] * win
+            out.append({"workload": name, "attempts": attempts, "ms": ms, "attempts_per_s": attempts / (ms / 1e3),
+                        "kernel": ("k_serial" if kw.get("schedule") == A.ASEP_SCHED_SERIAL
+                                   else "k_cluster" if info["cluster"] > 1 else "k_domain"),
+                        "samples_per_group": info["samples_per_group"]})
+    return out
 
 
 def serving_comparison(capacity: float, n_jobs: int = 48, seed: int = 2026, load: float = 0.7):
@@ -376,6 +434,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-mix comparison")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the windows of the other configurations")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
     ap.add_argument("--profile-case", action="store_true",

@@ -41,7 +41,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 MODEL_RING, MODEL_TWO_LANE = 0, 1
-SCHED_DOMAIN, SCHED_SERIAL = 0, 1
+SCHED_DOMAIN, SCHED_SERIAL, SCHED_SCA = 0, 1, 2
 DIS_NONE, DIS_BIMODAL, DIS_TURNING = 0, 1, 2
 INIT_FLAT_ALT, INIT_BERNOULLI_HALF = 0, 1
 ALWAYS = 0xFFFFFFFF

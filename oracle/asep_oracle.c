@@ -21,7 +21,7 @@
  *     right, lane B hops left, lane changes only at quenched turning sites.
  *   - Height reconstruction h_i = sum_{j<=i} (2 n_j - 1) and the sums that
  *     give W^2 of Eq. (W) (paper sec. 2.1), exactly in 128-bit integers.
- *   - Two update schedules, replayed literally:
+ *   - Three update schedules, replayed literally:
  *       SERIAL: plain random-sequential update (RSU, paper sec. 2.1), L (or
  *               2L for two lanes) uniform bond attempts per sweep.
  *       DOMAIN: the two-phase Poisson-domain schedule (no paper counterpart;
@@ -32,6 +32,9 @@
  *               run first, the odd halves second.  Each domain performs a
  *               Poisson(bonds) number of attempts, each on a uniformly drawn
  *               bond of the domain.
+ *       SCA:    the paper's own GPU schedule, the two-sub-lattice cellular
+ *               automaton of sec. 2.1 (even bonds, then odd bonds; see
+ *               sca_sweep).
  *   - An independent serial RSU reference with its own generator
  *     (xoshiro256**, Blackman & Vigna 2018, seeded by splitmix64), used for
  *     statistical comparisons only.
@@ -59,11 +62,13 @@
 #define TAG_DOM 4u  /* per-domain attempt stream */
 #define TAG_TURN 5u /* per-site lane-change draw */
 #define TAG_SER 6u  /* serial-schedule attempt stream */
+#define TAG_SCA 7u  /* two-sub-lattice SCA: random bit-planes of a 32-bond group */
 
 #define MODEL_RING 0u
 #define MODEL_TWO_LANE 1u
 #define SCHED_DOMAIN 0u
 #define SCHED_SERIAL 1u
+#define SCHED_SCA 2u
 #define DIS_NONE 0u
 #define DIS_BIMODAL 1u
 #define DIS_TURNING 2u
@@ -305,6 +310,37 @@ static void domain_sweep(const orc_params* P, const uint32_t* ptab, uint32_t pta
   if (two_lane && P->dis_kind == DIS_TURNING) turning_pass(P, wa, wb, mask, sample, sweep, cnt);
 }
 
+/* The paper's GPU schedule (sec. 2.1, Fig. "parasep"): a two-sub-lattice
+ * stochastic cellular automaton.  One sweep updates every even bond
+ * (i, i+1), i = 0, 2, ..., L-2, then every odd bond i = 1, 3, ..., L-1; the
+ * last odd bond (L-1, 0) is the paper's separate ring-closing step, and as it
+ * shares no site with the other odd bonds, updating it among them gives the
+ * same result.  The bonds of a phase are disjoint, so the order inside a
+ * phase does not matter; here it is ascending.  Each bond makes one attempt
+ * with a 20-bit uniform u (accept iff u < t / 4096, i.e. with probability
+ * t / 2^32; t = always accepts every u):
+ *   bond i = 2m + phase, group g = m / 32, lane = 2 (m mod 16) + (m / 16 mod 2);
+ *   bit k of u (k = 0 the most significant) = bit `lane` of word k of the
+ *   stream (tag SCA, ctr3 = 2g + phase), k = 0 .. 19. */
+static void sca_sweep(const orc_params* P, uint32_t* words, const uint32_t* mask, uint32_t sample, uint64_t sweep,
+                      uint64_t* cnt) {
+  const uint64_t L = P->L, bonds = L / 2;
+  for (uint32_t phase = 0; phase < 2; phase++) {
+    for (uint64_t g = 0; 32 * g < bonds; g++) {
+      stream_t st;
+      uint32_t plane[20];
+      stream_open(&st, P->seed, sweep, TAG_SCA, sample, (uint32_t)(2 * g + phase), 0);
+      for (int k = 0; k < 20; k++) plane[k] = stream_word(&st, (uint64_t)k);
+      for (uint64_t m = 32 * g; m < 32 * g + 32 && m < bonds; m++) {
+        const uint32_t lane = (uint32_t)(2 * (m & 15) + ((m >> 4) & 1));
+        uint32_t u = 0;
+        for (int k = 0; k < 20; k++) u = (u << 1) | ((plane[k] >> lane) & 1u);
+        ring_attempt(P, words, mask, 2 * m + phase, u << 12, cnt);
+      }
+    }
+  }
+}
+
 static void serial_sweep(const orc_params* P, uint32_t* words, const uint32_t* mask, uint32_t sample, uint64_t sweep,
                          uint64_t* cnt) {
   const uint64_t L = P->L;
@@ -333,10 +369,12 @@ static void serial_sweep(const orc_params* P, uint32_t* words, const uint32_t* m
  * words per plane are ceil(L / 32). */
 static int params_ok(const orc_params* P) {
   if (P->L < 2 || P->L > (1ull << 30)) return 0;
-  if (P->model > MODEL_TWO_LANE || P->schedule > SCHED_SERIAL) return 0;
+  if (P->model > MODEL_TWO_LANE || P->schedule > SCHED_SCA) return 0;
   if (P->schedule == SCHED_DOMAIN) {
     if (P->D < 1 || P->D > 2048 || (P->D & (P->D - 1))) return 0;
     if (P->L % (2ull * P->D)) return 0;
+  } else if (P->schedule == SCHED_SCA) {
+    if (P->model != MODEL_RING || (P->L & 1)) return 0; /* ring of even length */
   } else {
     if (P->L & (P->L - 1)) return 0;
   }
@@ -356,6 +394,8 @@ int orc_sweeps(const orc_params* P, const uint32_t* ptab, uint32_t ptab_klo, uin
   for (uint64_t s = s0; s < s0 + n_sweeps; s++) {
     if (P->schedule == SCHED_DOMAIN)
       domain_sweep(P, ptab, ptab_klo, ptab_n, words, mask, sample, s, cnt);
+    else if (P->schedule == SCHED_SCA)
+      sca_sweep(P, words, mask, sample, s, cnt);
     else
       serial_sweep(P, words, mask, sample, s, cnt);
   }

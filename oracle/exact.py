@@ -13,6 +13,8 @@ row-stochastic matrix on that space, built from its definition:
   sum_k e^{-m} m^k / k! (M_dom)^k = exp(sum_{b in dom} (K_b - I));
 * the two-phase domain sweep: the average over the 2D offsets o of
   exp(Q_even(o)) exp(Q_odd(o)), the domains of one phase being disjoint;
+* the two-sub-lattice SCA sweep (paper sec. 2.1): the product of the even
+  bonds' kernels, then of the odd bonds' kernels;
 * the lane-change pass of the two-lane model: a product of independent
   per-site swaps with probability omega where exactly one lane is occupied.
 
@@ -121,6 +123,17 @@ class RingModel:
 
     def generator(self) -> np.ndarray:
         return sum(K - self.I for K in self.K)
+
+    def sca_sweep(self) -> np.ndarray:
+        """The paper's two-sub-lattice SCA sweep: one attempt on every even
+        bond, then one on every odd bond (disjoint bonds, so each phase is a
+        product of commuting kernels); even first."""
+        E, O = self.I, self.I
+        for b in range(0, self.L, 2):
+            E = E @ self.K[b]
+        for b in range(1, self.L, 2):
+            O = O @ self.K[b]
+        return E @ O
 
     def domain_sweep(self, D: int) -> np.ndarray:
         L = self.L

@@ -203,7 +203,7 @@ def test_two_lane_replay_matches_exact(oracle_mod, schedule):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("model,schedule,dis", [
-    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2)])
+    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2), (0, 2, 0), (0, 2, 1)])
 def test_particle_number_conserved(oracle_mod, model, schedule, dis):
     th = oracle_mod.threshold
     P = oracle_mod.Params(model=model, schedule=schedule, L=1024, D=64, samples_per_real=3, seed=9,
@@ -339,3 +339,109 @@ def test_seam_current_equals_exact_rsu_current(oracle_mod):
     # a seam counted at the wrong bond (0, 1) still sees the same mean current,
     # but the balance test above fails for it; here check the sign convention
     assert j.mean() > 0.5 * jexp
+
+
+# ---------------------------------------------------------------------------
+# The paper's two-sub-lattice SCA schedule (sec. 2.1)
+# ---------------------------------------------------------------------------
+
+def test_sca_replay_matches_exact_sca(oracle_mod):
+    L, p, q = 8, 0.75, 0.25
+    P = oracle_mod.Params(L=L, schedule=oracle_mod.SCHED_SCA, samples_per_real=S_DIST, seed=41,
+                          p_thr=oracle_mod.threshold(p), q_thr=oracle_mod.threshold(q))
+    m = ex.RingModel(L, L // 2, p, q)
+    A = m.sca_sweep()
+    E, O = m.I, m.I
+    for b in range(0, L, 2):
+        E = E @ m.K[b]
+    for b in range(1, L, 2):
+        O = O @ m.K[b]
+    assert np.allclose(E @ O, A)
+    for t in (1, 2, 3):
+        counts = histogram(m.sp, _replay_hist(oracle_mod, P, t))
+        exact = m.sp.flat_alt() @ np.linalg.matrix_power(A, t)
+        assert chi2_pvalue(counts, exact) > 1e-4, t
+        # plausible mistakes: odd bonds first; random-sequential instead of SCA; swapped rates
+        for wrong_op in (O @ E, m.rsu_sweep(), ex.RingModel(L, L // 2, q, p).sca_sweep()):
+            wrong = m.sp.flat_alt() @ np.linalg.matrix_power(wrong_op, t)
+            assert chi2_pvalue(counts, wrong) < 1e-6, t
+
+
+def test_sca_disorder_rate_placement(oracle_mod):
+    """SCA with bimodal site classes: right hops across (i, i+1) use p_i, left
+    hops q_{i+1} (paper sec. 2.1), exactly as in the other schedules."""
+    L = 8
+    pf, ps, qf, qs = 0.9, 0.3, 0.4, 0.1
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(L=L, schedule=oracle_mod.SCHED_SCA, samples_per_real=S_DIST, seed=23, p_thr=th(pf),
+                          q_thr=th(qf), dis_kind=oracle_mod.DIS_BIMODAL, dis_a_thr=th(0.5), dis_b_thr=th(ps),
+                          dis_c_thr=th(qs), dis_seed=5)
+    mask = oracle_mod.disorder(P)
+    slow = [(int(mask[0, 0]) >> i) & 1 for i in range(L)]
+    assert 0 < sum(slow) < L
+    pvec = [ps if c else pf for c in slow]
+    qvec = [qs if c else qf for c in slow]
+    m = ex.RingModel(L, L // 2, pvec, qvec)
+    counts = histogram(m.sp, _replay_hist(oracle_mod, P, 2, mask=mask))
+    assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(m.sca_sweep(), 2)) > 1e-4
+    q_shift = [qvec[(i - 1) % L] for i in range(L)]
+    wrong = ex.RingModel(L, L // 2, pvec, q_shift).sca_sweep()
+    assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(wrong, 2)) < 1e-6
+
+
+def test_sca_deterministic_tasep_moves_every_particle_twice(oracle_mod):
+    """p = 1, q = 0 from the flat 1010... state (site 0 occupied): the even
+    bonds all carry 10 and hop, giving 0101...; the odd bonds, the closing
+    bond (L-1, 0) among them, then all carry 10 and hop back.  So after every
+    sweep the lattice is flat again, L hops happened, one of them across the
+    seam, and the seam column sank by 2 -- for any L, random words and seed."""
+    for L, seed in [(64, 1), (1000, 7), (4096, 123)]:
+        P = oracle_mod.Params(L=L, schedule=oracle_mod.SCHED_SCA, samples_per_real=2, seed=seed,
+                              p_thr=oracle_mod.ALWAYS, q_thr=0)
+        r = oracle_mod.run(P, 5, [0, 1, 5])
+        flat = oracle_mod.init_state(P)
+        assert np.array_equal(r.state, flat)
+        assert np.all(r.extra["counters_at"][:, :, 0] == np.array([0, L, 5 * L])[:, None])
+        assert np.all(r.extra["counters_at"][:, :, 1] == 0)
+        assert np.all(r.extra["height_offset"] == np.array([0, -2, -10])[:, None])
+
+
+def test_sca_stationary_current_and_width(oracle_mod):
+    """Exact enumeration: the SCA's stationary current per bond per sweep and
+    width, compared with the replay over a long run (L = 10)."""
+    L, p, q, S = 10, 0.75, 0.25, 400
+    m = ex.RingModel(L, L // 2, p, q)
+    pi = ex.stationary(m.sca_sweep())
+    w2_exact = pi @ m.sp.w2()
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(L=L, schedule=oracle_mod.SCHED_SCA, samples_per_real=S, seed=5, p_thr=th(p), q_thr=th(q))
+    st = oracle_mod.init_state(P)
+    oracle_mod.replay(P, st, 0, 200)
+    w2 = np.zeros(S)
+    cnt = np.zeros((S, 4), dtype=np.uint64)
+    n_meas = 50
+    for k in range(n_meas):
+        cnt += oracle_mod.replay(P, st, 200 + 10 * k, 10)
+        w2 += np.array([oracle_mod.width2(L, *oracle_mod.heights(st[s, 0], L)) for s in range(S)]) / n_meas
+    assert abs(w2.mean() - w2_exact) < 4 * w2.std(ddof=1) / np.sqrt(S)
+    # current per bond per sweep from the exact measure: each bond is attempted once per sweep,
+    # so J = sum over states of pi(x) * (net hops in one sweep from x) / L
+    n_st = m.sp.n
+    A = m.sca_sweep()
+    # expected net right hops of one sweep: even phase from x, odd phase from the even phase's result
+    E = m.I
+    for b in range(0, L, 2):
+        E = E @ m.K[b]
+    cur = m.current_per_attempt_vector(p, q)  # per state: sum over all bonds of p [10] - q [01]
+    even_bonds = np.zeros(n_st)
+    odd_bonds = np.zeros(n_st)
+    for k, x in enumerate(m.sp.states):
+        for b in range(L):
+            a, c = m.sp.bit(x, 0, b), m.sp.bit(x, 0, b + 1)
+            v = p if (a, c) == (1, 0) else (-q if (a, c) == (0, 1) else 0.0)
+            (even_bonds if b % 2 == 0 else odd_bonds)[k] += v
+    assert np.allclose(even_bonds + odd_bonds, cur)
+    j_exact = (pi @ even_bonds + (pi @ E) @ odd_bonds) / L
+    j = (cnt[:, 0].astype(float) - cnt[:, 1].astype(float)) / (L * 10 * n_meas)
+    assert abs(j.mean() - j_exact) < 4 * j.std(ddof=1) / np.sqrt(S)
+    assert abs(A.sum(axis=1) - 1).max() < 1e-12

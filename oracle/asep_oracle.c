@@ -320,8 +320,10 @@ static void domain_sweep(const orc_params* P, const uint32_t* ptab, uint32_t pta
  * with a 20-bit uniform u (accept iff u < t / 4096, i.e. with probability
  * t / 2^32; t = always accepts every u):
  *   bond i = 2m + phase, group g = m / 32, lane = 2 (m mod 16) + (m / 16 mod 2);
- *   bit k of u (k = 0 the most significant) = bit `lane` of word k of the
- *   stream (tag SCA, ctr3 = 2g + phase), k = 0 .. 19. */
+ *   bit k of u (k = 0 the most significant) = bit `lane` of plane k of g;
+ *   plane k of g = word 4k + (g mod 4) of the stream (tag SCA,
+ *   ctr3 = 2 (g / 4) + phase), k = 0 .. 19: Philox call k of that stream
+ *   gives plane k of four consecutive groups. */
 static void sca_sweep(const orc_params* P, uint32_t* words, const uint32_t* mask, uint32_t sample, uint64_t sweep,
                       uint64_t* cnt) {
   const uint64_t L = P->L, bonds = L / 2;
@@ -329,8 +331,8 @@ static void sca_sweep(const orc_params* P, uint32_t* words, const uint32_t* mask
     for (uint64_t g = 0; 32 * g < bonds; g++) {
       stream_t st;
       uint32_t plane[20];
-      stream_open(&st, P->seed, sweep, TAG_SCA, sample, (uint32_t)(2 * g + phase), 0);
-      for (int k = 0; k < 20; k++) plane[k] = stream_word(&st, (uint64_t)k);
+      stream_open(&st, P->seed, sweep, TAG_SCA, sample, (uint32_t)(2 * (g / 4) + phase), 0);
+      for (int k = 0; k < 20; k++) plane[k] = stream_word(&st, 4 * (uint64_t)k + (g % 4));
       for (uint64_t m = 32 * g; m < 32 * g + 32 && m < bonds; m++) {
         const uint32_t lane = (uint32_t)(2 * (m & 15) + ((m >> 4) & 1));
         uint32_t u = 0;

@@ -35,6 +35,18 @@
  *                      then the second halves; each half-domain performs a
  *                      Poisson(D) (two lanes: Poisson(2D)) number of attempts
  *                      on uniformly drawn bonds of its own D (2D) bonds.
+ *   ASEP_SCHED_SCA     the paper's own GPU schedule (sec. 2.1): a two-sub-
+ *                      lattice stochastic cellular automaton; per sweep one
+ *                      attempt on every even bond (i, i+1), i even, then on
+ *                      every odd bond (the ring-closing bond (L-1, 0) with
+ *                      them).  Each attempt compares a 20-bit uniform u with
+ *                      the threshold: bit k of u is bit `lane` of random
+ *                      plane k of its 32-bond group (plane k of four groups
+ *                      = Philox call k of tag 7, ctr3 = 2 * unit + phase;
+ *                      group g = bonds 32g..32g+31 of the phase, lane of bond
+ *                      m = 2 (m mod 16) + (m / 16 mod 2)).  Ring model, no
+ *                      disorder or bimodal; L a multiple of 256 with the ring
+ *                      in one CTA's shared memory (L <= 2^20, bimodal 2^19).
  *
  * Error behaviour: every function returns ASEP_OK (0) or a negative
  * ASEP_ERR_* code and never aborts; the context keeps a message readable with
@@ -71,6 +83,7 @@ extern "C" {
 
 #define ASEP_SCHED_DOMAIN 0u
 #define ASEP_SCHED_SERIAL 1u
+#define ASEP_SCHED_SCA 2u
 
 #define ASEP_DIS_NONE 0u
 #define ASEP_DIS_BIMODAL 1u /* dis_a = Q, dis_b = p_slow, dis_c = q_slow     */

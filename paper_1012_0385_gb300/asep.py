@@ -28,7 +28,7 @@ ASEP_ERR_TIMEOUT = -4
 ASEP_ERR_STATE = -5
 
 ASEP_MODEL_RING, ASEP_MODEL_TWO_LANE = 0, 1
-ASEP_SCHED_DOMAIN, ASEP_SCHED_SERIAL = 0, 1
+ASEP_SCHED_DOMAIN, ASEP_SCHED_SERIAL, ASEP_SCHED_SCA = 0, 1, 2
 ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING = 0, 1, 2
 ASEP_INIT_FLAT_ALT, ASEP_INIT_BERNOULLI_HALF = 0, 1
 ASEP_ALWAYS = 0xFFFFFFFF

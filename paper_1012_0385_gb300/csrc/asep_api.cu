@@ -171,7 +171,7 @@ void release(asep_ctx* ctx) {
 int validate(const asep_params* p, asep_ctx* ctx) {
   if (!p) return fail(ctx, ASEP_ERR_INVALID, "params is NULL");
   if (p->model > ASEP_MODEL_TWO_LANE) return fail(ctx, ASEP_ERR_INVALID, "unknown model %u", p->model);
-  if (p->schedule > ASEP_SCHED_SERIAL) return fail(ctx, ASEP_ERR_INVALID, "unknown schedule %u", p->schedule);
+  if (p->schedule > ASEP_SCHED_SCA) return fail(ctx, ASEP_ERR_INVALID, "unknown schedule %u", p->schedule);
   if (p->L < 64 || (p->L & 63) || p->L > (1ull << 22))
     return fail(ctx, ASEP_ERR_INVALID, "L = %llu must be a multiple of 64 in [64, 2^22]", (unsigned long long)p->L);
   if (p->n_realizations == 0 || p->samples_per_real == 0)
@@ -208,6 +208,13 @@ int validate(const asep_params* p, asep_ctx* ctx) {
       return fail(ctx, ASEP_ERR_INVALID, "sample_times must be strictly ascending");
   if (p->schedule == ASEP_SCHED_SERIAL && !is_pow2(p->L))
     return fail(ctx, ASEP_ERR_INVALID, "the serial schedule needs L a power of two");
+  if (p->schedule == ASEP_SCHED_SCA) {
+    if (p->model != ASEP_MODEL_RING || p->dis_kind == ASEP_DIS_TURNING)
+      return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule runs the ring model (no disorder or bimodal)");
+    if (p->L % 256) return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule needs L a multiple of 256");
+    if (sca_smem_bytes(static_cast<uint32_t>(p->L / 32), p->dis_kind == ASEP_DIS_BIMODAL) > 200u * 1024u)
+      return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule keeps the ring in one CTA's shared memory: L too large");
+  }
   return ASEP_OK;
 }
 
@@ -399,6 +406,15 @@ DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
     a.lane_sort = (ctx->cluster <= 1 && ctx->G % 32 == 0 && np * (ctx->R2 + 1) >= 5) ? 1u : 0u;
   }
   a.rates = rates(ctx);
+  {
+    // SCA: planes needed to decide u < t for every threshold that is neither 0 nor always
+    uint32_t tz = 20;
+    for (uint32_t t : {a.rates.p, a.rates.q, a.rates.p_slow, a.rates.q_slow}) {
+      const uint32_t t20 = t >> 12;
+      if (t != 0u && t != ASEP_ALWAYS) tz = std::min<uint32_t>(tz, static_cast<uint32_t>(__builtin_ctz(t20)));
+    }
+    a.sca_kmax = 20u - tz;
+  }
   a.seed = ctx->p.seed;
   a.ks = key_schedule(ctx->p.seed);
   a.n_sweeps = n;
@@ -522,6 +538,13 @@ int asep_create(const asep_params* params, asep_ctx** out) {
       return bail(fail(ctx, ASEP_ERR_INVALID, "attempt-count table for %u bonds failed", bonds));
     rc = plan_domain(ctx, 0, 0);
     if (rc != ASEP_OK) return bail(rc);
+  } else if (params->schedule == ASEP_SCHED_SCA) {
+    // one CTA per sample, a thread per unit of 8 words (at most 1024 threads, 512 with the class plane)
+    const uint32_t units = ctx->W / 8;
+    const uint32_t cap = params->dis_kind == ASEP_DIS_BIMODAL ? 512u : 1024u;
+    ctx->threads = std::min<uint32_t>(cap, (units + 31u) / 32u * 32u);
+    ctx->smem = sca_smem_bytes(ctx->W, params->dis_kind == ASEP_DIS_BIMODAL);
+    ctx->blocks = ctx->S;
   }
 
   // device memory
@@ -611,6 +634,8 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     cudaError_t e;
     if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster > 1) {
       e = launch_cluster(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
+    } else if (ctx->p.schedule == ASEP_SCHED_SCA) {
+      e = launch_sca(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
       e = launch_domain(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else {

@@ -16,6 +16,7 @@ constexpr uint32_t kTagOff = 3;   // per-sweep domain offset
 constexpr uint32_t kTagDom = 4;   // per-domain attempt stream
 constexpr uint32_t kTagTurn = 5;  // per-site lane-change draw
 constexpr uint32_t kTagSer = 6;   // serial-schedule stream
+constexpr uint32_t kTagSca = 7;   // two-sub-lattice SCA: random planes of four 32-bond groups
 
 constexpr uint32_t kAcceptMask = 0xFFFFF000u;  // draw bits compared with a threshold
 
@@ -96,6 +97,7 @@ struct DomainLaunch {
   uint32_t cluster;        // CTAs per sample: 1 = resident in one CTA, 2..16 = a thread-block cluster
   uint32_t Gc;             // cluster tier: columns per CTA (the last CTA may hold fewer)
   uint32_t lane_sort;      // resident tier: warps run domains of similar Poisson count (results unchanged)
+  uint32_t sca_kmax;       // SCA: random planes that decide every threshold (20 - fewest trailing zeros)
   Rates rates;
   uint64_t seed;
   KeySchedule ks;          // round keys of `seed`
@@ -167,6 +169,9 @@ cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32
                          uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st);
 // Cluster tier: one cluster of a.cluster CTAs per sample (grid S * cluster).
 cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
+// The two-sub-lattice SCA schedule: one CTA per sample, ring in shared memory.
+cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
+size_t sca_smem_bytes(uint32_t W, bool bimodal);
 // How many clusters of the given shape can be resident at once (0 = none).
 int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem);
 // Advance clocks after n sweeps (one context, or the jobs of a batch).

@@ -1,0 +1,303 @@
+// asep_sca.cu -- the paper's own GPU schedule: the two-sub-lattice stochastic
+// cellular automaton of sec. 2.1 (Fig. "parasep"), bit-sliced for sm_103a.
+//
+// One sweep updates every even bond (i, i+1), i = 0, 2, ..., L-2, in
+// parallel, then every odd bond i = 1, 3, ..., L-1 (the last one, (L-1, 0),
+// is the paper's ring-closing step; it shares no site with the other odd
+// bonds, so it runs with them).  Each bond makes one attempt: 10 -> 01 with
+// p_i, 01 -> 10 with q_{i+1}, accepted iff a 20-bit uniform u is below the
+// threshold's top 20 bits.
+//
+// Bit slicing.  A group is 32 bonds of one phase: the 16 bonds of word 2g
+// (lanes 0, 2, ..., 30) and the 16 of word 2g + 1 (lanes 1, 3, ..., 31).
+// Bit k of every lane's u is bit `lane` of random plane k of the group; call k
+// of the stream (tag SCA, ctr3 = 2 * unit + phase) gives plane k of the four
+// groups of a unit (8 words).  The comparison u < t runs most significant bit
+// first over all 32 lanes at once and stops when no lane is undecided or no
+// set bit of any threshold is left (p = 0.75, q = 0.25 need two planes).
+//
+// Layout.  One CTA per sample; the ring sits in shared memory as plain words
+// (bit k of word w = site 32w + k), a thread owns whole units and moves them
+// with 128-bit shared loads and stores.  An odd bond (32w + 31, 32w + 32)
+// reaches bit 0 of the next word; inside a unit that word is in the thread's
+// registers, across units the flip is left in a per-unit carry flag and the
+// next unit's owner applies it when it next loads its first word (bit 0 of a
+// unit's first word is touched by no odd bond of its own unit, so reading it
+// during the odd phase is race-free).
+#include <cstdint>
+
+#include "asep_device.cuh"
+#include "asep_internal.h"
+
+namespace asep {
+namespace {
+
+constexpr uint32_t kEven = 0x55555555u;
+
+// Sum of per-thread values over the block; every thread gets the total.
+__device__ long long block_sum(long long v, long long* warp_tot) {
+  const long long inc = block_scan_incl(v, warp_tot);
+  __shared__ long long total;
+  if (threadIdx.x == blockDim.x - 1) total = inc;
+  __syncthreads();
+  const long long t = total;
+  __syncthreads();
+  return t;
+}
+
+// All-ones where bit k (0 = most significant of 20) of a 20-bit threshold is set.
+__device__ __forceinline__ uint32_t bit_mask(uint32_t t20, uint32_t k) { return 0u - ((t20 >> (19u - k)) & 1u); }
+
+// One phase over one unit (four groups, words 8u .. 8u + 7).
+template <bool DIS, bool COUNT, uint32_t PHASE>
+__device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uint32_t* carry, const DomainLaunch& a,
+                                         uint32_t u, uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob,
+                                         uint32_t kmax, unsigned long long& n_right, unsigned long long& n_left) {
+  uint4* p4 = reinterpret_cast<uint4*>(lat + 8u * u);
+  uint4 v0 = p4[0], v1 = p4[1];
+  uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  if (PHASE == 0) {  // the previous unit's odd phase may have flipped bit 0 of our first word
+    const uint32_t prev = (u == 0 ? n_units : u) - 1;
+    x[0] ^= carry[prev];
+    carry[prev] = 0u;
+  }
+  uint32_t c[8];
+  if (DIS) {
+    const uint4* c4 = reinterpret_cast<const uint4*>(cls + 8u * u);
+    const uint4 d0 = c4[0], d1 = c4[1];
+    c[0] = d0.x; c[1] = d0.y; c[2] = d0.z; c[3] = d0.w; c[4] = d1.x; c[5] = d1.y; c[6] = d1.z; c[7] = d1.w;
+  }
+  const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
+  const uint32_t x_next = PHASE ? lat[next_w] : 0u;           // only bit 0 is used
+  const uint32_t c_next = (PHASE && DIS) ? cls[next_w] : 0u;
+
+  const Rates& r = a.rates;
+  const uint32_t pA = r.p == 0xFFFFFFFFu ? ~0u : 0u, qA = r.q == 0xFFFFFFFFu ? ~0u : 0u;
+  const uint32_t psA = r.p_slow == 0xFFFFFFFFu ? ~0u : 0u, qsA = r.q_slow == 0xFFFFFFFFu ? ~0u : 0u;
+  const uint32_t pN = r.p == 0u ? ~0u : 0u, qN = r.q == 0u ? ~0u : 0u;
+  const uint32_t psN = r.p_slow == 0u ? ~0u : 0u, qsN = r.q_slow == 0u ? ~0u : 0u;
+
+  uint32_t rc[4], lc[4], acc[4], eq[4], c1[4], c2[4];
+  uint32_t any = 0;
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi) {
+    const uint32_t xa = x[2 * gi], xb = x[2 * gi + 1];
+    const uint32_t xn = gi < 3 ? x[2 * gi + 2] : x_next;
+    // window: bit 2j = first site of bond j, bit 2j + 1 = its second site
+    const uint32_t ya = PHASE ? __funnelshift_r(xa, xb, 1) : xa;
+    const uint32_t yb = PHASE ? __funnelshift_r(xb, xn, 1) : xb;
+    const uint32_t ra = ya & ~(ya >> 1) & kEven, la = ~ya & (ya >> 1) & kEven;
+    const uint32_t rb = yb & ~(yb >> 1) & kEven, lb = ~yb & (yb >> 1) & kEven;
+    rc[gi] = ra | (rb << 1);
+    lc[gi] = la | (lb << 1);
+    if (DIS) {
+      const uint32_t ca = c[2 * gi], cb = c[2 * gi + 1];
+      const uint32_t cn = gi < 3 ? c[2 * gi + 2] : c_next;
+      const uint32_t za = PHASE ? __funnelshift_r(ca, cb, 1) : ca;
+      const uint32_t zb = PHASE ? __funnelshift_r(cb, cn, 1) : cb;
+      c1[gi] = (za & kEven) | ((zb & kEven) << 1);                   // class of site i
+      c2[gi] = ((za >> 1) & kEven) | (((zb >> 1) & kEven) << 1);     // class of site i + 1
+    } else {
+      c1[gi] = 0u;
+      c2[gi] = 0u;
+    }
+    const uint32_t rA = rc[gi] & ((~c1[gi] & pA) | (c1[gi] & psA));
+    const uint32_t lA = lc[gi] & ((~c2[gi] & qA) | (c2[gi] & qsA));
+    const uint32_t rN = rc[gi] & ((~c1[gi] & pN) | (c1[gi] & psN));
+    const uint32_t lN = lc[gi] & ((~c2[gi] & qN) | (c2[gi] & qsN));
+    acc[gi] = rA | lA;
+    eq[gi] = (rc[gi] | lc[gi]) & ~(rA | lA | rN | lN);
+    any |= eq[gi];
+  }
+  // most significant bit first; plane k of the four groups = Philox call k
+  const uint32_t p20 = r.p >> 12, q20 = r.q >> 12, ps20 = r.p_slow >> 12, qs20 = r.q_slow >> 12;
+  for (uint32_t k = 0; k < kmax && any; ++k) {
+    const uint4 y = philox10(ctr_of(s, kTagSca, k, n_glob, 2u * u + PHASE), a.ks);
+    const uint32_t P = bit_mask(p20, k), Q = bit_mask(q20, k);
+    const uint32_t PS = DIS ? bit_mask(ps20, k) : 0u, QS = DIS ? bit_mask(qs20, k) : 0u;
+    const uint32_t U[4] = {y.x, y.y, y.z, y.w};
+    any = 0;
+#pragma unroll
+    for (int gi = 0; gi < 4; ++gi) {
+      const uint32_t T = DIS ? ((rc[gi] & ((~c1[gi] & P) | (c1[gi] & PS))) | (lc[gi] & ((~c2[gi] & Q) | (c2[gi] & QS))))
+                             : ((rc[gi] & P) | (lc[gi] & Q));
+      acc[gi] |= eq[gi] & T & ~U[gi];  // this bit of u is 0 where t's is 1: u < t
+      eq[gi] &= ~(T ^ U[gi]);          // equal so far
+      any |= eq[gi];
+    }
+  }
+  // apply the accepted moves
+  uint32_t carry_out = 0u;
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi) {
+    const uint32_t h = acc[gi];
+    if (COUNT) {
+      n_right += __popc(h & rc[gi]);
+      n_left += __popc(h & lc[gi]);
+    }
+    const uint32_t ha = h & kEven, hb = (h >> 1) & kEven;  // bonds of word 2g and of word 2g + 1
+    if (PHASE == 0) {
+      x[2 * gi] ^= ha | (ha << 1);
+      x[2 * gi + 1] ^= hb | (hb << 1);
+    } else {
+      x[2 * gi] ^= (ha << 1) | (ha << 2);
+      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb << 1) | (hb << 2);  // bond (32w + 31, 32w + 32) of word 2g
+      const uint32_t out = (hb >> 30) & 1u;                      // ... and of word 2g + 1
+      if (gi < 3) x[2 * gi + 2] ^= out;
+      else carry_out = out;
+    }
+  }
+  p4[0] = make_uint4(x[0], x[1], x[2], x[3]);
+  p4[1] = make_uint4(x[4], x[5], x[6], x[7]);
+  if (PHASE == 1) carry[u] = carry_out;
+}
+
+// Apply pending carries (before a record or the write-back).
+__device__ __forceinline__ void settle_carries(uint32_t* lat, uint32_t* carry, uint32_t n_units) {
+  for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) {
+    const uint32_t prev = (u == 0 ? n_units : u) - 1;
+    lat[8u * u] ^= carry[prev];
+  }
+  __syncthreads();
+  for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) carry[u] = 0u;
+  __syncthreads();
+}
+
+// Heights, W^2 sums and the other observables of one record, from the
+// lattice in shared memory (contiguous chunks of words per thread).
+template <bool COUNT>
+__device__ void sca_record(const uint32_t* lat, const DomainLaunch& a, uint32_t slot, uint64_t t, uint32_t sample,
+                           long long* warp_tot, unsigned long long* warp_s2, unsigned long long& n_right,
+                           unsigned long long& n_left) {
+  const uint32_t W = a.geo.W;
+  const uint32_t chunk = (W + blockDim.x - 1) / blockDim.x;
+  const uint32_t w0 = min(W, threadIdx.x * chunk), w1 = min(W, w0 + chunk);
+  long long tot = 0;
+  for (uint32_t i = w0; i < w1; ++i) tot += 2 * __popc(lat[i]) - 32;
+  long long h = block_scan_incl(tot, warp_tot) - tot, s1 = 0;
+  unsigned long long s2 = 0;
+  for (uint32_t i = w0; i < w1; ++i) {
+    const uint32_t x = lat[i];
+    for (uint32_t b = 0; b < 32; ++b) {
+      h += ((x >> b) & 1u) ? 1 : -1;
+      s1 += h;
+      s2 += static_cast<unsigned long long>(h * h);
+    }
+  }
+  const long long s1_all = block_sum(s1, warp_tot);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31u) == 0) warp_s2[threadIdx.x >> 5] = s2;
+  // hop counters of this sample up to now
+  const long long nr = block_sum(static_cast<long long>(n_right), warp_tot);
+  const long long nl = block_sum(static_cast<long long>(n_left), warp_tot);
+  n_right = 0;
+  n_left = 0;
+  if (threadIdx.x == 0) {
+    unsigned __int128 acc = 0;
+    for (uint32_t i = 0; i < (blockDim.x >> 5); ++i) acc += warp_s2[i];
+    const size_t e = static_cast<size_t>(slot) * a.geo.S + sample;
+    a.tab_sh[e] = s1_all;
+    a.tab_sh2[2 * e] = static_cast<uint64_t>(acc);
+    a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(acc >> 64);
+    uint64_t* ctr = a.counters + 4ull * sample;
+    if (COUNT) {
+      ctr[0] += static_cast<uint64_t>(nr);
+      ctr[1] += static_cast<uint64_t>(nl);
+    }
+    for (int k = 0; k < 4; ++k) a.ex.tab_cnt[e * 4 + k] = static_cast<int64_t>(ctr[k]);
+  }
+  const Extras& ex = a.ex;
+  if (ex.profile || ex.snap) {
+    const size_t base = static_cast<size_t>(sample) * W;
+    long long ov = 0;
+    for (uint32_t i = w0; i < w1; ++i) {
+      const uint32_t x = lat[i];
+      if (ex.profile) ex.profile[base + i] += __popc(x);
+      if (ex.snap) {
+        if (t == ex.t0) ex.snap[base + i] = x;
+        if (t >= ex.t0) ov += __popc(x & ex.snap[base + i]);
+      }
+    }
+    if (ex.snap) {
+      const long long tot_ov = block_sum(ov, warp_tot);
+      if (threadIdx.x == 0) ex.tab_ac[static_cast<size_t>(slot) * a.geo.S + sample] = tot_ov;
+    }
+  }
+  __syncthreads();
+}
+
+// Bimodal rings carry a class plane through every step: at most 512 threads,
+// so the compiler may use up to 128 registers.
+template <bool DIS, bool COUNT>
+__global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long warp_tot[32];
+  __shared__ unsigned long long warp_s2[32];
+  const uint32_t W = a.geo.W, n_units = W / 8;
+  uint32_t* lat = reinterpret_cast<uint32_t*>(smem_raw);
+  uint32_t* cls = lat + W;
+  uint32_t* carry = cls + (DIS ? W : 0u);
+  const uint32_t sample = blockIdx.x;
+  const uint32_t n_glob = a.geo.first_sample + sample;
+  const uint64_t s0 = a.clock->sweep;
+  uint32_t rec = a.clock->next_time;
+  const uint32_t kmax = a.sca_kmax;
+
+  for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) {
+    lat[i] = a.state[static_cast<size_t>(sample) * W + i];
+    if (DIS) cls[i] = a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + i];
+  }
+  for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) carry[u] = 0u;
+  __syncthreads();
+
+  unsigned long long n_right = 0, n_left = 0;
+  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
+    const uint64_t s = s0 + it;
+    for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
+      sca_unit<DIS, COUNT, 0>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
+    __syncthreads();
+    for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
+      sca_unit<DIS, COUNT, 1>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
+    __syncthreads();
+    if (rec < a.n_times && a.times[rec] == s + 1) {
+      settle_carries(lat, carry, n_units);
+      sca_record<COUNT>(lat, a, rec, s + 1, sample, warp_tot, warp_s2, n_right, n_left);
+      ++rec;
+    }
+  }
+  settle_carries(lat, carry, n_units);
+  for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) a.state[static_cast<size_t>(sample) * W + i] = lat[i];
+  if (COUNT) {
+    const long long nr = block_sum(static_cast<long long>(n_right), warp_tot);
+    const long long nl = block_sum(static_cast<long long>(n_left), warp_tot);
+    if (threadIdx.x == 0) {
+      a.counters[4ull * sample] += static_cast<uint64_t>(nr);
+      a.counters[4ull * sample + 1] += static_cast<uint64_t>(nl);
+    }
+  }
+}
+
+template <bool DIS, bool COUNT>
+cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
+  (void)cudaGetLastError();
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_sca<DIS, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_sca<DIS, COUNT><<<a.geo.S, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t sca_smem_bytes(uint32_t W, bool dis) {
+  return static_cast<size_t>(W) * 4u * (dis ? 2u : 1u) + static_cast<size_t>(W / 8u) * 4u;
+}
+
+cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
+  const bool dis = a.dis == kDisBimodal, count = a.count_hops != 0;
+  if (dis) return count ? launch_sca_t<true, true>(a, threads, smem, st) : launch_sca_t<true, false>(a, threads, smem, st);
+  return count ? launch_sca_t<false, true>(a, threads, smem, st) : launch_sca_t<false, false>(a, threads, smem, st);
+}
+
+}  // namespace asep

@@ -93,6 +93,7 @@ def assert_same(g, ref, P, times):
 
 RING = A.ASEP_MODEL_RING
 TWO = A.ASEP_MODEL_TWO_LANE
+SCA = A.ASEP_SCHED_SCA
 CASES = {
     # several CTAs (16 samples each) with a ragged last CTA
     "ring_asep_ragged": (dict(L=4096, domain_sites=256, samples_per_real=20, p_thr=th(0.75), q_thr=th(0.25),
@@ -145,6 +146,24 @@ CASES = {
                             dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=3, seed=4),
                        20, [20]),
     # cluster tier: one sample spread over 2..16 CTAs of a thread-block cluster
+    # the paper's two-sub-lattice SCA schedule (bit-sliced, one CTA per ring)
+    "sca_asep": (dict(L=1 << 15, schedule=SCA, samples_per_real=6, p_thr=th(0.75), q_thr=th(0.25), seed=5,
+                      flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=3), 40, [0, 3, 17, 40]),
+    "sca_tasep_deterministic": (dict(L=4096, schedule=SCA, samples_per_real=3, seed=2), 25, [0, 1, 25]),
+    "sca_twenty_bit_rates": (dict(L=2048, schedule=SCA, samples_per_real=9, p_thr=th(0.6), q_thr=th(0.3), seed=8),
+                             30, [0, 7, 30]),
+    "sca_bimodal": (dict(L=1 << 14, schedule=SCA, n_realizations=2, samples_per_real=2, p_thr=th(0.9),
+                         q_thr=th(0.2), dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3),
+                         dis_c_thr=th(0.05), dis_seed=12, seed=14), 30, [0, 30]),
+    "sca_one_unit": (dict(L=256, schedule=SCA, samples_per_real=20, p_thr=th(0.7), q_thr=th(0.2), seed=6), 40,
+                     [0, 40]),
+    "sca_growth_regime_shape": (dict(L=1 << 17, schedule=SCA, samples_per_real=4, p_thr=th(0.75), q_thr=th(0.25),
+                                     seed=1, flags=A.ASEP_FLAG_NO_HOP_COUNTS), 20, [0, 10, 20]),
+    "sca_max_L": (dict(L=1 << 20, schedule=SCA, samples_per_real=1, p_thr=th(0.75), q_thr=th(0.25), seed=3), 3,
+                  [0, 3]),
+    "sca_bimodal_max_L": (dict(L=1 << 19, schedule=SCA, samples_per_real=1, p_thr=A.ASEP_ALWAYS, q_thr=0,
+                               dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=4,
+                               seed=7), 3, [0, 3]),
     "cluster_ring_2x": (dict(L=1 << 20, domain_sites=256, samples_per_real=2, p_thr=th(0.75), q_thr=th(0.25),
                              seed=51), 5, [0, 2, 5]),
     "cluster_ring_d64": (dict(L=1 << 18, domain_sites=64, samples_per_real=2, p_thr=th(0.6), seed=52), 6, [0, 6]),
@@ -174,6 +193,9 @@ def test_bit_exact_against_oracle(name):
                      else None)
     if P.dis_kind != 0:
         assert np.array_equal(g["dis"], oracle.disorder(P))
+    if kw.get("flags", 0) & A.ASEP_FLAG_NO_HOP_COUNTS:  # the ring's hop counters stay off
+        ref.counters[:] = 0
+        ref.extra["counters_at"][:] = 0
     assert_same(g, ref, P, times)
 
 

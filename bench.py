@@ -45,6 +45,13 @@ SEED = 1
 # load 1, straddle test 1, pattern extract 2, threshold select 2, masked
 # compare 2, flip mask and xor 2, store 1) = 10 + 14.
 OPS_PER_ATTEMPT = 24
+# The same count for the two-sub-lattice SCA kernel, per attempt = per bond of
+# a 32-bond group and phase: K random planes, each a quarter of one Philox
+# call (10 ops) and three comparator ops (threshold mask, less-than, equal),
+# plus 12 ops of pattern test and flips per group: (13 K + 12) / 32, with
+# K = 2 planes for p = 0.75, q = 0.25.
+SCA_PLANES = 2
+SCA_OPS_PER_ATTEMPT = (13 * SCA_PLANES + 12) / 32
 SMS, LANES_PER_SM = 152, 128  # GB300: 152 SMs x 4 schedulers x 32 lanes issue per clock
 
 WORKLOAD_NAME = ("growth regime, batched: L=2^17 ring (4096 u32 words, shared-memory resident), ASEP p=0.75 q=0.25, "
@@ -109,15 +116,25 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def _traffic_from_profile():
-    """DRAM bytes per launch of the domain kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def kernel_source_digest() -> str:
+    """sha256 prefix over the kernel sources (the .cu files and the device header)."""
+    import glob
     import hashlib
 
-    src = os.path.join(ROOT, "paper_1012_0385_gb300", "csrc", "asep_kernels.cu")
-    prof = os.path.join(ROOT, "profiles", "k_domain_growth_regime_traffic.txt")
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1012_0385_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(kernel: str = "domain"):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, if
+    it was taken on the current kernel sources."""
+    name = "k_domain_growth_regime_traffic.txt" if kernel == "domain" else "k_sca_growth_regime_traffic.txt"
+    prof = os.path.join(ROOT, "profiles", name)
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_source_digest()
         kv = dict(line.strip().split("=", 1) for line in open(prof) if "=" in line)
         if kv.get("kernel_source_sha256_16") == digest:
             return float(kv["dram_bytes_per_launch"])
@@ -312,6 +329,7 @@ def run_ours(args):
             line["autotune"] = [{k: r[k] for k in ("cluster", "samples_per_group", "ms_per_sweep")}
                                 for r in tune_table]
         if not args.no_workloads and world == 1:
+            line["sca"] = sca_growth(max(1, min(args.steps, 5)), peak_ops)
             line["workloads"] = other_workloads()
         if not args.no_serving and world == 1:
             line["serving"] = serving_comparison(capacity=value)
@@ -321,6 +339,44 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def sca_growth(steps: int, peak_ops: float):
+    """The benchmarked workload under the paper's own schedule, the
+    two-sub-lattice SCA (k_sca): same rings, rates, sweeps and sample times,
+    re-drawn initial state + 2^14 sweeps per step, device-timed."""
+    import torch
+
+    from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300.sampling import log_times
+
+    th = A.asep_threshold
+    prm = A.make_params(L=L_SITES, schedule=A.ASEP_SCHED_SCA, samples_per_real=SAMPLES, p_thr=th(P_RATE),
+                        q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
+    stream = torch.cuda.current_stream()
+    with A.asep_create(prm, sample_times=log_times(N_MCS)) as ctx:
+        A.asep_sweep(ctx, 256)  # warm-up
+        ms = []
+        for k in range(steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.asep_reset(ctx, seed=SEED + k)
+            A.asep_sweep(ctx, N_MCS)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        info = A.asep_get_info(ctx)
+    t = statistics.mean(ms)
+    rate = L_SITES * SAMPLES * N_MCS / (t / 1000.0)
+    achieved = rate * SCA_OPS_PER_ATTEMPT
+    return {"workload": "the same growth-regime workload under the paper's two-sub-lattice SCA schedule "
+                        "(even bonds, then odd bonds, one attempt per bond per sweep)",
+            "attempts_per_s": rate, "ms_per_step": t, "steps": steps, "kernel": "k_sca",
+            "threads_per_cta": info["threads"],
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": achieved / peak_ops, "ops_per_attempt": SCA_OPS_PER_ATTEMPT,
+                         "traffic": _traffic_from_profile("sca")}}
 
 
 def other_workloads():
@@ -404,19 +460,22 @@ def serving_comparison(capacity: float, n_jobs: int = 48, seed: int = 2026, load
             "p99_ratio": batched["p99_latency_s"] / plain["p99_latency_s"]}
 
 
-def profile_case():
-    """The benchmarked configuration with 64 sweeps instead of 2^14: the
-    domain kernel reads and writes each lattice once per launch, so its DRAM
-    traffic per launch is that of a full step; only the loop is shorter."""
+def profile_case(schedule: str = "domain"):
+    """The benchmarked configuration with 64 sweeps instead of 2^14 (one
+    height record, at the end): the kernel reads and writes each lattice once
+    per launch, so its DRAM traffic per launch is that of a full step; only
+    the loop is shorter.  schedule "sca" runs the same workload under the
+    two-sub-lattice SCA kernel."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
-    from paper_1012_0385_gb300.sampling import log_times
 
     th = A.asep_threshold
+    sched = A.ASEP_SCHED_SCA if schedule == "sca" else A.ASEP_SCHED_DOMAIN
     prm = A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE),
-                        q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
-    with A.asep_create(prm, sample_times=log_times(N_MCS)) as ctx:
+                        q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS, schedule=sched)
+    # one record, at the end: the full run records 131 times in 2^14 sweeps
+    with A.asep_create(prm, sample_times=[64]) as ctx:
         A.asep_sweep(ctx, 64)
         A.asep_sync(ctx)
     torch.cuda.synchronize()
@@ -437,11 +496,11 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the windows of the other configurations")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
-    ap.add_argument("--profile-case", action="store_true",
+    ap.add_argument("--profile-case", nargs="?", const="domain", choices=["domain", "sca"],
                     help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_case)
     if args.warmup < 3:
         args.warmup = 3
     DOMAIN = args.domain

@@ -30,6 +30,7 @@
 // phase), so that bond is "row + 1" like every other.  At the start of every
 // sweep the words are rotated ("realigned") from the previous offset to the
 // new one into a second buffer (double buffering), one funnel shift per word.
+#include <algorithm>
 #include <cstdint>
 
 #include <cooperative_groups.h>
@@ -916,15 +917,33 @@ __device__ __forceinline__ uint32_t bit_at(const uint32_t* w, uint64_t i) {
 }
 __device__ __forceinline__ void flip_at(uint32_t* w, uint64_t i) { w[i >> 5] ^= 1u << (i & 31u); }
 
-template <uint32_t MODEL, uint32_t DIS>
+// One thread per sample.  With SMEM the thread copies its lattice (and the
+// quenched plane) into its own slice of shared memory for the launch, so the
+// dependent read-modify-write chain of an attempt stays on chip; the next
+// Philox call is drawn while the current two attempts run.
+template <uint32_t MODEL, uint32_t DIS, bool SMEM>
 __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
+  extern __shared__ __align__(16) uint32_t serial_smem[];
   const uint32_t sample = blockIdx.x * blockDim.x + threadIdx.x;
   if (sample >= a.geo.S) return;
   const uint64_t L = a.geo.L;
   const uint32_t W = a.geo.W;
-  uint32_t* A = a.state + static_cast<size_t>(sample) * a.geo.planes * W;
-  uint32_t* B = A + W;
-  const uint32_t* M = (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+  constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + (DIS != kDisNone ? 1u : 0u);
+  uint32_t* gA = a.state + static_cast<size_t>(sample) * a.geo.planes * W;
+  const uint32_t* gM =
+      (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+  uint32_t* A = gA;
+  uint32_t* B = gA + W;
+  const uint32_t* M = gM;
+  if (SMEM) {
+    uint32_t* mine = serial_smem + static_cast<size_t>(threadIdx.x) * NPL * W;
+    for (uint32_t w = 0; w < a.geo.planes * W; ++w) mine[w] = gA[w];
+    if (DIS != kDisNone)
+      for (uint32_t w = 0; w < W; ++w) mine[a.geo.planes * W + w] = gM[w];
+    A = mine;
+    B = mine + W;
+    M = mine + a.geo.planes * W;
+  }
   const uint32_t n_glob = a.geo.first_sample + sample;
   const uint2 key = key_of(a.seed);
   const uint64_t n_att = MODEL == kTwoLane ? 2 * L : L;
@@ -970,10 +989,13 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
 
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
     const uint64_t s = s0 + it;
+    uint4 x = philox10(ctr_of(s, kTagSer, 0, n_glob, 0u), key);
     for (uint64_t k = 0; k < n_att; k += 2) {
-      const uint4 x = philox10(ctr_of(s, kTagSer, 0, n_glob, static_cast<uint32_t>(k >> 1)), key);
+      const uint32_t next = static_cast<uint32_t>(k >> 1) + 1u;  // drawn ahead; unused after the last pair
+      const uint4 xn = philox10(ctr_of(s, kTagSer, 0, n_glob, next), key);
       attempt(x.x, x.y);
       attempt(x.z, x.w);
+      x = xn;
     }
     if (MODEL == kTwoLane && DIS == kDisTurning) {
       for (uint32_t w = 0; w < W; ++w) {
@@ -1034,6 +1056,8 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
   my_ctr[1] = base1 + c1;
   my_ctr[2] = base2 + c2;
   my_ctr[3] = base3 + c3;
+  if (SMEM)
+    for (uint32_t w = 0; w < a.geo.planes * W; ++w) gA[w] = A[w];
 }
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
@@ -1057,9 +1081,23 @@ cudaError_t launch_domain_t(const DomainLaunch& a, uint32_t threads, size_t smem
 
 template <uint32_t MODEL, uint32_t DIS>
 cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
+  constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + (DIS != kDisNone ? 1u : 0u);
+  const size_t per_sample = static_cast<size_t>(NPL) * a.geo.W * 4u;
+  const size_t budget = 200u * 1024u;  // shared memory for the staged lattices of one block
+  if (per_sample <= budget) {
+    const uint32_t threads = static_cast<uint32_t>(std::min<size_t>(32u, budget / per_sample));
+    const size_t smem = per_sample * threads;
+    const uint32_t blocks = (a.geo.S + threads - 1) / threads;
+    (void)cudaGetLastError();
+    const cudaError_t e = cudaFuncSetAttribute(k_serial<MODEL, DIS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_serial<MODEL, DIS, true><<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+  }
   const uint32_t threads = 32;
   const uint32_t blocks = (a.geo.S + threads - 1) / threads;
-  k_serial<MODEL, DIS><<<blocks, threads, 0, st>>>(a);
+  k_serial<MODEL, DIS, false><<<blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -138,6 +138,9 @@ CASES = {
                           every(100, 200)),
     "serial_asep": (dict(L=1024, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=5, p_thr=th(0.75),
                          q_thr=th(0.25), seed=12), 30, [0, 10, 30]),
+    # 2^21 sites (256 KB per sample): too large to stage in shared memory, the lattice stays in global memory
+    "serial_global_lattice": (dict(L=1 << 21, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=2, p_thr=th(0.75),
+                                   q_thr=th(0.25), seed=21), 2, [0, 2]),
     "serial_two_lane": (dict(model=TWO, L=1024, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=3, init_kind=1,
                              init_seed=4, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
                              dis_seed=2, q_thr=A.ASEP_ALWAYS, seed=3,

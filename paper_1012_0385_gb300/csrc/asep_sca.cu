@@ -33,6 +33,7 @@ namespace asep {
 namespace {
 
 constexpr uint32_t kEven = 0x55555555u;
+constexpr uint32_t kOdd = 0xAAAAAAAAu;
 
 // Sum of per-thread values over the block; every thread gets the total.
 __device__ long long block_sum(long long v, long long* warp_tot) {
@@ -49,7 +50,7 @@ __device__ long long block_sum(long long v, long long* warp_tot) {
 __device__ __forceinline__ uint32_t bit_mask(uint32_t t20, uint32_t k) { return 0u - ((t20 >> (19u - k)) & 1u); }
 
 // One phase over one unit (four groups, words 8u .. 8u + 7).
-template <bool DIS, bool COUNT, uint32_t PHASE>
+template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
 __device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uint32_t* carry, const DomainLaunch& a,
                                          uint32_t u, uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob,
                                          uint32_t kmax, unsigned long long& n_right, unsigned long long& n_left) {
@@ -71,59 +72,106 @@ __device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uin
   const uint32_t x_next = PHASE ? lat[next_w] : 0u;           // only bit 0 is used
   const uint32_t c_next = (PHASE && DIS) ? cls[next_w] : 0u;
 
-  const Rates& r = a.rates;
-  const uint32_t pA = r.p == 0xFFFFFFFFu ? ~0u : 0u, qA = r.q == 0xFFFFFFFFu ? ~0u : 0u;
-  const uint32_t psA = r.p_slow == 0xFFFFFFFFu ? ~0u : 0u, qsA = r.q_slow == 0xFFFFFFFFu ? ~0u : 0u;
-  const uint32_t pN = r.p == 0u ? ~0u : 0u, qN = r.q == 0u ? ~0u : 0u;
-  const uint32_t psN = r.p_slow == 0u ? ~0u : 0u, qsN = r.q_slow == 0u ? ~0u : 0u;
-
-  uint32_t rc[4], lc[4], acc[4], eq[4], c1[4], c2[4];
-  uint32_t any = 0;
-#pragma unroll
-  for (int gi = 0; gi < 4; ++gi) {
-    const uint32_t xa = x[2 * gi], xb = x[2 * gi + 1];
-    const uint32_t xn = gi < 3 ? x[2 * gi + 2] : x_next;
-    // window: bit 2j = first site of bond j, bit 2j + 1 = its second site
-    const uint32_t ya = PHASE ? __funnelshift_r(xa, xb, 1) : xa;
-    const uint32_t yb = PHASE ? __funnelshift_r(xb, xn, 1) : xb;
-    const uint32_t ra = ya & ~(ya >> 1) & kEven, la = ~ya & (ya >> 1) & kEven;
-    const uint32_t rb = yb & ~(yb >> 1) & kEven, lb = ~yb & (yb >> 1) & kEven;
-    rc[gi] = ra | (rb << 1);
-    lc[gi] = la | (lb << 1);
-    if (DIS) {
-      const uint32_t ca = c[2 * gi], cb = c[2 * gi + 1];
-      const uint32_t cn = gi < 3 ? c[2 * gi + 2] : c_next;
-      const uint32_t za = PHASE ? __funnelshift_r(ca, cb, 1) : ca;
-      const uint32_t zb = PHASE ? __funnelshift_r(cb, cn, 1) : cb;
-      c1[gi] = (za & kEven) | ((zb & kEven) << 1);                   // class of site i
-      c2[gi] = ((za >> 1) & kEven) | (((zb >> 1) & kEven) << 1);     // class of site i + 1
-    } else {
-      c1[gi] = 0u;
-      c2[gi] = 0u;
-    }
-    const uint32_t rA = rc[gi] & ((~c1[gi] & pA) | (c1[gi] & psA));
-    const uint32_t lA = lc[gi] & ((~c2[gi] & qA) | (c2[gi] & qsA));
-    const uint32_t rN = rc[gi] & ((~c1[gi] & pN) | (c1[gi] & psN));
-    const uint32_t lN = lc[gi] & ((~c2[gi] & qN) | (c2[gi] & qsN));
-    acc[gi] = rA | lA;
-    eq[gi] = (rc[gi] | lc[gi]) & ~(rA | lA | rN | lN);
-    any |= eq[gi];
-  }
-  // most significant bit first; plane k of the four groups = Philox call k
-  const uint32_t p20 = r.p >> 12, q20 = r.q >> 12, ps20 = r.p_slow >> 12, qs20 = r.q_slow >> 12;
-  for (uint32_t k = 0; k < kmax && any; ++k) {
-    const uint4 y = philox10(ctr_of(s, kTagSca, k, n_glob, 2u * u + PHASE), a.ks);
-    const uint32_t P = bit_mask(p20, k), Q = bit_mask(q20, k);
-    const uint32_t PS = DIS ? bit_mask(ps20, k) : 0u, QS = DIS ? bit_mask(qs20, k) : 0u;
-    const uint32_t U[4] = {y.x, y.y, y.z, y.w};
-    any = 0;
+  uint32_t rc[4], lc[4], acc[4], eq[4];
+  if (FAST2) {
+    // No disorder, p and q neither 0 nor "always", at most two planes: every
+    // candidate lane is compared, and the threshold bit of a plane is p's on
+    // right candidates and q's on left ones (uniform per plane).
 #pragma unroll
     for (int gi = 0; gi < 4; ++gi) {
-      const uint32_t T = DIS ? ((rc[gi] & ((~c1[gi] & P) | (c1[gi] & PS))) | (lc[gi] & ((~c2[gi] & Q) | (c2[gi] & QS))))
-                             : ((rc[gi] & P) | (lc[gi] & Q));
-      acc[gi] |= eq[gi] & T & ~U[gi];  // this bit of u is 0 where t's is 1: u < t
-      eq[gi] &= ~(T ^ U[gi]);          // equal so far
+      const uint32_t xa = x[2 * gi], xb = x[2 * gi + 1];
+      const uint32_t xn = gi < 3 ? x[2 * gi + 2] : x_next;
+      const uint32_t ya = PHASE ? __funnelshift_r(xa, xb, 1) : xa;
+      const uint32_t yb = PHASE ? __funnelshift_r(xb, xn, 1) : xb;
+      // even lanes: bonds of word 2g (ya, ya >> 1); odd lanes: bonds of word 2g + 1 (yb << 1, yb)
+      const uint32_t sa = ya >> 1, tb = yb << 1;
+      rc[gi] = (ya & ~sa & kEven) | (tb & ~yb & kOdd);  // 10
+      lc[gi] = (~ya & sa & kEven) | (~tb & yb & kOdd);  // 01
+      acc[gi] = 0u;
+      eq[gi] = rc[gi] | lc[gi];
+    }
+    const uint32_t p20 = a.rates.p >> 12, q20 = a.rates.q >> 12;
+    for (uint32_t k = 0; k < kmax; ++k) {
+      const uint4 y = philox10(ctr_of(s, kTagSca, k, n_glob, 2u * u + PHASE), a.ks);
+      const uint32_t U[4] = {y.x, y.y, y.z, y.w};
+      const uint32_t pb = (p20 >> (19u - k)) & 1u, qb = (q20 >> (19u - k)) & 1u;
+      if (pb && qb) {  // threshold bit 1 on every candidate lane
+#pragma unroll
+        for (int gi = 0; gi < 4; ++gi) {
+          acc[gi] |= eq[gi] & ~U[gi];
+          eq[gi] &= U[gi];
+        }
+      } else if (pb) {  // 1 on right candidates, 0 on left ones
+#pragma unroll
+        for (int gi = 0; gi < 4; ++gi) {
+          acc[gi] |= eq[gi] & rc[gi] & ~U[gi];
+          eq[gi] &= ~(rc[gi] ^ U[gi]);
+        }
+      } else if (qb) {
+#pragma unroll
+        for (int gi = 0; gi < 4; ++gi) {
+          acc[gi] |= eq[gi] & lc[gi] & ~U[gi];
+          eq[gi] &= ~(lc[gi] ^ U[gi]);
+        }
+      } else {  // 0 on every lane: still equal only where u's bit is 0
+#pragma unroll
+        for (int gi = 0; gi < 4; ++gi) eq[gi] &= ~U[gi];
+      }
+    }
+  } else {
+    const Rates& r = a.rates;
+    const uint32_t pA = r.p == 0xFFFFFFFFu ? ~0u : 0u, qA = r.q == 0xFFFFFFFFu ? ~0u : 0u;
+    const uint32_t psA = r.p_slow == 0xFFFFFFFFu ? ~0u : 0u, qsA = r.q_slow == 0xFFFFFFFFu ? ~0u : 0u;
+    const uint32_t pN = r.p == 0u ? ~0u : 0u, qN = r.q == 0u ? ~0u : 0u;
+    const uint32_t psN = r.p_slow == 0u ? ~0u : 0u, qsN = r.q_slow == 0u ? ~0u : 0u;
+    uint32_t c1[4], c2[4];
+    uint32_t any = 0;
+#pragma unroll
+    for (int gi = 0; gi < 4; ++gi) {
+      const uint32_t xa = x[2 * gi], xb = x[2 * gi + 1];
+      const uint32_t xn = gi < 3 ? x[2 * gi + 2] : x_next;
+      // window: bit 2j = first site of bond j, bit 2j + 1 = its second site
+      const uint32_t ya = PHASE ? __funnelshift_r(xa, xb, 1) : xa;
+      const uint32_t yb = PHASE ? __funnelshift_r(xb, xn, 1) : xb;
+      const uint32_t ra = ya & ~(ya >> 1) & kEven, la = ~ya & (ya >> 1) & kEven;
+      const uint32_t rb = yb & ~(yb >> 1) & kEven, lb = ~yb & (yb >> 1) & kEven;
+      rc[gi] = ra | (rb << 1);
+      lc[gi] = la | (lb << 1);
+      if (DIS) {
+        const uint32_t ca = c[2 * gi], cb = c[2 * gi + 1];
+        const uint32_t cn = gi < 3 ? c[2 * gi + 2] : c_next;
+        const uint32_t za = PHASE ? __funnelshift_r(ca, cb, 1) : ca;
+        const uint32_t zb = PHASE ? __funnelshift_r(cb, cn, 1) : cb;
+        c1[gi] = (za & kEven) | ((zb & kEven) << 1);                   // class of site i
+        c2[gi] = ((za >> 1) & kEven) | (((zb >> 1) & kEven) << 1);     // class of site i + 1
+      } else {
+        c1[gi] = 0u;
+        c2[gi] = 0u;
+      }
+      const uint32_t rA = rc[gi] & ((~c1[gi] & pA) | (c1[gi] & psA));
+      const uint32_t lA = lc[gi] & ((~c2[gi] & qA) | (c2[gi] & qsA));
+      const uint32_t rN = rc[gi] & ((~c1[gi] & pN) | (c1[gi] & psN));
+      const uint32_t lN = lc[gi] & ((~c2[gi] & qN) | (c2[gi] & qsN));
+      acc[gi] = rA | lA;
+      eq[gi] = (rc[gi] | lc[gi]) & ~(rA | lA | rN | lN);
       any |= eq[gi];
+    }
+    // most significant bit first; plane k of the four groups = Philox call k
+    const uint32_t p20 = r.p >> 12, q20 = r.q >> 12, ps20 = r.p_slow >> 12, qs20 = r.q_slow >> 12;
+    for (uint32_t k = 0; k < kmax && any; ++k) {
+      const uint4 y = philox10(ctr_of(s, kTagSca, k, n_glob, 2u * u + PHASE), a.ks);
+      const uint32_t P = bit_mask(p20, k), Q = bit_mask(q20, k);
+      const uint32_t PS = DIS ? bit_mask(ps20, k) : 0u, QS = DIS ? bit_mask(qs20, k) : 0u;
+      const uint32_t U[4] = {y.x, y.y, y.z, y.w};
+      any = 0;
+#pragma unroll
+      for (int gi = 0; gi < 4; ++gi) {
+        const uint32_t T = DIS ? ((rc[gi] & ((~c1[gi] & P) | (c1[gi] & PS))) | (lc[gi] & ((~c2[gi] & Q) | (c2[gi] & QS))))
+                               : ((rc[gi] & P) | (lc[gi] & Q));
+        acc[gi] |= eq[gi] & T & ~U[gi];  // this bit of u is 0 where t's is 1: u < t
+        eq[gi] &= ~(T ^ U[gi]);          // equal so far
+        any |= eq[gi];
+      }
     }
   }
   // apply the accepted moves
@@ -229,7 +277,7 @@ __device__ void sca_record(const uint32_t* lat, const DomainLaunch& a, uint32_t 
 
 // Bimodal rings carry a class plane through every step: at most 512 threads,
 // so the compiler may use up to 128 registers.
-template <bool DIS, bool COUNT>
+template <bool DIS, bool COUNT, bool FAST2>
 __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long warp_tot[32];
@@ -255,10 +303,10 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
     const uint64_t s = s0 + it;
     for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-      sca_unit<DIS, COUNT, 0>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
+      sca_unit<DIS, COUNT, FAST2, 0>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
     __syncthreads();
     for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-      sca_unit<DIS, COUNT, 1>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
+      sca_unit<DIS, COUNT, FAST2, 1>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
     __syncthreads();
     if (rec < a.n_times && a.times[rec] == s + 1) {
       settle_carries(lat, carry, n_units);
@@ -278,13 +326,13 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
   }
 }
 
-template <bool DIS, bool COUNT>
+template <bool DIS, bool COUNT, bool FAST2>
 cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();
-  const cudaError_t e =
-      cudaFuncSetAttribute(k_sca<DIS, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const cudaError_t e = cudaFuncSetAttribute(k_sca<DIS, COUNT, FAST2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_sca<DIS, COUNT><<<a.geo.S, threads, smem, st>>>(a);
+  k_sca<DIS, COUNT, FAST2><<<a.geo.S, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -296,8 +344,17 @@ size_t sca_smem_bytes(uint32_t W, bool dis) {
 
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   const bool dis = a.dis == kDisBimodal, count = a.count_hops != 0;
-  if (dis) return count ? launch_sca_t<true, true>(a, threads, smem, st) : launch_sca_t<true, false>(a, threads, smem, st);
-  return count ? launch_sca_t<false, true>(a, threads, smem, st) : launch_sca_t<false, false>(a, threads, smem, st);
+  if (dis)
+    return count ? launch_sca_t<true, true, false>(a, threads, smem, st)
+                 : launch_sca_t<true, false, false>(a, threads, smem, st);
+  // rates neither 0 nor "always" and at most two random planes: the specialised comparison
+  const auto regular = [](uint32_t t) { return t != 0u && t != 0xFFFFFFFFu; };
+  const bool fast2 = regular(a.rates.p) && regular(a.rates.q) && a.sca_kmax <= 2;
+  if (fast2)
+    return count ? launch_sca_t<false, true, true>(a, threads, smem, st)
+                 : launch_sca_t<false, false, true>(a, threads, smem, st);
+  return count ? launch_sca_t<false, true, false>(a, threads, smem, st)
+               : launch_sca_t<false, false, false>(a, threads, smem, st);
 }
 
 }  // namespace asep

@@ -63,6 +63,7 @@
 #define TAG_TURN 5u /* per-site lane-change draw */
 #define TAG_SER 6u  /* serial-schedule attempt stream */
 #define TAG_SCA 7u  /* two-sub-lattice SCA: random bit-planes of a 32-bond group */
+#define TAG_SCA_TURN 8u /* two-lane SCA: one word per lane-change candidate site */
 
 #define MODEL_RING 0u
 #define MODEL_TWO_LANE 1u
@@ -322,23 +323,61 @@ static void domain_sweep(const orc_params* P, const uint32_t* ptab, uint32_t pta
  *   bond i = 2m + phase, group g = m / 32, lane = 2 (m mod 16) + (m / 16 mod 2);
  *   bit k of u (k = 0 the most significant) = bit `lane` of plane k of g;
  *   plane k of g = word 4k + (g mod 4) of the stream (tag SCA,
- *   ctr3 = 2 (g / 4) + phase), k = 0 .. 19: Philox call k of that stream
- *   gives plane k of four consecutive groups. */
+ *   ctr3 = 2 (g / 4) + phase + lane_of_model * 2^31), k = 0 .. 19: Philox
+ *   call k of that stream gives plane k of four consecutive groups.
+ * Two lanes (paper sec. 3, its five-step SCA sequence): the in-lane bonds of
+ * lane A (right hops, p_thr) and of lane B (left hops, q_thr) run in each
+ * phase, lane B's planes from the stream with bit 31 of ctr3 set; with
+ * turning sites, the even phase is followed by the A -> B lane changes and
+ * the odd phase by the B -> A ones (sca_lane_changes). */
+static void sca_lane_changes(const orc_params* P, uint32_t* wa, uint32_t* wb, const uint32_t* turn, uint32_t sample,
+                             uint64_t sweep, uint32_t step, uint64_t* cnt);
+
 static void sca_sweep(const orc_params* P, uint32_t* words, const uint32_t* mask, uint32_t sample, uint64_t sweep,
                       uint64_t* cnt) {
-  const uint64_t L = P->L, bonds = L / 2;
+  const uint64_t L = P->L, bonds = L / 2, W = (L + 31) / 32;
+  const int two_lane = (P->model == MODEL_TWO_LANE);
+  uint32_t* wa = words;
+  uint32_t* wb = two_lane ? words + W : NULL;
   for (uint32_t phase = 0; phase < 2; phase++) {
-    for (uint64_t g = 0; 32 * g < bonds; g++) {
-      stream_t st;
-      uint32_t plane[20];
-      stream_open(&st, P->seed, sweep, TAG_SCA, sample, (uint32_t)(2 * (g / 4) + phase), 0);
-      for (int k = 0; k < 20; k++) plane[k] = stream_word(&st, 4 * (uint64_t)k + (g % 4));
-      for (uint64_t m = 32 * g; m < 32 * g + 32 && m < bonds; m++) {
-        const uint32_t lane = (uint32_t)(2 * (m & 15) + ((m >> 4) & 1));
-        uint32_t u = 0;
-        for (int k = 0; k < 20; k++) u = (u << 1) | ((plane[k] >> lane) & 1u);
-        ring_attempt(P, words, mask, 2 * m + phase, u << 12, cnt);
+    for (uint32_t lane = 0; lane < (two_lane ? 2u : 1u); lane++) {
+      for (uint64_t g = 0; 32 * g < bonds; g++) {
+        stream_t st;
+        uint32_t plane[20];
+        stream_open(&st, P->seed, sweep, TAG_SCA, sample, (uint32_t)(2 * (g / 4) + phase) | (lane << 31), 0);
+        for (int k = 0; k < 20; k++) plane[k] = stream_word(&st, 4 * (uint64_t)k + (g % 4));
+        for (uint64_t m = 32 * g; m < 32 * g + 32 && m < bonds; m++) {
+          const uint32_t bit = (uint32_t)(2 * (m & 15) + ((m >> 4) & 1));
+          uint32_t u = 0;
+          for (int k = 0; k < 20; k++) u = (u << 1) | ((plane[k] >> bit) & 1u);
+          if (two_lane)
+            lane_attempt(P, wa, wb, (int)lane, 2 * m + phase, u << 12, cnt);
+          else
+            ring_attempt(P, wa, mask, 2 * m + phase, u << 12, cnt);
+        }
       }
+    }
+    if (two_lane && P->dis_kind == DIS_TURNING) sca_lane_changes(P, wa, wb, mask, sample, sweep, phase, cnt);
+  }
+}
+
+/* Lane changes of the two-lane SCA: step 0 moves A -> B, step 1 B -> A.  At
+ * a turning site i whose source lane is occupied and target lane empty, the
+ * particle moves with probability omega (dis_b_thr); the draw is word
+ * 4 step + (i mod 4) of the stream (tag SCA_TURN, ctr3 = i / 4).  Each event
+ * touches only (A_i, B_i), so the order over sites does not matter. */
+static void sca_lane_changes(const orc_params* P, uint32_t* wa, uint32_t* wb, const uint32_t* turn, uint32_t sample,
+                             uint64_t sweep, uint32_t step, uint64_t* cnt) {
+  uint32_t* src = step == 0 ? wa : wb;
+  uint32_t* dst = step == 0 ? wb : wa;
+  stream_t st;
+  for (uint64_t i = 0; i < P->L; i++) {
+    if (!get_site(turn, i) || !get_site(src, i) || get_site(dst, i)) continue;
+    stream_open(&st, P->seed, sweep, TAG_SCA_TURN, sample, (uint32_t)(i >> 2), 0);
+    if (accept(stream_word(&st, 4 * (uint64_t)step + (i & 3)), P->dis_b_thr)) {
+      flip_site(src, i);
+      flip_site(dst, i);
+      cnt[step == 0 ? 2 : 3]++;
     }
   }
 }
@@ -376,7 +415,7 @@ static int params_ok(const orc_params* P) {
     if (P->D < 1 || P->D > 2048 || (P->D & (P->D - 1))) return 0;
     if (P->L % (2ull * P->D)) return 0;
   } else if (P->schedule == SCHED_SCA) {
-    if (P->model != MODEL_RING || (P->L & 1)) return 0; /* ring of even length */
+    if (P->L & 1) return 0; /* rings of even length */
   } else {
     if (P->L & (P->L - 1)) return 0;
   }

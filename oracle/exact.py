@@ -14,7 +14,8 @@ row-stochastic matrix on that space, built from its definition:
 * the two-phase domain sweep: the average over the 2D offsets o of
   exp(Q_even(o)) exp(Q_odd(o)), the domains of one phase being disjoint;
 * the two-sub-lattice SCA sweep (paper sec. 2.1): the product of the even
-  bonds' kernels, then of the odd bonds' kernels;
+  bonds' kernels, then of the odd bonds' kernels; two lanes (sec. 3): with
+  the one-directional lane changes after each phase;
 * the lane-change pass of the two-lane model: a product of independent
   per-site swaps with probability omega where exactly one lane is occupied.
 
@@ -71,6 +72,23 @@ class Space:
             Ti = np.zeros((self.n, self.n))
             for k, x in enumerate(self.states):
                 if self.bit(x, 0, i) != self.bit(x, 1, i):
+                    y = self.flip(self.flip(x, 0, i), 1, i)
+                    Ti[k, self.index[y]] += omega
+                    Ti[k, k] += 1 - omega
+                else:
+                    Ti[k, k] += 1
+            T = T @ Ti
+        return T
+
+    def lane_change_kernel(self, turning_sites, omega: float, src: int) -> np.ndarray:
+        """Two lanes, one direction: at each turning site whose lane `src` is
+        occupied and other lane empty, the particle moves across with
+        probability omega."""
+        T = np.eye(self.n)
+        for i in turning_sites:
+            Ti = np.zeros((self.n, self.n))
+            for k, x in enumerate(self.states):
+                if self.bit(x, src, i) == 1 and self.bit(x, 1 - src, i) == 0:
                     y = self.flip(self.flip(x, 0, i), 1, i)
                     Ti[k, self.index[y]] += omega
                     Ti[k, k] += 1 - omega
@@ -176,6 +194,8 @@ class TwoLaneModel:
         self.KA = [self.sp.bond_kernel(0, b, pA, 0.0) for b in range(L)]
         self.KB = [self.sp.bond_kernel(1, b, 0.0, pB) for b in range(L)]
         self.T = self.sp.turning_kernel(list(turning_sites), omega)
+        self.TAB = self.sp.lane_change_kernel(list(turning_sites), omega, 0)
+        self.TBA = self.sp.lane_change_kernel(list(turning_sites), omega, 1)
         self.I = np.eye(self.sp.n)
 
     def rsu_sweep(self) -> np.ndarray:
@@ -197,6 +217,17 @@ class TwoLaneModel:
                 A = A @ expm(Q)
             total += A
         return (total / (2 * D)) @ self.T
+
+    def sca_sweep(self) -> np.ndarray:
+        """The two-lane SCA sweep (paper sec. 3, five steps): even bonds of
+        both lanes, A -> B lane changes, odd bonds of both lanes (the closing
+        bonds with them), B -> A lane changes."""
+        E, O = self.I, self.I
+        for b in range(0, self.L, 2):
+            E = E @ self.KA[b] @ self.KB[b]
+        for b in range(1, self.L, 2):
+            O = O @ self.KA[b] @ self.KB[b]
+        return E @ self.TAB @ O @ self.TBA
 
 
 def stationary(A: np.ndarray) -> np.ndarray:

@@ -203,7 +203,7 @@ def test_two_lane_replay_matches_exact(oracle_mod, schedule):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("model,schedule,dis", [
-    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2), (0, 2, 0), (0, 2, 1)])
+    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2), (0, 2, 0), (0, 2, 1), (1, 2, 2), (1, 2, 0)])
 def test_particle_number_conserved(oracle_mod, model, schedule, dis):
     th = oracle_mod.threshold
     P = oracle_mod.Params(model=model, schedule=schedule, L=1024, D=64, samples_per_real=3, seed=9,
@@ -445,3 +445,57 @@ def test_sca_stationary_current_and_width(oracle_mod):
     j = (cnt[:, 0].astype(float) - cnt[:, 1].astype(float)) / (L * 10 * n_meas)
     assert abs(j.mean() - j_exact) < 4 * j.std(ddof=1) / np.sqrt(S)
     assert abs(A.sum(axis=1) - 1).max() < 1e-12
+
+
+def test_two_lane_sca_replay_matches_exact(oracle_mod):
+    """The paper's two-lane SCA (sec. 3): even bonds of both lanes, A -> B
+    lane changes, odd bonds, B -> A lane changes; in-lane rates 0.5 as in the
+    paper's SCA runs, lane changes at turning sites."""
+    L, omega, p = 4, 0.5, 0.5
+    th = oracle_mod.threshold
+    P = oracle_mod.Params(model=oracle_mod.MODEL_TWO_LANE, L=L, schedule=oracle_mod.SCHED_SCA,
+                          samples_per_real=S_DIST, seed=37, p_thr=th(p), q_thr=th(p),
+                          dis_kind=oracle_mod.DIS_TURNING, dis_a_thr=th(0.5), dis_b_thr=th(omega), dis_seed=2)
+    mask = oracle_mod.disorder(P)
+    turning = [i for i in range(L) if (int(mask[0, 0]) >> i) & 1]
+    assert 0 < len(turning) < L
+    m = ex.TwoLaneModel(L, L, p, p, turning, omega)
+    A = m.sca_sweep()
+    for t in (1, 2):
+        counts = histogram(m.sp, _replay_hist(oracle_mod, P, t, mask=mask))
+        assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(A, t)) > 1e-4, t
+    # plausible mistakes: lane changes in both directions once per sweep (the RSU pass), B -> A first,
+    # lane B moving right
+    E, O = m.I, m.I
+    for b in range(0, L, 2):
+        E = E @ m.KA[b] @ m.KB[b]
+    for b in range(1, L, 2):
+        O = O @ m.KA[b] @ m.KB[b]
+    KBr = [m.sp.bond_kernel(1, b, p, 0.0) for b in range(L)]
+    Er, Or = m.I, m.I
+    for b in range(0, L, 2):
+        Er = Er @ m.KA[b] @ KBr[b]
+    for b in range(1, L, 2):
+        Or = Or @ m.KA[b] @ KBr[b]
+    for wrong in (E @ O @ m.T, E @ m.TBA @ O @ m.TAB, Er @ m.TAB @ Or @ m.TBA):
+        assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(wrong, 2)) < 1e-6
+
+
+def test_two_lane_sca_deterministic_counts(oracle_mod):
+    """Rate 1 in both lanes, no lane changes, flat 1010... start.  Lane A
+    (right hops) is flat again after every sweep, L hops each.  Lane B (left
+    hops, 01 -> 10): its even bonds carry 10 at first, so only the odd bonds
+    hop in sweep 1 (L/2 hops, leaving 0101...); from then on every bond of
+    every phase carries 01 and hops (L per sweep), and after an odd number of
+    sweeps lane B sits on the odd sites."""
+    L = 256
+    P = oracle_mod.Params(model=oracle_mod.MODEL_TWO_LANE, L=L, schedule=oracle_mod.SCHED_SCA, samples_per_real=2,
+                          seed=3, p_thr=oracle_mod.ALWAYS, q_thr=oracle_mod.ALWAYS)
+    r = oracle_mod.run(P, 3, [0, 1, 3])
+    flat = oracle_mod.init_state(P)
+    assert np.array_equal(r.state[:, 0], flat[:, 0])
+    assert np.all(r.state[:, 1] == 0xAAAAAAAA)
+    cur = r.extra["counters_at"]
+    assert np.all(cur[:, :, 0] == np.array([0, L, 3 * L])[:, None])
+    assert np.all(cur[:, :, 1] == np.array([0, L // 2, L // 2 + 2 * L])[:, None])
+    assert np.all(cur[:, :, 2:] == 0)

@@ -209,11 +209,10 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (p->schedule == ASEP_SCHED_SERIAL && !is_pow2(p->L))
     return fail(ctx, ASEP_ERR_INVALID, "the serial schedule needs L a power of two");
   if (p->schedule == ASEP_SCHED_SCA) {
-    if (p->model != ASEP_MODEL_RING || p->dis_kind == ASEP_DIS_TURNING)
-      return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule runs the ring model (no disorder or bimodal)");
     if (p->L % 256) return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule needs L a multiple of 256");
-    if (sca_smem_bytes(static_cast<uint32_t>(p->L / 32), p->dis_kind == ASEP_DIS_BIMODAL) > 200u * 1024u)
-      return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule keeps the ring in one CTA's shared memory: L too large");
+    const uint32_t planes = p->model == ASEP_MODEL_TWO_LANE ? 2u : 1u;
+    if (sca_smem_bytes(static_cast<uint32_t>(p->L / 32), planes, p->dis_kind != ASEP_DIS_NONE) > 200u * 1024u)
+      return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule keeps the lattice in one CTA's shared memory: L too large");
   }
   return ASEP_OK;
 }
@@ -539,11 +538,12 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     rc = plan_domain(ctx, 0, 0);
     if (rc != ASEP_OK) return bail(rc);
   } else if (params->schedule == ASEP_SCHED_SCA) {
-    // one CTA per sample, a thread per unit of 8 words (at most 1024 threads, 512 with the class plane)
+    // one CTA per sample, a thread per unit of 8 words (at most 1024 threads, 512 with a quenched plane)
     const uint32_t units = ctx->W / 8;
-    const uint32_t cap = params->dis_kind == ASEP_DIS_BIMODAL ? 512u : 1024u;
+    const bool quenched = params->dis_kind != ASEP_DIS_NONE;
+    const uint32_t cap = quenched ? 512u : 1024u;
     ctx->threads = std::min<uint32_t>(cap, (units + 31u) / 32u * 32u);
-    ctx->smem = sca_smem_bytes(ctx->W, params->dis_kind == ASEP_DIS_BIMODAL);
+    ctx->smem = sca_smem_bytes(ctx->W, ctx->planes, quenched);
     ctx->blocks = ctx->S;
   }
 

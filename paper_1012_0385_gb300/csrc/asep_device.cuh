@@ -57,6 +57,14 @@ __device__ __forceinline__ uint4 ctr_of(uint64_t sweep, uint32_t tag, uint32_t c
                     (static_cast<uint32_t>(sweep >> 32) & 0xFFu) | (tag << 8) | (call << 12), sample, d);
 }
 
+// Output word i of a Philox call.
+__device__ __forceinline__ uint32_t pick(const uint4 x, uint32_t i) {
+  return i == 0 ? x.x : (i == 1 ? x.y : (i == 2 ? x.z : x.w));
+}
+
+// A draw r accepts a move of threshold t (0, a multiple of 4096 or "always").
+__device__ __forceinline__ bool accept(uint32_t r, uint32_t t) { return (r & kAcceptMask) < t; }
+
 // ---------------------------------------------------------------------------
 // Block scans (all threads of the block must call; blockDim.x % 32 == 0)
 // ---------------------------------------------------------------------------

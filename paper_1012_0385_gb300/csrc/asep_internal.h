@@ -17,6 +17,7 @@ constexpr uint32_t kTagDom = 4;   // per-domain attempt stream
 constexpr uint32_t kTagTurn = 5;  // per-site lane-change draw
 constexpr uint32_t kTagSer = 6;   // serial-schedule stream
 constexpr uint32_t kTagSca = 7;   // two-sub-lattice SCA: random planes of four 32-bond groups
+constexpr uint32_t kTagScaTurn = 8;  // two-lane SCA: one word per lane-change candidate site
 
 constexpr uint32_t kAcceptMask = 0xFFFFF000u;  // draw bits compared with a threshold
 
@@ -171,7 +172,7 @@ cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32
 cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
 // The two-sub-lattice SCA schedule: one CTA per sample, ring in shared memory.
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
-size_t sca_smem_bytes(uint32_t W, bool bimodal);
+size_t sca_smem_bytes(uint32_t W, uint32_t planes, bool quenched);
 // How many clusters of the given shape can be resident at once (0 = none).
 int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem);
 // Advance clocks after n sweeps (one context, or the jobs of a batch).

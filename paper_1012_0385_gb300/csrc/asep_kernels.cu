@@ -41,11 +41,6 @@
 namespace asep {
 namespace {
 
-__device__ __forceinline__ uint32_t pick(const uint4 x, uint32_t i) {
-  return i == 0 ? x.x : (i == 1 ? x.y : (i == 2 ? x.z : x.w));
-}
-
-__device__ __forceinline__ bool accept(uint32_t r, uint32_t t) { return (r & kAcceptMask) < t; }
 
 // K = k_lo + #{ j : tab[j] <= w } (table ascending): inversion of the
 // Poisson CDF in u32 fixed point.

@@ -200,161 +200,324 @@ __device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uin
   if (PHASE == 1) carry[u] = carry_out;
 }
 
-// Apply pending carries (before a record or the write-back).
-__device__ __forceinline__ void settle_carries(uint32_t* lat, uint32_t* carry, uint32_t n_units) {
-  for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) {
-    const uint32_t prev = (u == 0 ? n_units : u) - 1;
-    lat[8u * u] ^= carry[prev];
-  }
+// Apply the pending carries of every plane (before a record or the write-back).
+__device__ __forceinline__ void settle_carries(uint32_t* lat, uint32_t* carry, uint32_t n_units, uint32_t W,
+                                               uint32_t planes) {
+  for (uint32_t p = 0; p < planes; ++p)
+    for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) {
+      const uint32_t prev = (u == 0 ? n_units : u) - 1;
+      lat[p * W + 8u * u] ^= carry[p * n_units + prev];
+    }
   __syncthreads();
-  for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) carry[u] = 0u;
+  for (uint32_t i = threadIdx.x; i < planes * n_units; i += blockDim.x) carry[i] = 0u;
   __syncthreads();
 }
 
-// Heights, W^2 sums and the other observables of one record, from the
-// lattice in shared memory (contiguous chunks of words per thread).
-template <bool COUNT>
+// In-lane bonds of one lane of the two-lane model over one unit: lane A
+// (LANE 0) moves particles right (10 -> 01) with threshold t = p, lane B
+// (LANE 1) left (01 -> 10) with t = q.  Lane B's planes come from the stream
+// with bit 31 of ctr3 set.  Every lane of a group has the same threshold, so
+// a plane's threshold bit is uniform.
+template <uint32_t LANE, uint32_t PHASE>
+__device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, const DomainLaunch& a, uint32_t u,
+                                              uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob, uint32_t t,
+                                              unsigned long long& hops) {
+  uint4* p4 = reinterpret_cast<uint4*>(plane + 8u * u);
+  const uint4 v0 = p4[0], v1 = p4[1];
+  uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  if (PHASE == 0) {
+    const uint32_t prev = (u == 0 ? n_units : u) - 1;
+    x[0] ^= carry[prev];
+    carry[prev] = 0u;
+  }
+  const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
+  const uint32_t x_next = PHASE ? plane[next_w] : 0u;
+  const bool always = t == 0xFFFFFFFFu, never = t == 0u;
+  uint32_t acc[4], eq[4];
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi) {
+    const uint32_t xa = x[2 * gi], xb = x[2 * gi + 1];
+    const uint32_t xn = gi < 3 ? x[2 * gi + 2] : x_next;
+    const uint32_t ya = PHASE ? __funnelshift_r(xa, xb, 1) : xa;
+    const uint32_t yb = PHASE ? __funnelshift_r(xb, xn, 1) : xb;
+    const uint32_t sa = ya >> 1, tb = yb << 1;
+    const uint32_t cand = LANE == 0 ? ((ya & ~sa & kEven) | (tb & ~yb & kOdd))    // 10
+                                    : ((~ya & sa & kEven) | (~tb & yb & kOdd));   // 01
+    acc[gi] = always ? cand : 0u;
+    eq[gi] = (always || never) ? 0u : cand;
+  }
+  const uint32_t t20 = t >> 12;
+  const uint32_t kmax = (always || never) ? 0u : 21u - static_cast<uint32_t>(__ffs(t20));
+  for (uint32_t k = 0; k < kmax; ++k) {
+    if (k > 0 && (eq[0] | eq[1] | eq[2] | eq[3]) == 0u) break;
+    const uint4 y = philox10(ctr_of(s, kTagSca, k, n_glob, (2u * u + PHASE) | (LANE << 31)), a.ks);
+    const uint32_t U[4] = {y.x, y.y, y.z, y.w};
+    if ((t20 >> (19u - k)) & 1u) {
+#pragma unroll
+      for (int gi = 0; gi < 4; ++gi) {
+        acc[gi] |= eq[gi] & ~U[gi];
+        eq[gi] &= U[gi];
+      }
+    } else {
+#pragma unroll
+      for (int gi = 0; gi < 4; ++gi) eq[gi] &= ~U[gi];
+    }
+  }
+  uint32_t carry_out = 0u;
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi) {
+    const uint32_t h = acc[gi];
+    hops += __popc(h);
+    const uint32_t ha = h & kEven, hb = (h >> 1) & kEven;
+    if (PHASE == 0) {
+      x[2 * gi] ^= ha | (ha << 1);
+      x[2 * gi + 1] ^= hb | (hb << 1);
+    } else {
+      x[2 * gi] ^= (ha << 1) | (ha << 2);
+      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb << 1) | (hb << 2);
+      const uint32_t out = (hb >> 30) & 1u;
+      if (gi < 3) x[2 * gi + 2] ^= out;
+      else carry_out = out;
+    }
+  }
+  p4[0] = make_uint4(x[0], x[1], x[2], x[3]);
+  p4[1] = make_uint4(x[4], x[5], x[6], x[7]);
+  if (PHASE == 1) carry[u] = carry_out;
+}
+
+// Lane changes of the two-lane model over one unit: STEP 0 (after the even
+// phase) moves A -> B, STEP 1 (after the odd phase) B -> A, at turning sites
+// whose source lane is occupied and target lane empty, with probability
+// omega; one draw per candidate site (tag SCA_TURN, call = STEP, ctr3 =
+// site / 4, word site mod 4).  STEP 1 first applies the odd phase's pending
+// flips of bit 0 of the unit's first words.
+template <uint32_t STEP>
+__device__ __forceinline__ void sca_turn_unit(uint32_t* A, uint32_t* B, const uint32_t* M, uint32_t* carry,
+                                              const DomainLaunch& a, uint32_t u, uint32_t n_units, uint64_t s,
+                                              uint32_t n_glob, unsigned long long& moves) {
+  uint4* pa = reinterpret_cast<uint4*>(A + 8u * u);
+  uint4* pb = reinterpret_cast<uint4*>(B + 8u * u);
+  const uint4* pm = reinterpret_cast<const uint4*>(M + 8u * u);
+  const uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1], m0 = pm[0], m1 = pm[1];
+  uint32_t xa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  uint32_t xb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  const uint32_t m[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+  if (STEP == 1) {
+    const uint32_t prev = (u == 0 ? n_units : u) - 1;
+    xa[0] ^= carry[prev];
+    xb[0] ^= carry[n_units + prev];
+    carry[prev] = 0u;
+    carry[n_units + prev] = 0u;
+  }
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    uint32_t c = m[w] & (STEP == 0 ? (xa[w] & ~xb[w]) : (xb[w] & ~xa[w]));
+    while (c) {
+      const uint32_t b = static_cast<uint32_t>(__ffs(c)) - 1u;
+      c &= c - 1u;
+      const uint32_t site = 32u * (8u * u + static_cast<uint32_t>(w)) + b;
+      const uint4 r = philox10(ctr_of(s, kTagScaTurn, STEP, n_glob, site >> 2), a.ks);
+      if (accept(pick(r, site & 3u), a.rates.omega)) {
+        xa[w] ^= 1u << b;
+        xb[w] ^= 1u << b;
+        ++moves;
+      }
+    }
+  }
+  pa[0] = make_uint4(xa[0], xa[1], xa[2], xa[3]);
+  pa[1] = make_uint4(xa[4], xa[5], xa[6], xa[7]);
+  pb[0] = make_uint4(xb[0], xb[1], xb[2], xb[3]);
+  pb[1] = make_uint4(xb[4], xb[5], xb[6], xb[7]);
+}
+
+// Heights, W^2 sums and the other observables of one record, per plane, from
+// the lattice in shared memory (contiguous chunks of words per thread), and
+// the hop counters of the sample (cnt: this thread's increments since the
+// last record, cleared here).
+template <uint32_t NOCC, bool COUNT>
 __device__ void sca_record(const uint32_t* lat, const DomainLaunch& a, uint32_t slot, uint64_t t, uint32_t sample,
-                           long long* warp_tot, unsigned long long* warp_s2, unsigned long long& n_right,
-                           unsigned long long& n_left) {
+                           long long* warp_tot, unsigned long long* warp_s2, unsigned long long* cnt) {
   const uint32_t W = a.geo.W;
   const uint32_t chunk = (W + blockDim.x - 1) / blockDim.x;
   const uint32_t w0 = min(W, threadIdx.x * chunk), w1 = min(W, w0 + chunk);
-  long long tot = 0;
-  for (uint32_t i = w0; i < w1; ++i) tot += 2 * __popc(lat[i]) - 32;
-  long long h = block_scan_incl(tot, warp_tot) - tot, s1 = 0;
-  unsigned long long s2 = 0;
-  for (uint32_t i = w0; i < w1; ++i) {
-    const uint32_t x = lat[i];
-    for (uint32_t b = 0; b < 32; ++b) {
-      h += ((x >> b) & 1u) ? 1 : -1;
-      s1 += h;
-      s2 += static_cast<unsigned long long>(h * h);
-    }
-  }
-  const long long s1_all = block_sum(s1, warp_tot);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-  if ((threadIdx.x & 31u) == 0) warp_s2[threadIdx.x >> 5] = s2;
-  // hop counters of this sample up to now
-  const long long nr = block_sum(static_cast<long long>(n_right), warp_tot);
-  const long long nl = block_sum(static_cast<long long>(n_left), warp_tot);
-  n_right = 0;
-  n_left = 0;
-  if (threadIdx.x == 0) {
-    unsigned __int128 acc = 0;
-    for (uint32_t i = 0; i < (blockDim.x >> 5); ++i) acc += warp_s2[i];
-    const size_t e = static_cast<size_t>(slot) * a.geo.S + sample;
-    a.tab_sh[e] = s1_all;
-    a.tab_sh2[2 * e] = static_cast<uint64_t>(acc);
-    a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(acc >> 64);
-    uint64_t* ctr = a.counters + 4ull * sample;
-    if (COUNT) {
-      ctr[0] += static_cast<uint64_t>(nr);
-      ctr[1] += static_cast<uint64_t>(nl);
-    }
-    for (int k = 0; k < 4; ++k) a.ex.tab_cnt[e * 4 + k] = static_cast<int64_t>(ctr[k]);
-  }
   const Extras& ex = a.ex;
-  if (ex.profile || ex.snap) {
-    const size_t base = static_cast<size_t>(sample) * W;
-    long long ov = 0;
+  for (uint32_t p = 0; p < NOCC; ++p) {
+    const uint32_t* pl = lat + p * W;
+    long long tot = 0;
+    for (uint32_t i = w0; i < w1; ++i) tot += 2 * __popc(pl[i]) - 32;
+    long long h = block_scan_incl(tot, warp_tot) - tot, s1 = 0;
+    unsigned long long s2 = 0;
     for (uint32_t i = w0; i < w1; ++i) {
-      const uint32_t x = lat[i];
-      if (ex.profile) ex.profile[base + i] += __popc(x);
-      if (ex.snap) {
-        if (t == ex.t0) ex.snap[base + i] = x;
-        if (t >= ex.t0) ov += __popc(x & ex.snap[base + i]);
+      const uint32_t x = pl[i];
+      for (uint32_t b = 0; b < 32; ++b) {
+        h += ((x >> b) & 1u) ? 1 : -1;
+        s1 += h;
+        s2 += static_cast<unsigned long long>(h * h);
       }
     }
-    if (ex.snap) {
-      const long long tot_ov = block_sum(ov, warp_tot);
-      if (threadIdx.x == 0) ex.tab_ac[static_cast<size_t>(slot) * a.geo.S + sample] = tot_ov;
+    const long long s1_all = block_sum(s1, warp_tot);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if ((threadIdx.x & 31u) == 0) warp_s2[threadIdx.x >> 5] = s2;
+    __syncthreads();
+    const size_t e = (static_cast<size_t>(slot) * a.geo.S + sample) * NOCC + p;
+    if (threadIdx.x == 0) {
+      unsigned __int128 acc = 0;
+      for (uint32_t i = 0; i < (blockDim.x >> 5); ++i) acc += warp_s2[i];
+      a.tab_sh[e] = s1_all;
+      a.tab_sh2[2 * e] = static_cast<uint64_t>(acc);
+      a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(acc >> 64);
+    }
+    if (ex.profile || ex.snap) {
+      const size_t base = (static_cast<size_t>(sample) * NOCC + p) * W;
+      long long ov = 0;
+      for (uint32_t i = w0; i < w1; ++i) {
+        const uint32_t x = pl[i];
+        if (ex.profile) ex.profile[base + i] += __popc(x);
+        if (ex.snap) {
+          if (t == ex.t0) ex.snap[base + i] = x;
+          if (t >= ex.t0) ov += __popc(x & ex.snap[base + i]);
+        }
+      }
+      if (ex.snap) {
+        const long long tot_ov = block_sum(ov, warp_tot);
+        if (threadIdx.x == 0) ex.tab_ac[e] = tot_ov;
+      }
+    }
+    __syncthreads();
+  }
+  // hop counters of this sample up to now
+  long long tot_cnt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    tot_cnt[k] = COUNT ? block_sum(static_cast<long long>(cnt[k]), warp_tot) : 0;
+    cnt[k] = 0;
+  }
+  if (threadIdx.x == 0) {
+    uint64_t* ctr = a.counters + 4ull * sample;
+    const size_t ec = (static_cast<size_t>(slot) * a.geo.S + sample) * 4;
+    for (int k = 0; k < 4; ++k) {
+      ctr[k] += static_cast<uint64_t>(tot_cnt[k]);
+      a.ex.tab_cnt[ec + k] = static_cast<int64_t>(ctr[k]);
     }
   }
   __syncthreads();
 }
 
-// Bimodal rings carry a class plane through every step: at most 512 threads,
-// so the compiler may use up to 128 registers.
-template <bool DIS, bool COUNT, bool FAST2>
+// The SCA kernel.  Ring (MODEL 0): one lattice plane, optionally a bimodal
+// class plane (DIS).  Two lanes (MODEL 1): planes A and B and, with turning
+// sites (DIS), the turning plane and the lane-change steps.  A quenched plane
+// costs registers in every step: at most 512 threads then, so the compiler
+// may use up to 128 registers.
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
 __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long warp_tot[32];
   __shared__ unsigned long long warp_s2[32];
+  constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
   const uint32_t W = a.geo.W, n_units = W / 8;
-  uint32_t* lat = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* cls = lat + W;
-  uint32_t* carry = cls + (DIS ? W : 0u);
+  uint32_t* lat = reinterpret_cast<uint32_t*>(smem_raw);  // NOCC planes
+  uint32_t* qp = lat + NOCC * W;                          // class or turning plane
+  uint32_t* carry = qp + (DIS ? W : 0u);                  // NOCC x n_units flags
   const uint32_t sample = blockIdx.x;
   const uint32_t n_glob = a.geo.first_sample + sample;
   const uint64_t s0 = a.clock->sweep;
   uint32_t rec = a.clock->next_time;
   const uint32_t kmax = a.sca_kmax;
 
-  for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) {
-    lat[i] = a.state[static_cast<size_t>(sample) * W + i];
-    if (DIS) cls[i] = a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + i];
-  }
-  for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) carry[u] = 0u;
+  for (uint32_t i = threadIdx.x; i < NOCC * W; i += blockDim.x)
+    lat[i] = a.state[static_cast<size_t>(sample) * NOCC * W + i];
+  if (DIS)
+    for (uint32_t i = threadIdx.x; i < W; i += blockDim.x)
+      qp[i] = a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + i];
+  for (uint32_t i = threadIdx.x; i < NOCC * n_units; i += blockDim.x) carry[i] = 0u;
   __syncthreads();
 
-  unsigned long long n_right = 0, n_left = 0;
+  unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
     const uint64_t s = s0 + it;
-    for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-      sca_unit<DIS, COUNT, FAST2, 0>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
-    __syncthreads();
-    for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-      sca_unit<DIS, COUNT, FAST2, 1>(lat, cls, carry, a, u, n_units, W, s, n_glob, kmax, n_right, n_left);
-    __syncthreads();
+    if (MODEL == kRing) {
+      for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
+        sca_unit<DIS, COUNT, FAST2, 0>(lat, qp, carry, a, u, n_units, W, s, n_glob, kmax, cnt[0], cnt[1]);
+      __syncthreads();
+      for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
+        sca_unit<DIS, COUNT, FAST2, 1>(lat, qp, carry, a, u, n_units, W, s, n_glob, kmax, cnt[0], cnt[1]);
+      __syncthreads();
+    } else {
+      uint32_t* A = lat;
+      uint32_t* B = lat + W;
+      for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) {
+        sca_lane_unit<0, 0>(A, carry, a, u, n_units, W, s, n_glob, a.rates.p, cnt[0]);
+        sca_lane_unit<1, 0>(B, carry + n_units, a, u, n_units, W, s, n_glob, a.rates.q, cnt[1]);
+      }
+      __syncthreads();
+      if (DIS) {
+        for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
+          sca_turn_unit<0>(A, B, qp, carry, a, u, n_units, s, n_glob, cnt[2]);
+        __syncthreads();
+      }
+      for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) {
+        sca_lane_unit<0, 1>(A, carry, a, u, n_units, W, s, n_glob, a.rates.p, cnt[0]);
+        sca_lane_unit<1, 1>(B, carry + n_units, a, u, n_units, W, s, n_glob, a.rates.q, cnt[1]);
+      }
+      __syncthreads();
+      if (DIS) {
+        for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
+          sca_turn_unit<1>(A, B, qp, carry, a, u, n_units, s, n_glob, cnt[3]);
+        __syncthreads();
+      }
+    }
     if (rec < a.n_times && a.times[rec] == s + 1) {
-      settle_carries(lat, carry, n_units);
-      sca_record<COUNT>(lat, a, rec, s + 1, sample, warp_tot, warp_s2, n_right, n_left);
+      settle_carries(lat, carry, n_units, W, NOCC);
+      sca_record<NOCC, COUNT>(lat, a, rec, s + 1, sample, warp_tot, warp_s2, cnt);
       ++rec;
     }
   }
-  settle_carries(lat, carry, n_units);
-  for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) a.state[static_cast<size_t>(sample) * W + i] = lat[i];
+  settle_carries(lat, carry, n_units, W, NOCC);
+  for (uint32_t i = threadIdx.x; i < NOCC * W; i += blockDim.x)
+    a.state[static_cast<size_t>(sample) * NOCC * W + i] = lat[i];
   if (COUNT) {
-    const long long nr = block_sum(static_cast<long long>(n_right), warp_tot);
-    const long long nl = block_sum(static_cast<long long>(n_left), warp_tot);
-    if (threadIdx.x == 0) {
-      a.counters[4ull * sample] += static_cast<uint64_t>(nr);
-      a.counters[4ull * sample + 1] += static_cast<uint64_t>(nl);
-    }
+    long long tot[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tot[k] = block_sum(static_cast<long long>(cnt[k]), warp_tot);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 4; ++k) a.counters[4ull * sample + k] += static_cast<uint64_t>(tot[k]);
   }
 }
 
-template <bool DIS, bool COUNT, bool FAST2>
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
 cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();
-  const cudaError_t e = cudaFuncSetAttribute(k_sca<DIS, COUNT, FAST2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+  const cudaError_t e = cudaFuncSetAttribute(k_sca<MODEL, DIS, COUNT, FAST2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_sca<DIS, COUNT, FAST2><<<a.geo.S, threads, smem, st>>>(a);
+  k_sca<MODEL, DIS, COUNT, FAST2><<<a.geo.S, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t sca_smem_bytes(uint32_t W, bool dis) {
-  return static_cast<size_t>(W) * 4u * (dis ? 2u : 1u) + static_cast<size_t>(W / 8u) * 4u;
+size_t sca_smem_bytes(uint32_t W, uint32_t planes, bool quenched) {
+  return static_cast<size_t>(W) * 4u * (planes + (quenched ? 1u : 0u)) + static_cast<size_t>(planes) * (W / 8u) * 4u;
 }
 
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
-  const bool dis = a.dis == kDisBimodal, count = a.count_hops != 0;
-  if (dis)
-    return count ? launch_sca_t<true, true, false>(a, threads, smem, st)
-                 : launch_sca_t<true, false, false>(a, threads, smem, st);
+  const bool count = a.count_hops != 0;
+  if (a.model == kTwoLane) {  // two lanes always count hops and turns
+    return a.dis == kDisTurning ? launch_sca_t<kTwoLane, true, true, false>(a, threads, smem, st)
+                                : launch_sca_t<kTwoLane, false, true, false>(a, threads, smem, st);
+  }
+  if (a.dis == kDisBimodal)
+    return count ? launch_sca_t<kRing, true, true, false>(a, threads, smem, st)
+                 : launch_sca_t<kRing, true, false, false>(a, threads, smem, st);
   // rates neither 0 nor "always" and at most two random planes: the specialised comparison
   const auto regular = [](uint32_t t) { return t != 0u && t != 0xFFFFFFFFu; };
   const bool fast2 = regular(a.rates.p) && regular(a.rates.q) && a.sca_kmax <= 2;
   if (fast2)
-    return count ? launch_sca_t<false, true, true>(a, threads, smem, st)
-                 : launch_sca_t<false, false, true>(a, threads, smem, st);
-  return count ? launch_sca_t<false, true, false>(a, threads, smem, st)
-               : launch_sca_t<false, false, false>(a, threads, smem, st);
+    return count ? launch_sca_t<kRing, false, true, true>(a, threads, smem, st)
+                 : launch_sca_t<kRing, false, false, true>(a, threads, smem, st);
+  return count ? launch_sca_t<kRing, false, true, false>(a, threads, smem, st)
+               : launch_sca_t<kRing, false, false, false>(a, threads, smem, st);
 }
 
 }  // namespace asep

@@ -66,8 +66,9 @@ def test_create_rejects_bad_params_without_device(A):
     bad = [dict(L=100), dict(L=1 << 23), dict(L=4096, domain_sites=48), dict(L=4096, p_thr=123),
            dict(L=4096, n_realizations=0), dict(L=4096, dis_kind=2), dict(L=4096, model=1, dis_kind=1),
            dict(L=4096 + 64, schedule=1), dict(L=4096, samples_per_real=3, first_sample=1),
-           # SCA schedule: ring only, no turning sites, L a multiple of 256, ring within one CTA
-           dict(L=4096 + 64, schedule=2), dict(L=4096, schedule=2, model=1), dict(L=1 << 21, schedule=2),
+           # SCA schedule: L a multiple of 256, the lattice within one CTA's shared memory
+           dict(L=4096 + 64, schedule=2), dict(L=1 << 21, schedule=2),
+           dict(L=1 << 19, schedule=2, model=1, dis_kind=2, dis_a_thr=4096, dis_b_thr=4096),
            dict(L=1 << 20, schedule=2, dis_kind=1, dis_a_thr=4096, dis_b_thr=4096), dict(L=4096, schedule=3)]
     for kw in bad:
         prm = A.make_params(**kw)

@@ -167,6 +167,19 @@ CASES = {
     "sca_bimodal_max_L": (dict(L=1 << 19, schedule=SCA, samples_per_real=1, p_thr=A.ASEP_ALWAYS, q_thr=0,
                                dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=4,
                                seed=7), 3, [0, 3]),
+    # the two-lane SCA (paper sec. 3): even bonds, A -> B, odd bonds, B -> A
+    "sca_two_lane_turning": (dict(model=TWO, L=4096, schedule=SCA, samples_per_real=3, init_kind=1, init_seed=9,
+                                  p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.1),
+                                  dis_b_thr=th(0.3), dis_seed=10, seed=11,
+                                  flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 20, [0, 5, 20]),
+    "sca_two_lane_rate1": (dict(model=TWO, L=1 << 16, schedule=SCA, samples_per_real=2, init_kind=1, init_seed=4,
+                                p_thr=A.ASEP_ALWAYS, q_thr=A.ASEP_ALWAYS, dis_kind=A.ASEP_DIS_TURNING,
+                                dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=5, seed=6), 10, [0, 10]),
+    "sca_two_lane_plain": (dict(model=TWO, L=2048, schedule=SCA, samples_per_real=5, init_kind=1, init_seed=2,
+                                p_thr=th(0.7), q_thr=th(0.4), seed=12), 25, [0, 12, 25]),
+    "sca_two_lane_max_L": (dict(model=TWO, L=1 << 18, schedule=SCA, samples_per_real=1, init_kind=1, init_seed=3,
+                                p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
+                                dis_b_thr=th(0.1), dis_seed=6, seed=7), 3, [0, 3]),
     "cluster_ring_2x": (dict(L=1 << 20, domain_sites=256, samples_per_real=2, p_thr=th(0.75), q_thr=th(0.25),
                              seed=51), 5, [0, 2, 5]),
     "cluster_ring_d64": (dict(L=1 << 18, domain_sites=64, samples_per_real=2, p_thr=th(0.6), seed=52), 6, [0, 6]),

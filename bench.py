@@ -386,7 +386,7 @@ def other_workloads():
     sweeps, snapshots every 100), quenched bimodal disorder and the two-lane
     model with turning sites (10^4-sweep windows of their 10^7 / 10^6 sweep
     runs, log-spaced sample times, two-lane currents, profile and
-    autocorrelation on)."""
+    autocorrelation on), the latter also under the paper's two-lane SCA."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
@@ -412,6 +412,12 @@ def other_workloads():
               p_thr=A.ASEP_ALWAYS, q_thr=A.ASEP_ALWAYS, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
               dis_b_thr=th(0.1), dis_seed=3, init_kind=A.ASEP_INIT_BERNOULLI_HALF, init_seed=4, seed=1,
               flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=t0), lt, 2),
+        ("two lanes, the paper's SCA sequence (even bonds, A->B, odd bonds, B->A) with its in-lane rate 0.5: "
+         "2 x L=2^16, turning density 0.05, omega 0.1, Bernoulli(1/2) start, 128 samples, 10^4-MCS window",
+         dict(model=A.ASEP_MODEL_TWO_LANE, L=1 << 16, schedule=A.ASEP_SCHED_SCA, samples_per_real=128,
+              p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
+              dis_seed=3, init_kind=A.ASEP_INIT_BERNOULLI_HALF, init_seed=4, seed=1,
+              flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=t0), lt, 2),
     ]
     stream = torch.cuda.current_stream()
     out = []
@@ -430,6 +436,7 @@ def other_workloads():
             attempts = lanes * kw["L"] * info["S"] * win
             out.append({"workload": name, "attempts": attempts, "ms": ms, "attempts_per_s": attempts / (ms / 1e3),
                         "kernel": ("k_serial" if kw.get("schedule") == A.ASEP_SCHED_SERIAL
+                                   else "k_sca" if kw.get("schedule") == A.ASEP_SCHED_SCA
                                    else "k_cluster" if info["cluster"] > 1 else "k_domain"),
                         "samples_per_group": info["samples_per_group"]})
     return out

@@ -44,9 +44,16 @@
  *                      plane k of its 32-bond group (plane k of four groups
  *                      = Philox call k of tag 7, ctr3 = 2 * unit + phase;
  *                      group g = bonds 32g..32g+31 of the phase, lane of bond
- *                      m = 2 (m mod 16) + (m / 16 mod 2)).  Ring model, no
- *                      disorder or bimodal; L a multiple of 256 with the ring
- *                      in one CTA's shared memory (L <= 2^20, bimodal 2^19).
+ *                      m = 2 (m mod 16) + (m / 16 mod 2)).  Two lanes (sec.
+ *                      3, its five-step sequence): the bonds of lane A (right
+ *                      hops, p) and of lane B (left hops, q; planes from
+ *                      ctr3 with bit 31 set) in each phase, with turning
+ *                      sites the A -> B lane changes after the even phase
+ *                      and B -> A after the odd one (probability omega, one
+ *                      draw per candidate site: tag 8, call = step, ctr3 =
+ *                      site / 4).  L a multiple of 256 with the lattice in
+ *                      one CTA's shared memory (ring L <= 2^20, bimodal or
+ *                      two lanes 2^19, two lanes with turning sites 2^18).
  *
  * Error behaviour: every function returns ASEP_OK (0) or a negative
  * ASEP_ERR_* code and never aborts; the context keeps a message readable with

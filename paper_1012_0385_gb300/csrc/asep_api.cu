@@ -1225,8 +1225,8 @@ int asep_destroy(asep_ctx* ctx) {
 // Some callers cannot allocate device memory at the moment they want to run
 // work: a host application whose device memory is owned by another allocator
 // or pool that refuses outside requests, code that must not grow its memory
-// footprint after start-up, or a thread that may not hit the driver's
-// allocation path (cudaMalloc can synchronise the device).  For them the
+// footprint after start-up, or a thread that may not enter cudaMalloc
+// (which can synchronise the device).  For them the
 // batch sweep below keeps its work queue -- context descriptors, the item
 // list and the queue counter -- in one fixed static device array instead of
 // a batch object's workspace.  The array belongs to the library: every GPU

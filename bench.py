@@ -116,15 +116,20 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-def kernel_source_digest() -> str:
-    """sha256 prefix over the kernel sources (the .cu files and the device header)."""
-    import glob
+KERNEL_SOURCES = {
+    "domain": ("asep_kernels.cu", "asep_device.cuh", "asep_internal.h"),
+    "sca": ("asep_sca.cu", "asep_device.cuh", "asep_internal.h"),
+}
+
+
+def kernel_source_digest(kernel: str = "domain") -> str:
+    """sha256 prefix over the source files a kernel is compiled from."""
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1012_0385_gb300", "csrc")
-    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
-        h.update(open(path, "rb").read())
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -134,7 +139,7 @@ def _traffic_from_profile(kernel: str = "domain"):
     name = "k_domain_growth_regime_traffic.txt" if kernel == "domain" else "k_sca_growth_regime_traffic.txt"
     prof = os.path.join(ROOT, "profiles", name)
     try:
-        digest = kernel_source_digest()
+        digest = kernel_source_digest(kernel)
         kv = dict(line.strip().split("=", 1) for line in open(prof) if "=" in line)
         if kv.get("kernel_source_sha256_16") == digest:
             return float(kv["dram_bytes_per_launch"])

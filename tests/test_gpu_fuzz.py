@@ -1,0 +1,88 @@
+"""Randomised parity: configurations drawn from a fixed seed across every
+schedule, model, disorder kind, size, rate class (0, "always", two-plane,
+twenty-bit), initial state, observable flag and sample-time pattern, each
+bit-exact against the oracle (lattices, every record of the height sums, the
+hop counters at every record, profiles, overlaps and the seam height)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_0385_gb300 import asep as A
+
+pytestmark = pytest.mark.gpu
+
+th = oracle.threshold
+N_CASES = 120
+RATES = [0, A.ASEP_ALWAYS, th(0.75), th(0.25), th(0.5), th(0.6), th(0.3), th(0.9)]
+
+
+def draw(k: int):
+    rng = np.random.default_rng(1000 + k)
+    schedule = int(rng.choice([A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_SCA, A.ASEP_SCHED_SERIAL]))
+    model = int(rng.integers(2))
+    dis = int(rng.choice([0, 2])) if model == 1 else int(rng.choice([0, 1]))
+    if schedule == A.ASEP_SCHED_SERIAL:
+        L = int(2 ** rng.integers(6, 12))
+        kw = dict(schedule=schedule)
+    elif schedule == A.ASEP_SCHED_SCA:
+        L = 256 * int(rng.integers(1, 24))
+        kw = dict(schedule=schedule)
+    else:
+        D = int(2 ** rng.integers(5, 9))
+        L = 2 * D * int(rng.integers(1, 40))
+        kw = dict(domain_sites=D)
+    n_real = int(rng.integers(1, 3)) if dis else 1
+    spr = int(rng.integers(1, 6))
+    p, q = (int(rng.choice(RATES)) for _ in range(2))
+    if model == 1 and schedule == A.ASEP_SCHED_DOMAIN and rng.random() < 0.5:
+        p = q = A.ASEP_ALWAYS  # the two-lane configuration's rate 1
+    kw.update(model=model, L=L, n_realizations=n_real, samples_per_real=spr, p_thr=p, q_thr=q,
+              seed=int(rng.integers(1, 2**40)), init_kind=int(rng.integers(2)), init_seed=int(rng.integers(1, 1000)))
+    if dis == 1:
+        kw.update(dis_kind=1, dis_a_thr=th(float(rng.choice([0.1, 0.5]))), dis_b_thr=int(rng.choice(RATES)),
+                  dis_c_thr=int(rng.choice(RATES)), dis_seed=int(rng.integers(1, 1000)))
+    elif dis == 2:
+        kw.update(dis_kind=2, dis_a_thr=th(float(rng.choice([0.05, 0.3]))), dis_b_thr=th(float(rng.choice([0.1, 0.7]))),
+                  dis_seed=int(rng.integers(1, 1000)))
+    n = int(rng.integers(1, 25))
+    times = sorted(set([0] * int(rng.integers(2)) + [int(x) for x in rng.integers(1, n + 1, size=int(rng.integers(1, 4)))]))
+    flags = 0
+    if model == 0 and rng.random() < 0.3:
+        flags |= A.ASEP_FLAG_NO_HOP_COUNTS
+    if rng.random() < 0.5:
+        flags |= A.ASEP_FLAG_PROFILE
+    if rng.random() < 0.5:
+        flags |= A.ASEP_FLAG_AUTOCORR
+        kw["autocorr_t0"] = int(rng.choice(times))
+    kw["flags"] = flags
+    chunks = [n] if rng.random() < 0.5 else [n // 2, n - n // 2]
+    return kw, [c for c in chunks if c > 0], times
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_0385_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("k", range(N_CASES))
+def test_random_configuration_bit_exact(k):
+    from test_gpu_parity import assert_same, oracle_params, run_gpu
+
+    kw, chunks, times = draw(k)
+    g = run_gpu(kw, chunks, times)
+    P = oracle_params(kw)
+    t0 = kw.get("autocorr_t0") if kw["flags"] & A.ASEP_FLAG_AUTOCORR else None
+    ref = oracle.run(P, sum(chunks), times, autocorr_t0=t0)
+    if kw["flags"] & A.ASEP_FLAG_NO_HOP_COUNTS:
+        ref.counters[:] = 0
+        ref.extra["counters_at"][:] = 0
+    if P.dis_kind != 0:
+        assert np.array_equal(g["dis"], oracle.disorder(P))
+    assert_same(g, ref, P, times)

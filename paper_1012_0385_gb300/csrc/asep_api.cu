@@ -641,6 +641,7 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     } else {
       SerialLaunch a;
       a.geo = geometry(ctx);
+      a.count_hops = (ctx->p.model == ASEP_MODEL_TWO_LANE || !(ctx->p.flags & ASEP_FLAG_NO_HOP_COUNTS)) ? 1u : 0u;
       a.state = ctx->d_state;
       a.mask = ctx->d_mask;
       a.rates = rates(ctx);

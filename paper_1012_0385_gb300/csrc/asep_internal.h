@@ -114,6 +114,7 @@ struct DomainLaunch {
 
 struct SerialLaunch {
   Geometry geo;
+  uint32_t count_hops;     // ring: count hops (two lanes always count)
   uint32_t* state;
   const uint32_t* mask;
   Rates rates;

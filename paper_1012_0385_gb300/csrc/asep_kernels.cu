@@ -976,8 +976,10 @@ __global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
       if (accept(ru, thr)) {
         flip_at(A, i);
         flip_at(A, i1);
-        c0 += x == 1u;
-        c1 += x != 1u;
+        if (a.count_hops) {
+          c0 += x == 1u;
+          c1 += x != 1u;
+        }
       }
     }
   };

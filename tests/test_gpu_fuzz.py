@@ -86,3 +86,45 @@ def test_random_configuration_bit_exact(k):
     if P.dis_kind != 0:
         assert np.array_equal(g["dis"], oracle.disorder(P))
     assert_same(g, ref, P, times)
+
+
+def test_random_contexts_in_one_batch_bit_exact():
+    """The domain-schedule draws, all in one persistent batch, advanced in
+    uneven steps (contexts join late and finish early), each bit-exact
+    against the oracle."""
+    from test_gpu_parity import assert_same, oracle_params
+
+    cases = [draw(k) for k in range(N_CASES)]
+    cases = [c for c in cases if c[0].get("schedule", A.ASEP_SCHED_DOMAIN) == A.ASEP_SCHED_DOMAIN][:16]
+    assert len(cases) >= 8
+    ctxs = [A.asep_create(A.make_params(**kw), sample_times=times) for kw, _, times in cases]
+    try:
+        left = [sum(chunks) for _, chunks, _ in cases]
+        rng = np.random.default_rng(7)
+        with A.asep_batch_create(max_jobs=len(ctxs), max_items=1 << 16) as b:
+            step = 0
+            while any(left):
+                active = [i for i in range(len(ctxs)) if left[i] and i <= 2 * step]
+                q = [min(left[i], int(rng.integers(1, 9))) for i in active]
+                A.asep_batch_sweep(b, [ctxs[i] for i in active], q)
+                for i, k in zip(active, q):
+                    left[i] -= k
+                step += 1
+        for (kw, chunks, times), c in zip(cases, ctxs):
+            words, sweep = A.asep_state(c)
+            sh, sh2, w2 = A.asep_width(c)
+            g = dict(words=words, sh=sh, sh2=sh2, w2=w2, cnt=A.asep_counters(c), dis=A.asep_disorder(c),
+                     cur=A.asep_currents(c), hoff=None,
+                     prof=A.asep_profile(c) if kw["flags"] & A.ASEP_FLAG_PROFILE else None,
+                     ac=A.asep_autocorr(c) if kw["flags"] & A.ASEP_FLAG_AUTOCORR else None)
+            assert sweep == sum(chunks)
+            P = oracle_params(kw)
+            t0 = kw.get("autocorr_t0") if kw["flags"] & A.ASEP_FLAG_AUTOCORR else None
+            ref = oracle.run(P, sum(chunks), times, autocorr_t0=t0)
+            if kw["flags"] & A.ASEP_FLAG_NO_HOP_COUNTS:
+                ref.counters[:] = 0
+                ref.extra["counters_at"][:] = 0
+            assert_same(g, ref, P, times)
+    finally:
+        for c in ctxs:
+            c.close()

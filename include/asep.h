@@ -82,7 +82,7 @@ extern "C" {
 #define ASEP_ERR_INVALID (-1) /* bad argument or unsupported combination */
 #define ASEP_ERR_NOMEM (-2)   /* device or host allocation failed */
 #define ASEP_ERR_CUDA (-3)    /* a CUDA runtime call failed */
-#define ASEP_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define ASEP_ERR_TIMEOUT (-4) /* reserved: no kernel of this library waits on another, so none times out */
 #define ASEP_ERR_STATE (-5)   /* call not valid in the context's state */
 
 #define ASEP_MODEL_RING 0u     /* one ring, right rate p_i, left rate q_{i+1} */
@@ -117,7 +117,8 @@ typedef void (*asep_free_fn)(void* ptr, size_t bytes, void* user);
 typedef struct asep_params {
   uint32_t model;            /* ASEP_MODEL_* */
   uint32_t schedule;         /* ASEP_SCHED_* */
-  uint64_t L;                /* sites per lane; DOMAIN: multiple of 2*domain_sites; SERIAL: power of two */
+  uint64_t L;                /* sites per lane, multiple of 64 in [64, 2^22]; DOMAIN: multiple of
+                                2*domain_sites; SERIAL: power of two; SCA: multiple of 256 */
   uint32_t domain_sites;     /* D: power of two in [32, 2048]; 0 = 256 or the largest that divides L/2 */
   uint32_t n_realizations;   /* quenched-disorder realizations (1 without disorder) */
   uint32_t samples_per_real; /* samples per realization */
@@ -185,7 +186,9 @@ int asep_width(asep_ctx* ctx, int64_t* sum_h, uint64_t* sum_h2, double* w2, size
 int asep_state(asep_ctx* ctx, uint32_t* words, size_t n_words, uint64_t* sweep_out);
 
 /* Replace the lattices and the sweep counter (resume from a checkpoint made
- * by asep_state, or set a test state).  Layout as asep_state. */
+ * by asep_state, or set a test state).  Layout as asep_state.  The hop
+ * counters keep running; the loaded lattice becomes the reference of
+ * asep_height_offset.  Synchronises. */
 int asep_load_state(asep_ctx* ctx, const uint32_t* words, size_t n_words, uint64_t sweep);
 
 /* Start the ensemble again on the same buffers: re-draw the initial state
@@ -228,9 +231,10 @@ int asep_autocorr(asep_ctx* ctx, int64_t* out, size_t n);
 /* Ring model with hop counting on: the height H(t) of the surface column
  * between sites L-1 and 0 at every sample time recorded so far, relative to
  * the lattice at the last asep_create, asep_reset or asep_load_state, layout
- * [n_recorded][S]; records taken before the last load read 0.  With h_i the open prefix sum of asep_width, the absolute
- * column heights are H + h_i and their mean H + sum_h / L; its slope in t is
- * the growth velocity (paper sec. 2, Eq. KPZ).  A right hop across a bond
+ * [n_recorded][S]; records taken before the last load read 0.  With h_i the
+ * open prefix sum of asep_width, the absolute column heights are H + h_i and
+ * their mean H + sum_h / L; its slope in t is the growth velocity (paper
+ * sec. 2, Eq. KPZ).  A right hop across a bond
  * lowers that bond's column by 2 and a left hop raises it, so
  * H(t) = (sum_h(ref) - sum_h(t) - 2 [(R - Lh)(t) - (R - Lh)(ref)]) / L exactly,
  * with R, Lh the cumulative right and left hop counters; the division is
@@ -238,6 +242,8 @@ int asep_autocorr(asep_ctx* ctx, int64_t* out, size_t n);
  * Synchronises. */
 int asep_height_offset(asep_ctx* ctx, int64_t* out, size_t n);
 
+/* Sizes, progress, device memory, launch count and launch plan of the
+ * context (no synchronisation; n_recorded and sweep count enqueued work). */
 int asep_get_info(const asep_ctx* ctx, asep_info* info);
 
 /* Choose the launch plan of a domain-schedule context (the autotuner's knob;

@@ -394,3 +394,44 @@ def test_width_within_3_sigma_of_serial_reference(case):
             a, b = g["w2"][ti, :, pl], ser[ti, :, pl]
             sig = np.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size)
             assert abs(a.mean() - b.mean()) < 3 * sig, (case, times[ti], pl, a.mean(), b.mean(), sig)
+
+
+# ---------------------------------------------------------------------------
+# Degenerate inputs
+# ---------------------------------------------------------------------------
+
+def test_zero_sweeps_and_no_sample_times():
+    """asep_sweep(0) changes nothing; a context without sample times runs and
+    reports an empty height table; the lattice still matches the oracle."""
+    kw = dict(L=4096, domain_sites=128, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=4)
+    with A.asep_create(A.make_params(**kw), sample_times=[]) as ctx:
+        before, s0 = A.asep_state(ctx)
+        A.asep_sweep(ctx, 0)
+        after, s1 = A.asep_state(ctx)
+        assert s0 == s1 == 0 and np.array_equal(before, after)
+        A.asep_sweep(ctx, 9)
+        words, s = A.asep_state(ctx)
+        sh, sh2, w2 = A.asep_width(ctx)
+        assert s == 9 and sh.shape[0] == 0 and A.asep_get_info(ctx)["n_recorded"] == 0
+    ref = oracle.run(oracle_params(kw), 9, [])
+    assert np.array_equal(words, ref.state)
+
+
+@pytest.mark.parametrize("schedule", [A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_SCA])
+def test_many_tiny_samples(schedule):
+    """Thousands of minimal rings (many samples per CTA, many CTAs), bit-exact
+    on sampled samples, counters and heights for all."""
+    L = 64 if schedule == A.ASEP_SCHED_DOMAIN else 256
+    kw = dict(L=L, schedule=schedule, samples_per_real=5000, p_thr=th(0.7), q_thr=th(0.2), seed=8)
+    if schedule == A.ASEP_SCHED_DOMAIN:
+        kw["domain_sites"] = 32
+    g = run_gpu(kw, [13], [0, 13])
+    P = oracle_params(kw)
+    ref = oracle.run(P, 13, [0, 13], samples=[0, 1, 2499, 4998, 4999])
+    for s in (0, 1, 2499, 4998, 4999):
+        assert np.array_equal(g["words"][s], ref.state[s]), s
+        assert np.array_equal(g["cnt"][s], ref.counters[s]), s
+        assert int(g["sh"][-1, s, 0]) == int(ref.sum_h[-1, s, 0]), s
+    # every ring keeps its particle number
+    pop = np.unpackbits(g["words"].view(np.uint8), axis=-1).sum(axis=-1)
+    assert np.all(pop == L // 2)

@@ -435,3 +435,23 @@ def test_many_tiny_samples(schedule):
     # every ring keeps its particle number
     pop = np.unpackbits(g["words"].view(np.uint8), axis=-1).sum(axis=-1)
     assert np.all(pop == L // 2)
+
+
+def test_sca_growth_exponent_is_kpz():
+    """The paper's SCA schedule stays in the KPZ class (sec. 2.2: the SCA
+    results were compared with RSU): W^2 - 1/4 grows as t^(2 beta) with
+    beta = alpha / z = 1/3 in the growth regime (t << L^(3/2) = 5.9e6).  The
+    local slope approaches 2/3 from below (0.56 at t = 16, 0.65 at t = 4096
+    for both schedules), so the fit window is t = 256 .. 4096.  (p = 1 from
+    the flat state is no test: the deterministic SCA returns to flat.)"""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as f:
+        g = json.load(f)["kpz_exponents"]
+    beta = g["alpha"] / g["z"]
+    times = [256, 512, 1024, 2048, 4096]
+    kw = dict(L=1 << 15, schedule=SCA, samples_per_real=128, seed=17, p_thr=th(0.75), q_thr=th(0.25))
+    w2 = run_gpu(kw, [times[-1]], times)["w2"][:, :, 0].mean(axis=1)
+    slope = np.polyfit(np.log(times), np.log(w2 - 0.25), 1)[0]
+    assert abs(slope - 2 * beta) < 0.07, slope

@@ -904,157 +904,204 @@ __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
 }
 
 // ---------------------------------------------------------------------------
-// Serial random-sequential update, one thread per sample
+// Serial random-sequential update, one warp per sample
 // ---------------------------------------------------------------------------
+//
+// The attempts of a sweep form one sequence; the warp takes them 32 at a
+// time in sequence order (lane k = attempt base + k).  Two attempts commute
+// when their bonds share no site, so the longest prefix of a batch in which
+// no attempt shares a site with an earlier one gives the same lattice
+// whether applied one after another or all at once.  The warp applies that
+// prefix (its flips are disjoint bits, written with shared-memory atomics)
+// and starts the next batch at the first attempt that collided.  Bonds i
+// and j share a site exactly when i / 2 == j / 2 or (i + 1 mod L) / 2 ==
+// (j + 1 mod L) / 2, so two match operations find every collision.  The
+// lattice (and the quenched plane) is staged in shared memory when it fits.
 
-__device__ __forceinline__ uint32_t bit_at(const uint32_t* w, uint64_t i) {
-  return (w[i >> 5] >> (i & 31u)) & 1u;
-}
-__device__ __forceinline__ void flip_at(uint32_t* w, uint64_t i) { w[i >> 5] ^= 1u << (i & 31u); }
-
-// One thread per sample.  With SMEM the thread copies its lattice (and the
-// quenched plane) into its own slice of shared memory for the launch, so the
-// dependent read-modify-write chain of an attempt stays on chip; the next
-// Philox call is drawn while the current two attempts run.
 template <uint32_t MODEL, uint32_t DIS, bool SMEM>
-__global__ void __launch_bounds__(32) k_serial(const SerialLaunch a) {
+__global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
   extern __shared__ __align__(16) uint32_t serial_smem[];
-  const uint32_t sample = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sample >= a.geo.S) return;
-  const uint64_t L = a.geo.L;
-  const uint32_t W = a.geo.W;
-  constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + (DIS != kDisNone ? 1u : 0u);
-  uint32_t* gA = a.state + static_cast<size_t>(sample) * a.geo.planes * W;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  const uint32_t sample = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (sample >= a.geo.S) return;  // whole warps leave together
+  const uint32_t L = static_cast<uint32_t>(a.geo.L), W = a.geo.W;
+  constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
+  constexpr uint32_t NPL = NOCC + (DIS != kDisNone ? 1u : 0u);
+  uint32_t* gA = a.state + static_cast<size_t>(sample) * NOCC * W;
   const uint32_t* gM =
       (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
   uint32_t* A = gA;
-  uint32_t* B = gA + W;
   const uint32_t* M = gM;
   if (SMEM) {
-    uint32_t* mine = serial_smem + static_cast<size_t>(threadIdx.x) * NPL * W;
-    for (uint32_t w = 0; w < a.geo.planes * W; ++w) mine[w] = gA[w];
+    uint32_t* mine = serial_smem + static_cast<size_t>(wib) * NPL * W;
+    for (uint32_t w = lane; w < NOCC * W; w += 32) mine[w] = gA[w];
     if (DIS != kDisNone)
-      for (uint32_t w = 0; w < W; ++w) mine[a.geo.planes * W + w] = gM[w];
+      for (uint32_t w = lane; w < W; w += 32) mine[NOCC * W + w] = gM[w];
     A = mine;
-    B = mine + W;
-    M = mine + a.geo.planes * W;
+    M = mine + NOCC * W;
+    __syncwarp();
   }
+  uint32_t* B = A + W;
   const uint32_t n_glob = a.geo.first_sample + sample;
   const uint2 key = key_of(a.seed);
-  const uint64_t n_att = MODEL == kTwoLane ? 2 * L : L;
-  const uint32_t logL = 63u - static_cast<uint32_t>(__clzll(static_cast<long long>(L)));
-  unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+  const uint32_t n_att = MODEL == kTwoLane ? 2u * L : L;
+  const uint32_t logL = 31u - static_cast<uint32_t>(__clz(static_cast<int>(L)));
+  unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;  // this lane's share of the sample's counters
   const uint64_t s0 = a.clock->sweep;
   uint32_t rec = a.clock->next_time;
-  uint64_t* my_ctr = a.counters + 4 * static_cast<size_t>(sample);
-  const uint64_t base0 = my_ctr[0], base1 = my_ctr[1], base2 = my_ctr[2], base3 = my_ctr[3];
+  const uint32_t lt_mask = (1u << lane) - 1u;
 
-  auto attempt = [&](uint32_t rb, uint32_t ru) {
-    if (MODEL == kTwoLane) {
-      const uint64_t j = rb & (n_att - 1);
-      const uint32_t lane = static_cast<uint32_t>(j >> logL);
-      const uint64_t i = j & (L - 1), i1 = (i + 1) & (L - 1);
-      uint32_t* pl = lane ? B : A;
-      const uint32_t x = bit_at(pl, i) | (bit_at(pl, i1) << 1);
-      const uint32_t thr = lane == 0 ? (x == 1u ? a.rates.p : 0u) : (x == 2u ? a.rates.q : 0u);
-      if (accept(ru, thr)) {
-        flip_at(pl, i);
-        flip_at(pl, i1);
-        c0 += lane ^ 1u;
-        c1 += lane;
+  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
+    const uint64_t s = s0 + it;
+    uint32_t base = 0;
+    while (base < n_att) {
+      const uint32_t b = min(32u, n_att - base);
+      const bool active = lane < b;
+      const uint32_t att = base + lane;
+      const uint4 x4 = philox10(ctr_of(s, kTagSer, 0, n_glob, att >> 1), key);
+      const uint32_t rb = (att & 1u) ? x4.z : x4.x, ru = (att & 1u) ? x4.w : x4.y;
+      uint32_t pl = 0, i;
+      if (MODEL == kTwoLane) {
+        const uint32_t j = rb & (n_att - 1u);
+        pl = j >> logL;
+        i = j & (L - 1u);
+      } else {
+        i = rb & (L - 1u);
       }
-    } else {
-      const uint64_t i = rb & (L - 1), i1 = (i + 1) & (L - 1);
-      const uint32_t x = bit_at(A, i) | (bit_at(A, i1) << 1);
+      const uint32_t i1 = (i + 1u) & (L - 1u);
+      uint32_t* P = pl ? B : A;
+      const uint32_t x = ((P[i >> 5] >> (i & 31u)) & 1u) | (((P[i1 >> 5] >> (i1 & 31u)) & 1u) << 1);
       uint32_t thr;
-      if (DIS == kDisBimodal) {
-        thr = x == 1u ? (bit_at(M, i) ? a.rates.p_slow : a.rates.p)
-                      : (x == 2u ? (bit_at(M, i1) ? a.rates.q_slow : a.rates.q) : 0u);
+      if (MODEL == kTwoLane) {
+        thr = pl == 0 ? (x == 1u ? a.rates.p : 0u) : (x == 2u ? a.rates.q : 0u);
+      } else if (DIS == kDisBimodal) {
+        thr = x == 1u ? (((M[i >> 5] >> (i & 31u)) & 1u) ? a.rates.p_slow : a.rates.p)
+                      : (x == 2u ? (((M[i1 >> 5] >> (i1 & 31u)) & 1u) ? a.rates.q_slow : a.rates.q) : 0u);
       } else {
         thr = x == 1u ? a.rates.p : (x == 2u ? a.rates.q : 0u);
       }
-      if (accept(ru, thr)) {
-        flip_at(A, i);
-        flip_at(A, i1);
-        if (a.count_hops) {
+      const bool hop = active && accept(ru, thr);
+      // collisions with earlier attempts of the batch (inactive lanes get keys no bond has)
+      const uint32_t k1 = active ? (pl << 31) | (i >> 1) : 0x7FE00000u | lane;
+      const uint32_t k2 = active ? (pl << 31) | (i1 >> 1) : 0x7FF00000u | lane;
+      const uint32_t same = __match_any_sync(0xffffffffu, k1) | __match_any_sync(0xffffffffu, k2);
+      const uint32_t coll = __ballot_sync(0xffffffffu, active && (same & lt_mask) != 0u);
+      const uint32_t c = coll ? static_cast<uint32_t>(__ffs(coll)) - 1u : b;
+      if (lane < c && hop) {
+        atomicXor(&P[i >> 5], 1u << (i & 31u));
+        atomicXor(&P[i1 >> 5], 1u << (i1 & 31u));
+        if (MODEL == kTwoLane) {
+          c0 += pl == 0u;
+          c1 += pl == 1u;
+        } else if (a.count_hops) {
           c0 += x == 1u;
           c1 += x != 1u;
         }
       }
-    }
-  };
-
-  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
-    const uint64_t s = s0 + it;
-    uint4 x = philox10(ctr_of(s, kTagSer, 0, n_glob, 0u), key);
-    for (uint64_t k = 0; k < n_att; k += 2) {
-      const uint32_t next = static_cast<uint32_t>(k >> 1) + 1u;  // drawn ahead; unused after the last pair
-      const uint4 xn = philox10(ctr_of(s, kTagSer, 0, n_glob, next), key);
-      attempt(x.x, x.y);
-      attempt(x.z, x.w);
-      x = xn;
+      __syncwarp();
+      base += c;
     }
     if (MODEL == kTwoLane && DIS == kDisTurning) {
-      for (uint32_t w = 0; w < W; ++w) {
+      // lane changes: every event touches only (A_i, B_i); words are split over the lanes
+      for (uint32_t w = lane; w < W; w += 32) {
         uint32_t e = M[w] & (A[w] ^ B[w]);
         while (e) {
-          const uint32_t b = __ffs(e) - 1;
+          const uint32_t bit = __ffs(e) - 1;
           e &= e - 1;
-          const uint64_t site = 32ull * w + b;
-          const uint4 x = philox10(ctr_of(s, kTagTurn, 0, n_glob, static_cast<uint32_t>(site >> 2)), key);
-          if (accept(pick(x, static_cast<uint32_t>(site & 3u)), a.rates.omega)) {
-            if (A[w] & (1u << b)) ++c2;
+          const uint32_t site = 32u * w + bit;
+          const uint4 r = philox10(ctr_of(s, kTagTurn, 0, n_glob, site >> 2), key);
+          if (accept(pick(r, site & 3u), a.rates.omega)) {
+            if (A[w] & (1u << bit)) ++c2;
             else ++c3;
-            A[w] ^= 1u << b;
-            B[w] ^= 1u << b;
+            A[w] ^= 1u << bit;
+            B[w] ^= 1u << bit;
           }
         }
       }
+      __syncwarp();
     }
     if (rec < a.n_times && a.times[rec] == s + 1) {
-      for (uint32_t p = 0; p < a.geo.planes; ++p) {
-        const uint32_t* pl = p ? B : A;
-        long long h = 0, s1 = 0;
-        unsigned __int128 s2 = 0;
-        for (uint32_t w = 0; w < W; ++w) {
-          const uint32_t x = pl[w];
-          for (uint32_t b = 0; b < 32; ++b) {
-            h += ((x >> b) & 1u) ? 1 : -1;
+      const uint32_t chunk = (W + 31u) / 32u;
+      const uint32_t w0 = min(W, lane * chunk), w1 = min(W, w0 + chunk);
+      for (uint32_t p = 0; p < NOCC; ++p) {
+        const uint32_t* pw = p ? B : A;
+        long long tot = 0;
+        for (uint32_t w = w0; w < w1; ++w) tot += 2 * __popc(pw[w]) - 32;
+        long long h = tot;  // inclusive warp scan of the chunk totals
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long t = __shfl_up_sync(0xffffffffu, h, o);
+          if (lane >= static_cast<uint32_t>(o)) h += t;
+        }
+        h -= tot;
+        long long s1 = 0;
+        unsigned long long s2 = 0;
+        for (uint32_t w = w0; w < w1; ++w) {
+          const uint32_t xw = pw[w];
+          for (uint32_t bb = 0; bb < 32; ++bb) {
+            h += ((xw >> bb) & 1u) ? 1 : -1;
             s1 += h;
             s2 += static_cast<unsigned long long>(h * h);
           }
         }
-        const size_t e = (static_cast<size_t>(rec) * a.geo.S + sample) * a.geo.planes + p;
-        a.tab_sh[e] = s1;
-        a.tab_sh2[2 * e] = static_cast<uint64_t>(s2);
-        a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2 >> 64);
         // profile and autocorrelation overlap of this plane
-        uint32_t* snap = a.ex.snap ? a.ex.snap + (static_cast<size_t>(sample) * a.geo.planes + p) * W : nullptr;
-        uint32_t* prof = a.ex.profile ? a.ex.profile + (static_cast<size_t>(sample) * a.geo.planes + p) * W : nullptr;
+        const size_t pbase = (static_cast<size_t>(sample) * NOCC + p) * W;
         long long ov = 0;
-        for (uint32_t w = 0; w < W; ++w) {
-          if (prof) prof[w] += __popc(pl[w]);
-          if (snap) {
-            if (s + 1 == a.ex.t0) snap[w] = pl[w];
-            if (s + 1 >= a.ex.t0) ov += __popc(pl[w] & snap[w]);
+        for (uint32_t w = w0; w < w1; ++w) {
+          if (a.ex.profile) a.ex.profile[pbase + w] += __popc(pw[w]);
+          if (a.ex.snap) {
+            if (s + 1 == a.ex.t0) a.ex.snap[pbase + w] = pw[w];
+            if (s + 1 >= a.ex.t0) ov += __popc(pw[w] & a.ex.snap[pbase + w]);
           }
         }
-        if (snap) a.ex.tab_ac[e] = ov;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          ov += __shfl_xor_sync(0xffffffffu, ov, o);
+        }
+        unsigned __int128 s2_all = 0;
+        for (int l = 0; l < 32; ++l) s2_all += __shfl_sync(0xffffffffu, s2, l);
+        if (lane == 0) {
+          const size_t e = (static_cast<size_t>(rec) * a.geo.S + sample) * NOCC + p;
+          a.tab_sh[e] = s1;
+          a.tab_sh2[2 * e] = static_cast<uint64_t>(s2_all);
+          a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2_all >> 64);
+          if (a.ex.snap) a.ex.tab_ac[e] = ov;
+        }
       }
-      const size_t ec = (static_cast<size_t>(rec) * a.geo.S + sample) * 4;
-      a.ex.tab_cnt[ec + 0] = static_cast<int64_t>(base0 + c0);
-      a.ex.tab_cnt[ec + 1] = static_cast<int64_t>(base1 + c1);
-      a.ex.tab_cnt[ec + 2] = static_cast<int64_t>(base2 + c2);
-      a.ex.tab_cnt[ec + 3] = static_cast<int64_t>(base3 + c3);
+      const unsigned long long mine[4] = {c0, c1, c2, c3};
+      unsigned long long tot_cnt[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        unsigned long long v = mine[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        tot_cnt[k] = v;
+      }
+      if (lane == 0) {
+        const size_t ec = (static_cast<size_t>(rec) * a.geo.S + sample) * 4;
+        for (int k = 0; k < 4; ++k) a.ex.tab_cnt[ec + k] = static_cast<int64_t>(a.counters[4ull * sample + k] + tot_cnt[k]);
+      }
+      __syncwarp();
       ++rec;
     }
   }
-  my_ctr[0] = base0 + c0;
-  my_ctr[1] = base1 + c1;
-  my_ctr[2] = base2 + c2;
-  my_ctr[3] = base3 + c3;
-  if (SMEM)
-    for (uint32_t w = 0; w < a.geo.planes * W; ++w) gA[w] = A[w];
+  const unsigned long long mine[4] = {c0, c1, c2, c3};
+  unsigned long long tot_cnt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long v = mine[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    tot_cnt[k] = v;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.counters[4ull * sample + k] += tot_cnt[k];
+  if (SMEM) {
+    __syncwarp();
+    for (uint32_t w = lane; w < NOCC * W; w += 32) gA[w] = A[w];
+  }
 }
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
@@ -1082,19 +1129,19 @@ cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
   const size_t per_sample = static_cast<size_t>(NPL) * a.geo.W * 4u;
   const size_t budget = 200u * 1024u;  // shared memory for the staged lattices of one block
   if (per_sample <= budget) {
-    const uint32_t threads = static_cast<uint32_t>(std::min<size_t>(32u, budget / per_sample));
-    const size_t smem = per_sample * threads;
-    const uint32_t blocks = (a.geo.S + threads - 1) / threads;
+    const uint32_t warps = static_cast<uint32_t>(std::min<size_t>(8u, budget / per_sample));
+    const size_t smem = per_sample * warps;
+    const uint32_t blocks = (a.geo.S + warps - 1) / warps;
     (void)cudaGetLastError();
     const cudaError_t e = cudaFuncSetAttribute(k_serial<MODEL, DIS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    k_serial<MODEL, DIS, true><<<blocks, threads, smem, st>>>(a);
+    k_serial<MODEL, DIS, true><<<blocks, 32 * warps, smem, st>>>(a);
     return cudaGetLastError();
   }
-  const uint32_t threads = 32;
-  const uint32_t blocks = (a.geo.S + threads - 1) / threads;
-  k_serial<MODEL, DIS, false><<<blocks, threads, 0, st>>>(a);
+  const uint32_t warps = 8;
+  const uint32_t blocks = (a.geo.S + warps - 1) / warps;
+  k_serial<MODEL, DIS, false><<<blocks, 32 * warps, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,245 @@
+// asep_serial.cu -- plain random-sequential update (paper sec. 2.1), exact:
+// the serial schedule of the library, one warp per sample.
+#include <algorithm>
+#include <cstdint>
+
+#include "asep_device.cuh"
+#include "asep_internal.h"
+
+namespace asep {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Serial random-sequential update, one warp per sample
+// ---------------------------------------------------------------------------
+//
+// The attempts of a sweep form one sequence; the warp takes them 32 at a
+// time in sequence order (lane k = attempt base + k).  Two attempts commute
+// when their bonds share no site, so the longest prefix of a batch in which
+// no attempt shares a site with an earlier one gives the same lattice
+// whether applied one after another or all at once.  The warp applies that
+// prefix (its flips are disjoint bits, written with shared-memory atomics)
+// and starts the next batch at the first attempt that collided.  Bonds i
+// and j share a site exactly when i / 2 == j / 2 or (i + 1 mod L) / 2 ==
+// (j + 1 mod L) / 2, so two match operations find every collision.  The
+// lattice (and the quenched plane) is staged in shared memory when it fits.
+
+template <uint32_t MODEL, uint32_t DIS, bool SMEM>
+__global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
+  extern __shared__ __align__(16) uint32_t serial_smem[];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  const uint32_t sample = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (sample >= a.geo.S) return;  // whole warps leave together
+  const uint32_t L = static_cast<uint32_t>(a.geo.L), W = a.geo.W;
+  constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
+  constexpr uint32_t NPL = NOCC + (DIS != kDisNone ? 1u : 0u);
+  uint32_t* gA = a.state + static_cast<size_t>(sample) * NOCC * W;
+  const uint32_t* gM =
+      (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+  uint32_t* A = gA;
+  const uint32_t* M = gM;
+  if (SMEM) {
+    uint32_t* mine = serial_smem + static_cast<size_t>(wib) * NPL * W;
+    for (uint32_t w = lane; w < NOCC * W; w += 32) mine[w] = gA[w];
+    if (DIS != kDisNone)
+      for (uint32_t w = lane; w < W; w += 32) mine[NOCC * W + w] = gM[w];
+    A = mine;
+    M = mine + NOCC * W;
+    __syncwarp();
+  }
+  uint32_t* B = A + W;
+  const uint32_t n_glob = a.geo.first_sample + sample;
+  const uint2 key = key_of(a.seed);
+  const uint32_t n_att = MODEL == kTwoLane ? 2u * L : L;
+  const uint32_t logL = 31u - static_cast<uint32_t>(__clz(static_cast<int>(L)));
+  unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;  // this lane's share of the sample's counters
+  const uint64_t s0 = a.clock->sweep;
+  uint32_t rec = a.clock->next_time;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+
+  for (uint32_t it = 0; it < a.n_sweeps; ++it) {
+    const uint64_t s = s0 + it;
+    uint32_t base = 0;
+    while (base < n_att) {
+      const uint32_t b = min(32u, n_att - base);
+      const bool active = lane < b;
+      const uint32_t att = base + lane;
+      const uint4 x4 = philox10(ctr_of(s, kTagSer, 0, n_glob, att >> 1), key);
+      const uint32_t rb = (att & 1u) ? x4.z : x4.x, ru = (att & 1u) ? x4.w : x4.y;
+      uint32_t pl = 0, i;
+      if (MODEL == kTwoLane) {
+        const uint32_t j = rb & (n_att - 1u);
+        pl = j >> logL;
+        i = j & (L - 1u);
+      } else {
+        i = rb & (L - 1u);
+      }
+      const uint32_t i1 = (i + 1u) & (L - 1u);
+      uint32_t* P = pl ? B : A;
+      const uint32_t x = ((P[i >> 5] >> (i & 31u)) & 1u) | (((P[i1 >> 5] >> (i1 & 31u)) & 1u) << 1);
+      uint32_t thr;
+      if (MODEL == kTwoLane) {
+        thr = pl == 0 ? (x == 1u ? a.rates.p : 0u) : (x == 2u ? a.rates.q : 0u);
+      } else if (DIS == kDisBimodal) {
+        thr = x == 1u ? (((M[i >> 5] >> (i & 31u)) & 1u) ? a.rates.p_slow : a.rates.p)
+                      : (x == 2u ? (((M[i1 >> 5] >> (i1 & 31u)) & 1u) ? a.rates.q_slow : a.rates.q) : 0u);
+      } else {
+        thr = x == 1u ? a.rates.p : (x == 2u ? a.rates.q : 0u);
+      }
+      const bool hop = active && accept(ru, thr);
+      // collisions with earlier attempts of the batch (inactive lanes get keys no bond has)
+      const uint32_t k1 = active ? (pl << 31) | (i >> 1) : 0x7FE00000u | lane;
+      const uint32_t k2 = active ? (pl << 31) | (i1 >> 1) : 0x7FF00000u | lane;
+      const uint32_t same = __match_any_sync(0xffffffffu, k1) | __match_any_sync(0xffffffffu, k2);
+      const uint32_t coll = __ballot_sync(0xffffffffu, active && (same & lt_mask) != 0u);
+      const uint32_t c = coll ? static_cast<uint32_t>(__ffs(coll)) - 1u : b;
+      if (lane < c && hop) {
+        atomicXor(&P[i >> 5], 1u << (i & 31u));
+        atomicXor(&P[i1 >> 5], 1u << (i1 & 31u));
+        if (MODEL == kTwoLane) {
+          c0 += pl == 0u;
+          c1 += pl == 1u;
+        } else if (a.count_hops) {
+          c0 += x == 1u;
+          c1 += x != 1u;
+        }
+      }
+      __syncwarp();
+      base += c;
+    }
+    if (MODEL == kTwoLane && DIS == kDisTurning) {
+      // lane changes: every event touches only (A_i, B_i); words are split over the lanes
+      for (uint32_t w = lane; w < W; w += 32) {
+        uint32_t e = M[w] & (A[w] ^ B[w]);
+        while (e) {
+          const uint32_t bit = __ffs(e) - 1;
+          e &= e - 1;
+          const uint32_t site = 32u * w + bit;
+          const uint4 r = philox10(ctr_of(s, kTagTurn, 0, n_glob, site >> 2), key);
+          if (accept(pick(r, site & 3u), a.rates.omega)) {
+            if (A[w] & (1u << bit)) ++c2;
+            else ++c3;
+            A[w] ^= 1u << bit;
+            B[w] ^= 1u << bit;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (rec < a.n_times && a.times[rec] == s + 1) {
+      const uint32_t chunk = (W + 31u) / 32u;
+      const uint32_t w0 = min(W, lane * chunk), w1 = min(W, w0 + chunk);
+      for (uint32_t p = 0; p < NOCC; ++p) {
+        const uint32_t* pw = p ? B : A;
+        long long tot = 0;
+        for (uint32_t w = w0; w < w1; ++w) tot += 2 * __popc(pw[w]) - 32;
+        long long h = tot;  // inclusive warp scan of the chunk totals
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long t = __shfl_up_sync(0xffffffffu, h, o);
+          if (lane >= static_cast<uint32_t>(o)) h += t;
+        }
+        h -= tot;
+        long long s1 = 0;
+        unsigned long long s2 = 0;
+        for (uint32_t w = w0; w < w1; ++w) {
+          const uint32_t xw = pw[w];
+          for (uint32_t bb = 0; bb < 32; ++bb) {
+            h += ((xw >> bb) & 1u) ? 1 : -1;
+            s1 += h;
+            s2 += static_cast<unsigned long long>(h * h);
+          }
+        }
+        // profile and autocorrelation overlap of this plane
+        const size_t pbase = (static_cast<size_t>(sample) * NOCC + p) * W;
+        long long ov = 0;
+        for (uint32_t w = w0; w < w1; ++w) {
+          if (a.ex.profile) a.ex.profile[pbase + w] += __popc(pw[w]);
+          if (a.ex.snap) {
+            if (s + 1 == a.ex.t0) a.ex.snap[pbase + w] = pw[w];
+            if (s + 1 >= a.ex.t0) ov += __popc(pw[w] & a.ex.snap[pbase + w]);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          ov += __shfl_xor_sync(0xffffffffu, ov, o);
+        }
+        unsigned __int128 s2_all = 0;
+        for (int l = 0; l < 32; ++l) s2_all += __shfl_sync(0xffffffffu, s2, l);
+        if (lane == 0) {
+          const size_t e = (static_cast<size_t>(rec) * a.geo.S + sample) * NOCC + p;
+          a.tab_sh[e] = s1;
+          a.tab_sh2[2 * e] = static_cast<uint64_t>(s2_all);
+          a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(s2_all >> 64);
+          if (a.ex.snap) a.ex.tab_ac[e] = ov;
+        }
+      }
+      const unsigned long long mine[4] = {c0, c1, c2, c3};
+      unsigned long long tot_cnt[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        unsigned long long v = mine[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        tot_cnt[k] = v;
+      }
+      if (lane == 0) {
+        const size_t ec = (static_cast<size_t>(rec) * a.geo.S + sample) * 4;
+        for (int k = 0; k < 4; ++k) a.ex.tab_cnt[ec + k] = static_cast<int64_t>(a.counters[4ull * sample + k] + tot_cnt[k]);
+      }
+      __syncwarp();
+      ++rec;
+    }
+  }
+  const unsigned long long mine[4] = {c0, c1, c2, c3};
+  unsigned long long tot_cnt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long v = mine[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    tot_cnt[k] = v;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.counters[4ull * sample + k] += tot_cnt[k];
+  if (SMEM) {
+    __syncwarp();
+    for (uint32_t w = lane; w < NOCC * W; w += 32) gA[w] = A[w];
+  }
+}
+
+template <uint32_t MODEL, uint32_t DIS>
+cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
+  constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + (DIS != kDisNone ? 1u : 0u);
+  const size_t per_sample = static_cast<size_t>(NPL) * a.geo.W * 4u;
+  const size_t budget = 200u * 1024u;  // shared memory for the staged lattices of one block
+  if (per_sample <= budget) {
+    const uint32_t warps = static_cast<uint32_t>(std::min<size_t>(8u, budget / per_sample));
+    const size_t smem = per_sample * warps;
+    const uint32_t blocks = (a.geo.S + warps - 1) / warps;
+    (void)cudaGetLastError();
+    const cudaError_t e = cudaFuncSetAttribute(k_serial<MODEL, DIS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_serial<MODEL, DIS, true><<<blocks, 32 * warps, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+  const uint32_t warps = 8;
+  const uint32_t blocks = (a.geo.S + warps - 1) / warps;
+  k_serial<MODEL, DIS, false><<<blocks, 32 * warps, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st) {
+  if (model == kRing && dis == kDisNone) return launch_serial_t<kRing, kDisNone>(a, st);
+  if (model == kRing && dis == kDisBimodal) return launch_serial_t<kRing, kDisBimodal>(a, st);
+  if (model == kTwoLane && dis == kDisNone) return launch_serial_t<kTwoLane, kDisNone>(a, st);
+  if (model == kTwoLane && dis == kDisTurning) return launch_serial_t<kTwoLane, kDisTurning>(a, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace asep

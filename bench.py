@@ -412,8 +412,8 @@ def other_workloads():
          dict(L=1 << 16, domain_sites=256, n_realizations=64, samples_per_real=4, p_thr=A.ASEP_ALWAYS, q_thr=0,
               dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=2, seed=1), lt, 1),
         ("two lanes: 2 x L=2^16, rate 1 both lanes, turning density 0.05, omega 0.1, Bernoulli(1/2) start, "
-         "128 samples, 10^4-MCS window, currents + profile + autocorrelation",
-         dict(model=A.ASEP_MODEL_TWO_LANE, L=1 << 16, domain_sites=256, samples_per_real=128,
+         "128 samples, 10^4-MCS window, currents + profile + autocorrelation, D=128 (256 bonds per domain)",
+         dict(model=A.ASEP_MODEL_TWO_LANE, L=1 << 16, domain_sites=128, samples_per_real=128,
               p_thr=A.ASEP_ALWAYS, q_thr=A.ASEP_ALWAYS, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
               dis_b_thr=th(0.1), dis_seed=3, init_kind=A.ASEP_INIT_BERNOULLI_HALF, init_seed=4, seed=1,
               flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=t0), lt, 2),

@@ -371,7 +371,7 @@ def _serial_w2(P, times, mask=None):
     return out
 
 
-@pytest.mark.parametrize("case", ["asep", "tasep", "bimodal", "two_lane"])
+@pytest.mark.parametrize("case", ["asep", "tasep", "bimodal", "two_lane", "two_lane_d128"])
 def test_width_within_3_sigma_of_serial_reference(case):
     times = [4, 16, 64]
     if case == "asep":
@@ -381,10 +381,10 @@ def test_width_within_3_sigma_of_serial_reference(case):
     elif case == "bimodal":
         kw = dict(L=1 << 14, domain_sites=256, n_realizations=1, samples_per_real=96, dis_kind=A.ASEP_DIS_BIMODAL,
                   dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=23, seed=29)
-    else:
-        kw = dict(model=TWO, L=1 << 14, domain_sites=256, samples_per_real=96, init_kind=1, init_seed=3,
-                  dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=31,
-                  q_thr=A.ASEP_ALWAYS, seed=37)
+    else:  # two lanes; D = 128 gives a domain 256 bonds, as the ring's D = 256
+        kw = dict(model=TWO, L=1 << 14, domain_sites=128 if case == "two_lane_d128" else 256, samples_per_real=96,
+                  init_kind=1, init_seed=3, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
+                  dis_seed=31, q_thr=A.ASEP_ALWAYS, seed=37)
     g = run_gpu(kw, [times[-1]], times)
     P = oracle_params(kw)
     mask = oracle.disorder(P)

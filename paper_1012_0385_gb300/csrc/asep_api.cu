@@ -46,6 +46,7 @@ struct asep_ctx {
   int64_t* d_href = nullptr;     // [S][planes] sum h of the reference lattice (last create / reset / load)
   uint64_t* d_href2 = nullptr;   // [S][planes][2] its sum h^2 (not used)
   int64_t* d_hrefcnt = nullptr;  // [S][4] hop counters at the reference
+  uint32_t err_seen = 0;
   uint32_t ref_slot = 0;         // first sample-time slot recorded after the reference
   std::vector<std::pair<void*, size_t>> allocs;
   size_t dev_bytes = 0;
@@ -54,7 +55,9 @@ struct asep_ctx {
   uint32_t ptab_klo = 0;
   // resident launch plan
   uint32_t R2 = 0, logR2 = 0, G = 0, spc = 1, C = 0, Cp = 0, threads = 0, blocks = 0;
-  uint32_t cluster = 1, Gc = 0;  // cluster tier: CTAs per sample, columns per CTA
+  uint32_t cluster = 1, Gc = 0;  // cluster tier: CTAs per sample, columns per CTA (kStreamTier: streamed)
+  uint32_t tiles = 0;             // streamed tier: tiles per sample
+  uint32_t* d_err = nullptr;      // device flag: a streamed tile's copy wait gave up
   size_t smem = 0;
   uint32_t max_sweeps_per_launch = 1;
   uint64_t launches = 0;
@@ -172,8 +175,8 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (!p) return fail(ctx, ASEP_ERR_INVALID, "params is NULL");
   if (p->model > ASEP_MODEL_TWO_LANE) return fail(ctx, ASEP_ERR_INVALID, "unknown model %u", p->model);
   if (p->schedule > ASEP_SCHED_SCA) return fail(ctx, ASEP_ERR_INVALID, "unknown schedule %u", p->schedule);
-  if (p->L < 64 || (p->L & 63) || p->L > (1ull << 22))
-    return fail(ctx, ASEP_ERR_INVALID, "L = %llu must be a multiple of 64 in [64, 2^22]", (unsigned long long)p->L);
+  if (p->L < 64 || (p->L & 63) || p->L > (1ull << 28))
+    return fail(ctx, ASEP_ERR_INVALID, "L = %llu must be a multiple of 64 in [64, 2^28]", (unsigned long long)p->L);
   if (p->n_realizations == 0 || p->samples_per_real == 0)
     return fail(ctx, ASEP_ERR_INVALID, "n_realizations and samples_per_real must be >= 1");
   const uint64_t S = static_cast<uint64_t>(p->n_realizations) * p->samples_per_real;
@@ -259,7 +262,8 @@ int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
     if (!placed && (force_cluster == 1 || force_spc))
       return fail(ctx, ASEP_ERR_INVALID, "the requested resident plan does not fit one CTA");
   }
-  for (uint32_t nc = force_cluster > 1 ? force_cluster : 2; !placed && nc <= 16; nc *= 2) {
+  for (uint32_t nc = force_cluster > 1 ? force_cluster : 2; !placed && nc <= 16 && force_cluster != kStreamTier;
+       nc *= 2) {
     const uint32_t Gc = static_cast<uint32_t>((G + nc - 1) / nc);
     const bool ok = Gc <= 1024 && (G + Gc - 1) / Gc == nc;  // every CTA of the cluster holds columns
     const uint32_t Cp = (Gc + 31) / 32 * 32;
@@ -277,10 +281,28 @@ int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
     }
     if (force_cluster > 1) break;
   }
+  // streamed tier: tiles of C columns (a multiple of 32, at least two tiles) through shared memory
+  if (!placed && (force_cluster == 0 || force_cluster == kStreamTier) && ctx->W % 4 == 0) {
+    for (uint32_t C = 1024; C >= 32 && !placed; C -= 32) {
+      if (2ull * C > G) continue;
+      const size_t smem = stream_smem_bytes(ctx->p.model, dis, ctx->R2, C, ptab_n);
+      if (smem > 200u * 1024u) continue;
+      ctx->cluster = kStreamTier;
+      ctx->spc = 1;
+      ctx->C = C;
+      ctx->Gc = 0;
+      ctx->Cp = C;
+      ctx->threads = C;
+      ctx->smem = smem;
+      ctx->tiles = static_cast<uint32_t>((G + C - 1) / C);
+      ctx->blocks = ctx->tiles * ctx->S;
+      placed = true;
+    }
+  }
   if (!placed)
-    return fail(ctx, ASEP_ERR_INVALID, "L = %llu (%llu columns, %u planes) fits neither one CTA nor a cluster of "
-                "up to 16 CTAs on this device%s", (unsigned long long)ctx->L, (unsigned long long)G, ctx->planes,
-                force_cluster > 1 ? " with the requested cluster size" : "");
+    return fail(ctx, ASEP_ERR_INVALID, "L = %llu (%llu columns, %u planes) fits neither one CTA, a cluster of "
+                "up to 16 CTAs nor streamed tiles on this device%s", (unsigned long long)ctx->L,
+                (unsigned long long)G, ctx->planes, force_cluster > 1 ? " with the requested plan" : "");
   // per-lane 32-bit hop counters: at most 2 phases x largest count + 2D turns per sweep
   const uint64_t per_sweep = 2ull * (ctx->ptab_klo + ctx->ptab.size() + 1) + 2ull * D;
   ctx->max_sweeps_per_launch = static_cast<uint32_t>(std::max<uint64_t>(1, 4000000000ull / per_sweep));
@@ -561,6 +583,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   ctx->d_href = static_cast<int64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * ctx->planes * 8));
   ctx->d_href2 = static_cast<uint64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * ctx->planes * 16));
   ctx->d_hrefcnt = static_cast<int64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * 32));
+  ctx->d_err = static_cast<uint32_t*>(dev_alloc(ctx, 16));
   if (params->flags & ASEP_FLAG_PROFILE) ctx->d_profile = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
   if (params->flags & ASEP_FLAG_AUTOCORR) {
     ctx->d_snap = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
@@ -569,7 +592,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   if (ctx->R) ctx->d_mask = static_cast<uint32_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->R) * ctx->W * 4));
   if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
   if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || !ctx->d_clock ||
-      !ctx->d_tab_cnt || !ctx->d_href || !ctx->d_href2 || !ctx->d_hrefcnt ||
+      !ctx->d_tab_cnt || !ctx->d_href || !ctx->d_href2 || !ctx->d_hrefcnt || !ctx->d_err ||
       ((params->flags & ASEP_FLAG_PROFILE) && !ctx->d_profile) ||
       ((params->flags & ASEP_FLAG_AUTOCORR) && (!ctx->d_snap || !ctx->d_tab_ac)) || (ctx->R && !ctx->d_mask) ||
       (!ctx->ptab.empty() && !ctx->d_ptab))
@@ -584,7 +607,8 @@ int asep_create(const asep_params* params, asep_ctx** out) {
       (e = cudaMemcpyAsync(ctx->d_ptab, ctx->ptab.data(), ctx->ptab.size() * 4, cudaMemcpyHostToDevice,
                            ctx->stream)) != cudaSuccess)
     return bail(cuda_fail(ctx, e, "copy attempt-count table"));
-  if ((e = cudaMemsetAsync(ctx->d_cnt, 0, static_cast<size_t>(ctx->S) * 32, ctx->stream)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ctx->d_cnt, 0, static_cast<size_t>(ctx->S) * 32, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_err, 0, 16, ctx->stream)) != cudaSuccess)
     return bail(cuda_fail(ctx, e, "clear counters"));
   if ((e = cudaMemsetAsync(ctx->d_sh, 0, entries * 8, ctx->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(ctx->d_sh2, 0, entries * 16, ctx->stream)) != cudaSuccess)
@@ -632,7 +656,15 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     const uint32_t cap = ctx->p.schedule == ASEP_SCHED_DOMAIN ? ctx->max_sweeps_per_launch : (1u << 20);
     if (n > cap) n = cap;
     cudaError_t e;
-    if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster > 1) {
+    if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster == kStreamTier) {
+      // one sweep per step: both phases, lane changes, the record, the clock
+      n = 1;
+      e = launch_stream_sweep(domain_desc(ctx, 1), ctx->tiles, ctx->threads, ctx->smem, ctx->d_err, ctx->stream);
+      if (e == cudaSuccess && ctx->next_time < ctx->times.size() && ctx->times[ctx->next_time] == ctx->sweep + 1) {
+        const int rc = record_now(ctx, ctx->next_time);
+        if (rc != ASEP_OK) return rc;
+      }
+    } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster > 1) {
       e = launch_cluster(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else if (ctx->p.schedule == ASEP_SCHED_SCA) {
       e = launch_sca(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
@@ -701,9 +733,18 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
 
 int asep_sync(asep_ctx* ctx) {
   if (!ctx) return ASEP_ERR_INVALID;
-  const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
-  return ASEP_OK;
+  if (ctx->cluster == kStreamTier && ctx->d_err && !ctx->err_seen) {
+    uint32_t flag = 0;
+    if ((e = cudaMemcpy(&flag, ctx->d_err, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(ctx, e, "read the streamed tier's error flag");
+    if (flag) {
+      ctx->err_seen = 1;
+      return fail(ctx, ASEP_ERR_TIMEOUT, "a streamed tile's bulk copy did not complete; results are invalid");
+    }
+  }
+  return ctx->err_seen ? fail(ctx, ASEP_ERR_TIMEOUT, "a streamed tile's bulk copy did not complete earlier") : ASEP_OK;
 }
 
 int asep_width(asep_ctx* ctx, int64_t* sum_h, uint64_t* sum_h2, double* w2, size_t n_entries) {
@@ -898,6 +939,8 @@ int batch_check(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uin
     if (!ctxs[j]) return bfail(b, ASEP_ERR_INVALID, "context %u is NULL", j);
     if (ctxs[j]->p.schedule != ASEP_SCHED_DOMAIN)
       return bfail(b, ASEP_ERR_INVALID, "context %u: only the domain schedule runs in a batch", j);
+    if (ctxs[j]->cluster == kStreamTier)
+      return bfail(b, ASEP_ERR_INVALID, "context %u streams its lattice from global memory; use asep_sweep", j);
     if (ctxs[j]->sweep + n_mcs[j] >= (1ull << 40)) return bfail(b, ASEP_ERR_INVALID, "context %u: sweep >= 2^40", j);
     if (ctxs[j]->blocks > (1u << 20)) return bfail(b, ASEP_ERR_INVALID, "context %u: more than 2^20 groups", j);
     for (uint32_t k = 0; k < j; ++k)
@@ -1116,8 +1159,8 @@ const char* asep_batch_last_error(const asep_batch* b) { return b ? b->err.c_str
 int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
   if (!ctx) return ASEP_ERR_INVALID;
   if (ctx->p.schedule != ASEP_SCHED_DOMAIN) return fail(ctx, ASEP_ERR_INVALID, "plans apply to the domain schedule");
-  if (cluster > 16 || (cluster > 1 && (cluster & (cluster - 1))))
-    return fail(ctx, ASEP_ERR_INVALID, "cluster must be 0, 1, 2, 4, 8 or 16");
+  if (cluster != kStreamTier && (cluster > 16 || (cluster > 1 && (cluster & (cluster - 1)))))
+    return fail(ctx, ASEP_ERR_INVALID, "cluster must be 0, 1, 2, 4, 8, 16 or 32 (streamed)");
   if (samples_per_group && cluster > 1)
     return fail(ctx, ASEP_ERR_INVALID, "samples_per_group applies to the resident plan (cluster 0 or 1)");
   if (samples_per_group > ctx->S) return fail(ctx, ASEP_ERR_INVALID, "samples_per_group exceeds the samples");
@@ -1133,6 +1176,7 @@ int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
     ctx->threads = saved.threads;
     ctx->smem = saved.smem;
     ctx->blocks = saved.blocks;
+    ctx->tiles = saved.tiles;
     ctx->max_sweeps_per_launch = saved.max_sweeps_per_launch;
     ctx->err = msg;
   }

@@ -171,6 +171,12 @@ cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32
                          uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st);
 // Cluster tier: one cluster of a.cluster CTAs per sample (grid S * cluster).
 cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
+// Streamed tier of the domain schedule (lattice in global memory, tiles of
+// columns through shared memory); plan code kStreamTier in `cluster`.
+constexpr uint32_t kStreamTier = 32;
+size_t stream_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t C, uint32_t ptab_n);
+cudaError_t launch_stream_sweep(const DomainLaunch& a, uint32_t tiles, uint32_t threads, size_t smem, uint32_t* err,
+                                cudaStream_t st);
 // The two-sub-lattice SCA schedule: one CTA per sample, ring in shared memory.
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
 size_t sca_smem_bytes(uint32_t W, uint32_t planes, bool quenched);

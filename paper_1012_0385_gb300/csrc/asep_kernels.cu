@@ -36,23 +36,11 @@
 #include <cooperative_groups.h>
 
 #include "asep_device.cuh"
+#include "asep_domain.cuh"
 #include "asep_internal.h"
 
 namespace asep {
 namespace {
-
-
-// K = k_lo + #{ j : tab[j] <= w } (table ascending): inversion of the
-// Poisson CDF in u32 fixed point.
-__device__ __forceinline__ uint32_t poisson_count(const uint32_t* tab, uint32_t n, uint32_t klo, uint32_t w) {
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (tab[mid] <= w) lo = mid + 1;
-    else hi = mid;
-  }
-  return klo + lo;
-}
 
 // ---------------------------------------------------------------------------
 // Segmented scan (all threads of the block must call)
@@ -177,20 +165,6 @@ __global__ void __launch_bounds__(256) k_heights(const HeightsLaunch a) {
 // ---------------------------------------------------------------------------
 
 // Hop counters of one lane (named fields so they stay in registers).
-struct Cnt {
-  uint32_t a = 0, b = 0, c = 0, d = 0;  // ring: right, left; two lanes: A hops, B hops, A->B, B->A
-};
-
-struct Lane {
-  uint32_t c;        // column in the CTA
-  uint32_t g;        // super-domain index within the sample
-  uint32_t col0;     // first column of the sample
-  uint32_t c_next;   // column of super-domain g+1 (ring)
-  uint32_t c_prev;   // column of super-domain g-1 (ring)
-  uint32_t sample;   // sample index in the context
-  uint32_t n_glob;   // global sample id (Philox counter)
-  bool active;
-};
 
 // Rotate the planes of one column from frame offset R_old to R_new:
 // new frame word f = g*R2 + r holds logical sites R_new + 32 f .. + 31.
@@ -209,132 +183,6 @@ __device__ __forceinline__ void realign(const uint32_t* src, uint32_t* dst, cons
 #pragma unroll
     for (uint32_t p = 0; p < NP; ++p)
       dst[p * PW + r * Cp + ln.c] = __funnelshift_r(src[p * PW + ia], src[p * PW + ib], sh);
-  }
-}
-
-// One attempt of a half-domain phase, without branches.  The bond's two
-// words are rows `row` and `row + 1` of the lane's own column (row 2D/32 is
-// the mirror of the next column's row 0), both loaded unconditionally; the
-// 64-bit flip mask (3 << j across the word pair) is applied under one
-// predicate.  Thresholds t are 0, multiples of 4096 or "always", and for the
-// multiples r < t is the same test as (r & 0xfffff000) < t, so only the
-// always flag needs separate handling.  `valid` is k <= K.
-template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
-__device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& a, uint32_t PWb, uint32_t base_b,
-                                        uint32_t row_scale_b, uint32_t r, bool valid, Cnt& cnt) {
-  // byte offset of row (j >> 5) of this half: (r & (D - 1) & ~31) * (4 Cp / 32)
-  const uint32_t cpb = CP ? CP * 4u : a.Cp * 4u;  // row pitch in bytes (compile-time when CP != 0)
-  uint32_t o0 = base_b + (r & a.row_bits) * row_scale_b;
-  bool okR, okL;
-  if (MODEL == kTwoLane) {
-    const uint32_t laneB = (r >> a.logD) & 1u;
-    o0 += laneB * PWb;
-    okR = !laneB && (a.rates.p_always || r < a.rates.p);  // lane A: 10 -> 01
-    okL = laneB && (a.rates.q_always || r < a.rates.q);   // lane B: 01 -> 10
-  } else if (DIS == kDisBimodal) {
-    const uint32_t c0 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0);
-    const uint32_t c1 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0 + cpb);
-    const uint32_t pc = __funnelshift_r(c0, c1, r);  // bit0: class of site i, bit1: of site i+1
-    const uint32_t u = r & kAcceptMask;
-    okR = u < ((pc & 1u) ? a.rates.p_slow : a.rates.p);
-    okL = u < ((pc & 2u) ? a.rates.q_slow : a.rates.q);
-  } else {
-    okR = a.rates.p_always || r < a.rates.p;
-    okL = a.rates.q_always || r < a.rates.q;
-  }
-  uint32_t* p0 = reinterpret_cast<uint32_t*>(cur + o0);
-  uint32_t* p1 = reinterpret_cast<uint32_t*>(cur + o0 + cpb);
-  const uint32_t w0 = *p0;
-  const uint32_t w1 = *p1;
-  const uint32_t pat = __funnelshift_r(w0, w1, r) & 3u;  // bit0 = site i, bit1 = site i+1 (shift = r mod 32)
-  const bool hopR = okR && pat == 1u;
-  const bool hopL = okL && pat == 2u;
-  if (valid && (hopR || hopL)) {
-    *p0 = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
-    *p1 = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
-  }
-  if (COUNT) {
-    cnt.a += valid && hopR;
-    cnt.b += valid && hopL;
-  }
-}
-
-// One half-domain phase of one sweep.  All threads of the block must call.
-//
-// Lane sort: the lanes of a warp run to the largest Poisson count of the
-// warp, so a warp whose domains drew similar counts wastes fewer slots.  With
-// `a.lane_sort` (every warp inside one sample, and a scratch area of 5 words
-// per column) each thread ranks its domain's count among the domains of the
-// same shared-memory bank in its sample (columns lane, lane + 32, ...) and
-// warp w runs the domains of rank w.  A domain's attempts are the same
-// whichever thread runs them, and a thread stays in its own sample and bank,
-// so results and bank mapping are unchanged; only the slots a warp wastes
-// shrink.  `scr` is the idle realign buffer (overwritten by the next realign).
-// The cluster tier passes sort = false: there other CTAs may still read that
-// buffer remotely during the first phase.
-template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP, uint32_t PHASE>
-__device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sort, const DomainLaunch& a,
-                                          const uint32_t* tab, uint32_t PW, uint64_t s, const Lane& ln, uint2 key,
-                                          Cnt& cnt) {
-  const uint32_t d = 2 * ln.g + PHASE;
-  uint4 x0 = make_uint4(0u, 0u, 0u, 0u);
-  uint32_t K = 0;
-  if (ln.active) {
-    x0 = philox10(ctr_of(s, kTagDom, 0, ln.n_glob, d), a.ks);
-    K = poisson_count(tab, a.ptab_n, a.ptab_klo, x0.x);
-  }
-  const uint32_t cp = CP ? CP : a.Cp;
-  uint32_t col = ln.c;  // the column (domain pair) this thread runs
-  uint32_t dd = d;      // its domain index in the sample
-  if (sort) {
-    // Only the group's own columns (c < C) take part: a persistent CTA may be
-    // wider than the group, and its extra threads keep K = 0 and no column.
-    const bool in_group = ln.c < a.C;
-    uint32_t* sK = scr;
-    uint32_t* sPerm = scr + cp;
-    uint32_t* sX = scr + 2 * cp;
-    if (in_group) {
-      sK[ln.c] = K;
-      sX[ln.c] = x0.y;
-      sX[cp + ln.c] = x0.z;
-      sX[2 * cp + ln.c] = x0.w;
-    }
-    __syncthreads();
-    if (in_group) {
-      const uint32_t lane = ln.c & 31u;
-      uint32_t rank = 0;
-      for (uint32_t q = ln.col0 + lane; q < ln.col0 + a.G; q += 32) {
-        const uint32_t kq = sK[q];
-        rank += (kq < K || (kq == K && q < ln.c)) ? 1u : 0u;
-      }
-      sPerm[ln.col0 + (rank << 5) + lane] = ln.c;
-    }
-    __syncthreads();
-    if (in_group) {
-      col = sPerm[ln.c];
-      dd = 2 * (ln.g - ln.c + col) + PHASE;
-      K = sK[col];
-      x0.y = sX[col];
-      x0.z = sX[cp + col];
-      x0.w = sX[2 * cp + col];
-    }
-  }
-  const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
-  unsigned char* cb = reinterpret_cast<unsigned char*>(cur);
-  const uint32_t base_b = (PHASE * (a.D >> 5) * cp + col) * 4u;
-  const uint32_t row_scale_b = cp >> 3;  // 4 * Cp / 32
-  const uint32_t PWb = PW * 4u;
-  attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.y, 1 <= K, cnt);
-  attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.z, 2 <= K, cnt);
-  attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
-#pragma unroll 2
-  for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
-    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
-    const uint32_t k = call << 2;
-    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);
-    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, k + 1 <= K, cnt);
-    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.z, k + 2 <= K, cnt);
-    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.w, k + 3 <= K, cnt);
   }
 }
 

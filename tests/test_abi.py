@@ -63,7 +63,7 @@ def test_sampling_times_match_paper_and_oracle(oracle_mod):
 
 def test_create_rejects_bad_params_without_device(A):
     """Validation happens before any CUDA call."""
-    bad = [dict(L=100), dict(L=1 << 23), dict(L=4096, domain_sites=48), dict(L=4096, p_thr=123),
+    bad = [dict(L=100), dict(L=1 << 29), dict(L=4096, domain_sites=48), dict(L=4096, p_thr=123),
            dict(L=4096, n_realizations=0), dict(L=4096, dis_kind=2), dict(L=4096, model=1, dis_kind=1),
            dict(L=4096 + 64, schedule=1), dict(L=4096, samples_per_real=3, first_sample=1),
            # SCA schedule: L a multiple of 256, the lattice within one CTA's shared memory

@@ -33,7 +33,7 @@ def _device():
     torch.cuda.set_device(0)
 
 
-ORACLE_KEYS = {"flags": None, "autocorr_t0": None, "model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
+ORACLE_KEYS = {"flags": None, "autocorr_t0": None, "plan": None, "model": "model", "schedule": "schedule", "L": "L", "domain_sites": "D",
                "n_realizations": "n_realizations", "samples_per_real": "samples_per_real",
                "first_sample": "first_sample", "p_thr": "p_thr", "q_thr": "q_thr", "dis_kind": "dis_kind",
                "dis_a_thr": "dis_a_thr", "dis_b_thr": "dis_b_thr", "dis_c_thr": "dis_c_thr",
@@ -51,8 +51,10 @@ def oracle_params(kw):
 
 
 def run_gpu(kw, chunks, times):
-    prm = A.make_params(**kw)
+    prm = A.make_params(**{k: v for k, v in kw.items() if k != "plan"})
     with A.asep_create(prm, sample_times=times) as ctx:
+        if "plan" in kw:
+            A.asep_set_plan(ctx, *kw["plan"])
         for c in chunks:
             A.asep_sweep(ctx, c)
         words, sweep = A.asep_state(ctx)
@@ -180,6 +182,22 @@ CASES = {
     "sca_two_lane_max_L": (dict(model=TWO, L=1 << 18, schedule=SCA, samples_per_real=1, init_kind=1, init_seed=3,
                                 p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
                                 dis_b_thr=th(0.1), dis_seed=6, seed=7), 3, [0, 3]),
+    # streamed tier (plan 32): lattice in global memory, tiles of columns through shared memory
+    "stream_ring": (dict(L=1 << 16, domain_sites=256, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=61,
+                         plan=(32, 0), flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 13,
+                    [0, 5, 13]),
+    "stream_ring_four_tiles": (dict(L=1 << 18, domain_sites=32, samples_per_real=2, p_thr=th(0.6), q_thr=th(0.3),
+                                    seed=62, plan=(32, 0)), 6, [0, 6]),
+    "stream_bimodal": (dict(L=1 << 16, domain_sites=128, n_realizations=2, samples_per_real=2, p_thr=A.ASEP_ALWAYS,
+                            dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_c_thr=th(0.05),
+                            q_thr=th(0.1), dis_seed=63, seed=64, plan=(32, 0)), 9, [0, 9]),
+    "stream_two_lane": (dict(model=TWO, L=1 << 16, domain_sites=128, samples_per_real=2, init_kind=1, init_seed=65,
+                             dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=66,
+                             q_thr=A.ASEP_ALWAYS, seed=67, plan=(32, 0),
+                             flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=4), 8, [0, 4, 8]),
+    # 2^24 sites = 32768 columns: more than 16 CTAs of 1024 columns, so the streamed tier is chosen
+    "stream_beyond_cluster": (dict(L=1 << 24, domain_sites=256, samples_per_real=1, p_thr=th(0.75), q_thr=th(0.25),
+                                   seed=68), 2, [0, 2]),
     "cluster_ring_2x": (dict(L=1 << 20, domain_sites=256, samples_per_real=2, p_thr=th(0.75), q_thr=th(0.25),
                              seed=51), 5, [0, 2, 5]),
     "cluster_ring_d64": (dict(L=1 << 18, domain_sites=64, samples_per_real=2, p_thr=th(0.6), seed=52), 6, [0, 6]),
@@ -455,3 +473,14 @@ def test_sca_growth_exponent_is_kpz():
     w2 = run_gpu(kw, [times[-1]], times)["w2"][:, :, 0].mean(axis=1)
     slope = np.polyfit(np.log(times), np.log(w2 - 0.25), 1)[0]
     assert abs(slope - 2 * beta) < 0.07, slope
+
+
+def test_streamed_tier_is_chosen_beyond_a_cluster():
+    with A.asep_create(A.make_params(L=1 << 24, domain_sites=256, samples_per_real=1), sample_times=[]) as ctx:
+        info = A.asep_get_info(ctx)
+        assert info["cluster"] == 32 and info["groups"] >= 2
+    with A.asep_create(A.make_params(L=1 << 16, domain_sites=256, samples_per_real=2), sample_times=[]) as ctx:
+        with A.asep_batch_create(max_jobs=2, max_items=64) as b:
+            A.asep_set_plan(ctx, 32, 0)
+            with pytest.raises(A.AsepError):
+                A.asep_batch_sweep(b, [ctx], [1])  # streamed contexts are swept with asep_sweep

@@ -82,7 +82,7 @@ extern "C" {
 #define ASEP_ERR_INVALID (-1) /* bad argument or unsupported combination */
 #define ASEP_ERR_NOMEM (-2)   /* device or host allocation failed */
 #define ASEP_ERR_CUDA (-3)    /* a CUDA runtime call failed */
-#define ASEP_ERR_TIMEOUT (-4) /* reserved: no kernel of this library waits on another, so none times out */
+#define ASEP_ERR_TIMEOUT (-4) /* a streamed tile's bounded wait for its bulk copy gave up (results invalid) */
 #define ASEP_ERR_STATE (-5)   /* call not valid in the context's state */
 
 #define ASEP_MODEL_RING 0u     /* one ring, right rate p_i, left rate q_{i+1} */
@@ -117,8 +117,9 @@ typedef void (*asep_free_fn)(void* ptr, size_t bytes, void* user);
 typedef struct asep_params {
   uint32_t model;            /* ASEP_MODEL_* */
   uint32_t schedule;         /* ASEP_SCHED_* */
-  uint64_t L;                /* sites per lane, multiple of 64 in [64, 2^22]; DOMAIN: multiple of
-                                2*domain_sites; SERIAL: power of two; SCA: multiple of 256 */
+  uint64_t L;                /* sites per lane, multiple of 64 in [64, 2^28]; DOMAIN: multiple of
+                                2*domain_sites (beyond a 16-CTA cluster, also of 128); SERIAL: power
+                                of two; SCA: multiple of 256 */
   uint32_t domain_sites;     /* D: power of two in [32, 2048]; 0 = 256 or the largest that divides L/2 */
   uint32_t n_realizations;   /* quenched-disorder realizations (1 without disorder) */
   uint32_t samples_per_real; /* samples per realization */
@@ -249,7 +250,11 @@ int asep_get_info(const asep_ctx* ctx, asep_info* info);
 /* Choose the launch plan of a domain-schedule context (the autotuner's knob;
  * results never depend on it).  cluster: 0 = automatic, 1 = whole samples in
  * one CTA, 2/4/8/16 = each sample spread over that many CTAs of a
- * thread-block cluster (columns of 2D sites split evenly).  samples_per_group:
+ * thread-block cluster (columns of 2D sites split evenly), 32 = streamed: the
+ * lattice stays in global memory and tiles of columns pass through shared
+ * memory once per phase (the automatic choice when a sample fits neither one
+ * CTA nor a 16-CTA cluster; one launch per phase, records between sweeps;
+ * not in batches).  samples_per_group:
  * samples per CTA of the one-CTA plan (0 = automatic).  Returns
  * ASEP_ERR_INVALID, keeping the previous plan, when the plan does not fit the
  * device.  Takes effect for the next launch. */

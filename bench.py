@@ -423,6 +423,10 @@ def other_workloads():
               p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
               dis_seed=3, init_kind=A.ASEP_INIT_BERNOULLI_HALF, init_seed=4, seed=1,
               flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=t0), lt, 2),
+        ("streamed tier: L=2^24 rings (beyond a 16-CTA cluster; lattice in HBM, tiles through shared memory), "
+         "ASEP p=0.75 q=0.25, 16 samples, 200-MCS window",
+         dict(L=1 << 24, domain_sites=256, samples_per_real=16, p_thr=th(0.75), q_thr=th(0.25), seed=1,
+              flags=A.ASEP_FLAG_NO_HOP_COUNTS), [200], 1),
     ]
     stream = torch.cuda.current_stream()
     out = []
@@ -433,15 +437,17 @@ def other_workloads():
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            A.asep_sweep(ctx, win)
+            n_sweeps = max(times) if times else win
+            A.asep_sweep(ctx, n_sweeps)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             info = A.asep_get_info(ctx)
-            attempts = lanes * kw["L"] * info["S"] * win
+            attempts = lanes * kw["L"] * info["S"] * n_sweeps
             out.append({"workload": name, "attempts": attempts, "ms": ms, "attempts_per_s": attempts / (ms / 1e3),
                         "kernel": ("k_serial" if kw.get("schedule") == A.ASEP_SCHED_SERIAL
                                    else "k_sca" if kw.get("schedule") == A.ASEP_SCHED_SCA
+                                   else "k_stream" if info["cluster"] == 32
                                    else "k_cluster" if info["cluster"] > 1 else "k_domain"),
                         "samples_per_group": info["samples_per_group"]})
     return out

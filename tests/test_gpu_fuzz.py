@@ -128,3 +128,36 @@ def test_random_contexts_in_one_batch_bit_exact():
     finally:
         for c in ctxs:
             c.close()
+
+
+def draw_streamed(k: int):
+    """A draw of the domain schedule on a lattice wide enough for the streamed
+    tier (64 .. 300 columns, L a multiple of 128), other parameters as draw()."""
+    kw, chunks, times = draw(k)
+    rng = np.random.default_rng(5000 + k)
+    D = int(rng.choice([32, 64, 128]))
+    G = 2 * int(rng.integers(32, 151))
+    kw = {x: v for x, v in kw.items() if x != "schedule"}
+    kw.update(L=2 * D * G, domain_sites=D, samples_per_real=min(kw["samples_per_real"], 2))
+    return kw, chunks, times
+
+
+N_STREAMED = 24
+
+
+@pytest.mark.parametrize("k", range(N_STREAMED))
+def test_random_configuration_streamed_tier_bit_exact(k):
+    """Draws forced onto the streamed tier (tiles through shared memory,
+    boundary words merged atomically), bit-exact against the oracle."""
+    from test_gpu_parity import assert_same, oracle_params, run_gpu
+
+    kw, chunks, times = draw_streamed(k)
+    kw = dict(kw, plan=(32, 0))
+    g = run_gpu(kw, chunks, times)
+    P = oracle_params(kw)
+    t0 = kw.get("autocorr_t0") if kw["flags"] & A.ASEP_FLAG_AUTOCORR else None
+    ref = oracle.run(P, sum(chunks), times, autocorr_t0=t0)
+    if kw["flags"] & A.ASEP_FLAG_NO_HOP_COUNTS:
+        ref.counters[:] = 0
+        ref.extra["counters_at"][:] = 0
+    assert_same(g, ref, P, times)

@@ -51,9 +51,13 @@
  *                      sites the A -> B lane changes after the even phase
  *                      and B -> A after the odd one (probability omega, one
  *                      draw per candidate site: tag 8, call = step, ctr3 =
- *                      site / 4).  L a multiple of 256 with the lattice in
- *                      one CTA's shared memory (ring L <= 2^20, bimodal or
- *                      two lanes 2^19, two lanes with turning sites 2^18).
+ *                      site / 4).  L a multiple of 256.  The lattice sits
+ *                      in one CTA's shared memory while it fits (ring L up
+ *                      to about 1.4 * 2^20, bimodal or two lanes 2^19,
+ *                      two lanes with turning sites 2^18); beyond that
+ *                      (or on request, asep_set_plan) it stays in global
+ *                      memory and each phase is one launch over all units
+ *                      of 8 words (results identical).
  *
  * Error behaviour: every function returns ASEP_OK (0) or a negative
  * ASEP_ERR_* code and never aborts; the context keeps a message readable with
@@ -110,7 +114,11 @@ typedef struct asep_ctx asep_ctx; /* opaque; owns every device buffer it allocat
 
 /* Device allocator hook: when alloc is non-NULL the context obtains all of
  * its device memory through it (e.g. a framework's caching allocator) and
- * returns it through free_fn; otherwise it uses cudaMalloc / cudaFree. */
+ * returns it through free_fn; otherwise it uses cudaMalloc / cudaFree.  A
+ * block must start on a 256-byte boundary (as cudaMalloc's do): the kernels
+ * move the lattice with 16- and 32-byte accesses and bulk copies.  A
+ * misaligned block is handed back through free_fn and asep_create fails
+ * with ASEP_ERR_NOMEM. */
 typedef void* (*asep_alloc_fn)(size_t bytes, void* user);
 typedef void (*asep_free_fn)(void* ptr, size_t bytes, void* user);
 
@@ -154,7 +162,8 @@ typedef struct asep_info {
   uint64_t attempts_per_sweep; /* L * planes per sample */
   uint64_t device_bytes;  /* device memory held by the context */
   uint64_t kernel_launches; /* kernels the context has enqueued so far */
-  uint32_t cluster;       /* CTAs per sample: 1 = one CTA holds whole samples, 2..16 = a thread-block cluster */
+  uint32_t cluster;       /* CTAs per sample: 1 = one CTA holds whole samples, 2..16 = a thread-block
+                             cluster, 32 = streamed from global memory */
   uint32_t samples_per_group; /* samples per CTA (resident) or 1 (cluster) */
   uint32_t groups;        /* CTAs (resident) or clusters per sweep launch */
   uint32_t threads;       /* threads per CTA */
@@ -247,8 +256,11 @@ int asep_height_offset(asep_ctx* ctx, int64_t* out, size_t n);
  * context (no synchronisation; n_recorded and sweep count enqueued work). */
 int asep_get_info(const asep_ctx* ctx, asep_info* info);
 
-/* Choose the launch plan of a domain-schedule context (the autotuner's knob;
- * results never depend on it).  cluster: 0 = automatic, 1 = whole samples in
+/* Choose the launch plan of a domain- or SCA-schedule context (the
+ * autotuner's knob; results never depend on it).  SCA: cluster 0 =
+ * automatic, 1 = the ring in one CTA's shared memory (ASEP_ERR_INVALID when
+ * it does not fit), 32 = streamed from global memory; samples_per_group 0.
+ * Domain schedule: cluster 0 = automatic, 1 = whole samples in
  * one CTA, 2/4/8/16 = each sample spread over that many CTAs of a
  * thread-block cluster (columns of 2D sites split evenly), 32 = streamed: the
  * lattice stays in global memory and tiles of columns pass through shared

@@ -147,6 +147,10 @@ void* dev_alloc(asep_ctx* ctx, size_t bytes) {
   void* ptr = nullptr;
   if (ctx->p.alloc) {
     ptr = ctx->p.alloc(bytes, ctx->p.alloc_user);
+    if (ptr && (reinterpret_cast<uintptr_t>(ptr) & 255u)) {  // the kernels need 256-byte aligned blocks
+      ctx->p.free_fn(ptr, bytes, ctx->p.alloc_user);
+      ptr = nullptr;
+    }
   } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
     (void)cudaGetLastError();
     ptr = nullptr;
@@ -211,12 +215,8 @@ int validate(const asep_params* p, asep_ctx* ctx) {
       return fail(ctx, ASEP_ERR_INVALID, "sample_times must be strictly ascending");
   if (p->schedule == ASEP_SCHED_SERIAL && !is_pow2(p->L))
     return fail(ctx, ASEP_ERR_INVALID, "the serial schedule needs L a power of two");
-  if (p->schedule == ASEP_SCHED_SCA) {
-    if (p->L % 256) return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule needs L a multiple of 256");
-    const uint32_t planes = p->model == ASEP_MODEL_TWO_LANE ? 2u : 1u;
-    if (sca_smem_bytes(static_cast<uint32_t>(p->L / 32), planes, p->dis_kind != ASEP_DIS_NONE) > 200u * 1024u)
-      return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule keeps the lattice in one CTA's shared memory: L too large");
-  }
+  if (p->schedule == ASEP_SCHED_SCA && p->L % 256)
+    return fail(ctx, ASEP_ERR_INVALID, "the SCA schedule needs L a multiple of 256");
   return ASEP_OK;
 }
 
@@ -228,6 +228,34 @@ int validate(const asep_params* p, asep_ctx* ctx) {
 // force_cluster: 0 = choose, 1 = resident only, n > 1 = exactly n CTAs per
 // sample.  force_spc: samples per CTA for the resident plan (0 = choose).
 // The plan changes only the launch shape, never the results.
+// SCA plan.  Resident: one CTA per sample holding the ring in shared memory,
+// a thread per unit of 8 words (at most 1024 threads, 512 with a quenched
+// plane).  Streamed (kStreamTier): the ring in global memory, a thread per
+// unit, one launch per phase.  force: 0 = resident when it fits, 1 =
+// resident, kStreamTier = streamed.
+int plan_sca(asep_ctx* ctx, uint32_t force) {
+  const uint32_t units = ctx->W / 8;
+  const bool quenched = ctx->p.dis_kind != ASEP_DIS_NONE;
+  const size_t smem = sca_smem_bytes(ctx->W, ctx->planes, quenched);
+  const bool fits = smem <= 200u * 1024u;
+  if (force == 1 && !fits)
+    return fail(ctx, ASEP_ERR_INVALID, "the resident SCA plan needs %zu bytes of shared memory (at most 200 KB)",
+                smem);
+  if (force == kStreamTier || !fits) {
+    ctx->cluster = kStreamTier;
+    ctx->threads = 256;
+    ctx->smem = 0;
+    ctx->blocks = ctx->S * ((units + 255u) / 256u);
+  } else {
+    const uint32_t cap = quenched ? 512u : 1024u;
+    ctx->cluster = 1;
+    ctx->threads = std::min<uint32_t>(cap, (units + 31u) / 32u * 32u);
+    ctx->smem = smem;
+    ctx->blocks = ctx->S;
+  }
+  return ASEP_OK;
+}
+
 int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
   const uint32_t D = ctx->D;
   ctx->R2 = 2 * D / 32;
@@ -560,13 +588,8 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     rc = plan_domain(ctx, 0, 0);
     if (rc != ASEP_OK) return bail(rc);
   } else if (params->schedule == ASEP_SCHED_SCA) {
-    // one CTA per sample, a thread per unit of 8 words (at most 1024 threads, 512 with a quenched plane)
-    const uint32_t units = ctx->W / 8;
-    const bool quenched = params->dis_kind != ASEP_DIS_NONE;
-    const uint32_t cap = quenched ? 512u : 1024u;
-    ctx->threads = std::min<uint32_t>(cap, (units + 31u) / 32u * 32u);
-    ctx->smem = sca_smem_bytes(ctx->W, ctx->planes, quenched);
-    ctx->blocks = ctx->S;
+    rc = plan_sca(ctx, 0);
+    if (rc != ASEP_OK) return bail(rc);
   }
 
   // device memory
@@ -666,6 +689,13 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
       }
     } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster > 1) {
       e = launch_cluster(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
+    } else if (ctx->p.schedule == ASEP_SCHED_SCA && ctx->cluster == kStreamTier) {
+      n = 1;  // one sweep per step: both phases, then the record and the clock
+      e = launch_sca_stream(domain_desc(ctx, 1), ctx->stream);
+      if (e == cudaSuccess && ctx->next_time < ctx->times.size() && ctx->times[ctx->next_time] == ctx->sweep + 1) {
+        const int rc = record_now(ctx, ctx->next_time);
+        if (rc != ASEP_OK) return rc;
+      }
     } else if (ctx->p.schedule == ASEP_SCHED_SCA) {
       e = launch_sca(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
@@ -692,7 +722,12 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     if ((e = launch_advance(ctx->d_clock, ctx->d_times, static_cast<uint32_t>(ctx->times.size()),
                             static_cast<uint32_t>(n), ctx->stream)) != cudaSuccess)
       return cuda_fail(ctx, e, "clock advance");
-    ctx->launches += 2;
+    // the sweep kernels (streamed tiers: one per phase, plus the lane changes
+    // of the streamed domain schedule with turning sites) and the clock
+    uint32_t sweep_launches = 1;
+    if (ctx->cluster == kStreamTier)
+      sweep_launches = (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->p.dis_kind == ASEP_DIS_TURNING) ? 3u : 2u;
+    ctx->launches += sweep_launches + 1;
     advance_host(ctx, n);
     done += n;
   }
@@ -1158,7 +1193,24 @@ const char* asep_batch_last_error(const asep_batch* b) { return b ? b->err.c_str
 
 int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
   if (!ctx) return ASEP_ERR_INVALID;
-  if (ctx->p.schedule != ASEP_SCHED_DOMAIN) return fail(ctx, ASEP_ERR_INVALID, "plans apply to the domain schedule");
+  if (ctx->p.schedule == ASEP_SCHED_SCA) {
+    if (cluster > 1 && cluster != kStreamTier)
+      return fail(ctx, ASEP_ERR_INVALID, "SCA plans: cluster 0 (choose), 1 (resident) or 32 (streamed)");
+    if (samples_per_group) return fail(ctx, ASEP_ERR_INVALID, "samples_per_group applies to the domain schedule");
+    const asep_ctx saved = *ctx;
+    const int rc = plan_sca(ctx, cluster);
+    if (rc != ASEP_OK) {
+      const std::string msg = ctx->err;
+      ctx->cluster = saved.cluster;
+      ctx->threads = saved.threads;
+      ctx->smem = saved.smem;
+      ctx->blocks = saved.blocks;
+      ctx->err = msg;
+    }
+    return rc;
+  }
+  if (ctx->p.schedule != ASEP_SCHED_DOMAIN)
+    return fail(ctx, ASEP_ERR_INVALID, "plans apply to the domain and SCA schedules");
   if (cluster != kStreamTier && (cluster > 16 || (cluster > 1 && (cluster & (cluster - 1)))))
     return fail(ctx, ASEP_ERR_INVALID, "cluster must be 0, 1, 2, 4, 8, 16 or 32 (streamed)");
   if (samples_per_group && cluster > 1)

@@ -179,6 +179,9 @@ cudaError_t launch_stream_sweep(const DomainLaunch& a, uint32_t tiles, uint32_t 
                                 cudaStream_t st);
 // The two-sub-lattice SCA schedule: one CTA per sample, ring in shared memory.
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
+// Streamed SCA: one sweep (both phases; two lanes: with the lane changes)
+// over every sample, lattice in global memory; results identical to launch_sca.
+cudaError_t launch_sca_stream(const DomainLaunch& a, cudaStream_t st);
 size_t sca_smem_bytes(uint32_t W, uint32_t planes, bool quenched);
 // How many clusters of the given shape can be resident at once (0 = none).
 int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem);

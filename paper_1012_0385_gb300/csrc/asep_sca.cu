@@ -49,29 +49,15 @@ __device__ long long block_sum(long long v, long long* warp_tot) {
 // All-ones where bit k (0 = most significant of 20) of a 20-bit threshold is set.
 __device__ __forceinline__ uint32_t bit_mask(uint32_t t20, uint32_t k) { return 0u - ((t20 >> (19u - k)) & 1u); }
 
-// One phase over one unit (four groups, words 8u .. 8u + 7).
+// One phase over one unit (four groups, global unit index u) held in registers: x = its 8
+// words, c = its 8 class words (DIS), x_next / c_next = the next unit's first
+// words (only bit 0 is used, odd phase).  Returns the flip of bit 0 of the
+// next unit's first word that the unit's last odd bond makes (odd phase).
 template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
-__device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uint32_t* carry, const DomainLaunch& a,
-                                         uint32_t u, uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob,
-                                         uint32_t kmax, unsigned long long& n_right, unsigned long long& n_left) {
-  uint4* p4 = reinterpret_cast<uint4*>(lat + 8u * u);
-  uint4 v0 = p4[0], v1 = p4[1];
-  uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-  if (PHASE == 0) {  // the previous unit's odd phase may have flipped bit 0 of our first word
-    const uint32_t prev = (u == 0 ? n_units : u) - 1;
-    x[0] ^= carry[prev];
-    carry[prev] = 0u;
-  }
-  uint32_t c[8];
-  if (DIS) {
-    const uint4* c4 = reinterpret_cast<const uint4*>(cls + 8u * u);
-    const uint4 d0 = c4[0], d1 = c4[1];
-    c[0] = d0.x; c[1] = d0.y; c[2] = d0.z; c[3] = d0.w; c[4] = d1.x; c[5] = d1.y; c[6] = d1.z; c[7] = d1.w;
-  }
-  const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
-  const uint32_t x_next = PHASE ? lat[next_w] : 0u;           // only bit 0 is used
-  const uint32_t c_next = (PHASE && DIS) ? cls[next_w] : 0u;
-
+__device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t (&c)[8], uint32_t x_next,
+                                               uint32_t c_next, const DomainLaunch& a, uint32_t u, uint64_t s,
+                                               uint32_t n_glob, uint32_t kmax, unsigned long long& n_right,
+                                               unsigned long long& n_left) {
   uint32_t rc[4], lc[4], acc[4], eq[4];
   if (FAST2) {
     // No disorder, p and q neither 0 nor "always", at most two planes: every
@@ -195,6 +181,34 @@ __device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uin
       else carry_out = out;
     }
   }
+  return carry_out;
+}
+
+// One phase over unit u of a ring resident in shared memory; the flip of
+// bit 0 of the next unit's first word is left in carry[u] for its owner.
+template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
+__device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uint32_t* carry, const DomainLaunch& a,
+                                         uint32_t u, uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob,
+                                         uint32_t kmax, unsigned long long& n_right, unsigned long long& n_left) {
+  uint4* p4 = reinterpret_cast<uint4*>(lat + 8u * u);
+  const uint4 v0 = p4[0], v1 = p4[1];
+  uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  if (PHASE == 0) {  // the previous unit's odd phase may have flipped bit 0 of our first word
+    const uint32_t prev = (u == 0 ? n_units : u) - 1;
+    x[0] ^= carry[prev];
+    carry[prev] = 0u;
+  }
+  uint32_t c[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  if (DIS) {
+    const uint4* c4 = reinterpret_cast<const uint4*>(cls + 8u * u);
+    const uint4 d0 = c4[0], d1 = c4[1];
+    c[0] = d0.x; c[1] = d0.y; c[2] = d0.z; c[3] = d0.w; c[4] = d1.x; c[5] = d1.y; c[6] = d1.z; c[7] = d1.w;
+  }
+  const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
+  const uint32_t x_next = PHASE ? lat[next_w] : 0u;  // only bit 0 is used
+  const uint32_t c_next = (PHASE && DIS) ? cls[next_w] : 0u;
+  const uint32_t carry_out =
+      sca_update<DIS, COUNT, FAST2, PHASE>(x, c, x_next, c_next, a, u, s, n_glob, kmax, n_right, n_left);
   p4[0] = make_uint4(x[0], x[1], x[2], x[3]);
   p4[1] = make_uint4(x[4], x[5], x[6], x[7]);
   if (PHASE == 1) carry[u] = carry_out;
@@ -218,20 +232,12 @@ __device__ __forceinline__ void settle_carries(uint32_t* lat, uint32_t* carry, u
 // (LANE 1) left (01 -> 10) with t = q.  Lane B's planes come from the stream
 // with bit 31 of ctr3 set.  Every lane of a group has the same threshold, so
 // a plane's threshold bit is uniform.
+// Register form: x = the unit's 8 words, x_next = the next unit's first word
+// (bit 0, odd phase); returns the flip of that bit (odd phase).
 template <uint32_t LANE, uint32_t PHASE>
-__device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, const DomainLaunch& a, uint32_t u,
-                                              uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob, uint32_t t,
-                                              unsigned long long& hops) {
-  uint4* p4 = reinterpret_cast<uint4*>(plane + 8u * u);
-  const uint4 v0 = p4[0], v1 = p4[1];
-  uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-  if (PHASE == 0) {
-    const uint32_t prev = (u == 0 ? n_units : u) - 1;
-    x[0] ^= carry[prev];
-    carry[prev] = 0u;
-  }
-  const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
-  const uint32_t x_next = PHASE ? plane[next_w] : 0u;
+__device__ __forceinline__ uint32_t sca_lane_update(uint32_t (&x)[8], uint32_t x_next, const DomainLaunch& a,
+                                                    uint32_t u, uint64_t s, uint32_t n_glob, uint32_t t,
+                                                    unsigned long long& hops) {
   const bool always = t == 0xFFFFFFFFu, never = t == 0u;
   uint32_t acc[4], eq[4];
 #pragma unroll
@@ -280,6 +286,25 @@ __device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, 
       else carry_out = out;
     }
   }
+  return carry_out;
+}
+
+// One lane's in-lane phase over unit u of a plane resident in shared memory.
+template <uint32_t LANE, uint32_t PHASE>
+__device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, const DomainLaunch& a, uint32_t u,
+                                              uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob, uint32_t t,
+                                              unsigned long long& hops) {
+  uint4* p4 = reinterpret_cast<uint4*>(plane + 8u * u);
+  const uint4 v0 = p4[0], v1 = p4[1];
+  uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  if (PHASE == 0) {
+    const uint32_t prev = (u == 0 ? n_units : u) - 1;
+    x[0] ^= carry[prev];
+    carry[prev] = 0u;
+  }
+  const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
+  const uint32_t x_next = PHASE ? plane[next_w] : 0u;
+  const uint32_t carry_out = sca_lane_update<LANE, PHASE>(x, x_next, a, u, s, n_glob, t, hops);
   p4[0] = make_uint4(x[0], x[1], x[2], x[3]);
   p4[1] = make_uint4(x[4], x[5], x[6], x[7]);
   if (PHASE == 1) carry[u] = carry_out;
@@ -291,6 +316,31 @@ __device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, 
 // omega; one draw per candidate site (tag SCA_TURN, call = STEP, ctr3 =
 // site / 4, word site mod 4).  STEP 1 first applies the odd phase's pending
 // flips of bit 0 of the unit's first words.
+// The lane changes of one word (global word index `word`): candidate sites
+// are the set bits of `sel` (turning sites with source occupied and target
+// empty); returns the bits that move.
+template <uint32_t STEP>
+__device__ __forceinline__ uint32_t sca_turn_word(uint32_t sel, uint32_t word, const DomainLaunch& a, uint64_t s,
+                                                  uint32_t n_glob, unsigned long long& moves) {
+  uint32_t f = 0u;
+  while (sel) {
+    const uint32_t b = static_cast<uint32_t>(__ffs(sel)) - 1u;
+    sel &= sel - 1u;
+    const uint32_t site = 32u * word + b;
+    const uint4 r = philox10(ctr_of(s, kTagScaTurn, STEP, n_glob, site >> 2), a.ks);
+    if (accept(pick(r, site & 3u), a.rates.omega)) {
+      f |= 1u << b;
+      ++moves;
+    }
+  }
+  return f;
+}
+
+template <uint32_t STEP>
+__device__ __forceinline__ uint32_t turn_candidates(uint32_t xa, uint32_t xb, uint32_t m) {
+  return m & (STEP == 0 ? (xa & ~xb) : (xb & ~xa));
+}
+
 template <uint32_t STEP>
 __device__ __forceinline__ void sca_turn_unit(uint32_t* A, uint32_t* B, const uint32_t* M, uint32_t* carry,
                                               const DomainLaunch& a, uint32_t u, uint32_t n_units, uint64_t s,
@@ -311,18 +361,9 @@ __device__ __forceinline__ void sca_turn_unit(uint32_t* A, uint32_t* B, const ui
   }
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
-    uint32_t c = m[w] & (STEP == 0 ? (xa[w] & ~xb[w]) : (xb[w] & ~xa[w]));
-    while (c) {
-      const uint32_t b = static_cast<uint32_t>(__ffs(c)) - 1u;
-      c &= c - 1u;
-      const uint32_t site = 32u * (8u * u + static_cast<uint32_t>(w)) + b;
-      const uint4 r = philox10(ctr_of(s, kTagScaTurn, STEP, n_glob, site >> 2), a.ks);
-      if (accept(pick(r, site & 3u), a.rates.omega)) {
-        xa[w] ^= 1u << b;
-        xb[w] ^= 1u << b;
-        ++moves;
-      }
-    }
+    const uint32_t f = sca_turn_word<STEP>(turn_candidates<STEP>(xa[w], xb[w], m[w]), 8u * u + w, a, s, n_glob, moves);
+    xa[w] ^= f;
+    xb[w] ^= f;
   }
   pa[0] = make_uint4(xa[0], xa[1], xa[2], xa[3]);
   pa[1] = make_uint4(xa[4], xa[5], xa[6], xa[7]);
@@ -485,6 +526,13 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
   }
 }
 
+// Ring without disorder, rates neither 0 nor "always", at most two random
+// planes: the specialised comparison.
+bool sca_fast2(const DomainLaunch& a) {
+  const auto regular = [](uint32_t t) { return t != 0u && t != 0xFFFFFFFFu; };
+  return regular(a.rates.p) && regular(a.rates.q) && a.sca_kmax <= 2;
+}
+
 template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
 cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();
@@ -492,6 +540,138 @@ cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, c
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   k_sca<MODEL, DIS, COUNT, FAST2><<<a.geo.S, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Streamed SCA, for rings beyond one CTA's shared memory (the paper's mode of
+// one large sample per GPU held in device memory).  The lattice stays in
+// global memory in its natural layout; a sweep is one launch per phase, one
+// thread per unit (two 128-bit loads per plane).  Even bonds lie inside a
+// word, so the even phase needs nothing from other units.  The odd bond
+// (32w + 31, 32w + 32) that ends in the next unit flips bit 0 of that unit's
+// first word, a bit no bond of its owner touches: the owner merges the bits
+// it changed in its first word with an atomic XOR, the previous unit's owner
+// flips bit 0 the same way, so the lattice is settled after every launch.
+//
+// Two lanes: the lane changes that follow a phase are fused into its launch.
+// After the even phase a unit's sites depend on that unit alone.  After the
+// odd phase site 256(u + 1) also depends on unit u's last bond, so the owner
+// of unit u takes the lane changes of sites 256u + 1 .. 256(u + 1) and merges
+// them into the next unit's first words with its carry.
+constexpr uint32_t kScaStreamThreads = 256;
+
+__device__ __forceinline__ void load8(const uint32_t* p, uint32_t (&x)[8]) {
+  const uint4 v0 = reinterpret_cast<const uint4*>(p)[0], v1 = reinterpret_cast<const uint4*>(p)[1];
+  x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w; x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+}
+
+// Write back a unit: all 8 words after an even phase; after an odd phase
+// words 1..7 plainly and word 0 as the XOR of the bits this thread changed
+// (`old0` = word 0 as loaded), then the carry into the next unit (`nw`).
+template <uint32_t PHASE>
+__device__ __forceinline__ void store_unit(uint32_t* p, const uint32_t (&x)[8], uint32_t old0, uint32_t* nw,
+                                           uint32_t carry) {
+  if (PHASE == 0) {
+    reinterpret_cast<uint4*>(p)[0] = make_uint4(x[0], x[1], x[2], x[3]);
+    reinterpret_cast<uint4*>(p)[1] = make_uint4(x[4], x[5], x[6], x[7]);
+  } else {
+    p[1] = x[1];
+    *reinterpret_cast<uint2*>(p + 2) = make_uint2(x[2], x[3]);
+    reinterpret_cast<uint4*>(p)[1] = make_uint4(x[4], x[5], x[6], x[7]);
+    if (x[0] != old0) atomicXor(p, x[0] ^ old0);
+    if (carry) atomicXor(nw, carry);
+  }
+}
+
+// One phase over every sample.  Grid: S x blocks_per_sample CTAs,
+// blockIdx.x = sample * blocks_per_sample + block.
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
+__global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream(const DomainLaunch a, uint32_t blocks_per_sample) {
+  __shared__ unsigned long long red[kScaStreamThreads / 32][4];
+  const uint32_t W = a.geo.W, n_units = W / 8;
+  const uint32_t sample = blockIdx.x / blocks_per_sample;
+  const uint32_t u = (blockIdx.x - sample * blocks_per_sample) * kScaStreamThreads + threadIdx.x;
+  const uint32_t n_glob = a.geo.first_sample + sample;
+  const uint64_t s = a.clock->sweep;
+  unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
+  if (u < n_units) {
+    const uint32_t nw = (8u * u + 8u == W) ? 0u : 8u * u + 8u;  // the next unit's first word
+    const size_t real = sample / a.geo.samples_per_real;
+    if (MODEL == kRing) {
+      uint32_t* lat = a.state + static_cast<size_t>(sample) * W;
+      uint32_t x[8], c[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      load8(lat + 8u * u, x);
+      const uint32_t old0 = x[0];
+      const uint32_t x_next = PHASE ? lat[nw] : 0u;  // only bit 0, which only this thread changes
+      uint32_t c_next = 0u;
+      if (DIS) {
+        const uint32_t* cls = a.mask + real * W;
+        load8(cls + 8u * u, c);
+        if (PHASE) c_next = cls[nw];
+      }
+      const uint32_t out =
+          sca_update<DIS, COUNT, FAST2, PHASE>(x, c, x_next, c_next, a, u, s, n_glob, a.sca_kmax, cnt[0], cnt[1]);
+      store_unit<PHASE>(lat + 8u * u, x, old0, lat + nw, out);
+    } else {
+      uint32_t* A = a.state + static_cast<size_t>(sample) * 2u * W;
+      uint32_t* B = A + W;
+      uint32_t xa[8], xb[8];
+      load8(A + 8u * u, xa);
+      load8(B + 8u * u, xb);
+      const uint32_t a0 = xa[0], b0 = xb[0];
+      const uint32_t na = PHASE ? A[nw] : 0u, nb = PHASE ? B[nw] : 0u;
+      uint32_t oa = sca_lane_update<0, PHASE>(xa, na, a, u, s, n_glob, a.rates.p, cnt[0]);
+      uint32_t ob = sca_lane_update<1, PHASE>(xb, nb, a, u, s, n_glob, a.rates.q, cnt[1]);
+      if (DIS) {
+        const uint32_t* M = a.mask + real * W;
+        uint32_t m[8];
+        load8(M + 8u * u, m);
+        if (PHASE == 1) m[0] &= ~1u;  // site 256u belongs to the previous unit's owner
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const uint32_t f = sca_turn_word<PHASE>(turn_candidates<PHASE>(xa[w], xb[w], m[w]), 8u * u + w, a, s,
+                                                  n_glob, cnt[2 + PHASE]);
+          xa[w] ^= f;
+          xb[w] ^= f;
+        }
+        if (PHASE == 1) {  // site 256(u + 1) = bit 0 of word nw, after this unit's last bond
+          const uint32_t f = sca_turn_word<1>(turn_candidates<1>(na ^ oa, nb ^ ob, M[nw] & 1u), nw, a, s, n_glob,
+                                              cnt[3]);
+          oa ^= f;
+          ob ^= f;
+        }
+      }
+      store_unit<PHASE>(A + 8u * u, xa, a0, A + nw, oa);
+      store_unit<PHASE>(B + 8u * u, xb, b0, B + nw, ob);
+    }
+  }
+  if (COUNT) {
+    constexpr int NK = MODEL == kTwoLane ? (DIS ? 4 : 2) : 2;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      unsigned long long v = cnt[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31u) == 0) red[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NK) {
+      unsigned long long v = 0;
+      for (uint32_t w = 0; w < kScaStreamThreads / 32; ++w) v += red[w][threadIdx.x];
+      if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.counters + 4ull * sample + threadIdx.x), v);
+    }
+  }
+}
+
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
+cudaError_t launch_sca_stream_t(const DomainLaunch& a, cudaStream_t st) {
+  const uint32_t n_units = a.geo.W / 8;
+  const uint32_t bps = (n_units + kScaStreamThreads - 1) / kScaStreamThreads;
+  const uint32_t grid = bps * a.geo.S;
+  (void)cudaGetLastError();
+  k_sca_stream<MODEL, DIS, COUNT, FAST2, 0><<<grid, kScaStreamThreads, 0, st>>>(a, bps);
+  k_sca_stream<MODEL, DIS, COUNT, FAST2, 1><<<grid, kScaStreamThreads, 0, st>>>(a, bps);
   return cudaGetLastError();
 }
 
@@ -510,14 +690,27 @@ cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cud
   if (a.dis == kDisBimodal)
     return count ? launch_sca_t<kRing, true, true, false>(a, threads, smem, st)
                  : launch_sca_t<kRing, true, false, false>(a, threads, smem, st);
-  // rates neither 0 nor "always" and at most two random planes: the specialised comparison
-  const auto regular = [](uint32_t t) { return t != 0u && t != 0xFFFFFFFFu; };
-  const bool fast2 = regular(a.rates.p) && regular(a.rates.q) && a.sca_kmax <= 2;
-  if (fast2)
+  if (sca_fast2(a))
     return count ? launch_sca_t<kRing, false, true, true>(a, threads, smem, st)
                  : launch_sca_t<kRing, false, false, true>(a, threads, smem, st);
   return count ? launch_sca_t<kRing, false, true, false>(a, threads, smem, st)
                : launch_sca_t<kRing, false, false, false>(a, threads, smem, st);
+}
+
+
+cudaError_t launch_sca_stream(const DomainLaunch& a, cudaStream_t st) {
+  const bool count = a.count_hops != 0;
+  if (a.model == kTwoLane)
+    return a.dis == kDisTurning ? launch_sca_stream_t<kTwoLane, true, true, false>(a, st)
+                                : launch_sca_stream_t<kTwoLane, false, true, false>(a, st);
+  if (a.dis == kDisBimodal)
+    return count ? launch_sca_stream_t<kRing, true, true, false>(a, st)
+                 : launch_sca_stream_t<kRing, true, false, false>(a, st);
+  if (sca_fast2(a))
+    return count ? launch_sca_stream_t<kRing, false, true, true>(a, st)
+                 : launch_sca_stream_t<kRing, false, false, true>(a, st);
+  return count ? launch_sca_stream_t<kRing, false, true, false>(a, st)
+               : launch_sca_stream_t<kRing, false, false, false>(a, st);
 }
 
 }  // namespace asep

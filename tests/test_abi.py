@@ -66,10 +66,9 @@ def test_create_rejects_bad_params_without_device(A):
     bad = [dict(L=100), dict(L=1 << 29), dict(L=4096, domain_sites=48), dict(L=4096, p_thr=123),
            dict(L=4096, n_realizations=0), dict(L=4096, dis_kind=2), dict(L=4096, model=1, dis_kind=1),
            dict(L=4096 + 64, schedule=1), dict(L=4096, samples_per_real=3, first_sample=1),
-           # SCA schedule: L a multiple of 256, the lattice within one CTA's shared memory
-           dict(L=4096 + 64, schedule=2), dict(L=1 << 21, schedule=2),
-           dict(L=1 << 19, schedule=2, model=1, dis_kind=2, dis_a_thr=4096, dis_b_thr=4096),
-           dict(L=1 << 20, schedule=2, dis_kind=1, dis_a_thr=4096, dis_b_thr=4096), dict(L=4096, schedule=3)]
+           # SCA schedule: L a multiple of 256 (beyond shared memory it streams, up to 2^28)
+           dict(L=4096 + 64, schedule=2), dict(L=(1 << 21) + 128, schedule=2), dict(L=1 << 29, schedule=2),
+           dict(L=4096, schedule=3)]
     for kw in bad:
         prm = A.make_params(**kw)
         with pytest.raises(A.AsepError) as ei:
@@ -127,3 +126,28 @@ def test_allocation_failure_frees_everything_without_device(A, flags, dis):
         assert err.code == A.ASEP_ERR_NOMEM and "allocation failed" in str(err), k
         assert calls == n_calls  # every request is made, then the context is released as a whole
         assert sorted(freed) == sorted(live.items()), k
+
+
+def test_misaligned_allocation_is_refused_without_device(A):
+    """A block that does not start on a 256-byte boundary is handed straight
+    back through free_fn and counts as a failed allocation: asep_create
+    returns ASEP_ERR_NOMEM and every block is freed exactly once."""
+    for bad in range(3):
+        live, freed, calls = {}, [], [0]
+
+        def alloc(nbytes, user):
+            k = calls[0]
+            calls[0] += 1
+            ptr = 0x10000 * (k + 1) + (16 if k == bad else 0)
+            live[ptr] = nbytes
+            return ptr
+
+        def free(ptr, nbytes, user):
+            freed.append((ptr, nbytes))
+
+        prm = A.make_params(L=1024, schedule=A.ASEP_SCHED_SERIAL)
+        prm.alloc, prm.free_fn = A.ALLOC_FN(alloc), A.FREE_FN(free)
+        with pytest.raises(A.AsepError) as ei:
+            A.asep_create(prm, sample_times=[0, 5], torch_alloc=False, stream=0)
+        assert ei.value.code == A.ASEP_ERR_NOMEM and "allocation failed" in str(ei.value)
+        assert sorted(freed) == sorted(live.items()), bad

@@ -161,3 +161,34 @@ def test_random_configuration_streamed_tier_bit_exact(k):
         ref.counters[:] = 0
         ref.extra["counters_at"][:] = 0
     assert_same(g, ref, P, times)
+
+
+def draw_sca_streamed(k: int):
+    """A draw moved onto the streamed SCA (L = 256 .. 256 * 40 in units of
+    256, so the last block of threads is mostly idle), other parameters as
+    draw()."""
+    kw, chunks, times = draw(k)
+    rng = np.random.default_rng(9000 + k)
+    kw = dict(kw, schedule=A.ASEP_SCHED_SCA, L=256 * int(rng.integers(1, 41)), plan=(32, 0))
+    kw.pop("domain_sites", None)
+    return kw, chunks, times
+
+
+N_SCA_STREAMED = 24
+
+
+@pytest.mark.parametrize("k", range(N_SCA_STREAMED))
+def test_random_configuration_streamed_sca_bit_exact(k):
+    """Draws on the streamed SCA (lattice in global memory, a thread per
+    unit, boundary words merged atomically), bit-exact against the oracle."""
+    from test_gpu_parity import assert_same, oracle_params, run_gpu
+
+    kw, chunks, times = draw_sca_streamed(k)
+    g = run_gpu(kw, chunks, times)
+    P = oracle_params(kw)
+    t0 = kw.get("autocorr_t0") if kw["flags"] & A.ASEP_FLAG_AUTOCORR else None
+    ref = oracle.run(P, sum(chunks), times, autocorr_t0=t0)
+    if kw["flags"] & A.ASEP_FLAG_NO_HOP_COUNTS:
+        ref.counters[:] = 0
+        ref.extra["counters_at"][:] = 0
+    assert_same(g, ref, P, times)

@@ -182,6 +182,43 @@ CASES = {
     "sca_two_lane_max_L": (dict(model=TWO, L=1 << 18, schedule=SCA, samples_per_real=1, init_kind=1, init_seed=3,
                                 p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
                                 dis_b_thr=th(0.1), dis_seed=6, seed=7), 3, [0, 3]),
+    # streamed SCA (plan 32): the ring in global memory, one launch per phase, a thread per unit of 8 words;
+    # ragged unit counts leave most of the last block idle, one unit wraps onto its own first word
+    "sca_stream_asep": (dict(L=1 << 15, schedule=SCA, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=5,
+                             plan=(32, 0), flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=3), 25,
+                        [0, 3, 17, 25]),
+    "sca_stream_twenty_bit_ragged": (dict(L=256 * 9, schedule=SCA, samples_per_real=7, p_thr=th(0.6),
+                                          q_thr=th(0.3), seed=8, plan=(32, 0)), 30, [0, 7, 30]),
+    "sca_stream_tasep_deterministic": (dict(L=4096, schedule=SCA, samples_per_real=3, seed=2, plan=(32, 0)), 25,
+                                       [0, 1, 25]),
+    "sca_stream_bimodal_ragged": (dict(L=(1 << 14) + 768, schedule=SCA, n_realizations=2, samples_per_real=2,
+                                       p_thr=th(0.9), q_thr=th(0.2), dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1),
+                                       dis_b_thr=th(0.3), dis_c_thr=th(0.05), dis_seed=12, seed=14, plan=(32, 0)),
+                                  30, [0, 30]),
+    "sca_stream_one_unit": (dict(L=256, schedule=SCA, samples_per_real=20, p_thr=th(0.7), q_thr=th(0.2), seed=6,
+                                 plan=(32, 0)), 40, [0, 40]),
+    "sca_stream_two_lane_turning": (dict(model=TWO, L=4096 + 256, schedule=SCA, samples_per_real=3, init_kind=1,
+                                         init_seed=9, p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING,
+                                         dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=10, seed=11, plan=(32, 0),
+                                         flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 20,
+                                    [0, 5, 20]),
+    "sca_stream_two_lane_dense_turning": (dict(model=TWO, L=2048, schedule=SCA, samples_per_real=4, init_kind=1,
+                                               init_seed=19, p_thr=A.ASEP_ALWAYS, q_thr=th(0.8),
+                                               dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.9), dis_b_thr=th(0.6),
+                                               dis_seed=20, seed=21, plan=(32, 0)), 15, [0, 15]),
+    "sca_stream_two_lane_one_unit": (dict(model=TWO, L=256, schedule=SCA, samples_per_real=6, init_kind=1,
+                                          init_seed=3, p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING,
+                                          dis_a_thr=th(0.5), dis_b_thr=th(0.5), dis_seed=4, seed=5, plan=(32, 0)),
+                                     30, [0, 30]),
+    "sca_stream_two_lane_plain": (dict(model=TWO, L=2048, schedule=SCA, samples_per_real=5, init_kind=1,
+                                       init_seed=2, p_thr=th(0.7), q_thr=th(0.4), seed=12, plan=(32, 0)), 25,
+                                  [0, 12, 25]),
+    # beyond one CTA's shared memory the SCA streams by itself
+    "sca_stream_beyond_smem": (dict(L=1 << 21, schedule=SCA, samples_per_real=2, p_thr=th(0.75), q_thr=th(0.25),
+                                    seed=13), 3, [0, 3]),
+    "sca_stream_two_lane_beyond_smem": (dict(model=TWO, L=1 << 20, schedule=SCA, samples_per_real=1, init_kind=1,
+                                             init_seed=3, p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING,
+                                             dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=6, seed=7), 2, [0, 2]),
     # streamed tier (plan 32): lattice in global memory, tiles of columns through shared memory
     "stream_ring": (dict(L=1 << 16, domain_sites=256, samples_per_real=3, p_thr=th(0.75), q_thr=th(0.25), seed=61,
                          plan=(32, 0), flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 13,
@@ -473,6 +510,35 @@ def test_sca_growth_exponent_is_kpz():
     w2 = run_gpu(kw, [times[-1]], times)["w2"][:, :, 0].mean(axis=1)
     slope = np.polyfit(np.log(times), np.log(w2 - 0.25), 1)[0]
     assert abs(slope - 2 * beta) < 0.07, slope
+
+
+def test_sca_plans_switch_mid_run_without_changing_results():
+    """The SCA's resident and streamed plans, switched between sweeps and
+    with launches split differently, give the same lattices, records and
+    counters; a ring one CTA cannot hold is streamed and refuses the
+    resident plan."""
+    kw = dict(model=TWO, L=8192, schedule=SCA, samples_per_real=3, init_kind=1, init_seed=4, p_thr=th(0.6),
+              q_thr=th(0.45), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.2), dis_b_thr=th(0.4), dis_seed=8, seed=9)
+    times = [0, 3, 9, 16]
+    ref = run_gpu(kw, [16], times)
+    with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
+        assert A.asep_get_info(ctx)["cluster"] == 1
+        for k, plan in enumerate([32, 1, 32, 0, 32]):
+            A.asep_set_plan(ctx, plan, 0)
+            A.asep_sweep(ctx, [2, 5, 1, 4, 4][k])
+        words, sweep = A.asep_state(ctx)
+        sh, sh2, _ = A.asep_width(ctx)
+        assert sweep == 16
+        assert np.array_equal(words, ref["words"]) and np.array_equal(sh, ref["sh"]) and np.array_equal(sh2, ref["sh2"])
+        assert np.array_equal(A.asep_counters(ctx), ref["cnt"])
+        assert np.array_equal(A.asep_currents(ctx), ref["cur"])
+    with A.asep_create(A.make_params(L=1 << 21, schedule=SCA), sample_times=[]) as ctx:
+        assert A.asep_get_info(ctx)["cluster"] == 32
+        with pytest.raises(A.AsepError):
+            A.asep_set_plan(ctx, 1, 0)
+        assert A.asep_get_info(ctx)["cluster"] == 32  # the previous plan stays
+        with pytest.raises(A.AsepError):
+            A.asep_set_plan(ctx, 4, 0)
 
 
 def test_streamed_tier_is_chosen_beyond_a_cluster():

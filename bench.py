@@ -391,7 +391,9 @@ def other_workloads():
     sweeps, snapshots every 100), quenched bimodal disorder and the two-lane
     model with turning sites (10^4-sweep windows of their 10^7 / 10^6 sweep
     runs, log-spaced sample times, two-lane currents, profile and
-    autocorrelation on), the latter also under the paper's two-lane SCA."""
+    autocorrelation on), the latter also under the paper's two-lane SCA; and
+    the two streamed modes (domain schedule and SCA) on rings far beyond
+    shared memory."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
@@ -427,6 +429,10 @@ def other_workloads():
          "ASEP p=0.75 q=0.25, 16 samples, 200-MCS window",
          dict(L=1 << 24, domain_sites=256, samples_per_real=16, p_thr=th(0.75), q_thr=th(0.25), seed=1,
               flags=A.ASEP_FLAG_NO_HOP_COUNTS), [200], 1),
+        ("streamed SCA: L=2^28 rings (the paper's one-large-sample-per-GPU mode; lattice in HBM, a thread per "
+         "8 words, one launch per phase), ASEP p=0.75 q=0.25, 8 samples (256 MB, beyond L2), 200-MCS window",
+         dict(L=1 << 28, schedule=A.ASEP_SCHED_SCA, samples_per_real=8, p_thr=th(0.75), q_thr=th(0.25), seed=1,
+              flags=A.ASEP_FLAG_NO_HOP_COUNTS), [200], 1),
     ]
     stream = torch.cuda.current_stream()
     out = []
@@ -446,7 +452,8 @@ def other_workloads():
             attempts = lanes * kw["L"] * info["S"] * n_sweeps
             out.append({"workload": name, "attempts": attempts, "ms": ms, "attempts_per_s": attempts / (ms / 1e3),
                         "kernel": ("k_serial" if kw.get("schedule") == A.ASEP_SCHED_SERIAL
-                                   else "k_sca" if kw.get("schedule") == A.ASEP_SCHED_SCA
+                                   else ("k_sca_stream" if info["cluster"] == 32 else "k_sca")
+                                   if kw.get("schedule") == A.ASEP_SCHED_SCA
                                    else "k_stream" if info["cluster"] == 32
                                    else "k_cluster" if info["cluster"] > 1 else "k_domain"),
                         "samples_per_group": info["samples_per_group"]})

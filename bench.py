@@ -117,8 +117,14 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {
-    "domain": ("asep_kernels.cu", "asep_device.cuh", "asep_internal.h"),
+    "domain": ("asep_kernels.cu", "asep_domain.cuh", "asep_device.cuh", "asep_internal.h"),
     "sca": ("asep_sca.cu", "asep_device.cuh", "asep_internal.h"),
+    "sca_stream": ("asep_sca.cu", "asep_device.cuh", "asep_internal.h"),
+}
+TRAFFIC_FILES = {
+    "domain": "k_domain_growth_regime_traffic.txt",
+    "sca": "k_sca_growth_regime_traffic.txt",
+    "sca_stream": "k_sca_stream_large_rings_traffic.txt",
 }
 
 
@@ -136,8 +142,7 @@ def kernel_source_digest(kernel: str = "domain") -> str:
 def _traffic_from_profile(kernel: str = "domain"):
     """DRAM bytes per launch of the kernel from the committed ncu summary, if
     it was taken on the current kernel sources."""
-    name = "k_domain_growth_regime_traffic.txt" if kernel == "domain" else "k_sca_growth_regime_traffic.txt"
-    prof = os.path.join(ROOT, "profiles", name)
+    prof = os.path.join(ROOT, "profiles", TRAFFIC_FILES[kernel])
     try:
         digest = kernel_source_digest(kernel)
         kv = dict(line.strip().split("=", 1) for line in open(prof) if "=" in line)
@@ -450,13 +455,25 @@ def other_workloads():
             ms = e0.elapsed_time(e1)
             info = A.asep_get_info(ctx)
             attempts = lanes * kw["L"] * info["S"] * n_sweeps
-            out.append({"workload": name, "attempts": attempts, "ms": ms, "attempts_per_s": attempts / (ms / 1e3),
-                        "kernel": ("k_serial" if kw.get("schedule") == A.ASEP_SCHED_SERIAL
-                                   else ("k_sca_stream" if info["cluster"] == 32 else "k_sca")
-                                   if kw.get("schedule") == A.ASEP_SCHED_SCA
-                                   else "k_stream" if info["cluster"] == 32
-                                   else "k_cluster" if info["cluster"] > 1 else "k_domain"),
-                        "samples_per_group": info["samples_per_group"]})
+            row = {"workload": name, "attempts": attempts, "ms": ms, "attempts_per_s": attempts / (ms / 1e3),
+                   "kernel": ("k_serial" if kw.get("schedule") == A.ASEP_SCHED_SERIAL
+                              else ("k_sca_stream" if info["cluster"] == 32 else "k_sca")
+                              if kw.get("schedule") == A.ASEP_SCHED_SCA
+                              else "k_stream" if info["cluster"] == 32
+                              else "k_cluster" if info["cluster"] > 1 else "k_domain"),
+                   "samples_per_group": info["samples_per_group"]}
+            if info["cluster"] == 32:
+                # streamed: each phase reads and writes every lattice word once (4 x L/8 bytes per plane
+                # and sweep); the whole window, launch gaps and records included, against measured HBM
+                alg = 4 * (kw["L"] // 8) * lanes * info["S"] * n_sweeps
+                gbs = alg / (ms / 1e3) / 1e9
+                measured = _peaks().get("hbm_gbs")
+                peak = measured or 6800.0
+                row["hbm"] = {"algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+                              "peak_basis": "of measured copy bandwidth" if measured else "of fallback 6.8 TB/s"}
+                if kw.get("schedule") == A.ASEP_SCHED_SCA:
+                    row["hbm"]["traffic_per_launch"] = _traffic_from_profile("sca_stream")
+            out.append(row)
     return out
 
 
@@ -490,12 +507,22 @@ def profile_case(schedule: str = "domain"):
     height record, at the end): the kernel reads and writes each lattice once
     per launch, so its DRAM traffic per launch is that of a full step; only
     the loop is shorter.  schedule "sca" runs the same workload under the
-    two-sub-lattice SCA kernel."""
+    two-sub-lattice SCA kernel; "sca_stream" runs two sweeps (four launches,
+    one per phase) of the streamed SCA on 8 rings of 2^28 sites (256 MB)."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
 
     th = A.asep_threshold
+    if schedule == "sca_stream":
+        prm = A.make_params(L=1 << 28, schedule=A.ASEP_SCHED_SCA, samples_per_real=8, p_thr=th(P_RATE),
+                            q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
+        with A.asep_create(prm, sample_times=[]) as ctx:
+            A.asep_sweep(ctx, 2)
+            A.asep_sync(ctx)
+        torch.cuda.synchronize()
+        print("profile case done", flush=True)
+        return 0
     sched = A.ASEP_SCHED_SCA if schedule == "sca" else A.ASEP_SCHED_DOMAIN
     prm = A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE),
                         q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS, schedule=sched)
@@ -521,7 +548,7 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the windows of the other configurations")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
-    ap.add_argument("--profile-case", nargs="?", const="domain", choices=["domain", "sca"],
+    ap.add_argument("--profile-case", nargs="?", const="domain", choices=["domain", "sca", "sca_stream"],
                     help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")
     args = ap.parse_args()
     if args.profile_case:

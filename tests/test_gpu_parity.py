@@ -213,6 +213,18 @@ CASES = {
     "sca_stream_two_lane_plain": (dict(model=TWO, L=2048, schedule=SCA, samples_per_real=5, init_kind=1,
                                        init_seed=2, p_thr=th(0.7), q_thr=th(0.4), seed=12, plan=(32, 0)), 25,
                                   [0, 12, 25]),
+    # many blocks of 256 unit threads, the last one ragged (2085 units = 9 blocks, 1025 units = 5), so carries
+    # and lane-change sites cross block boundaries
+    "sca_stream_ring_nine_blocks": (dict(L=256 * 2085, schedule=SCA, n_realizations=2, samples_per_real=1,
+                                         p_thr=th(0.8), q_thr=th(0.35), dis_kind=A.ASEP_DIS_BIMODAL,
+                                         dis_a_thr=th(0.2), dis_b_thr=th(0.4), dis_c_thr=th(0.1), dis_seed=31,
+                                         seed=32, plan=(32, 0)), 7, [0, 1, 4, 7]),
+    "sca_stream_ring_five_blocks_fast": (dict(L=256 * 1025, schedule=SCA, samples_per_real=3, p_thr=th(0.75),
+                                              q_thr=th(0.25), seed=33, plan=(32, 0)), 6, [0, 3, 6]),
+    "sca_stream_two_lane_nine_blocks": (dict(model=TWO, L=256 * 2085, schedule=SCA, samples_per_real=1,
+                                             init_kind=1, init_seed=40, p_thr=th(0.6), q_thr=th(0.45),
+                                             dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.3), dis_b_thr=th(0.5),
+                                             dis_seed=41, seed=42, plan=(32, 0)), 5, [0, 5]),
     # beyond one CTA's shared memory the SCA streams by itself
     "sca_stream_beyond_smem": (dict(L=1 << 21, schedule=SCA, samples_per_real=2, p_thr=th(0.75), q_thr=th(0.25),
                                     seed=13), 3, [0, 3]),
@@ -512,13 +524,18 @@ def test_sca_growth_exponent_is_kpz():
     assert abs(slope - 2 * beta) < 0.07, slope
 
 
-def test_sca_plans_switch_mid_run_without_changing_results():
+@pytest.mark.parametrize("model", [0, 1])
+def test_sca_plans_switch_mid_run_without_changing_results(model):
     """The SCA's resident and streamed plans, switched between sweeps and
     with launches split differently, give the same lattices, records and
     counters; a ring one CTA cannot hold is streamed and refuses the
     resident plan."""
-    kw = dict(model=TWO, L=8192, schedule=SCA, samples_per_real=3, init_kind=1, init_seed=4, p_thr=th(0.6),
-              q_thr=th(0.45), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.2), dis_b_thr=th(0.4), dis_seed=8, seed=9)
+    if model == 1:
+        kw = dict(model=TWO, L=8192, schedule=SCA, samples_per_real=3, init_kind=1, init_seed=4, p_thr=th(0.6),
+                  q_thr=th(0.45), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.2), dis_b_thr=th(0.4), dis_seed=8,
+                  seed=9)
+    else:
+        kw = dict(L=8192, schedule=SCA, samples_per_real=3, p_thr=th(0.6), q_thr=th(0.45), seed=9)
     times = [0, 3, 9, 16]
     ref = run_gpu(kw, [16], times)
     with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
@@ -539,6 +556,7 @@ def test_sca_plans_switch_mid_run_without_changing_results():
         assert A.asep_get_info(ctx)["cluster"] == 32  # the previous plan stays
         with pytest.raises(A.AsepError):
             A.asep_set_plan(ctx, 4, 0)
+
 
 
 def test_streamed_tier_is_chosen_beyond_a_cluster():

@@ -46,6 +46,7 @@ struct asep_ctx {
   int64_t* d_href = nullptr;     // [S][planes] sum h of the reference lattice (last create / reset / load)
   uint64_t* d_href2 = nullptr;   // [S][planes][2] its sum h^2 (not used)
   int64_t* d_hrefcnt = nullptr;  // [S][4] hop counters at the reference
+  HeightPart* d_parts = nullptr;  // [S][planes][chunks] partial sums of a record over a long lattice
   uint32_t err_seen = 0;
   uint32_t ref_slot = 0;         // first sample-time slot recorded after the reference
   std::vector<std::pair<void*, size_t>> allocs;
@@ -404,9 +405,10 @@ int record_reference(asep_ctx* ctx) {
   h.counters = ctx->d_cnt;
   h.ex = Extras{};
   h.ex.tab_cnt = ctx->d_hrefcnt;
+  h.parts = ctx->d_parts;
   const cudaError_t e = launch_heights(h, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "reference heights kernel");
-  ++ctx->launches;
+  ctx->launches += height_chunks(ctx->W) > 1 ? 2 : 1;
   return ASEP_OK;
 }
 
@@ -420,9 +422,10 @@ int record_now(asep_ctx* ctx, uint32_t slot) {
   h.tab_sh2 = ctx->d_sh2;
   h.counters = ctx->d_cnt;
   h.ex = extras(ctx);
+  h.parts = ctx->d_parts;
   const cudaError_t e = launch_heights(h, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "heights kernel");
-  ++ctx->launches;
+  ctx->launches += height_chunks(ctx->W) > 1 ? 2 : 1;
   return ASEP_OK;
 }
 
@@ -607,6 +610,9 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   ctx->d_href2 = static_cast<uint64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * ctx->planes * 16));
   ctx->d_hrefcnt = static_cast<int64_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->S) * 32));
   ctx->d_err = static_cast<uint32_t*>(dev_alloc(ctx, 16));
+  if (height_chunks(ctx->W) > 1)
+    ctx->d_parts = static_cast<HeightPart*>(
+        dev_alloc(ctx, static_cast<size_t>(ctx->S) * ctx->planes * height_chunks(ctx->W) * sizeof(HeightPart)));
   if (params->flags & ASEP_FLAG_PROFILE) ctx->d_profile = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
   if (params->flags & ASEP_FLAG_AUTOCORR) {
     ctx->d_snap = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
@@ -616,6 +622,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
   if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || !ctx->d_clock ||
       !ctx->d_tab_cnt || !ctx->d_href || !ctx->d_href2 || !ctx->d_hrefcnt || !ctx->d_err ||
+      (height_chunks(ctx->W) > 1 && !ctx->d_parts) ||
       ((params->flags & ASEP_FLAG_PROFILE) && !ctx->d_profile) ||
       ((params->flags & ASEP_FLAG_AUTOCORR) && (!ctx->d_snap || !ctx->d_tab_ac)) || (ctx->R && !ctx->d_mask) ||
       (!ctx->ptab.empty() && !ctx->d_ptab))

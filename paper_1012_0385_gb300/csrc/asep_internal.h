@@ -145,6 +145,18 @@ struct DisorderLaunch {
   uint32_t* mask;
 };
 
+// Per-chunk partial sums of a record over a long lattice (see k_heights_part).
+struct HeightPart {
+  int64_t tot;   // height change across the chunk: sum of (2 n_i - 1)
+  int64_t s1;    // sum of the heights relative to the chunk's entry height
+  uint64_t s2lo, s2hi;  // sum of their squares (128 bits)
+  int64_t ov;    // autocorrelation overlap of the chunk
+};
+
+// Lattices of more than this many words per plane are recorded in chunks of
+// this size, one CTA each, and combined by a second launch.
+constexpr uint32_t kHeightChunkWords = 1u << 14;
+
 struct HeightsLaunch {
   Geometry geo;
   const uint32_t* state;
@@ -154,6 +166,7 @@ struct HeightsLaunch {
   uint64_t* tab_sh2;
   const uint64_t* counters;
   Extras ex;
+  HeightPart* parts;       // [S][planes][chunks] when W > kHeightChunkWords (else unused)
 };
 
 // Shared memory of the resident kernel, in bytes (planes of R2 + 1 rows:
@@ -162,6 +175,9 @@ size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp,
 
 cudaError_t launch_init(const InitLaunch& a, cudaStream_t st);
 cudaError_t launch_disorder(const DisorderLaunch& a, cudaStream_t st);
+// Chunks per plane of a record (1: one CTA per sample and plane); a.parts
+// must hold S * planes * chunks entries when it is above 1.
+uint32_t height_chunks(uint32_t W);
 cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st);
 // One CTA per sample group of one context.
 cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);

@@ -15,7 +15,8 @@
 //               or more whole rings in shared memory for a whole launch.
 //   (k_serial, the exact serial schedule, is in asep_serial.cu; k_sca, the
 //   paper's two-sub-lattice schedule, in asep_sca.cu.)
-//   k_heights   h_i = sum_{j<=i} (2 n_j - 1) and the sums of Eq. (W).
+//   k_heights   h_i = sum_{j<=i} (2 n_j - 1) and the sums of Eq. (W)
+//               (k_heights_part + k_heights_combine for long lattices).
 //
 // Resident layout.  For sweep s with offset o the ring is cut into G = L/2D
 // super-domains of 2D sites starting at o; super-domain g is column g of a
@@ -157,6 +158,90 @@ __global__ void __launch_bounds__(256) k_heights(const HeightsLaunch a) {
     const long long tot = block_scan_incl(ov, warp_tot);
     if (threadIdx.x == blockDim.x - 1)
       a.ex.tab_ac[(static_cast<size_t>(a.slot) * a.geo.S + sample) * planes + p] = tot;
+  }
+}
+
+// Long lattices: chunk j of plane p of a sample (kHeightChunkWords words) per
+// CTA.  Heights inside the chunk are taken relative to its entry height H_j
+// (the sum of the earlier chunks' changes), which the combine step adds back
+// exactly: sum (H + h') = sum h' + H n and sum (H + h')^2 = sum h'^2 +
+// 2 H sum h' + H^2 n.
+__global__ void __launch_bounds__(256) k_heights_part(const HeightsLaunch a, uint32_t chunks) {
+  __shared__ long long warp_tot[32];
+  __shared__ unsigned long long warp_s2[32];
+  const uint32_t planes = a.geo.planes, W = a.geo.W;
+  const uint32_t sp = blockIdx.x / chunks, j = blockIdx.x - sp * chunks;  // sp = sample * planes + p
+  const uint32_t p = sp % planes;
+  const uint32_t* w = a.state + static_cast<size_t>(sp) * W;
+  const uint32_t c0 = j * kHeightChunkWords, c1 = min(W, c0 + kHeightChunkWords);
+  const uint32_t per = (c1 - c0 + blockDim.x - 1) / blockDim.x;
+  const uint32_t w0 = min(c1, c0 + threadIdx.x * per), w1 = min(c1, w0 + per);
+  long long tot = 0;
+  for (uint32_t i = w0; i < w1; ++i) tot += 2 * __popc(w[i]) - 32;
+  const long long incl = block_scan_incl(tot, warp_tot);
+  long long h = incl - tot, s1 = 0;
+  unsigned long long s2 = 0;
+  for (uint32_t i = w0; i < w1; ++i) {
+    const uint32_t x = w[i];
+    for (uint32_t b = 0; b < 32; ++b) {
+      h += ((x >> b) & 1u) ? 1 : -1;
+      s1 += h;
+      s2 += static_cast<unsigned long long>(h * h);
+    }
+  }
+  const long long s1_all = block_scan_incl(s1, warp_tot);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31u) == 0) warp_s2[threadIdx.x >> 5] = s2;
+  const size_t pbase = static_cast<size_t>(sp) * W;
+  long long ov = 0;
+  for (uint32_t i = w0; i < w1; ++i) {
+    if (a.ex.profile) a.ex.profile[pbase + i] += __popc(w[i]);
+    if (a.ex.snap) {
+      if (a.t == a.ex.t0) a.ex.snap[pbase + i] = w[i];
+      if (a.t >= a.ex.t0) ov += __popc(w[i] & a.ex.snap[pbase + i]);
+    }
+  }
+  const long long ov_all = block_scan_incl(ov, warp_tot);  // also orders warp_s2 before the read below
+  if (threadIdx.x == blockDim.x - 1) {
+    unsigned __int128 acc = 0;
+    for (uint32_t i = 0; i < (blockDim.x >> 5); ++i) acc += warp_s2[i];
+    HeightPart& part = a.parts[static_cast<size_t>(sp) * chunks + j];
+    part.tot = incl;
+    part.s1 = s1_all;
+    part.s2lo = static_cast<uint64_t>(acc);
+    part.s2hi = static_cast<uint64_t>(acc >> 64);
+    part.ov = ov_all;
+  }
+  (void)p;
+}
+
+// One thread per sample and plane: the exact combination of its chunks.
+__global__ void k_heights_combine(const HeightsLaunch a, uint32_t chunks) {
+  const uint32_t planes = a.geo.planes, W = a.geo.W;
+  const uint32_t sp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sp >= a.geo.S * planes) return;
+  const uint32_t sample = sp / planes, p = sp - sample * planes;
+  __int128 H = 0, sh = 0, sh2 = 0;
+  long long ov = 0;
+  for (uint32_t j = 0; j < chunks; ++j) {
+    const HeightPart& part = a.parts[static_cast<size_t>(sp) * chunks + j];
+    const __int128 n = 32 * static_cast<__int128>(min(W, (j + 1) * kHeightChunkWords) - j * kHeightChunkWords);
+    const __int128 s2 = (static_cast<__int128>(part.s2hi) << 64) | part.s2lo;
+    sh += part.s1 + H * n;
+    sh2 += s2 + 2 * H * part.s1 + H * H * n;
+    H += part.tot;
+    ov += part.ov;
+  }
+  const size_t e = (static_cast<size_t>(a.slot) * a.geo.S + sample) * planes + p;
+  a.tab_sh[e] = static_cast<int64_t>(sh);
+  const unsigned __int128 u2 = static_cast<unsigned __int128>(sh2);
+  a.tab_sh2[2 * e] = static_cast<uint64_t>(u2);
+  a.tab_sh2[2 * e + 1] = static_cast<uint64_t>(u2 >> 64);
+  if (a.ex.snap) a.ex.tab_ac[e] = ov;
+  if (p == 0 && a.ex.tab_cnt) {
+    const size_t ec = (static_cast<size_t>(a.slot) * a.geo.S + sample) * 4;
+    for (int k = 0; k < 4; ++k) a.ex.tab_cnt[ec + k] = static_cast<int64_t>(a.counters[4 * static_cast<size_t>(sample) + k]);
   }
 }
 
@@ -813,9 +898,19 @@ cudaError_t launch_disorder(const DisorderLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+uint32_t height_chunks(uint32_t W) { return W > kHeightChunkWords ? (W + kHeightChunkWords - 1) / kHeightChunkWords : 1u; }
+
 cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st) {
   (void)cudaGetLastError();
-  k_heights<<<a.geo.S * a.geo.planes, 256, 0, st>>>(a);
+  const uint32_t chunks = height_chunks(a.geo.W);
+  if (chunks == 1) {
+    k_heights<<<a.geo.S * a.geo.planes, 256, 0, st>>>(a);
+  } else {
+    if (!a.parts) return cudaErrorInvalidValue;
+    const uint32_t sp = a.geo.S * a.geo.planes;
+    k_heights_part<<<sp * chunks, 256, 0, st>>>(a, chunks);
+    k_heights_combine<<<(sp + 127) / 128, 128, 0, st>>>(a, chunks);
+  }
   return cudaGetLastError();
 }
 

@@ -584,10 +584,12 @@ __device__ __forceinline__ void store_unit(uint32_t* p, const uint32_t (&x)[8], 
   }
 }
 
-// One phase over every sample.  Grid: S x blocks_per_sample CTAs,
-// blockIdx.x = sample * blocks_per_sample + block.
-template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
-__global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream(const DomainLaunch a, uint32_t blocks_per_sample) {
+// Two lanes: one phase and its lane changes over every sample, a thread per
+// unit.  Grid: S x blocks_per_sample CTAs, blockIdx.x = sample *
+// blocks_per_sample + block.  DIS: turning sites.
+template <bool DIS, uint32_t PHASE>
+__global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream_lanes(const DomainLaunch a,
+                                                                         uint32_t blocks_per_sample) {
   __shared__ unsigned long long red[kScaStreamThreads / 32][4];
   const uint32_t W = a.geo.W, n_units = W / 8;
   const uint32_t sample = blockIdx.x / blocks_per_sample;
@@ -598,22 +600,7 @@ __global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream(const DomainLa
   if (u < n_units) {
     const uint32_t nw = (8u * u + 8u == W) ? 0u : 8u * u + 8u;  // the next unit's first word
     const size_t real = sample / a.geo.samples_per_real;
-    if (MODEL == kRing) {
-      uint32_t* lat = a.state + static_cast<size_t>(sample) * W;
-      uint32_t x[8], c[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-      load8(lat + 8u * u, x);
-      const uint32_t old0 = x[0];
-      const uint32_t x_next = PHASE ? lat[nw] : 0u;  // only bit 0, which only this thread changes
-      uint32_t c_next = 0u;
-      if (DIS) {
-        const uint32_t* cls = a.mask + real * W;
-        load8(cls + 8u * u, c);
-        if (PHASE) c_next = cls[nw];
-      }
-      const uint32_t out =
-          sca_update<DIS, COUNT, FAST2, PHASE>(x, c, x_next, c_next, a, u, s, n_glob, a.sca_kmax, cnt[0], cnt[1]);
-      store_unit<PHASE>(lat + 8u * u, x, old0, lat + nw, out);
-    } else {
+    {
       uint32_t* A = a.state + static_cast<size_t>(sample) * 2u * W;
       uint32_t* B = A + W;
       uint32_t xa[8], xb[8];
@@ -646,8 +633,8 @@ __global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream(const DomainLa
       store_unit<PHASE>(B + 8u * u, xb, b0, B + nw, ob);
     }
   }
-  if (COUNT) {
-    constexpr int NK = MODEL == kTwoLane ? (DIS ? 4 : 2) : 2;
+  {
+    constexpr int NK = DIS ? 4 : 2;
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
       unsigned long long v = cnt[k];
@@ -664,14 +651,125 @@ __global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream(const DomainLa
   }
 }
 
+// The ring: a thread takes `upt` units, T apart (coalesced), and loads the
+// next one's words while it updates the current one, so that two units'
+// loads are in flight per thread (the one-unit form stalls on them).  The
+// 32 lanes of a warp hold 32 consecutive units, so in the odd phase a lane
+// takes bit 0 of the next unit's first word from its neighbour lane and
+// passes its carry to it by shuffles, and stores its 8 words plainly after
+// merging the carry it received.  Only the warp's ends touch other warps'
+// units: the last active lane loads the next unit's first word and merges
+// its carry into it atomically, lane 0 merges the bits it changed in its
+// first word atomically (that word receives the previous warp's carry).
+// A first word lane 0 prefetched may or may not hold that carry already:
+// bit 0 is not read by the odd phase.
+template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
+__global__ void __launch_bounds__(kScaStreamThreads, DIS ? 2 : 4) k_sca_stream_ring(const DomainLaunch a,
+                                                                        uint32_t blocks_per_sample, uint32_t upt) {
+  constexpr uint32_t T = kScaStreamThreads;
+  __shared__ unsigned long long red[T / 32][2];
+  const uint32_t W = a.geo.W, n_units = W / 8;
+  const uint32_t sample = blockIdx.x / blocks_per_sample;
+  const uint32_t u_first = (blockIdx.x - sample * blocks_per_sample) * (T * upt) + threadIdx.x;
+  const uint32_t n_glob = a.geo.first_sample + sample;
+  const uint64_t s = a.clock->sweep;
+  const uint32_t kmax = a.sca_kmax;
+  uint32_t* lat = a.state + static_cast<size_t>(sample) * W;
+  const uint32_t* cls = DIS ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+  unsigned long long nr = 0ull, nl = 0ull;
+  const uint32_t lane = threadIdx.x & 31u;
+  // active lanes of the warp for unit u (lane `lane`): a prefix of the warp
+  auto n_active = [&](uint32_t u) { return min(32u, n_units - (u - lane)); };
+  uint32_t px[8], pc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, pxn = 0u, pcn = 0u;  // the next unit's words
+  auto fetch = [&](uint32_t u) {
+    load8(lat + 8u * u, px);
+    if (DIS) load8(cls + 8u * u, pc);
+    if (PHASE && lane + 1 == n_active(u)) {  // the warp's last unit: the next unit's first words
+      const uint32_t nw = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
+      pxn = lat[nw];  // only bit 0, which only this thread changes
+      if (DIS) pcn = cls[nw];
+    }
+  };
+  if (u_first < n_units) fetch(u_first);
+#pragma unroll 1
+  for (uint32_t k = 0; k < upt; ++k) {
+    const uint32_t u = u_first + k * T;
+    if (u >= n_units) break;
+    uint32_t x[8], c[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      x[w] = px[w];
+      c[w] = pc[w];
+    }
+    uint32_t x_next = pxn, c_next = pcn;
+    const uint32_t na = n_active(u);
+    const unsigned act = na == 32u ? 0xffffffffu : (1u << na) - 1u;
+    const bool last = lane + 1 == na;
+    if (PHASE) {
+      const uint32_t xs = __shfl_down_sync(act, x[0], 1);
+      const uint32_t cs = DIS ? __shfl_down_sync(act, c[0], 1) : 0u;
+      if (!last) {
+        x_next = xs;
+        c_next = cs;
+      }
+    }
+    if (k + 1 < upt && u + T < n_units) fetch(u + T);
+    const uint32_t old0 = x[0];
+    const uint32_t out = sca_update<DIS, COUNT, FAST2, PHASE>(x, c, x_next, c_next, a, u, s, n_glob, kmax, nr, nl);
+    uint32_t* p = lat + 8u * u;
+    if (PHASE == 0) {
+      reinterpret_cast<uint4*>(p)[0] = make_uint4(x[0], x[1], x[2], x[3]);
+      reinterpret_cast<uint4*>(p)[1] = make_uint4(x[4], x[5], x[6], x[7]);
+    } else {
+      const uint32_t cin = __shfl_up_sync(act, out, 1);  // the carry of the unit before, from lane - 1
+      if (lane > 0) {
+        x[0] ^= cin;
+        reinterpret_cast<uint4*>(p)[0] = make_uint4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<uint4*>(p)[1] = make_uint4(x[4], x[5], x[6], x[7]);
+      } else {
+        store_unit<1>(p, x, old0, nullptr, 0u);  // words 1..7 plainly, word 0 by atomic XOR of the change
+      }
+      if (last && out) atomicXor(lat + ((8u * u + 8u == W) ? 0u : 8u * u + 8u), out);
+    }
+  }
+  if (COUNT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nr += __shfl_xor_sync(0xffffffffu, nr, o);
+      nl += __shfl_xor_sync(0xffffffffu, nl, o);
+    }
+    if ((threadIdx.x & 31u) == 0) {
+      red[threadIdx.x >> 5][0] = nr;
+      red[threadIdx.x >> 5][1] = nl;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      unsigned long long v = 0;
+      for (uint32_t w = 0; w < T / 32; ++w) v += red[w][threadIdx.x];
+      if (v) atomicAdd(reinterpret_cast<unsigned long long*>(a.counters + 4ull * sample + threadIdx.x), v);
+    }
+  }
+}
+
 template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
 cudaError_t launch_sca_stream_t(const DomainLaunch& a, cudaStream_t st) {
   const uint32_t n_units = a.geo.W / 8;
-  const uint32_t bps = (n_units + kScaStreamThreads - 1) / kScaStreamThreads;
-  const uint32_t grid = bps * a.geo.S;
   (void)cudaGetLastError();
-  k_sca_stream<MODEL, DIS, COUNT, FAST2, 0><<<grid, kScaStreamThreads, 0, st>>>(a, bps);
-  k_sca_stream<MODEL, DIS, COUNT, FAST2, 1><<<grid, kScaStreamThreads, 0, st>>>(a, bps);
+  if constexpr (MODEL == kRing) {
+    // units per thread: 4, 2 or 1, the most that still leaves eight waves of CTAs (152 SMs x 5), so
+    // that the last, partial wave costs little; in practice lattices far beyond L2 get 4, the rest 1
+    const uint64_t units = static_cast<uint64_t>(n_units) * a.geo.S;
+    uint32_t upt = 4;
+    while (upt > 1 && units < static_cast<uint64_t>(upt) * kScaStreamThreads * 8u * 152u * 5u) upt >>= 1;
+    const uint32_t per_block = kScaStreamThreads * upt;
+    const uint32_t bps = (n_units + per_block - 1) / per_block;
+    k_sca_stream_ring<DIS, COUNT, FAST2, 0><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
+    k_sca_stream_ring<DIS, COUNT, FAST2, 1><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
+  } else {
+    const uint32_t bps = (n_units + kScaStreamThreads - 1) / kScaStreamThreads;
+    k_sca_stream_lanes<DIS, 0><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
+    k_sca_stream_lanes<DIS, 1><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
+  }
   return cudaGetLastError();
 }
 

@@ -213,12 +213,13 @@ CASES = {
     "sca_stream_two_lane_plain": (dict(model=TWO, L=2048, schedule=SCA, samples_per_real=5, init_kind=1,
                                        init_seed=2, p_thr=th(0.7), q_thr=th(0.4), seed=12, plan=(32, 0)), 25,
                                   [0, 12, 25]),
-    # many blocks of 256 unit threads, the last one ragged (2085 units = 9 blocks, 1025 units = 5), so carries
-    # and lane-change sites cross block boundaries
+    # many blocks of unit threads, the last one ragged (2085 units, 1025 units), so carries and lane-change
+    # sites cross block boundaries; 16680 words per lattice: records in two chunks (16384 + 296 words)
     "sca_stream_ring_nine_blocks": (dict(L=256 * 2085, schedule=SCA, n_realizations=2, samples_per_real=1,
                                          p_thr=th(0.8), q_thr=th(0.35), dis_kind=A.ASEP_DIS_BIMODAL,
                                          dis_a_thr=th(0.2), dis_b_thr=th(0.4), dis_c_thr=th(0.1), dis_seed=31,
-                                         seed=32, plan=(32, 0)), 7, [0, 1, 4, 7]),
+                                         seed=32, plan=(32, 0), flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR,
+                                         autocorr_t0=1), 7, [0, 1, 4, 7]),
     "sca_stream_ring_five_blocks_fast": (dict(L=256 * 1025, schedule=SCA, samples_per_real=3, p_thr=th(0.75),
                                               q_thr=th(0.25), seed=33, plan=(32, 0)), 6, [0, 3, 6]),
     "sca_stream_two_lane_nine_blocks": (dict(model=TWO, L=256 * 2085, schedule=SCA, samples_per_real=1,
@@ -557,6 +558,20 @@ def test_sca_plans_switch_mid_run_without_changing_results(model):
         with pytest.raises(A.AsepError):
             A.asep_set_plan(ctx, 4, 0)
 
+
+
+def test_streamed_sca_units_per_thread_do_not_change_results():
+    """Streamed SCA rings of 2^23 sites: 192 samples run with four units per
+    thread, 96 with two, one with one (the count follows the launch size);
+    sample 0 is the same in all three and equals the oracle's."""
+    kw = dict(L=1 << 23, schedule=SCA, p_thr=th(0.75), q_thr=th(0.25), seed=71)
+    runs = {S: run_gpu(dict(kw, samples_per_real=S), [3], [0, 3]) for S in (192, 96, 1)}
+    P = oracle_params(dict(kw, samples_per_real=1))
+    assert_same(runs[1], oracle.run(P, 3, [0, 3]), P, [0, 3])
+    for S in (192, 96):
+        assert np.array_equal(runs[S]["words"].reshape(S, -1)[0], runs[1]["words"].reshape(-1)), S
+        assert np.array_equal(runs[S]["cnt"][0], runs[1]["cnt"][0]), S
+        assert np.array_equal(runs[S]["sh"][:, 0], runs[1]["sh"][:, 0]), S
 
 
 def test_streamed_tier_is_chosen_beyond_a_cluster():

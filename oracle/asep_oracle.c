@@ -73,6 +73,7 @@
 #define DIS_NONE 0u
 #define DIS_BIMODAL 1u
 #define DIS_TURNING 2u
+#define DIS_BIMODAL_PQ 3u /* independent slow classes for right (p) and left (q) hops */
 #define INIT_FLAT_ALT 0u
 #define INIT_BERNOULLI_HALF 1u
 
@@ -182,13 +183,17 @@ static void flip_site(uint32_t* w, uint64_t i) { w[i >> 5] ^= 1u << (i & 31); }
 
 static int accept(uint32_t r, uint32_t t) { return (r & ACCEPT_MASK) < t; }
 
-/* rate for a right hop leaving site i (p_i) and a left hop leaving site i (q_i) */
+/* rate for a right hop leaving site i (p_i) and a left hop leaving site i
+ * (q_i).  BIMODAL: one slow class per site for both.  BIMODAL_PQ (the paper's
+ * separate tag bits for reduced forward and backward rates, Eq. bimodal with
+ * the same distribution for q_i): the q classes are the second plane. */
 static uint32_t rate_p(const orc_params* P, const uint32_t* cls, uint64_t i) {
-  if (P->dis_kind == DIS_BIMODAL && get_site(cls, i)) return P->dis_b_thr;
+  if ((P->dis_kind == DIS_BIMODAL || P->dis_kind == DIS_BIMODAL_PQ) && get_site(cls, i)) return P->dis_b_thr;
   return P->p_thr;
 }
 static uint32_t rate_q(const orc_params* P, const uint32_t* cls, uint64_t i) {
   if (P->dis_kind == DIS_BIMODAL && get_site(cls, i)) return P->dis_c_thr;
+  if (P->dis_kind == DIS_BIMODAL_PQ && get_site(cls + (P->L + 31) / 32, i)) return P->dis_c_thr;
   return P->q_thr;
 }
 
@@ -475,17 +480,22 @@ int orc_init(const orc_params* P, uint32_t* words, uint32_t sample) {
   return -1;
 }
 
-/* mask: [ceil(L/32)] for realization `real`.  BIMODAL: bit i = site i is slow
- * (probability Q = dis_a_thr, Eq. bimodal).  TURNING: bit i = site i is a
- * turning site (probability density = dis_a_thr). */
+/* mask: [planes][ceil(L/32)] for realization `real`.  BIMODAL: bit i = site
+ * i is slow (probability Q = dis_a_thr, Eq. bimodal).  BIMODAL_PQ: plane 0
+ * the slow sites of right hops, plane 1 (drawn independently, call 1 of the
+ * same stream) those of left hops.  TURNING: bit i = site i is a turning
+ * site (probability density = dis_a_thr). */
 int orc_disorder(const orc_params* P, uint32_t* mask, uint32_t real) {
   stream_t st;
-  memset(mask, 0, (size_t)((P->L + 31) / 32) * sizeof(uint32_t));
+  const uint64_t W = (P->L + 31) / 32;
+  const uint32_t planes = P->dis_kind == DIS_BIMODAL_PQ ? 2u : 1u;
+  memset(mask, 0, (size_t)(W * planes) * sizeof(uint32_t));
   if (P->dis_kind == DIS_NONE) return 0;
-  for (uint64_t i = 0; i < P->L; i++) {
-    stream_open(&st, P->dis_seed, 0, TAG_DIS, real, (uint32_t)(i >> 2), 0);
-    if (accept(stream_word(&st, i & 3), P->dis_a_thr)) mask[i >> 5] |= 1u << (i & 31);
-  }
+  for (uint32_t pl = 0; pl < planes; pl++)
+    for (uint64_t i = 0; i < P->L; i++) {
+      stream_open(&st, P->dis_seed, 0, TAG_DIS, real, (uint32_t)(i >> 2), 0);
+      if (accept(stream_word(&st, 4u * pl + (i & 3)), P->dis_a_thr)) mask[pl * W + (i >> 5)] |= 1u << (i & 31);
+    }
   return 0;
 }
 

@@ -389,6 +389,64 @@ def test_sca_disorder_rate_placement(oracle_mod):
     assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(wrong, 2)) < 1e-6
 
 
+def test_independent_pq_class_draws(oracle_mod):
+    """Independent p and q classes (the paper tags reduced forward and
+    backward rates with separate bits, both with the distribution of Eq.
+    bimodal): plane 0 is the one-class draw itself, plane 1 has the same
+    frequency Q and is uncorrelated with plane 0."""
+    th = oracle_mod.threshold
+    L, Q = 1 << 16, 0.3
+    kw = dict(L=L, schedule=oracle_mod.SCHED_SCA, n_realizations=2, samples_per_real=1, dis_a_thr=th(Q),
+              dis_b_thr=th(0.1), dis_c_thr=th(0.2), dis_seed=17)
+    one = oracle_mod.disorder(oracle_mod.Params(dis_kind=oracle_mod.DIS_BIMODAL, **kw))
+    two = oracle_mod.disorder(oracle_mod.Params(dis_kind=oracle_mod.DIS_BIMODAL_PQ, **kw))
+    W = L // 32
+    assert two.shape == (2, 2 * W)
+    assert np.array_equal(two[:, :W], one)
+    bits = np.unpackbits(two.view(np.uint8), bitorder="little").reshape(2, 2, L).astype(np.float64)
+    n = 2 * L
+    for pl in range(2):
+        f = bits[:, pl].mean()
+        assert abs(f - Q) < 5 * np.sqrt(Q * (1 - Q) / n), (pl, f)
+    both = (bits[:, 0] * bits[:, 1]).mean()
+    assert abs(both - Q * Q) < 5 * np.sqrt(Q * Q * (1 - Q * Q) / n), both
+    assert not np.array_equal(two[:, :W], two[:, W:])
+
+
+@pytest.mark.parametrize("schedule", ["sca", "serial"])
+def test_independent_pq_classes_rate_placement(oracle_mod, schedule):
+    """Independent classes: right hops across (i, i+1) use p_i from the p
+    plane, left hops q_{i+1} from the q plane.  Chi-square against the exact
+    operator; rejected: the one-class reading (q classes from the p plane)
+    and left hops keyed by the departure site's predecessor."""
+    L = 8
+    pf, ps, qf, qs = 0.9, 0.2, 0.7, 0.1
+    th = oracle_mod.threshold
+    sched = oracle_mod.SCHED_SCA if schedule == "sca" else oracle_mod.SCHED_SERIAL
+    P = oracle_mod.Params(L=L, schedule=sched, samples_per_real=S_DIST, seed=29, p_thr=th(pf), q_thr=th(qf),
+                          dis_kind=oracle_mod.DIS_BIMODAL_PQ, dis_a_thr=th(0.5), dis_b_thr=th(ps),
+                          dis_c_thr=th(qs), dis_seed=11)
+    mask = oracle_mod.disorder(P)
+    pslow = [(int(mask[0, 0]) >> i) & 1 for i in range(L)]
+    qslow = [(int(mask[0, 1]) >> i) & 1 for i in range(L)]
+    assert pslow != qslow and 0 < sum(pslow) < L and 0 < sum(qslow) < L
+    pvec = [ps if c else pf for c in pslow]
+    qvec = [qs if c else qf for c in qslow]
+
+    def op(pv, qv):
+        m = ex.RingModel(L, L // 2, pv, qv)
+        return m.sca_sweep() if schedule == "sca" else m.rsu_sweep()
+
+    sp = ex.RingModel(L, L // 2, pf, qf).sp
+    counts = histogram(sp, _replay_hist(oracle_mod, P, 2, mask=mask))
+    assert chi2_pvalue(counts, sp.flat_alt() @ np.linalg.matrix_power(op(pvec, qvec), 2)) > 1e-4
+    one_class = [qs if c else qf for c in pslow]
+    q_shift = [qvec[(i - 1) % L] for i in range(L)]
+    for wrong_q in (one_class, q_shift):
+        wrong = sp.flat_alt() @ np.linalg.matrix_power(op(pvec, wrong_q), 2)
+        assert chi2_pvalue(counts, wrong) < 1e-6
+
+
 def test_sca_deterministic_tasep_moves_every_particle_twice(oracle_mod):
     """p = 1, q = 0 from the flat 1010... state (site 0 occupied): the even
     bonds all carry 10 and hop, giving 0101...; the odd bonds, the closing

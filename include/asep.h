@@ -99,6 +99,13 @@ extern "C" {
 #define ASEP_DIS_NONE 0u
 #define ASEP_DIS_BIMODAL 1u /* dis_a = Q, dis_b = p_slow, dis_c = q_slow     */
 #define ASEP_DIS_TURNING 2u /* two lanes: dis_a = site density, dis_b = omega */
+/* Ring, SCA or serial schedule: independent slow classes for right and left
+ * hops (sec. 3, Eq. bimodal; the paper tags reduced forward and backward
+ * rates with separate bits, the same distribution for q_i as for p_i):
+ * dis_a = Q for both, dis_b = p_slow, dis_c = q_slow.  Plane 0 of a
+ * realization holds the p classes (the ASEP_DIS_BIMODAL draw), plane 1 the q
+ * classes (call 1 of the disorder stream).  Not under the domain schedule. */
+#define ASEP_DIS_BIMODAL_PQ 3u
 
 #define ASEP_INIT_FLAT_ALT 0u       /* 1010...: site i occupied iff i even (paper sec. 2.1) */
 #define ASEP_INIT_BERNOULLI_HALF 1u /* every lane site occupied with probability 1/2 (sec. 3) */
@@ -214,8 +221,9 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed);
  * J = c[0] - c[1].  Synchronises. */
 int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n);
 
-/* Copy the quenched planes, layout [n_realizations][L/32] (bit = slow site
- * for BIMODAL, turning site for TURNING).  Synchronises. */
+/* Copy the quenched planes, layout [n_realizations][planes][L/32] (planes =
+ * 2 for BIMODAL_PQ: p classes, then q classes; else 1; bit = slow site for
+ * the bimodal kinds, turning site for TURNING).  Synchronises. */
 int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words);
 
 /* Hop counters (layout of asep_counters) at every sample time recorded so

@@ -193,9 +193,11 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (!thr_ok(p->p_thr) || !thr_ok(p->q_thr) || !thr_ok(p->dis_a_thr) || !thr_ok(p->dis_b_thr) ||
       !thr_ok(p->dis_c_thr))
     return fail(ctx, ASEP_ERR_INVALID, "thresholds must be 0, ASEP_ALWAYS or multiples of 4096");
-  if (p->dis_kind > ASEP_DIS_TURNING) return fail(ctx, ASEP_ERR_INVALID, "unknown dis_kind %u", p->dis_kind);
-  if (p->dis_kind == ASEP_DIS_BIMODAL && p->model != ASEP_MODEL_RING)
+  if (p->dis_kind > ASEP_DIS_BIMODAL_PQ) return fail(ctx, ASEP_ERR_INVALID, "unknown dis_kind %u", p->dis_kind);
+  if ((p->dis_kind == ASEP_DIS_BIMODAL || p->dis_kind == ASEP_DIS_BIMODAL_PQ) && p->model != ASEP_MODEL_RING)
     return fail(ctx, ASEP_ERR_INVALID, "bimodal disorder is defined for the ring model");
+  if (p->dis_kind == ASEP_DIS_BIMODAL_PQ && p->schedule == ASEP_SCHED_DOMAIN)
+    return fail(ctx, ASEP_ERR_INVALID, "independent p and q classes run under the SCA and serial schedules");
   if (p->dis_kind == ASEP_DIS_TURNING && p->model != ASEP_MODEL_TWO_LANE)
     return fail(ctx, ASEP_ERR_INVALID, "turning sites are defined for the two-lane model");
   if (p->init_kind > ASEP_INIT_BERNOULLI_HALF) return fail(ctx, ASEP_ERR_INVALID, "unknown init_kind %u", p->init_kind);
@@ -237,7 +239,7 @@ int validate(const asep_params* p, asep_ctx* ctx) {
 int plan_sca(asep_ctx* ctx, uint32_t force) {
   const uint32_t units = ctx->W / 8;
   const bool quenched = ctx->p.dis_kind != ASEP_DIS_NONE;
-  const size_t smem = sca_smem_bytes(ctx->W, ctx->planes, quenched);
+  const size_t smem = sca_smem_bytes(ctx->W, ctx->planes, dis_planes(ctx->p.dis_kind));
   const bool fits = smem <= 200u * 1024u;
   if (force == 1 && !fits)
     return fail(ctx, ASEP_ERR_INVALID, "the resident SCA plan needs %zu bytes of shared memory (at most 200 KB)",
@@ -353,8 +355,9 @@ Rates rates(const asep_ctx* ctx) {
   Rates r;
   r.p = ctx->p.p_thr;
   r.q = ctx->p.q_thr;
-  r.p_slow = ctx->p.dis_kind == ASEP_DIS_BIMODAL ? ctx->p.dis_b_thr : ctx->p.p_thr;
-  r.q_slow = ctx->p.dis_kind == ASEP_DIS_BIMODAL ? ctx->p.dis_c_thr : ctx->p.q_thr;
+  const bool bimodal = ctx->p.dis_kind == ASEP_DIS_BIMODAL || ctx->p.dis_kind == ASEP_DIS_BIMODAL_PQ;
+  r.p_slow = bimodal ? ctx->p.dis_b_thr : ctx->p.p_thr;
+  r.q_slow = bimodal ? ctx->p.dis_c_thr : ctx->p.q_thr;
   r.omega = ctx->p.dis_kind == ASEP_DIS_TURNING ? ctx->p.dis_b_thr : 0u;
   r.p_always = r.p == ASEP_ALWAYS;
   r.q_always = r.q == ASEP_ALWAYS;
@@ -618,7 +621,9 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     ctx->d_snap = static_cast<uint32_t*>(dev_alloc(ctx, state_words * 4));
     ctx->d_tab_ac = static_cast<int64_t*>(dev_alloc(ctx, entries * 8));
   }
-  if (ctx->R) ctx->d_mask = static_cast<uint32_t*>(dev_alloc(ctx, static_cast<size_t>(ctx->R) * ctx->W * 4));
+  if (ctx->R)
+    ctx->d_mask = static_cast<uint32_t*>(
+        dev_alloc(ctx, static_cast<size_t>(ctx->R) * dis_planes(params->dis_kind) * ctx->W * 4));
   if (!ctx->ptab.empty()) ctx->d_ptab = static_cast<uint32_t*>(dev_alloc(ctx, ctx->ptab.size() * 4));
   if (!ctx->d_state || !ctx->d_cnt || !ctx->d_sh || !ctx->d_sh2 || !ctx->d_times || !ctx->d_clock ||
       !ctx->d_tab_cnt || !ctx->d_href || !ctx->d_href2 || !ctx->d_hrefcnt || !ctx->d_err ||
@@ -657,6 +662,7 @@ int asep_create(const asep_params* params, asep_ctx** out) {
     dl.L = ctx->L;
     dl.W = ctx->W;
     dl.R = ctx->R;
+    dl.planes = dis_planes(params->dis_kind);
     dl.first_real = params->first_sample / params->samples_per_real;
     dl.thr = params->dis_a_thr;
     dl.dis_seed = params->dis_seed;
@@ -864,7 +870,7 @@ int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n) {
 
 int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words) {
   if (!ctx || !words) return ASEP_ERR_INVALID;
-  const size_t need = static_cast<size_t>(ctx->R) * ctx->W;
+  const size_t need = static_cast<size_t>(ctx->R) * dis_planes(ctx->p.dis_kind) * ctx->W;
   if (n_words < need) return fail(ctx, ASEP_ERR_INVALID, "n_words = %zu < %zu", n_words, need);
   int rc = asep_sync(ctx);
   if (rc != ASEP_OK) return rc;

@@ -22,7 +22,11 @@ constexpr uint32_t kTagScaTurn = 8;  // two-lane SCA: one word per lane-change c
 constexpr uint32_t kAcceptMask = 0xFFFFF000u;  // draw bits compared with a threshold
 
 enum Model : uint32_t { kRing = 0, kTwoLane = 1 };
-enum Dis : uint32_t { kDisNone = 0, kDisBimodal = 1, kDisTurning = 2 };
+enum Dis : uint32_t { kDisNone = 0, kDisBimodal = 1, kDisTurning = 2, kDisBimodalPQ = 3 };
+
+// Quenched planes per realization: the class plane (bimodal), the turning
+// plane (two lanes), or the p-class and q-class planes (bimodal, independent).
+constexpr uint32_t dis_planes(uint32_t dis) { return dis == kDisNone ? 0u : (dis == kDisBimodalPQ ? 2u : 1u); }
 
 // Rates of one context (u32 thresholds).
 struct Rates {
@@ -139,6 +143,7 @@ struct InitLaunch {
 struct DisorderLaunch {
   uint64_t L;
   uint32_t W, R;
+  uint32_t planes;         // 1, or 2 for independent p and q classes (plane 1: call 1 of the stream)
   uint32_t first_real;
   uint32_t thr;
   uint64_t dis_seed;
@@ -198,7 +203,7 @@ cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cud
 // Streamed SCA: one sweep (both phases; two lanes: with the lane changes)
 // over every sample, lattice in global memory; results identical to launch_sca.
 cudaError_t launch_sca_stream(const DomainLaunch& a, cudaStream_t st);
-size_t sca_smem_bytes(uint32_t W, uint32_t planes, bool quenched);
+size_t sca_smem_bytes(uint32_t W, uint32_t planes, uint32_t quenched_planes);
 // How many clusters of the given shape can be resident at once (0 = none).
 int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem);
 // Advance clocks after n sweeps (one context, or the jobs of a batch).

@@ -83,15 +83,17 @@ __global__ void k_init(const InitLaunch a) {
 }
 
 __global__ void k_disorder(const DisorderLaunch a) {
-  const size_t total = static_cast<size_t>(a.R) * a.W;
+  const size_t per_real = static_cast<size_t>(a.planes) * a.W;
+  const size_t total = static_cast<size_t>(a.R) * per_real;
   const uint2 key = key_of(a.dis_seed);
   for (size_t idx = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; idx < total;
        idx += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const uint32_t r = static_cast<uint32_t>(idx / a.W);
-    const uint32_t w = static_cast<uint32_t>(idx - static_cast<size_t>(r) * a.W);
+    const uint32_t r = static_cast<uint32_t>(idx / per_real);
+    const uint32_t pw = static_cast<uint32_t>(idx - static_cast<size_t>(r) * per_real);
+    const uint32_t pl = pw / a.W, w = pw - pl * a.W;  // plane pl: call pl of the stream
     uint32_t v = 0;
     for (uint32_t q = 0; q < 8; ++q) {  // site group 8w + q holds sites 32w + 4q .. +3
-      const uint4 x = philox10(ctr_of(0, kTagDis, 0, a.first_real + r, 8u * w + q), key);
+      const uint4 x = philox10(ctr_of(0, kTagDis, pl, a.first_real + r, 8u * w + q), key);
       v |= (static_cast<uint32_t>(accept(x.x, a.thr)) << (4 * q)) |
            (static_cast<uint32_t>(accept(x.y, a.thr)) << (4 * q + 1)) |
            (static_cast<uint32_t>(accept(x.z, a.thr)) << (4 * q + 2)) |

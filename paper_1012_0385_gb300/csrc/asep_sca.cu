@@ -46,17 +46,27 @@ __device__ long long block_sum(long long v, long long* warp_tot) {
   return t;
 }
 
+// Eight consecutive words (16-byte aligned) into registers.
+__device__ __forceinline__ void load8(const uint32_t* p, uint32_t (&x)[8]) {
+  const uint4 v0 = reinterpret_cast<const uint4*>(p)[0], v1 = reinterpret_cast<const uint4*>(p)[1];
+  x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w; x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+}
+
 // All-ones where bit k (0 = most significant of 20) of a 20-bit threshold is set.
 __device__ __forceinline__ uint32_t bit_mask(uint32_t t20, uint32_t k) { return 0u - ((t20 >> (19u - k)) & 1u); }
 
-// One phase over one unit (four groups, global unit index u) held in registers: x = its 8
-// words, c = its 8 class words (DIS), x_next / c_next = the next unit's first
-// words (only bit 0 is used, odd phase).  Returns the flip of bit 0 of the
-// next unit's first word that the unit's last odd bond makes (odd phase).
-template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
-__device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t (&c)[8], uint32_t x_next,
-                                               uint32_t c_next, const DomainLaunch& a, uint32_t u, uint64_t s,
-                                               uint32_t n_glob, uint32_t kmax, unsigned long long& n_right,
+// One phase over one unit (four groups, global unit index u) held in
+// registers: x = its 8 words, c = its 8 class words (DIS: the classes of
+// right hops, and of left hops too unless PQ), d = the classes of left hops
+// (PQ: independent p and q classes), x_next / c_next / d_next = the next
+// unit's first words (only bit 0 is used, odd phase).  Returns the flip of
+// bit 0 of the next unit's first word that the unit's last odd bond makes
+// (odd phase).
+template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE, bool PQ = false>
+__device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t (&c)[8], const uint32_t (&d)[8],
+                                               uint32_t x_next, uint32_t c_next, uint32_t d_next,
+                                               const DomainLaunch& a, uint32_t u, uint64_t s, uint32_t n_glob,
+                                               uint32_t kmax, unsigned long long& n_right,
                                                unsigned long long& n_left) {
   uint32_t rc[4], lc[4], acc[4], eq[4];
   if (FAST2) {
@@ -130,6 +140,13 @@ __device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t 
         const uint32_t zb = PHASE ? __funnelshift_r(cb, cn, 1) : cb;
         c1[gi] = (za & kEven) | ((zb & kEven) << 1);                   // class of site i
         c2[gi] = ((za >> 1) & kEven) | (((zb >> 1) & kEven) << 1);     // class of site i + 1
+        if (PQ) {  // left hops: the q class of site i + 1
+          const uint32_t da = d[2 * gi], db = d[2 * gi + 1];
+          const uint32_t dn = gi < 3 ? d[2 * gi + 2] : d_next;
+          const uint32_t wa = PHASE ? __funnelshift_r(da, db, 1) : da;
+          const uint32_t wb = PHASE ? __funnelshift_r(db, dn, 1) : db;
+          c2[gi] = ((wa >> 1) & kEven) | (((wb >> 1) & kEven) << 1);
+        }
       } else {
         c1[gi] = 0u;
         c2[gi] = 0u;
@@ -186,7 +203,7 @@ __device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t 
 
 // One phase over unit u of a ring resident in shared memory; the flip of
 // bit 0 of the next unit's first word is left in carry[u] for its owner.
-template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
+template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE, bool PQ = false>
 __device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uint32_t* carry, const DomainLaunch& a,
                                          uint32_t u, uint32_t n_units, uint32_t W, uint64_t s, uint32_t n_glob,
                                          uint32_t kmax, unsigned long long& n_right, unsigned long long& n_left) {
@@ -204,11 +221,14 @@ __device__ __forceinline__ void sca_unit(uint32_t* lat, const uint32_t* cls, uin
     const uint4 d0 = c4[0], d1 = c4[1];
     c[0] = d0.x; c[1] = d0.y; c[2] = d0.z; c[3] = d0.w; c[4] = d1.x; c[5] = d1.y; c[6] = d1.z; c[7] = d1.w;
   }
+  uint32_t d[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  if (PQ) load8(cls + W + 8u * u, d);  // the q classes follow the p classes
   const uint32_t next_w = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
   const uint32_t x_next = PHASE ? lat[next_w] : 0u;  // only bit 0 is used
   const uint32_t c_next = (PHASE && DIS) ? cls[next_w] : 0u;
-  const uint32_t carry_out =
-      sca_update<DIS, COUNT, FAST2, PHASE>(x, c, x_next, c_next, a, u, s, n_glob, kmax, n_right, n_left);
+  const uint32_t d_next = (PHASE && PQ) ? cls[W + next_w] : 0u;
+  const uint32_t carry_out = sca_update<DIS, COUNT, FAST2, PHASE, PQ>(x, c, d, x_next, c_next, d_next, a, u, s,
+                                                                      n_glob, kmax, n_right, n_left);
   p4[0] = make_uint4(x[0], x[1], x[2], x[3]);
   p4[1] = make_uint4(x[4], x[5], x[6], x[7]);
   if (PHASE == 1) carry[u] = carry_out;
@@ -446,11 +466,12 @@ __device__ void sca_record(const uint32_t* lat, const DomainLaunch& a, uint32_t 
 }
 
 // The SCA kernel.  Ring (MODEL 0): one lattice plane, optionally a bimodal
-// class plane (DIS).  Two lanes (MODEL 1): planes A and B and, with turning
-// sites (DIS), the turning plane and the lane-change steps.  A quenched plane
-// costs registers in every step: at most 512 threads then, so the compiler
-// may use up to 128 registers.
-template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
+// class plane (DIS), or the p-class and q-class planes (DIS and PQ).  Two
+// lanes (MODEL 1): planes A and B and, with turning sites (DIS), the turning
+// plane and the lane-change steps.  A quenched plane costs registers in
+// every step: at most 512 threads then, so the compiler may use up to 128
+// registers.
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2, bool PQ = false>
 __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long warp_tot[32];
@@ -458,8 +479,9 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
   const uint32_t W = a.geo.W, n_units = W / 8;
   uint32_t* lat = reinterpret_cast<uint32_t*>(smem_raw);  // NOCC planes
-  uint32_t* qp = lat + NOCC * W;                          // class or turning plane
-  uint32_t* carry = qp + (DIS ? W : 0u);                  // NOCC x n_units flags
+  constexpr uint32_t NQ = DIS ? (PQ ? 2u : 1u) : 0u;      // quenched planes
+  uint32_t* qp = lat + NOCC * W;                          // class (p, q classes) or turning plane
+  uint32_t* carry = qp + NQ * W;                          // NOCC x n_units flags
   const uint32_t sample = blockIdx.x;
   const uint32_t n_glob = a.geo.first_sample + sample;
   const uint64_t s0 = a.clock->sweep;
@@ -469,8 +491,8 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
   for (uint32_t i = threadIdx.x; i < NOCC * W; i += blockDim.x)
     lat[i] = a.state[static_cast<size_t>(sample) * NOCC * W + i];
   if (DIS)
-    for (uint32_t i = threadIdx.x; i < W; i += blockDim.x)
-      qp[i] = a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + i];
+    for (uint32_t i = threadIdx.x; i < NQ * W; i += blockDim.x)
+      qp[i] = a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * NQ * W + i];
   for (uint32_t i = threadIdx.x; i < NOCC * n_units; i += blockDim.x) carry[i] = 0u;
   __syncthreads();
 
@@ -479,10 +501,10 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
     const uint64_t s = s0 + it;
     if (MODEL == kRing) {
       for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-        sca_unit<DIS, COUNT, FAST2, 0>(lat, qp, carry, a, u, n_units, W, s, n_glob, kmax, cnt[0], cnt[1]);
+        sca_unit<DIS, COUNT, FAST2, 0, PQ>(lat, qp, carry, a, u, n_units, W, s, n_glob, kmax, cnt[0], cnt[1]);
       __syncthreads();
       for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-        sca_unit<DIS, COUNT, FAST2, 1>(lat, qp, carry, a, u, n_units, W, s, n_glob, kmax, cnt[0], cnt[1]);
+        sca_unit<DIS, COUNT, FAST2, 1, PQ>(lat, qp, carry, a, u, n_units, W, s, n_glob, kmax, cnt[0], cnt[1]);
       __syncthreads();
     } else {
       uint32_t* A = lat;
@@ -533,13 +555,13 @@ bool sca_fast2(const DomainLaunch& a) {
   return regular(a.rates.p) && regular(a.rates.q) && a.sca_kmax <= 2;
 }
 
-template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2, bool PQ = false>
 cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   (void)cudaGetLastError();
-  const cudaError_t e = cudaFuncSetAttribute(k_sca<MODEL, DIS, COUNT, FAST2>,
+  const cudaError_t e = cudaFuncSetAttribute(k_sca<MODEL, DIS, COUNT, FAST2, PQ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_sca<MODEL, DIS, COUNT, FAST2><<<a.geo.S, threads, smem, st>>>(a);
+  k_sca<MODEL, DIS, COUNT, FAST2, PQ><<<a.geo.S, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -560,11 +582,6 @@ cudaError_t launch_sca_t(const DomainLaunch& a, uint32_t threads, size_t smem, c
 // of unit u takes the lane changes of sites 256u + 1 .. 256(u + 1) and merges
 // them into the next unit's first words with its carry.
 constexpr uint32_t kScaStreamThreads = 256;
-
-__device__ __forceinline__ void load8(const uint32_t* p, uint32_t (&x)[8]) {
-  const uint4 v0 = reinterpret_cast<const uint4*>(p)[0], v1 = reinterpret_cast<const uint4*>(p)[1];
-  x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w; x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
-}
 
 // Write back a unit: all 8 words after an even phase; after an odd phase
 // words 1..7 plainly and word 0 as the XOR of the bits this thread changed
@@ -663,7 +680,7 @@ __global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream_lanes(const Do
 // first word atomically (that word receives the previous warp's carry).
 // A first word lane 0 prefetched may or may not hold that carry already:
 // bit 0 is not read by the odd phase.
-template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE>
+template <bool DIS, bool COUNT, bool FAST2, uint32_t PHASE, bool PQ = false>
 __global__ void __launch_bounds__(kScaStreamThreads, DIS ? 2 : 4) k_sca_stream_ring(const DomainLaunch a,
                                                                         uint32_t blocks_per_sample, uint32_t upt) {
   constexpr uint32_t T = kScaStreamThreads;
@@ -675,19 +692,23 @@ __global__ void __launch_bounds__(kScaStreamThreads, DIS ? 2 : 4) k_sca_stream_r
   const uint64_t s = a.clock->sweep;
   const uint32_t kmax = a.sca_kmax;
   uint32_t* lat = a.state + static_cast<size_t>(sample) * W;
-  const uint32_t* cls = DIS ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+  constexpr uint32_t NQ = DIS ? (PQ ? 2u : 1u) : 0u;  // p classes, then (PQ) q classes
+  const uint32_t* cls = DIS ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * NQ * W : nullptr;
   unsigned long long nr = 0ull, nl = 0ull;
   const uint32_t lane = threadIdx.x & 31u;
   // active lanes of the warp for unit u (lane `lane`): a prefix of the warp
   auto n_active = [&](uint32_t u) { return min(32u, n_units - (u - lane)); };
-  uint32_t px[8], pc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, pxn = 0u, pcn = 0u;  // the next unit's words
+  uint32_t px[8], pc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, pd[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  uint32_t pxn = 0u, pcn = 0u, pdn = 0u;  // the next unit's words
   auto fetch = [&](uint32_t u) {
     load8(lat + 8u * u, px);
     if (DIS) load8(cls + 8u * u, pc);
+    if (PQ) load8(cls + W + 8u * u, pd);
     if (PHASE && lane + 1 == n_active(u)) {  // the warp's last unit: the next unit's first words
       const uint32_t nw = (8u * u + 8u == W) ? 0u : 8u * u + 8u;
       pxn = lat[nw];  // only bit 0, which only this thread changes
       if (DIS) pcn = cls[nw];
+      if (PQ) pdn = cls[W + nw];
     }
   };
   if (u_first < n_units) fetch(u_first);
@@ -695,27 +716,31 @@ __global__ void __launch_bounds__(kScaStreamThreads, DIS ? 2 : 4) k_sca_stream_r
   for (uint32_t k = 0; k < upt; ++k) {
     const uint32_t u = u_first + k * T;
     if (u >= n_units) break;
-    uint32_t x[8], c[8];
+    uint32_t x[8], c[8], d[8];
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       x[w] = px[w];
       c[w] = pc[w];
+      d[w] = pd[w];
     }
-    uint32_t x_next = pxn, c_next = pcn;
+    uint32_t x_next = pxn, c_next = pcn, d_next = pdn;
     const uint32_t na = n_active(u);
     const unsigned act = na == 32u ? 0xffffffffu : (1u << na) - 1u;
     const bool last = lane + 1 == na;
     if (PHASE) {
       const uint32_t xs = __shfl_down_sync(act, x[0], 1);
       const uint32_t cs = DIS ? __shfl_down_sync(act, c[0], 1) : 0u;
+      const uint32_t ds = PQ ? __shfl_down_sync(act, d[0], 1) : 0u;
       if (!last) {
         x_next = xs;
         c_next = cs;
+        d_next = ds;
       }
     }
     if (k + 1 < upt && u + T < n_units) fetch(u + T);
     const uint32_t old0 = x[0];
-    const uint32_t out = sca_update<DIS, COUNT, FAST2, PHASE>(x, c, x_next, c_next, a, u, s, n_glob, kmax, nr, nl);
+    const uint32_t out = sca_update<DIS, COUNT, FAST2, PHASE, PQ>(x, c, d, x_next, c_next, d_next, a, u, s, n_glob,
+                                                                  kmax, nr, nl);
     uint32_t* p = lat + 8u * u;
     if (PHASE == 0) {
       reinterpret_cast<uint4*>(p)[0] = make_uint4(x[0], x[1], x[2], x[3]);
@@ -751,7 +776,7 @@ __global__ void __launch_bounds__(kScaStreamThreads, DIS ? 2 : 4) k_sca_stream_r
   }
 }
 
-template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2>
+template <uint32_t MODEL, bool DIS, bool COUNT, bool FAST2, bool PQ = false>
 cudaError_t launch_sca_stream_t(const DomainLaunch& a, cudaStream_t st) {
   const uint32_t n_units = a.geo.W / 8;
   (void)cudaGetLastError();
@@ -763,8 +788,8 @@ cudaError_t launch_sca_stream_t(const DomainLaunch& a, cudaStream_t st) {
     while (upt > 1 && units < static_cast<uint64_t>(upt) * kScaStreamThreads * 8u * 152u * 5u) upt >>= 1;
     const uint32_t per_block = kScaStreamThreads * upt;
     const uint32_t bps = (n_units + per_block - 1) / per_block;
-    k_sca_stream_ring<DIS, COUNT, FAST2, 0><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
-    k_sca_stream_ring<DIS, COUNT, FAST2, 1><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
+    k_sca_stream_ring<DIS, COUNT, FAST2, 0, PQ><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
+    k_sca_stream_ring<DIS, COUNT, FAST2, 1, PQ><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
   } else {
     const uint32_t bps = (n_units + kScaStreamThreads - 1) / kScaStreamThreads;
     k_sca_stream_lanes<DIS, 0><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
@@ -775,8 +800,8 @@ cudaError_t launch_sca_stream_t(const DomainLaunch& a, cudaStream_t st) {
 
 }  // namespace
 
-size_t sca_smem_bytes(uint32_t W, uint32_t planes, bool quenched) {
-  return static_cast<size_t>(W) * 4u * (planes + (quenched ? 1u : 0u)) + static_cast<size_t>(planes) * (W / 8u) * 4u;
+size_t sca_smem_bytes(uint32_t W, uint32_t planes, uint32_t quenched_planes) {
+  return static_cast<size_t>(W) * 4u * (planes + quenched_planes) + static_cast<size_t>(planes) * (W / 8u) * 4u;
 }
 
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
@@ -788,6 +813,9 @@ cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cud
   if (a.dis == kDisBimodal)
     return count ? launch_sca_t<kRing, true, true, false>(a, threads, smem, st)
                  : launch_sca_t<kRing, true, false, false>(a, threads, smem, st);
+  if (a.dis == kDisBimodalPQ)
+    return count ? launch_sca_t<kRing, true, true, false, true>(a, threads, smem, st)
+                 : launch_sca_t<kRing, true, false, false, true>(a, threads, smem, st);
   if (sca_fast2(a))
     return count ? launch_sca_t<kRing, false, true, true>(a, threads, smem, st)
                  : launch_sca_t<kRing, false, false, true>(a, threads, smem, st);
@@ -804,6 +832,9 @@ cudaError_t launch_sca_stream(const DomainLaunch& a, cudaStream_t st) {
   if (a.dis == kDisBimodal)
     return count ? launch_sca_stream_t<kRing, true, true, false>(a, st)
                  : launch_sca_stream_t<kRing, true, false, false>(a, st);
+  if (a.dis == kDisBimodalPQ)
+    return count ? launch_sca_stream_t<kRing, true, true, false, true>(a, st)
+                 : launch_sca_stream_t<kRing, true, false, false, true>(a, st);
   if (sca_fast2(a))
     return count ? launch_sca_stream_t<kRing, false, true, true>(a, st)
                  : launch_sca_stream_t<kRing, false, false, true>(a, st);

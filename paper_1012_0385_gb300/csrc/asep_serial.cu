@@ -32,17 +32,18 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
   if (sample >= a.geo.S) return;  // whole warps leave together
   const uint32_t L = static_cast<uint32_t>(a.geo.L), W = a.geo.W;
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
-  constexpr uint32_t NPL = NOCC + (DIS != kDisNone ? 1u : 0u);
+  constexpr uint32_t NQ = dis_planes(DIS);  // quenched planes (independent p, q classes: two)
+  constexpr uint32_t NPL = NOCC + NQ;
   uint32_t* gA = a.state + static_cast<size_t>(sample) * NOCC * W;
   const uint32_t* gM =
-      (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W : nullptr;
+      (DIS != kDisNone) ? a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * NQ * W : nullptr;
   uint32_t* A = gA;
   const uint32_t* M = gM;
   if (SMEM) {
     uint32_t* mine = serial_smem + static_cast<size_t>(wib) * NPL * W;
     for (uint32_t w = lane; w < NOCC * W; w += 32) mine[w] = gA[w];
     if (DIS != kDisNone)
-      for (uint32_t w = lane; w < W; w += 32) mine[NOCC * W + w] = gM[w];
+      for (uint32_t w = lane; w < NQ * W; w += 32) mine[NOCC * W + w] = gM[w];
     A = mine;
     M = mine + NOCC * W;
     __syncwarp();
@@ -80,9 +81,10 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
       uint32_t thr;
       if (MODEL == kTwoLane) {
         thr = pl == 0 ? (x == 1u ? a.rates.p : 0u) : (x == 2u ? a.rates.q : 0u);
-      } else if (DIS == kDisBimodal) {
+      } else if (DIS == kDisBimodal || DIS == kDisBimodalPQ) {
+        const uint32_t* Mq = DIS == kDisBimodalPQ ? M + W : M;  // the classes of left hops
         thr = x == 1u ? (((M[i >> 5] >> (i & 31u)) & 1u) ? a.rates.p_slow : a.rates.p)
-                      : (x == 2u ? (((M[i1 >> 5] >> (i1 & 31u)) & 1u) ? a.rates.q_slow : a.rates.q) : 0u);
+                      : (x == 2u ? (((Mq[i1 >> 5] >> (i1 & 31u)) & 1u) ? a.rates.q_slow : a.rates.q) : 0u);
       } else {
         thr = x == 1u ? a.rates.p : (x == 2u ? a.rates.q : 0u);
       }
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
 
 template <uint32_t MODEL, uint32_t DIS>
 cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
-  constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + (DIS != kDisNone ? 1u : 0u);
+  constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + dis_planes(DIS);
   const size_t per_sample = static_cast<size_t>(NPL) * a.geo.W * 4u;
   const size_t budget = 200u * 1024u;  // shared memory for the staged lattices of one block
   if (per_sample <= budget) {
@@ -237,6 +239,7 @@ cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
 cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st) {
   if (model == kRing && dis == kDisNone) return launch_serial_t<kRing, kDisNone>(a, st);
   if (model == kRing && dis == kDisBimodal) return launch_serial_t<kRing, kDisBimodal>(a, st);
+  if (model == kRing && dis == kDisBimodalPQ) return launch_serial_t<kRing, kDisBimodalPQ>(a, st);
   if (model == kTwoLane && dis == kDisNone) return launch_serial_t<kTwoLane, kDisNone>(a, st);
   if (model == kTwoLane && dis == kDisTurning) return launch_serial_t<kTwoLane, kDisTurning>(a, st);
   return cudaErrorInvalidValue;

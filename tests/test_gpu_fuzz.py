@@ -20,7 +20,12 @@ def draw(k: int):
     rng = np.random.default_rng(1000 + k)
     schedule = int(rng.choice([A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_SCA, A.ASEP_SCHED_SERIAL]))
     model = int(rng.integers(2))
-    dis = int(rng.choice([0, 2])) if model == 1 else int(rng.choice([0, 1]))
+    if model == 1:
+        dis = int(rng.choice([0, 2]))
+    elif schedule == A.ASEP_SCHED_DOMAIN:
+        dis = int(rng.choice([0, 1]))
+    else:  # independent p and q classes run under the SCA and serial schedules
+        dis = int(rng.choice([0, 1, 3]))
     if schedule == A.ASEP_SCHED_SERIAL:
         L = int(2 ** rng.integers(6, 12))
         kw = dict(schedule=schedule)
@@ -38,8 +43,8 @@ def draw(k: int):
         p = q = A.ASEP_ALWAYS  # the two-lane configuration's rate 1
     kw.update(model=model, L=L, n_realizations=n_real, samples_per_real=spr, p_thr=p, q_thr=q,
               seed=int(rng.integers(1, 2**40)), init_kind=int(rng.integers(2)), init_seed=int(rng.integers(1, 1000)))
-    if dis == 1:
-        kw.update(dis_kind=1, dis_a_thr=th(float(rng.choice([0.1, 0.5]))), dis_b_thr=int(rng.choice(RATES)),
+    if dis in (1, 3):
+        kw.update(dis_kind=dis, dis_a_thr=th(float(rng.choice([0.1, 0.5]))), dis_b_thr=int(rng.choice(RATES)),
                   dis_c_thr=int(rng.choice(RATES)), dis_seed=int(rng.integers(1, 1000)))
     elif dis == 2:
         kw.update(dis_kind=2, dis_a_thr=th(float(rng.choice([0.05, 0.3]))), dis_b_thr=th(float(rng.choice([0.1, 0.7]))),
@@ -138,6 +143,8 @@ def draw_streamed(k: int):
     D = int(rng.choice([32, 64, 128]))
     G = 2 * int(rng.integers(32, 151))
     kw = {x: v for x, v in kw.items() if x != "schedule"}
+    if kw.get("dis_kind") == A.ASEP_DIS_BIMODAL_PQ:  # the domain schedule takes one class plane
+        kw["dis_kind"] = A.ASEP_DIS_BIMODAL
     kw.update(L=2 * D * G, domain_sites=D, samples_per_real=min(kw["samples_per_real"], 2))
     return kw, chunks, times
 

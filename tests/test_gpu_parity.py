@@ -96,6 +96,7 @@ def assert_same(g, ref, P, times):
 RING = A.ASEP_MODEL_RING
 TWO = A.ASEP_MODEL_TWO_LANE
 SCA = A.ASEP_SCHED_SCA
+PQ = A.ASEP_DIS_BIMODAL_PQ
 CASES = {
     # several CTAs (16 samples each) with a ragged last CTA
     "ring_asep_ragged": (dict(L=4096, domain_sites=256, samples_per_real=20, p_thr=th(0.75), q_thr=th(0.25),
@@ -213,6 +214,25 @@ CASES = {
     "sca_stream_two_lane_plain": (dict(model=TWO, L=2048, schedule=SCA, samples_per_real=5, init_kind=1,
                                        init_seed=2, p_thr=th(0.7), q_thr=th(0.4), seed=12, plan=(32, 0)), 25,
                                   [0, 12, 25]),
+    # independent p and q classes (the paper's separate tag bits; Q-SSEP): resident and streamed SCA, serial
+    "sca_bimodal_pq": (dict(L=1 << 14, schedule=SCA, n_realizations=2, samples_per_real=2, p_thr=th(0.5),
+                            q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1), dis_c_thr=th(0.1),
+                            dis_seed=44, seed=45, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=6),
+                       30, [0, 6, 30]),
+    "sca_bimodal_pq_twenty_bit": (dict(L=4096, schedule=SCA, n_realizations=3, samples_per_real=1, p_thr=th(0.6),
+                                       q_thr=th(0.3), dis_kind=PQ, dis_a_thr=th(0.3), dis_b_thr=th(0.15),
+                                       dis_c_thr=A.ASEP_ALWAYS, dis_seed=46, seed=47), 25, [0, 25]),
+    "sca_stream_bimodal_pq": (dict(L=256 * 2085, schedule=SCA, n_realizations=2, samples_per_real=1,
+                                   p_thr=th(0.5), q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5),
+                                   dis_b_thr=th(0.1), dis_c_thr=th(0.1), dis_seed=48, seed=49, plan=(32, 0)), 6,
+                              [0, 3, 6]),
+    # two quenched planes do not fit one CTA's shared memory at 2^20 sites: streamed by itself
+    "sca_bimodal_pq_beyond_smem": (dict(L=1 << 20, schedule=SCA, samples_per_real=1, p_thr=th(0.5),
+                                        q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1),
+                                        dis_c_thr=th(0.1), dis_seed=50, seed=51), 3, [0, 3]),
+    "serial_bimodal_pq": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
+                               p_thr=th(0.5), q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1),
+                               dis_c_thr=th(0.1), dis_seed=52, seed=53), 12, [0, 12]),
     # many blocks of unit threads, the last one ragged (2085 units, 1025 units), so carries and lane-change
     # sites cross block boundaries; 16680 words per lattice: records in two chunks (16384 + 296 words)
     "sca_stream_ring_nine_blocks": (dict(L=256 * 2085, schedule=SCA, n_realizations=2, samples_per_real=1,

@@ -396,7 +396,8 @@ def other_workloads():
     sweeps, snapshots every 100), quenched bimodal disorder and the two-lane
     model with turning sites (10^4-sweep windows of their 10^7 / 10^6 sweep
     runs, log-spaced sample times, two-lane currents, profile and
-    autocorrelation on), the latter also under the paper's two-lane SCA; and
+    autocorrelation on), the latter also under the paper's two-lane SCA; the
+    paper's quenched SSEP (independent slow classes for both directions); and
     the two streamed modes (domain schedule and SCA) on rings far beyond
     shared memory."""
     import torch
@@ -430,6 +431,11 @@ def other_workloads():
               p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1),
               dis_seed=3, init_kind=A.ASEP_INIT_BERNOULLI_HALF, init_seed=4, seed=1,
               flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=t0), lt, 2),
+        ("Q-SSEP (the paper's quenched SSEP, SCA schedule, its p=0.8): L=2^16, p=q=0.8, independent slow classes "
+         "for right and left hops (Q=0.5 each, r=0.2), 256 realizations, 10^4-MCS window, log times",
+         dict(L=1 << 16, schedule=A.ASEP_SCHED_SCA, n_realizations=256, samples_per_real=1, p_thr=th(0.8),
+              q_thr=th(0.8), dis_kind=A.ASEP_DIS_BIMODAL_PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.16),
+              dis_c_thr=th(0.16), dis_seed=2, seed=1), lt, 1),
         ("streamed tier: L=2^24 rings (beyond a 16-CTA cluster; lattice in HBM, tiles through shared memory), "
          "ASEP p=0.75 q=0.25, 16 samples, 200-MCS window",
          dict(L=1 << 24, domain_sites=256, samples_per_real=16, p_thr=th(0.75), q_thr=th(0.25), seed=1,

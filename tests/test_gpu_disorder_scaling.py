@@ -6,8 +6,10 @@ Q-SSEP: forward and backward hops both present, each site slow for right hops
 with probability Q = 0.5 and, independently, slow for left hops with the same
 probability (the paper's separate tag bits), slow rate r p with r = 0.2.  The
 paper finds activated growth W ~ (ln t)^beta~ with beta~ = 2.85(30) and a
-saturated width scaling with alpha = 1.  Statistical tests: 128-256 disorder
-realizations, a few seconds each on a GB300."""
+saturated width scaling with alpha = 1.  Q-TASEP (q = 0, Q = 0.5; the paper
+does not print its r, 0.2 here): saturated width with alpha = 1.
+Statistical tests: 128-256 disorder realizations, a few seconds each on a
+GB300."""
 import json
 import os
 
@@ -79,3 +81,20 @@ def test_qssep_saturated_width_scales_with_alpha_one():
     _, b1 = qssep_width2(512, 400_000, 256, dis_kind=A.ASEP_DIS_BIMODAL)
     alpha1 = 0.5 * np.log2(b1[-6:].mean() / a1[-6:].mean())
     assert abs(alpha1 - 0.5) < 0.15, alpha1
+
+
+def test_qtasep_saturated_width_scales_with_alpha_one():
+    """Q-TASEP (columnar-disorder KPZ) at L = 256 and 512, saturated: alpha
+    within 0.15 of the paper's alpha = 1 (clean KPZ has 1/2)."""
+    g = GOLDEN["qtasep_exponents"]
+    w = []
+    for L in (256, 512):
+        times = log_times(400_000)
+        prm = A.make_params(L=L, schedule=A.ASEP_SCHED_SCA, n_realizations=256, samples_per_real=1, p_thr=th(0.8),
+                            q_thr=0, dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.5), dis_b_thr=th(0.16),
+                            dis_seed=3, seed=5, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
+        with A.asep_create(prm, sample_times=times) as ctx:
+            A.asep_sweep(ctx, 400_000)
+            w.append(A.asep_width(ctx)[2][-10:, :, 0].mean())
+    alpha = 0.5 * np.log2(w[1] / w[0])
+    assert abs(alpha - g["alpha"]) < 0.15, alpha

@@ -280,8 +280,20 @@ int asep_get_info(const asep_ctx* ctx, asep_info* info);
  * device.  Takes effect for the next launch. */
 int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group);
 
-/* Wait for all work of the context. */
+/* Wait for all work of the context.  ASEP_ERR_TIMEOUT: a streamed tile's
+ * wait for its bulk copy ran out (after one second); the results since are
+ * invalid and every later call reports it until asep_reset or
+ * asep_load_state replaces the lattice. */
 int asep_sync(asep_ctx* ctx);
+
+/* Fault injection for tests of the timeout path (default ASEP_FAULT_NONE).
+ * ASEP_FAULT_COPY_STALL: the streamed domain tier's tile copies announce 16
+ * bytes more than they carry, so the bounded wait for them runs out and the
+ * sweep reports ASEP_ERR_TIMEOUT at the next synchronising call; nothing
+ * faults or hangs.  Takes effect for the next launch. */
+#define ASEP_FAULT_NONE 0u
+#define ASEP_FAULT_COPY_STALL 1u
+int asep_inject_fault(asep_ctx* ctx, uint32_t fault);
 
 /* Free everything the context owns.  NULL-safe; synchronises first. */
 int asep_destroy(asep_ctx* ctx);

@@ -32,6 +32,7 @@ ASEP_SCHED_DOMAIN, ASEP_SCHED_SERIAL, ASEP_SCHED_SCA = 0, 1, 2
 ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING, ASEP_DIS_BIMODAL_PQ = 0, 1, 2, 3
 ASEP_INIT_FLAT_ALT, ASEP_INIT_BERNOULLI_HALF = 0, 1
 ASEP_ALWAYS = 0xFFFFFFFF
+ASEP_FAULT_NONE, ASEP_FAULT_COPY_STALL = 0, 1
 ASEP_FLAG_NO_HOP_COUNTS = 1
 ASEP_FLAG_PROFILE = 2
 ASEP_FLAG_AUTOCORR = 4
@@ -94,7 +95,7 @@ EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_
             "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
             "asep_batch_sweep_static", "asep_set_plan", "asep_currents", "asep_profile", "asep_autocorr",
-            "asep_height_offset")
+            "asep_height_offset", "asep_inject_fault")
 
 
 class AsepError(RuntimeError):
@@ -128,6 +129,7 @@ def lib():
             L.asep_disorder.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_size_t]
             L.asep_get_info.argtypes = [vp, P(asep_info)]
             L.asep_sync.argtypes = [vp]
+            L.asep_inject_fault.argtypes = [vp, ctypes.c_uint32]
             L.asep_destroy.argtypes = [vp]
             L.asep_last_error.argtypes = [vp]
             L.asep_last_error.restype = ctypes.c_char_p
@@ -318,6 +320,11 @@ def asep_get_info(ctx) -> dict:
     info = asep_info()
     _check(lib().asep_get_info(_h(ctx), ctypes.byref(info)), _h(ctx))
     return {f: getattr(info, f) for f, _ in asep_info._fields_}
+
+
+def asep_inject_fault(ctx, fault: int) -> None:
+    """Fault injection for tests of the timeout path (ASEP_FAULT_*)."""
+    _check(lib().asep_inject_fault(_h(ctx), int(fault)), _h(ctx))
 
 
 def asep_set_plan(ctx, cluster: int = 0, samples_per_group: int = 0) -> None:

@@ -59,6 +59,7 @@ struct asep_ctx {
   uint32_t cluster = 1, Gc = 0;  // cluster tier: CTAs per sample, columns per CTA (kStreamTier: streamed)
   uint32_t tiles = 0;             // streamed tier: tiles per sample
   uint32_t* d_err = nullptr;      // device flag: a streamed tile's copy wait gave up
+  uint32_t fault = ASEP_FAULT_NONE;  // injected fault (asep_inject_fault)
   size_t smem = 0;
   uint32_t max_sweeps_per_launch = 1;
   uint64_t launches = 0;
@@ -397,6 +398,16 @@ int copy_out(asep_ctx* ctx, void* dst, const void* src, size_t bytes, const char
 
 // Heights and hop counters of the current lattice as the reference of
 // asep_height_offset (a record into the reference tables, no observables).
+// Forget a streamed tile's copy timeout (for a call that replaces the
+// lattice): wait for the context's work, then clear the device flag.
+int clear_timeout(asep_ctx* ctx) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  if (ctx->d_err && (e = cudaMemset(ctx->d_err, 0, 16)) != cudaSuccess) return cuda_fail(ctx, e, "clear error flag");
+  ctx->err_seen = 0;
+  return ASEP_OK;
+}
+
 int record_reference(asep_ctx* ctx) {
   HeightsLaunch h;
   h.geo = geometry(ctx);
@@ -695,7 +706,8 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster == kStreamTier) {
       // one sweep per step: both phases, lane changes, the record, the clock
       n = 1;
-      e = launch_stream_sweep(domain_desc(ctx, 1), ctx->tiles, ctx->threads, ctx->smem, ctx->d_err, ctx->stream);
+      e = launch_stream_sweep(domain_desc(ctx, 1), ctx->tiles, ctx->threads, ctx->smem, ctx->d_err,
+                              ctx->fault == ASEP_FAULT_COPY_STALL ? 16u : 0u, ctx->stream);
       if (e == cudaSuccess && ctx->next_time < ctx->times.size() && ctx->times[ctx->next_time] == ctx->sweep + 1) {
         const int rc = record_now(ctx, ctx->next_time);
         if (rc != ASEP_OK) return rc;
@@ -749,6 +761,8 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
 
 int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
   if (!ctx) return ASEP_ERR_INVALID;
+  const int rct = clear_timeout(ctx);  // a new initial state replaces results a timed-out sweep invalidated
+  if (rct != ASEP_OK) return rct;
   ctx->p.seed = seed;
   ctx->p.init_seed = init_seed;
   const size_t n_times = std::max<size_t>(1, ctx->times.size());
@@ -777,6 +791,13 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
     next = 1;
   }
   return set_clock(ctx, 0, next);
+}
+
+int asep_inject_fault(asep_ctx* ctx, uint32_t fault) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  if (fault > ASEP_FAULT_COPY_STALL) return fail(ctx, ASEP_ERR_INVALID, "unknown fault %u", fault);
+  ctx->fault = fault;
+  return ASEP_OK;
 }
 
 int asep_sync(asep_ctx* ctx) {
@@ -844,7 +865,7 @@ int asep_load_state(asep_ctx* ctx, const uint32_t* words, size_t n_words, uint64
   const size_t need = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
   if (n_words < need) return fail(ctx, ASEP_ERR_INVALID, "n_words = %zu < %zu", n_words, need);
   if (sweep >= (1ull << 40)) return fail(ctx, ASEP_ERR_INVALID, "sweep index >= 2^40");
-  int rc = asep_sync(ctx);
+  int rc = clear_timeout(ctx);  // the loaded state replaces results a timed-out sweep invalidated
   if (rc != ASEP_OK) return rc;
   const cudaError_t e = cudaMemcpy(ctx->d_state, words, need * 4, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "load state");

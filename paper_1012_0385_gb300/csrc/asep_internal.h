@@ -196,8 +196,10 @@ cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem,
 // columns through shared memory); plan code kStreamTier in `cluster`.
 constexpr uint32_t kStreamTier = 32;
 size_t stream_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t C, uint32_t ptab_n);
+// err: set when a tile's copy wait runs out (bounded to one second); stall:
+// extra bytes each tile's copies announce (0; fault injection for tests).
 cudaError_t launch_stream_sweep(const DomainLaunch& a, uint32_t tiles, uint32_t threads, size_t smem, uint32_t* err,
-                                cudaStream_t st);
+                                uint32_t stall, cudaStream_t st);
 // The two-sub-lattice SCA schedule: one CTA per sample, ring in shared memory.
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
 // Streamed SCA: one sweep (both phases; two lanes: with the lane changes)

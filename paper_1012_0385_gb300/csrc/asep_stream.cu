@@ -24,7 +24,14 @@
 namespace asep {
 namespace {
 
-constexpr uint32_t kWaitSpins = 1u << 24;  // bound of the mbarrier wait (a copy of < 1 MB takes far fewer)
+constexpr uint32_t kWaitSpins = 1u << 24;        // poll bound of the mbarrier wait (a backstop)
+constexpr uint64_t kWaitNs = 1000000000ull;      // wall-clock bound: a copy of < 1 MB takes microseconds
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -53,6 +60,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Wait for the phase with the given parity to complete, for at most one
+// second (and kWaitSpins polls); false when it did not.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kWaitSpins; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
 // Global -> shared bulk copy of `bytes` (both addresses 16-byte aligned,
 // bytes a multiple of 16), completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -63,8 +82,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // One phase of one tile.  Grid: tiles x S CTAs, blockIdx.x = sample * tiles + tile.
+// stall: bytes the tile's copies announce beyond what they carry (0; a test
+// of the timeout path sets it, so that the wait for them runs out).
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t PHASE>
-__global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t tiles, uint32_t* err) {
+__global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t tiles, uint32_t* err,
+                                                 uint32_t stall) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
@@ -94,7 +116,7 @@ __global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t 
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, NP * n_al * 4u);
+    mbar_expect_tx(&bar, NP * n_al * 4u + stall);
     for (uint32_t p = 0; p < NP; ++p) {
       const uint32_t* base = p < NOCC ? a.state + (static_cast<size_t>(sample) * NOCC + p) * W
                                       : a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W;
@@ -103,12 +125,10 @@ __global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t 
     }
   }
   for (uint32_t i = threadIdx.x; i < a.ptab_n; i += blockDim.x) tab[i] = a.ptab[i];
-  bool done = false;
-  for (uint32_t i = 0; i < kWaitSpins && !done; ++i) done = mbar_try_wait(&bar, 0);
+  const bool done = mbar_wait_bounded(&bar, 0);
   if (__syncthreads_or(!done)) {  // copies did not complete: report, let them land, give up
     if (threadIdx.x == 0) atomicExch(err, 1u);
-    for (uint32_t i = 0; i < kWaitSpins && !mbar_try_wait(&bar, 0); ++i) {
-    }
+    (void)mbar_wait_bounded(&bar, 0);
     return;
   }
 
@@ -233,21 +253,21 @@ __global__ void k_stream_turn(const DomainLaunch a) {
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t PHASE>
 cudaError_t launch_stream_t(const DomainLaunch& a, uint32_t tiles, uint32_t threads, size_t smem, uint32_t* err,
-                            cudaStream_t st) {
+                            uint32_t stall, cudaStream_t st) {
   (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(k_stream<MODEL, DIS, COUNT, PHASE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  k_stream<MODEL, DIS, COUNT, PHASE><<<tiles * a.geo.S, threads, smem, st>>>(a, tiles, err);
+  k_stream<MODEL, DIS, COUNT, PHASE><<<tiles * a.geo.S, threads, smem, st>>>(a, tiles, err, stall);
   return cudaGetLastError();
 }
 
 template <uint32_t MODEL, uint32_t DIS, bool COUNT>
 cudaError_t launch_stream_phases(const DomainLaunch& a, uint32_t tiles, uint32_t threads, size_t smem, uint32_t* err,
-                                 cudaStream_t st) {
-  cudaError_t e = launch_stream_t<MODEL, DIS, COUNT, 0>(a, tiles, threads, smem, err, st);
+                                 uint32_t stall, cudaStream_t st) {
+  cudaError_t e = launch_stream_t<MODEL, DIS, COUNT, 0>(a, tiles, threads, smem, err, stall, st);
   if (e != cudaSuccess) return e;
-  e = launch_stream_t<MODEL, DIS, COUNT, 1>(a, tiles, threads, smem, err, st);
+  e = launch_stream_t<MODEL, DIS, COUNT, 1>(a, tiles, threads, smem, err, stall, st);
   if (e != cudaSuccess) return e;
   if (MODEL == kTwoLane && DIS == kDisTurning) {
     const size_t total = static_cast<size_t>(a.geo.S) * a.geo.W;
@@ -269,17 +289,17 @@ size_t stream_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t C, 
 // One sweep of the streamed tier (both phases and, for two lanes with
 // turning sites, the lane changes) at the sweep index held by a.clock.
 cudaError_t launch_stream_sweep(const DomainLaunch& a, uint32_t tiles, uint32_t threads, size_t smem, uint32_t* err,
-                                cudaStream_t st) {
+                                uint32_t stall, cudaStream_t st) {
   const bool count = a.count_hops != 0;
   if (a.model == kTwoLane) {
-    return a.dis == kDisTurning ? launch_stream_phases<kTwoLane, kDisTurning, true>(a, tiles, threads, smem, err, st)
-                                : launch_stream_phases<kTwoLane, kDisNone, true>(a, tiles, threads, smem, err, st);
+    return a.dis == kDisTurning ? launch_stream_phases<kTwoLane, kDisTurning, true>(a, tiles, threads, smem, err, stall, st)
+                                : launch_stream_phases<kTwoLane, kDisNone, true>(a, tiles, threads, smem, err, stall, st);
   }
   if (a.dis == kDisBimodal)
-    return count ? launch_stream_phases<kRing, kDisBimodal, true>(a, tiles, threads, smem, err, st)
-                 : launch_stream_phases<kRing, kDisBimodal, false>(a, tiles, threads, smem, err, st);
-  return count ? launch_stream_phases<kRing, kDisNone, true>(a, tiles, threads, smem, err, st)
-               : launch_stream_phases<kRing, kDisNone, false>(a, tiles, threads, smem, err, st);
+    return count ? launch_stream_phases<kRing, kDisBimodal, true>(a, tiles, threads, smem, err, stall, st)
+                 : launch_stream_phases<kRing, kDisBimodal, false>(a, tiles, threads, smem, err, stall, st);
+  return count ? launch_stream_phases<kRing, kDisNone, true>(a, tiles, threads, smem, err, stall, st)
+               : launch_stream_phases<kRing, kDisNone, false>(a, tiles, threads, smem, err, stall, st);
 }
 
 }  // namespace asep

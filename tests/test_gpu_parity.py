@@ -594,6 +594,48 @@ def test_streamed_sca_units_per_thread_do_not_change_results():
         assert np.array_equal(runs[S]["sh"][:, 0], runs[1]["sh"][:, 0]), S
 
 
+def test_streamed_copy_wait_runs_out_and_the_context_recovers():
+    """Fault injection on the streamed tier: each tile's copies announce 16
+    bytes more than they carry, so the kernels' wait for them runs out after
+    its one-second bound; the host reports ASEP_ERR_TIMEOUT (and keeps
+    reporting it), the GPU stays usable, and loading a state clears it --
+    the sweeps after that are bit-exact again."""
+    import time
+
+    kw = dict(L=1 << 16, domain_sites=256, samples_per_real=1, p_thr=th(0.75), q_thr=th(0.25), seed=81)
+    ref = run_gpu(dict(kw, plan=(32, 0)), [3], [0, 3])
+    with A.asep_create(A.make_params(**kw), sample_times=[0, 3]) as ctx:
+        A.asep_set_plan(ctx, 32, 0)
+        start, _ = A.asep_state(ctx)
+        A.asep_inject_fault(ctx, A.ASEP_FAULT_COPY_STALL)
+        t0 = time.time()
+        A.asep_sweep(ctx, 1)
+        with pytest.raises(A.AsepError) as ei:
+            A.asep_sync(ctx)
+        assert ei.value.code == A.ASEP_ERR_TIMEOUT
+        assert time.time() - t0 < 30  # two launches, each bounded by the one-second wait (twice)
+        with pytest.raises(A.AsepError) as ei:
+            A.asep_counters(ctx)
+        assert ei.value.code == A.ASEP_ERR_TIMEOUT
+        A.asep_inject_fault(ctx, A.ASEP_FAULT_NONE)
+        A.asep_load_state(ctx, start, 0)
+        A.asep_sweep(ctx, 3)
+        words, sweep = A.asep_state(ctx)
+        assert sweep == 3 and np.array_equal(words, ref["words"])
+        with pytest.raises(A.AsepError):
+            A.asep_inject_fault(ctx, 7)
+    x = torch_probe_ok()
+    assert x
+
+
+def torch_probe_ok() -> bool:
+    """A plain device computation after the timeout test: the GPU answers."""
+    import torch
+
+    y = torch.arange(1024, device="cuda", dtype=torch.int64).sum().item()
+    return y == 1023 * 1024 // 2
+
+
 def test_streamed_tier_is_chosen_beyond_a_cluster():
     with A.asep_create(A.make_params(L=1 << 24, domain_sites=256, samples_per_real=1), sample_times=[]) as ctx:
         info = A.asep_get_info(ctx)

@@ -303,17 +303,13 @@ __device__ __forceinline__ void turning(uint32_t* cur, const DomainLaunch& a, ui
   for (uint32_t r = 0; r < a.R2; ++r) {
     const uint32_t idx = r * a.Cp + ln.c;
     uint32_t av = A[idx], bv = B[idx];
-    uint32_t e = M[idx] & (av ^ bv), g_prev = 0xFFFFFFFFu;
-    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t e = M[idx] & (av ^ bv);
     while (e) {
       const uint32_t b = __ffs(e) - 1;
       e &= e - 1;
       uint64_t site = static_cast<uint64_t>(R_cur) + 32ull * (ln.g * a.R2 + r) + b;
       if (site >= L) site -= L;
-      if (static_cast<uint32_t>(site >> 2) != g_prev) {  // one call serves four consecutive sites
-        g_prev = static_cast<uint32_t>(site >> 2);
-        x = philox10(ctr_of(s, kTagTurn, 0, ln.n_glob, g_prev), key);
-      }
+      const uint4 x = philox10(ctr_of(s, kTagTurn, 0, ln.n_glob, static_cast<uint32_t>(site >> 2)), key);
       if (accept(pick(x, static_cast<uint32_t>(site & 3u)), a.rates.omega)) {
         const uint32_t bit = 1u << b;
         if (av & bit) ++cnt.c;

@@ -342,16 +342,12 @@ __device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, 
 template <uint32_t STEP>
 __device__ __forceinline__ uint32_t sca_turn_word(uint32_t sel, uint32_t word, const DomainLaunch& a, uint64_t s,
                                                   uint32_t n_glob, unsigned long long& moves) {
-  uint32_t f = 0u, g_prev = 0xFFFFFFFFu;
-  uint4 r = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t f = 0u;
   while (sel) {
     const uint32_t b = static_cast<uint32_t>(__ffs(sel)) - 1u;
     sel &= sel - 1u;
     const uint32_t site = 32u * word + b;
-    if ((site >> 2) != g_prev) {  // one call serves four consecutive sites
-      g_prev = site >> 2;
-      r = philox10(ctr_of(s, kTagScaTurn, STEP, n_glob, g_prev), a.ks);
-    }
+    const uint4 r = philox10(ctr_of(s, kTagScaTurn, STEP, n_glob, site >> 2), a.ks);
     if (accept(pick(r, site & 3u), a.rates.omega)) {
       f |= 1u << b;
       ++moves;

@@ -112,16 +112,12 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
     if (MODEL == kTwoLane && DIS == kDisTurning) {
       // lane changes: every event touches only (A_i, B_i); words are split over the lanes
       for (uint32_t w = lane; w < W; w += 32) {
-        uint32_t e = M[w] & (A[w] ^ B[w]), g_prev = 0xFFFFFFFFu;
-        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t e = M[w] & (A[w] ^ B[w]);
         while (e) {
           const uint32_t bit = __ffs(e) - 1;
           e &= e - 1;
           const uint32_t site = 32u * w + bit;
-          if ((site >> 2) != g_prev) {  // one call serves four consecutive sites
-            g_prev = site >> 2;
-            r = philox10(ctr_of(s, kTagTurn, 0, n_glob, g_prev), key);
-          }
+          const uint4 r = philox10(ctr_of(s, kTagTurn, 0, n_glob, site >> 2), key);
           if (accept(pick(r, site & 3u), a.rates.omega)) {
             if (A[w] & (1u << bit)) ++c2;
             else ++c3;

@@ -230,16 +230,12 @@ __global__ void k_stream_turn(const DomainLaunch a) {
     uint32_t e = m & (av ^ bv);
     if (!e) continue;
     const uint32_t n_glob = a.geo.first_sample + sample;
-    uint32_t ab = 0, ba = 0, g_prev = 0xFFFFFFFFu;
-    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t ab = 0, ba = 0;
     while (e) {
       const uint32_t b = __ffs(e) - 1;
       e &= e - 1;
       const uint32_t site = 32u * w + b;
-      if ((site >> 2) != g_prev) {  // one call serves four consecutive sites
-        g_prev = site >> 2;
-        x = philox10(ctr_of(s, kTagTurn, 0, n_glob, g_prev), key);
-      }
+      const uint4 x = philox10(ctr_of(s, kTagTurn, 0, n_glob, site >> 2), key);
       if (accept(pick(x, site & 3u), a.rates.omega)) {
         if (av & (1u << b)) ++ab;
         else ++ba;

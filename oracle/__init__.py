@@ -42,7 +42,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
 MODEL_RING, MODEL_TWO_LANE = 0, 1
 SCHED_DOMAIN, SCHED_SERIAL, SCHED_SCA = 0, 1, 2
-DIS_NONE, DIS_BIMODAL, DIS_TURNING, DIS_BIMODAL_PQ = 0, 1, 2, 3
+DIS_NONE, DIS_BIMODAL, DIS_TURNING, DIS_BIMODAL_PQ, DIS_CROSSING = 0, 1, 2, 3, 4
 INIT_FLAT_ALT, INIT_BERNOULLI_HALF = 0, 1
 ALWAYS = 0xFFFFFFFF
 
@@ -278,11 +278,12 @@ def init_state(P: Params) -> np.ndarray:
 
 def disorder(P: Params) -> np.ndarray | None:
     """Quenched planes, shape [R, planes * L/32] (planes = 2 for independent
-    p and q classes, else 1: a realization's planes one after the other), or
-    None when there is no disorder."""
+    p and q classes and for the two lanes' u and v crossing classes, else 1: a
+    realization's planes one after the other), or None when there is no
+    disorder."""
     if P.dis_kind == DIS_NONE:
         return None
-    n = P.W * (2 if P.dis_kind == DIS_BIMODAL_PQ else 1)
+    n = P.W * (2 if P.dis_kind in (DIS_BIMODAL_PQ, DIS_CROSSING) else 1)
     m = np.zeros((P.n_realizations, n), dtype=np.uint32)
     cp = P.c()
     first_real = P.first_sample // P.samples_per_real

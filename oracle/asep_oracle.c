@@ -74,6 +74,7 @@
 #define DIS_BIMODAL 1u
 #define DIS_TURNING 2u
 #define DIS_BIMODAL_PQ 3u /* independent slow classes for right (p) and left (q) hops */
+#define DIS_CROSSING 4u   /* two lanes: crossing at every site, u_i (A->B) and v_i (B->A) bimodal */
 #define INIT_FLAT_ALT 0u
 #define INIT_BERNOULLI_HALF 1u
 
@@ -197,6 +198,24 @@ static uint32_t rate_q(const orc_params* P, const uint32_t* cls, uint64_t i) {
   return P->q_thr;
 }
 
+/* Two lanes: may a particle change lanes at site i, and with which
+ * probability, A -> B (dir 0) or B -> A (dir 1)?  TURNING: only at turning
+ * sites, with omega (dis_b_thr) both ways.  CROSSING (sec. 3: crossing
+ * probabilities u_i, v_i, quenched with the distribution of Eq. bimodal, the
+ * reduced value at sites marked by separate bits for u and v): every site;
+ * u_i from plane 0, v_i from plane 1 of the realization, dis_b_thr unmarked,
+ * dis_c_thr marked. */
+static int crosses(const orc_params* P, const uint32_t* turn, uint64_t i) {
+  return P->dis_kind == DIS_CROSSING ? 1 : get_site(turn, i);
+}
+static uint32_t cross_thr(const orc_params* P, const uint32_t* turn, uint64_t i, uint32_t dir) {
+  if (P->dis_kind == DIS_CROSSING && get_site(turn + dir * ((P->L + 31) / 32), i)) return P->dis_c_thr;
+  return P->dis_b_thr;
+}
+static int lane_changes_on(const orc_params* P) {
+  return P->dis_kind == DIS_TURNING || P->dis_kind == DIS_CROSSING;
+}
+
 /* One attempt on ring bond (i, i+1): 10 -> 01 with p_i, 01 -> 10 with q_{i+1}. */
 static void ring_attempt(const orc_params* P, uint32_t* w, const uint32_t* cls, uint64_t i, uint32_t r,
                          uint64_t* cnt) {
@@ -247,12 +266,12 @@ static void turning_pass(const orc_params* P, uint32_t* wa, uint32_t* wb, const 
                          uint64_t sweep, uint64_t* cnt) {
   stream_t st;
   for (uint64_t i = 0; i < P->L; i++) {
-    if (!get_site(turn, i)) continue;
+    if (!crosses(P, turn, i)) continue;
     int a = get_site(wa, i), b = get_site(wb, i);
     if (a == b) continue;
     stream_open(&st, P->seed, sweep, TAG_TURN, sample, (uint32_t)(i >> 2), 0);
     uint32_t r = stream_word(&st, i & 3);
-    if (accept(r, P->dis_b_thr)) {
+    if (accept(r, cross_thr(P, turn, i, a ? 0u : 1u))) {
       flip_site(wa, i);
       flip_site(wb, i);
       if (a) cnt[2]++;
@@ -313,7 +332,7 @@ static void domain_sweep(const orc_params* P, const uint32_t* ptab, uint32_t pta
       }
     }
   }
-  if (two_lane && P->dis_kind == DIS_TURNING) turning_pass(P, wa, wb, mask, sample, sweep, cnt);
+  if (two_lane && lane_changes_on(P)) turning_pass(P, wa, wb, mask, sample, sweep, cnt);
 }
 
 /* The paper's GPU schedule (sec. 2.1, Fig. "parasep"): a two-sub-lattice
@@ -362,7 +381,7 @@ static void sca_sweep(const orc_params* P, uint32_t* words, const uint32_t* mask
         }
       }
     }
-    if (two_lane && P->dis_kind == DIS_TURNING) sca_lane_changes(P, wa, wb, mask, sample, sweep, phase, cnt);
+    if (two_lane && lane_changes_on(P)) sca_lane_changes(P, wa, wb, mask, sample, sweep, phase, cnt);
   }
 }
 
@@ -377,9 +396,9 @@ static void sca_lane_changes(const orc_params* P, uint32_t* wa, uint32_t* wb, co
   uint32_t* dst = step == 0 ? wb : wa;
   stream_t st;
   for (uint64_t i = 0; i < P->L; i++) {
-    if (!get_site(turn, i) || !get_site(src, i) || get_site(dst, i)) continue;
+    if (!crosses(P, turn, i) || !get_site(src, i) || get_site(dst, i)) continue;
     stream_open(&st, P->seed, sweep, TAG_SCA_TURN, sample, (uint32_t)(i >> 2), 0);
-    if (accept(stream_word(&st, 4 * (uint64_t)step + (i & 3)), P->dis_b_thr)) {
+    if (accept(stream_word(&st, 4 * (uint64_t)step + (i & 3)), cross_thr(P, turn, i, step))) {
       flip_site(src, i);
       flip_site(dst, i);
       cnt[step == 0 ? 2 : 3]++;
@@ -408,7 +427,7 @@ static void serial_sweep(const orc_params* P, uint32_t* words, const uint32_t* m
       lane_attempt(P, wa, wb, (int)(j >> logL), j & (L - 1), ru, cnt);
     }
   }
-  if (two_lane && P->dis_kind == DIS_TURNING) turning_pass(P, wa, wb, mask, sample, sweep, cnt);
+  if (two_lane && lane_changes_on(P)) turning_pass(P, wa, wb, mask, sample, sweep, cnt);
 }
 
 /* The oracle accepts tiny rings (exact-enumeration tests use L <= 12);
@@ -484,11 +503,13 @@ int orc_init(const orc_params* P, uint32_t* words, uint32_t sample) {
  * i is slow (probability Q = dis_a_thr, Eq. bimodal).  BIMODAL_PQ: plane 0
  * the slow sites of right hops, plane 1 (drawn independently, call 1 of the
  * same stream) those of left hops.  TURNING: bit i = site i is a turning
- * site (probability density = dis_a_thr). */
+ * site (probability density = dis_a_thr).  CROSSING: plane 0 the sites
+ * whose A -> B crossing probability is reduced, plane 1 (call 1) those of
+ * B -> A, each with probability dis_a_thr. */
 int orc_disorder(const orc_params* P, uint32_t* mask, uint32_t real) {
   stream_t st;
   const uint64_t W = (P->L + 31) / 32;
-  const uint32_t planes = P->dis_kind == DIS_BIMODAL_PQ ? 2u : 1u;
+  const uint32_t planes = (P->dis_kind == DIS_BIMODAL_PQ || P->dis_kind == DIS_CROSSING) ? 2u : 1u;
   memset(mask, 0, (size_t)(W * planes) * sizeof(uint32_t));
   if (P->dis_kind == DIS_NONE) return 0;
   for (uint32_t pl = 0; pl < planes; pl++)
@@ -591,13 +612,13 @@ int orc_serial_reference(const orc_params* P, uint32_t* words, const uint32_t* m
         uint32_t r = (uint32_t)(xoshiro_next(&x) >> 32);
         lane_attempt(P, wa, wb, (int)(j / L), j % L, r, cnt);
       }
-      if (P->dis_kind == DIS_TURNING) {
+      if (lane_changes_on(P)) {
         for (uint64_t i = 0; i < L; i++) {
-          if (!get_site(mask, i)) continue;
+          if (!crosses(P, mask, i)) continue;
           int a = get_site(wa, i), b = get_site(wb, i);
           if (a == b) continue;
           uint32_t r = (uint32_t)(xoshiro_next(&x) >> 32);
-          if (accept(r, P->dis_b_thr)) {
+          if (accept(r, cross_thr(P, mask, i, a ? 0u : 1u))) {
             flip_site(wa, i);
             flip_site(wb, i);
             if (a) cnt[2]++;

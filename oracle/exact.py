@@ -64,34 +64,38 @@ class Space:
                 K[k, k] += 1
         return K
 
-    def turning_kernel(self, turning_sites, omega: float) -> np.ndarray:
+    def turning_kernel(self, turning_sites, omega, omega_ba=None) -> np.ndarray:
         """Two lanes: at each turning site with exactly one lane occupied, the
-        particle moves to the other lane with probability omega."""
+        particle moves to the other lane with probability omega (a number or a
+        per-site dict; with ``omega_ba`` the moves from lane B use that one)."""
         T = np.eye(self.n)
         for i in turning_sites:
             Ti = np.zeros((self.n, self.n))
             for k, x in enumerate(self.states):
                 if self.bit(x, 0, i) != self.bit(x, 1, i):
                     y = self.flip(self.flip(x, 0, i), 1, i)
-                    Ti[k, self.index[y]] += omega
-                    Ti[k, k] += 1 - omega
+                    w = omega if self.bit(x, 0, i) or omega_ba is None else omega_ba
+                    w = w[i] if isinstance(w, dict) else w
+                    Ti[k, self.index[y]] += w
+                    Ti[k, k] += 1 - w
                 else:
                     Ti[k, k] += 1
             T = T @ Ti
         return T
 
-    def lane_change_kernel(self, turning_sites, omega: float, src: int) -> np.ndarray:
+    def lane_change_kernel(self, turning_sites, omega, src: int) -> np.ndarray:
         """Two lanes, one direction: at each turning site whose lane `src` is
         occupied and other lane empty, the particle moves across with
-        probability omega."""
+        probability omega (a number or a per-site dict)."""
         T = np.eye(self.n)
         for i in turning_sites:
+            w = omega[i] if isinstance(omega, dict) else omega
             Ti = np.zeros((self.n, self.n))
             for k, x in enumerate(self.states):
                 if self.bit(x, src, i) == 1 and self.bit(x, 1 - src, i) == 0:
                     y = self.flip(self.flip(x, 0, i), 1, i)
-                    Ti[k, self.index[y]] += omega
-                    Ti[k, k] += 1 - omega
+                    Ti[k, self.index[y]] += w
+                    Ti[k, k] += 1 - w
                 else:
                     Ti[k, k] += 1
             T = T @ Ti
@@ -186,16 +190,19 @@ class RingModel:
 
 class TwoLaneModel:
     """Two rings: lane A hops right with pA, lane B hops left with pB; lane
-    changes at ``turning_sites`` with probability omega once per sweep."""
+    changes at ``turning_sites`` with probability omega once per sweep (A -> B
+    with ``omega``, B -> A with ``omega_ba`` when given; either may be a
+    per-site dict, the paper's crossing probabilities u_i and v_i)."""
 
-    def __init__(self, L: int, N: int, pA: float, pB: float, turning_sites, omega: float):
+    def __init__(self, L: int, N: int, pA: float, pB: float, turning_sites, omega, omega_ba=None):
         self.sp = Space(L, N, 2)
         self.L = L
         self.KA = [self.sp.bond_kernel(0, b, pA, 0.0) for b in range(L)]
         self.KB = [self.sp.bond_kernel(1, b, 0.0, pB) for b in range(L)]
-        self.T = self.sp.turning_kernel(list(turning_sites), omega)
+        ba = omega if omega_ba is None else omega_ba
+        self.T = self.sp.turning_kernel(list(turning_sites), omega, ba)
         self.TAB = self.sp.lane_change_kernel(list(turning_sites), omega, 0)
-        self.TBA = self.sp.lane_change_kernel(list(turning_sites), omega, 1)
+        self.TBA = self.sp.lane_change_kernel(list(turning_sites), ba, 1)
         self.I = np.eye(self.sp.n)
 
     def rsu_sweep(self) -> np.ndarray:

@@ -203,7 +203,8 @@ def test_two_lane_replay_matches_exact(oracle_mod, schedule):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("model,schedule,dis", [
-    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2), (0, 2, 0), (0, 2, 1), (1, 2, 2), (1, 2, 0)])
+    (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2), (0, 2, 0), (0, 2, 1), (1, 2, 2), (1, 2, 0), (1, 2, 4),
+    (1, 1, 4)])
 def test_particle_number_conserved(oracle_mod, model, schedule, dis):
     th = oracle_mod.threshold
     P = oracle_mod.Params(model=model, schedule=schedule, L=1024, D=64, samples_per_real=3, seed=9,
@@ -537,6 +538,39 @@ def test_two_lane_sca_replay_matches_exact(oracle_mod):
         Or = Or @ m.KA[b] @ KBr[b]
     for wrong in (E @ O @ m.T, E @ m.TBA @ O @ m.TAB, Er @ m.TAB @ Or @ m.TBA):
         assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(wrong, 2)) < 1e-6
+
+
+@pytest.mark.parametrize("schedule", ["sca", "serial"])
+def test_two_lane_crossing_classes_match_exact(oracle_mod, schedule):
+    """The paper's two-lane crossing (sec. 3): every site may cross, A -> B
+    with u_i and B -> A with v_i, each 0.8 unless the site is marked (0.2) in
+    its own class plane.  Chi-square against the exact operator; rejected:
+    u and v swapped, and the u plane used for both directions."""
+    L, p = 4, 0.5
+    th = oracle_mod.threshold
+    uf, us = 0.8, 0.2
+    sched = oracle_mod.SCHED_SCA if schedule == "sca" else oracle_mod.SCHED_SERIAL
+    P = oracle_mod.Params(model=oracle_mod.MODEL_TWO_LANE, L=L, schedule=sched, samples_per_real=S_DIST, seed=41,
+                          p_thr=th(p), q_thr=th(p), dis_kind=oracle_mod.DIS_CROSSING, dis_a_thr=th(0.5),
+                          dis_b_thr=th(uf), dis_c_thr=th(us), dis_seed=5)
+    mask = oracle_mod.disorder(P)
+    assert mask.shape == (1, 2)
+    mu = [(int(mask[0, 0]) >> i) & 1 for i in range(L)]
+    mv = [(int(mask[0, 1]) >> i) & 1 for i in range(L)]
+    assert mu != mv
+    u = {i: us if mu[i] else uf for i in range(L)}
+    v = {i: us if mv[i] else uf for i in range(L)}
+
+    def op(uu, vv):
+        m = ex.TwoLaneModel(L, L, p, p, range(L), uu, vv)
+        return m.sca_sweep() if schedule == "sca" else m.rsu_sweep(), m.sp
+
+    A, sp = op(u, v)
+    counts = histogram(sp, _replay_hist(oracle_mod, P, 2, mask=mask))
+    assert chi2_pvalue(counts, sp.flat_alt() @ np.linalg.matrix_power(A, 2)) > 1e-4
+    for uu, vv in ((v, u), (u, u)):
+        wrong, _ = op(uu, vv)
+        assert chi2_pvalue(counts, sp.flat_alt() @ np.linalg.matrix_power(wrong, 2)) < 1e-6
 
 
 def test_two_lane_sca_deterministic_counts(oracle_mod):

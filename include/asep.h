@@ -106,6 +106,15 @@ extern "C" {
  * realization holds the p classes (the ASEP_DIS_BIMODAL draw), plane 1 the q
  * classes (call 1 of the disorder stream).  Not under the domain schedule. */
 #define ASEP_DIS_BIMODAL_PQ 3u
+/* Two lanes, SCA or serial schedule: the paper's crossing probabilities
+ * (sec. 3): a particle may change lanes at every site, A -> B with u_i and
+ * B -> A with v_i, quenched with the distribution of Eq. bimodal: dis_a =
+ * fraction of marked sites (for u and v independently), dis_b = the crossing
+ * probability of unmarked sites (0.8 in the paper), dis_c = of marked ones
+ * (0.2).  Plane 0 marks u, plane 1 (call 1 of the disorder stream) marks v.
+ * Same draws per candidate site as ASEP_DIS_TURNING.  Not under the domain
+ * schedule. */
+#define ASEP_DIS_CROSSING 4u
 
 #define ASEP_INIT_FLAT_ALT 0u       /* 1010...: site i occupied iff i even (paper sec. 2.1) */
 #define ASEP_INIT_BERNOULLI_HALF 1u /* every lane site occupied with probability 1/2 (sec. 3) */
@@ -222,8 +231,9 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed);
 int asep_counters(asep_ctx* ctx, uint64_t* counters, size_t n);
 
 /* Copy the quenched planes, layout [n_realizations][planes][L/32] (planes =
- * 2 for BIMODAL_PQ: p classes, then q classes; else 1; bit = slow site for
- * the bimodal kinds, turning site for TURNING).  Synchronises. */
+ * 2 for BIMODAL_PQ: p classes, then q classes, and for CROSSING: u marks,
+ * then v marks; else 1; bit = slow site for the bimodal kinds, turning site
+ * for TURNING).  Synchronises. */
 int asep_disorder(asep_ctx* ctx, uint32_t* words, size_t n_words);
 
 /* Hop counters (layout of asep_counters) at every sample time recorded so

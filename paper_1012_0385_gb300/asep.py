@@ -29,7 +29,7 @@ ASEP_ERR_STATE = -5
 
 ASEP_MODEL_RING, ASEP_MODEL_TWO_LANE = 0, 1
 ASEP_SCHED_DOMAIN, ASEP_SCHED_SERIAL, ASEP_SCHED_SCA = 0, 1, 2
-ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING, ASEP_DIS_BIMODAL_PQ = 0, 1, 2, 3
+ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING, ASEP_DIS_BIMODAL_PQ, ASEP_DIS_CROSSING = 0, 1, 2, 3, 4
 ASEP_INIT_FLAT_ALT, ASEP_INIT_BERNOULLI_HALF = 0, 1
 ASEP_ALWAYS = 0xFFFFFFFF
 ASEP_FAULT_NONE, ASEP_FAULT_COPY_STALL = 0, 1
@@ -408,10 +408,10 @@ def asep_height_offset(ctx) -> np.ndarray:
 
 def asep_disorder(ctx) -> np.ndarray:
     """Quenched planes, [R, planes * L/32] (independent p and q classes: the
-    p-class plane, then the q-class plane)."""
+    p-class plane, then the q-class plane; crossing kind: u marks, v marks)."""
     p = ctx.params
     R = p.n_realizations if p.dis_kind != ASEP_DIS_NONE else 0
-    planes = 2 if p.dis_kind == ASEP_DIS_BIMODAL_PQ else 1
+    planes = 2 if p.dis_kind in (ASEP_DIS_BIMODAL_PQ, ASEP_DIS_CROSSING) else 1
     m = np.zeros((max(R, 1), planes * (p.L // 32)), dtype=np.uint32)
     _check(lib().asep_disorder(_h(ctx), _ptr(m, ctypes.c_uint32), m.size), _h(ctx))
     return m[:R]

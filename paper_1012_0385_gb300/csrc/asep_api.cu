@@ -194,7 +194,11 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (!thr_ok(p->p_thr) || !thr_ok(p->q_thr) || !thr_ok(p->dis_a_thr) || !thr_ok(p->dis_b_thr) ||
       !thr_ok(p->dis_c_thr))
     return fail(ctx, ASEP_ERR_INVALID, "thresholds must be 0, ASEP_ALWAYS or multiples of 4096");
-  if (p->dis_kind > ASEP_DIS_BIMODAL_PQ) return fail(ctx, ASEP_ERR_INVALID, "unknown dis_kind %u", p->dis_kind);
+  if (p->dis_kind > ASEP_DIS_CROSSING) return fail(ctx, ASEP_ERR_INVALID, "unknown dis_kind %u", p->dis_kind);
+  if (p->dis_kind == ASEP_DIS_CROSSING && p->model != ASEP_MODEL_TWO_LANE)
+    return fail(ctx, ASEP_ERR_INVALID, "crossing probabilities are defined for the two-lane model");
+  if (p->dis_kind == ASEP_DIS_CROSSING && p->schedule == ASEP_SCHED_DOMAIN)
+    return fail(ctx, ASEP_ERR_INVALID, "crossing at every site runs under the SCA and serial schedules");
   if ((p->dis_kind == ASEP_DIS_BIMODAL || p->dis_kind == ASEP_DIS_BIMODAL_PQ) && p->model != ASEP_MODEL_RING)
     return fail(ctx, ASEP_ERR_INVALID, "bimodal disorder is defined for the ring model");
   if (p->dis_kind == ASEP_DIS_BIMODAL_PQ && p->schedule == ASEP_SCHED_DOMAIN)
@@ -359,7 +363,9 @@ Rates rates(const asep_ctx* ctx) {
   const bool bimodal = ctx->p.dis_kind == ASEP_DIS_BIMODAL || ctx->p.dis_kind == ASEP_DIS_BIMODAL_PQ;
   r.p_slow = bimodal ? ctx->p.dis_b_thr : ctx->p.p_thr;
   r.q_slow = bimodal ? ctx->p.dis_c_thr : ctx->p.q_thr;
-  r.omega = ctx->p.dis_kind == ASEP_DIS_TURNING ? ctx->p.dis_b_thr : 0u;
+  const bool lanes = ctx->p.dis_kind == ASEP_DIS_TURNING || ctx->p.dis_kind == ASEP_DIS_CROSSING;
+  r.omega = lanes ? ctx->p.dis_b_thr : 0u;
+  r.omega_slow = ctx->p.dis_kind == ASEP_DIS_CROSSING ? ctx->p.dis_c_thr : r.omega;
   r.p_always = r.p == ASEP_ALWAYS;
   r.q_always = r.q == ASEP_ALWAYS;
   return r;

@@ -22,17 +22,21 @@ constexpr uint32_t kTagScaTurn = 8;  // two-lane SCA: one word per lane-change c
 constexpr uint32_t kAcceptMask = 0xFFFFF000u;  // draw bits compared with a threshold
 
 enum Model : uint32_t { kRing = 0, kTwoLane = 1 };
-enum Dis : uint32_t { kDisNone = 0, kDisBimodal = 1, kDisTurning = 2, kDisBimodalPQ = 3 };
+enum Dis : uint32_t { kDisNone = 0, kDisBimodal = 1, kDisTurning = 2, kDisBimodalPQ = 3, kDisCrossing = 4 };
 
 // Quenched planes per realization: the class plane (bimodal), the turning
-// plane (two lanes), or the p-class and q-class planes (bimodal, independent).
-constexpr uint32_t dis_planes(uint32_t dis) { return dis == kDisNone ? 0u : (dis == kDisBimodalPQ ? 2u : 1u); }
+// plane (two lanes), the p-class and q-class planes (bimodal, independent),
+// or the u-class and v-class planes (two lanes, crossing at every site).
+constexpr uint32_t dis_planes(uint32_t dis) {
+  return dis == kDisNone ? 0u : ((dis == kDisBimodalPQ || dis == kDisCrossing) ? 2u : 1u);
+}
 
 // Rates of one context (u32 thresholds).
 struct Rates {
   uint32_t p, q;          // ring: fast right/left; two lanes: lane A / lane B
   uint32_t p_slow, q_slow;  // bimodal slow class
-  uint32_t omega;         // two lanes: lane-change probability per sweep
+  uint32_t omega;         // two lanes: lane-change probability per sweep (crossing kind: unmarked sites)
+  uint32_t omega_slow;    // two lanes, crossing kind: lane-change probability at marked sites
   bool p_always, q_always;  // p / q == 0xffffffff (a draw r < t test alone cannot say "always")
 };
 

@@ -337,18 +337,20 @@ __device__ __forceinline__ void sca_lane_unit(uint32_t* plane, uint32_t* carry, 
 // site / 4, word site mod 4).  STEP 1 first applies the odd phase's pending
 // flips of bit 0 of the unit's first words.
 // The lane changes of one word (global word index `word`): candidate sites
-// are the set bits of `sel` (turning sites with source occupied and target
-// empty); returns the bits that move.
+// are the set bits of `sel` (turning sites -- or, crossing kind, any site --
+// with source occupied and target empty), accepted with omega, or with
+// omega_slow where `marked` has the bit set (the crossing kind's reduced u_i
+// or v_i); returns the bits that move.
 template <uint32_t STEP>
 __device__ __forceinline__ uint32_t sca_turn_word(uint32_t sel, uint32_t word, const DomainLaunch& a, uint64_t s,
-                                                  uint32_t n_glob, unsigned long long& moves) {
+                                                  uint32_t n_glob, unsigned long long& moves, uint32_t marked = 0u) {
   uint32_t f = 0u;
   while (sel) {
     const uint32_t b = static_cast<uint32_t>(__ffs(sel)) - 1u;
     sel &= sel - 1u;
     const uint32_t site = 32u * word + b;
     const uint4 r = philox10(ctr_of(s, kTagScaTurn, STEP, n_glob, site >> 2), a.ks);
-    if (accept(pick(r, site & 3u), a.rates.omega)) {
+    if (accept(pick(r, site & 3u), ((marked >> b) & 1u) ? a.rates.omega_slow : a.rates.omega)) {
       f |= 1u << b;
       ++moves;
     }
@@ -361,17 +363,27 @@ __device__ __forceinline__ uint32_t turn_candidates(uint32_t xa, uint32_t xb, ui
   return m & (STEP == 0 ? (xa & ~xb) : (xb & ~xa));
 }
 
-template <uint32_t STEP>
+// XC (crossing kind): every site may cross; M holds the u-class plane, then
+// the v-class plane, and STEP selects the one of its direction.
+template <uint32_t STEP, bool XC = false>
 __device__ __forceinline__ void sca_turn_unit(uint32_t* A, uint32_t* B, const uint32_t* M, uint32_t* carry,
-                                              const DomainLaunch& a, uint32_t u, uint32_t n_units, uint64_t s,
-                                              uint32_t n_glob, unsigned long long& moves) {
+                                              const DomainLaunch& a, uint32_t u, uint32_t n_units, uint32_t W,
+                                              uint64_t s, uint32_t n_glob, unsigned long long& moves) {
   uint4* pa = reinterpret_cast<uint4*>(A + 8u * u);
   uint4* pb = reinterpret_cast<uint4*>(B + 8u * u);
-  const uint4* pm = reinterpret_cast<const uint4*>(M + 8u * u);
-  const uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1], m0 = pm[0], m1 = pm[1];
+  const uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
   uint32_t xa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
   uint32_t xb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-  const uint32_t m[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+  uint32_t m[8], mk[8];  // candidate sites, marked sites
+  if (XC) {
+    load8(M + STEP * W + 8u * u, mk);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m[w] = ~0u;
+  } else {
+    load8(M + 8u * u, m);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) mk[w] = 0u;
+  }
   if (STEP == 1) {
     const uint32_t prev = (u == 0 ? n_units : u) - 1;
     xa[0] ^= carry[prev];
@@ -381,7 +393,8 @@ __device__ __forceinline__ void sca_turn_unit(uint32_t* A, uint32_t* B, const ui
   }
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
-    const uint32_t f = sca_turn_word<STEP>(turn_candidates<STEP>(xa[w], xb[w], m[w]), 8u * u + w, a, s, n_glob, moves);
+    const uint32_t f =
+        sca_turn_word<STEP>(turn_candidates<STEP>(xa[w], xb[w], m[w]), 8u * u + w, a, s, n_glob, moves, mk[w]);
     xa[w] ^= f;
     xb[w] ^= f;
   }
@@ -516,7 +529,7 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
       __syncthreads();
       if (DIS) {
         for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-          sca_turn_unit<0>(A, B, qp, carry, a, u, n_units, s, n_glob, cnt[2]);
+          sca_turn_unit<0, PQ>(A, B, qp, carry, a, u, n_units, W, s, n_glob, cnt[2]);
         __syncthreads();
       }
       for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x) {
@@ -526,7 +539,7 @@ __global__ void __launch_bounds__(DIS ? 512 : 1024) k_sca(const DomainLaunch a) 
       __syncthreads();
       if (DIS) {
         for (uint32_t u = threadIdx.x; u < n_units; u += blockDim.x)
-          sca_turn_unit<1>(A, B, qp, carry, a, u, n_units, s, n_glob, cnt[3]);
+          sca_turn_unit<1, PQ>(A, B, qp, carry, a, u, n_units, W, s, n_glob, cnt[3]);
         __syncthreads();
       }
     }
@@ -604,7 +617,7 @@ __device__ __forceinline__ void store_unit(uint32_t* p, const uint32_t (&x)[8], 
 // Two lanes: one phase and its lane changes over every sample, a thread per
 // unit.  Grid: S x blocks_per_sample CTAs, blockIdx.x = sample *
 // blocks_per_sample + block.  DIS: turning sites.
-template <bool DIS, uint32_t PHASE>
+template <bool DIS, uint32_t PHASE, bool XC = false>
 __global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream_lanes(const DomainLaunch a,
                                                                          uint32_t blocks_per_sample) {
   __shared__ unsigned long long red[kScaStreamThreads / 32][4];
@@ -628,20 +641,31 @@ __global__ void __launch_bounds__(kScaStreamThreads) k_sca_stream_lanes(const Do
       uint32_t oa = sca_lane_update<0, PHASE>(xa, na, a, u, s, n_glob, a.rates.p, cnt[0]);
       uint32_t ob = sca_lane_update<1, PHASE>(xb, nb, a, u, s, n_glob, a.rates.q, cnt[1]);
       if (DIS) {
-        const uint32_t* M = a.mask + real * W;
-        uint32_t m[8];
-        load8(M + 8u * u, m);
+        // turning plane, or (XC) every site with the u-class / v-class plane of this phase's direction
+        const uint32_t* M = a.mask + real * (XC ? 2u : 1u) * W;
+        const uint32_t* Mk = M + PHASE * W;
+        uint32_t m[8], mk[8];
+        if (XC) {
+          load8(Mk + 8u * u, mk);
+#pragma unroll
+          for (int w = 0; w < 8; ++w) m[w] = ~0u;
+        } else {
+          load8(M + 8u * u, m);
+#pragma unroll
+          for (int w = 0; w < 8; ++w) mk[w] = 0u;
+        }
         if (PHASE == 1) m[0] &= ~1u;  // site 256u belongs to the previous unit's owner
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
           const uint32_t f = sca_turn_word<PHASE>(turn_candidates<PHASE>(xa[w], xb[w], m[w]), 8u * u + w, a, s,
-                                                  n_glob, cnt[2 + PHASE]);
+                                                  n_glob, cnt[2 + PHASE], mk[w]);
           xa[w] ^= f;
           xb[w] ^= f;
         }
         if (PHASE == 1) {  // site 256(u + 1) = bit 0 of word nw, after this unit's last bond
-          const uint32_t f = sca_turn_word<1>(turn_candidates<1>(na ^ oa, nb ^ ob, M[nw] & 1u), nw, a, s, n_glob,
-                                              cnt[3]);
+          const uint32_t cand = XC ? 1u : (M[nw] & 1u), marked = XC ? (Mk[nw] & 1u) : 0u;
+          const uint32_t f = sca_turn_word<1>(turn_candidates<1>(na ^ oa, nb ^ ob, cand), nw, a, s, n_glob,
+                                              cnt[3], marked);
           oa ^= f;
           ob ^= f;
         }
@@ -792,8 +816,8 @@ cudaError_t launch_sca_stream_t(const DomainLaunch& a, cudaStream_t st) {
     k_sca_stream_ring<DIS, COUNT, FAST2, 1, PQ><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps, upt);
   } else {
     const uint32_t bps = (n_units + kScaStreamThreads - 1) / kScaStreamThreads;
-    k_sca_stream_lanes<DIS, 0><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
-    k_sca_stream_lanes<DIS, 1><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
+    k_sca_stream_lanes<DIS, 0, PQ><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
+    k_sca_stream_lanes<DIS, 1, PQ><<<bps * a.geo.S, kScaStreamThreads, 0, st>>>(a, bps);
   }
   return cudaGetLastError();
 }
@@ -807,6 +831,7 @@ size_t sca_smem_bytes(uint32_t W, uint32_t planes, uint32_t quenched_planes) {
 cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st) {
   const bool count = a.count_hops != 0;
   if (a.model == kTwoLane) {  // two lanes always count hops and turns
+    if (a.dis == kDisCrossing) return launch_sca_t<kTwoLane, true, true, false, true>(a, threads, smem, st);
     return a.dis == kDisTurning ? launch_sca_t<kTwoLane, true, true, false>(a, threads, smem, st)
                                 : launch_sca_t<kTwoLane, false, true, false>(a, threads, smem, st);
   }
@@ -826,9 +851,11 @@ cudaError_t launch_sca(const DomainLaunch& a, uint32_t threads, size_t smem, cud
 
 cudaError_t launch_sca_stream(const DomainLaunch& a, cudaStream_t st) {
   const bool count = a.count_hops != 0;
-  if (a.model == kTwoLane)
+  if (a.model == kTwoLane) {  // two lanes always count hops and turns
+    if (a.dis == kDisCrossing) return launch_sca_stream_t<kTwoLane, true, true, false, true>(a, st);
     return a.dis == kDisTurning ? launch_sca_stream_t<kTwoLane, true, true, false>(a, st)
                                 : launch_sca_stream_t<kTwoLane, false, true, false>(a, st);
+  }
   if (a.dis == kDisBimodal)
     return count ? launch_sca_stream_t<kRing, true, true, false>(a, st)
                  : launch_sca_stream_t<kRing, true, false, false>(a, st);

@@ -109,16 +109,22 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
       __syncwarp();
       base += c;
     }
-    if (MODEL == kTwoLane && DIS == kDisTurning) {
-      // lane changes: every event touches only (A_i, B_i); words are split over the lanes
+    if (MODEL == kTwoLane && (DIS == kDisTurning || DIS == kDisCrossing)) {
+      // lane changes: every event touches only (A_i, B_i); words are split over the lanes.  Crossing kind:
+      // every site, u_i (plane 0) for a particle in lane A, v_i (plane 1) for one in lane B
       for (uint32_t w = lane; w < W; w += 32) {
-        uint32_t e = M[w] & (A[w] ^ B[w]);
+        uint32_t e = (DIS == kDisCrossing ? ~0u : M[w]) & (A[w] ^ B[w]);
         while (e) {
           const uint32_t bit = __ffs(e) - 1;
           e &= e - 1;
           const uint32_t site = 32u * w + bit;
           const uint4 r = philox10(ctr_of(s, kTagTurn, 0, n_glob, site >> 2), key);
-          if (accept(pick(r, site & 3u), a.rates.omega)) {
+          uint32_t thr = a.rates.omega;
+          if (DIS == kDisCrossing) {
+            const uint32_t marked = ((A[w] >> bit) & 1u) ? M[w] : M[W + w];
+            thr = ((marked >> bit) & 1u) ? a.rates.omega_slow : a.rates.omega;
+          }
+          if (accept(pick(r, site & 3u), thr)) {
             if (A[w] & (1u << bit)) ++c2;
             else ++c3;
             A[w] ^= 1u << bit;
@@ -242,6 +248,7 @@ cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, c
   if (model == kRing && dis == kDisBimodalPQ) return launch_serial_t<kRing, kDisBimodalPQ>(a, st);
   if (model == kTwoLane && dis == kDisNone) return launch_serial_t<kTwoLane, kDisNone>(a, st);
   if (model == kTwoLane && dis == kDisTurning) return launch_serial_t<kTwoLane, kDisTurning>(a, st);
+  if (model == kTwoLane && dis == kDisCrossing) return launch_serial_t<kTwoLane, kDisCrossing>(a, st);
   return cudaErrorInvalidValue;
 }
 

@@ -71,7 +71,9 @@ def test_create_rejects_bad_params_without_device(A):
            dict(L=4096, schedule=3),
            # independent p and q classes: ring, SCA or serial schedule only; no kind 4
            dict(L=4096, dis_kind=3, dis_a_thr=4096), dict(L=4096, schedule=2, model=1, dis_kind=3, dis_a_thr=4096),
-           dict(L=4096, schedule=2, dis_kind=4)]
+           dict(L=4096, schedule=2, dis_kind=5),
+           # crossing probabilities: two lanes, SCA or serial schedule only
+           dict(L=4096, schedule=2, dis_kind=4, dis_a_thr=4096), dict(L=4096, model=1, dis_kind=4, dis_a_thr=4096)]
     for kw in bad:
         prm = A.make_params(**kw)
         with pytest.raises(A.AsepError) as ei:

@@ -21,7 +21,8 @@ def draw(k: int):
     schedule = int(rng.choice([A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_SCA, A.ASEP_SCHED_SERIAL]))
     model = int(rng.integers(2))
     if model == 1:
-        dis = int(rng.choice([0, 2]))
+        # the paper's crossing probabilities at every site run under the SCA and serial schedules
+        dis = int(rng.choice([0, 2] if schedule == A.ASEP_SCHED_DOMAIN else [0, 2, 4]))
     elif schedule == A.ASEP_SCHED_DOMAIN:
         dis = int(rng.choice([0, 1]))
     else:  # independent p and q classes run under the SCA and serial schedules
@@ -46,9 +47,9 @@ def draw(k: int):
     if dis in (1, 3):
         kw.update(dis_kind=dis, dis_a_thr=th(float(rng.choice([0.1, 0.5]))), dis_b_thr=int(rng.choice(RATES)),
                   dis_c_thr=int(rng.choice(RATES)), dis_seed=int(rng.integers(1, 1000)))
-    elif dis == 2:
-        kw.update(dis_kind=2, dis_a_thr=th(float(rng.choice([0.05, 0.3]))), dis_b_thr=th(float(rng.choice([0.1, 0.7]))),
-                  dis_seed=int(rng.integers(1, 1000)))
+    elif dis in (2, 4):
+        kw.update(dis_kind=dis, dis_a_thr=th(float(rng.choice([0.05, 0.3]))), dis_b_thr=th(float(rng.choice([0.1, 0.7]))),
+                  dis_seed=int(rng.integers(1, 1000)), dis_c_thr=th(0.2))
     n = int(rng.integers(1, 25))
     times = sorted(set([0] * int(rng.integers(2)) + [int(x) for x in rng.integers(1, n + 1, size=int(rng.integers(1, 4)))]))
     flags = 0
@@ -145,6 +146,8 @@ def draw_streamed(k: int):
     kw = {x: v for x, v in kw.items() if x != "schedule"}
     if kw.get("dis_kind") == A.ASEP_DIS_BIMODAL_PQ:  # the domain schedule takes one class plane
         kw["dis_kind"] = A.ASEP_DIS_BIMODAL
+    if kw.get("dis_kind") == A.ASEP_DIS_CROSSING:  # ... and turning sites, not crossing at every site
+        kw["dis_kind"] = A.ASEP_DIS_TURNING
     kw.update(L=2 * D * G, domain_sites=D, samples_per_real=min(kw["samples_per_real"], 2))
     return kw, chunks, times
 

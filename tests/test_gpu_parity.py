@@ -97,6 +97,7 @@ RING = A.ASEP_MODEL_RING
 TWO = A.ASEP_MODEL_TWO_LANE
 SCA = A.ASEP_SCHED_SCA
 PQ = A.ASEP_DIS_BIMODAL_PQ
+XING = A.ASEP_DIS_CROSSING
 CASES = {
     # several CTAs (16 samples each) with a ragged last CTA
     "ring_asep_ragged": (dict(L=4096, domain_sites=256, samples_per_real=20, p_thr=th(0.75), q_thr=th(0.25),
@@ -233,6 +234,24 @@ CASES = {
     "serial_bimodal_pq": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
                                p_thr=th(0.5), q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1),
                                dis_c_thr=th(0.1), dis_seed=52, seed=53), 12, [0, 12]),
+    # the paper's two-lane crossing probabilities: every site, u_i / v_i 0.8 or 0.2 at marked sites
+    "sca_two_lane_crossing": (dict(model=TWO, L=4096, schedule=SCA, n_realizations=2, samples_per_real=2,
+                                   init_kind=1, init_seed=12, p_thr=th(0.5), q_thr=th(0.5), dis_kind=XING,
+                                   dis_a_thr=th(0.5), dis_b_thr=th(0.8), dis_c_thr=th(0.2), dis_seed=13, seed=14,
+                                   flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=4), 15, [0, 4, 15]),
+    "sca_stream_two_lane_crossing": (dict(model=TWO, L=256 * 2085, schedule=SCA, n_realizations=2,
+                                          samples_per_real=1, init_kind=1, init_seed=15, p_thr=th(0.5),
+                                          q_thr=th(0.5), dis_kind=XING, dis_a_thr=th(0.5), dis_b_thr=th(0.8),
+                                          dis_c_thr=th(0.2), dis_seed=16, seed=17, plan=(32, 0)), 4, [0, 4]),
+    # two lanes and two class planes do not fit one CTA's shared memory at 2^19 sites: streamed by itself
+    "sca_two_lane_crossing_beyond_smem": (dict(model=TWO, L=1 << 19, schedule=SCA, samples_per_real=1,
+                                               init_kind=1, init_seed=18, p_thr=th(0.5), q_thr=th(0.5),
+                                               dis_kind=XING, dis_a_thr=th(0.5), dis_b_thr=th(0.8),
+                                               dis_c_thr=th(0.2), dis_seed=19, seed=20), 2, [0, 2]),
+    "serial_two_lane_crossing": (dict(model=TWO, L=1024, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2,
+                                      samples_per_real=2, init_kind=1, init_seed=21, q_thr=A.ASEP_ALWAYS,
+                                      dis_kind=XING, dis_a_thr=th(0.5), dis_b_thr=th(0.8), dis_c_thr=th(0.2),
+                                      dis_seed=22, seed=23), 10, [0, 10]),
     # many blocks of unit threads, the last one ragged (2085 units, 1025 units), so carries and lane-change
     # sites cross block boundaries; 16680 words per lattice: records in two chunks (16384 + 296 words)
     "sca_stream_ring_nine_blocks": (dict(L=256 * 2085, schedule=SCA, n_realizations=2, samples_per_real=1,

@@ -340,7 +340,7 @@ def run_ours(args):
                                 for r in tune_table]
         if not args.no_workloads and world == 1:
             line["sca"] = sca_growth(max(1, min(args.steps, 5)), peak_ops)
-            line["workloads"] = other_workloads()
+            line["workloads"] = other_workloads(tune=not args.no_autotune)
         if not args.no_serving and world == 1:
             line["serving"] = serving_comparison(capacity=value)
         if not args.no_cpu_baseline and world == 1:
@@ -389,7 +389,7 @@ def sca_growth(steps: int, peak_ops: float):
                          "traffic": _traffic_from_profile("sca")}}
 
 
-def other_workloads():
+def other_workloads(tune: bool = True):
     """Device-timed windows of the other configurations of the study (one
     run each after a warm-up launch, CUDA events on the launching stream):
     plain TASEP under serial RSU and under the domain schedule (full 10^4
@@ -399,7 +399,8 @@ def other_workloads():
     autocorrelation on), the latter also under the paper's two-lane SCA; the
     paper's quenched SSEP (independent slow classes for both directions); and
     the two streamed modes (domain schedule and SCA) on rings far beyond
-    shared memory."""
+    shared memory.  Resident domain-schedule windows first take the
+    autotuner's plan (bit-exactness guarded; `tune`)."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
@@ -449,8 +450,16 @@ def other_workloads():
     out = []
     for name, kw, times, lanes in cases:
         with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
+            tuned = None
+            if tune and kw.get("schedule", A.ASEP_SCHED_DOMAIN) == A.ASEP_SCHED_DOMAIN and \
+                    A.asep_get_info(ctx)["cluster"] != 32:
+                from paper_1012_0385_gb300.autotune import autotune
+
+                choice, _ = autotune(ctx, probe_sweeps=16)
+                tuned = {"cluster": choice.cluster, "samples_per_group": choice.samples_per_group, "autotuned": True}
+            A.asep_reset(ctx, seed=kw["seed"], init_seed=kw.get("init_seed", 0))
             A.asep_sweep(ctx, 8)  # warm-up launch
-            A.asep_reset(ctx, seed=kw["seed"])
+            A.asep_reset(ctx, seed=kw["seed"], init_seed=kw.get("init_seed", 0))
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -468,6 +477,8 @@ def other_workloads():
                               else "k_stream" if info["cluster"] == 32
                               else "k_cluster" if info["cluster"] > 1 else "k_domain"),
                    "samples_per_group": info["samples_per_group"]}
+            if tuned:
+                row["plan"] = tuned
             if info["cluster"] == 32:
                 # streamed: each phase reads and writes every lattice word once (4 x L/8 bytes per plane
                 # and sweep); the whole window, launch gaps and records included, against measured HBM

@@ -155,7 +155,8 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.y, 1 <= K, cnt);
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.z, 2 <= K, cnt);
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
-#pragma unroll 2
+  // one call per iteration on the plain ring (measured fastest), two with a quenched or second plane
+#pragma unroll(MODEL == kRing && DIS == kDisNone ? 1 : 2)
   for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
     const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
     const uint32_t k = call << 2;

@@ -87,7 +87,9 @@ __device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t 
       eq[gi] = rc[gi] | lc[gi];
     }
     const uint32_t p20 = a.rates.p >> 12, q20 = a.rates.q >> 12;
-    for (uint32_t k = 0; k < kmax; ++k) {
+#pragma unroll
+    for (uint32_t k = 0; k < 2; ++k) {  // FAST2: at most two planes (kmax <= 2)
+      if (k >= kmax) break;
       const uint4 y = philox10(ctr_of(s, kTagSca, k, n_glob, 2u * u + PHASE), a.ks);
       const uint32_t U[4] = {y.x, y.y, y.z, y.w};
       const uint32_t pb = (p20 >> (19u - k)) & 1u, qb = (q20 >> (19u - k)) & 1u;

@@ -148,6 +148,7 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
     }
   }
   const uint32_t Kmax = __reduce_max_sync(0xffffffffu, K);
+  const uint32_t Kmin = __reduce_min_sync(0xffffffffu, K);
   unsigned char* cb = reinterpret_cast<unsigned char*>(cur);
   const uint32_t base_b = (PHASE * (a.D >> 5) * cp + col) * 4u;
   const uint32_t row_scale_b = cp >> 3;  // 4 * Cp / 32
@@ -155,9 +156,21 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.y, 1 <= K, cnt);
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.z, 2 <= K, cnt);
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
-  // one call per iteration on the plain ring (measured fastest), two with a quenched or second plane
+  // Calls whose four attempts every lane of the warp makes (k + 3 <= Kmin) need
+  // no per-attempt count test; the remaining calls up to Kmax test k <= K.  A
+  // domain's attempts keep their order either way.  One call per iteration on
+  // the plain ring (measured fastest), two with a quenched or second plane.
+  uint32_t call = 1;
 #pragma unroll(MODEL == kRing && DIS == kDisNone ? 1 : 2)
-  for (uint32_t call = 1; (call << 2) <= Kmax; ++call) {
+  for (; (call << 2) + 3 <= Kmin; ++call) {
+    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, true, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, true, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.z, true, cnt);
+    attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.w, true, cnt);
+  }
+#pragma unroll 1
+  for (; (call << 2) <= Kmax; ++call) {
     const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
     const uint32_t k = call << 2;
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);

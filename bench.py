@@ -307,6 +307,17 @@ def run_ours(args):
     A.asep_philox_bench(152 * 8, 256, 1 << 12, sink.data_ptr(), stream.cuda_stream)
     ph_ms = A.asep_philox_bench(152 * 8, 256, 1 << 14, sink.data_ptr(), stream.cuda_stream)
     philox_calls_s = 152 * 8 * 256 * (1 << 14) / (ph_ms / 1000.0)
+    # the same stream driving the plain-ring bit operations on register-held
+    # word pairs (no lattice memory): at full occupancy, and in the kernel's
+    # own launch shape (one thread per column of every sample)
+    rb_sink = torch.empty(2 * 152 * 8 * 256, dtype=torch.int32, device="cuda")
+    pt, qt = th(P_RATE), th(Q_RATE)
+    A.asep_attempt_bench(152 * 8, 256, 1 << 10, pt, qt, rb_sink.data_ptr(), stream.cuda_stream)
+    rb_ms = A.asep_attempt_bench(152 * 8, 256, 1 << 13, pt, qt, rb_sink.data_ptr(), stream.cuda_stream)
+    rb_attempts_s = 4 * 152 * 8 * 256 * (1 << 13) / (rb_ms / 1000.0)
+    n_cols = SAMPLES * (L_SITES // (2 * DOMAIN))
+    rbk_ms = A.asep_attempt_bench(max(1, n_cols // 256), 256, 1 << 13, pt, qt, rb_sink.data_ptr(), stream.cuda_stream)
+    rbk_attempts_s = 4 * max(1, n_cols // 256) * 256 * (1 << 13) / (rbk_ms / 1000.0)
 
     if rank == 0:
         peaks = _peaks()
@@ -330,7 +341,10 @@ def run_ours(args):
                          "kernel": "k_domain<ring>", "kernel_ms": kernel_ms,
                          "ops_per_attempt": OPS_PER_ATTEMPT,
                          "peak_basis": f"{SMS} SMs x {LANES_PER_SM} int32 lanes/clk x {max_mhz:.0f} MHz (issue)",
-                         "philox_only_attempts_per_s": 4 * philox_calls_s},
+                         "philox_only_attempts_per_s": 4 * philox_calls_s,
+                         "rng_bitop_only_attempts_per_s": rb_attempts_s,
+                         "rng_bitop_only_at_kernel_shape_attempts_per_s": rbk_attempts_s,
+                         "frac_of_rng_bitop_only": value / rb_attempts_s},
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,

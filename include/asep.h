@@ -387,6 +387,23 @@ int asep_poisson_table(uint32_t m, uint32_t* k_lo, uint32_t* table, uint32_t cap
  * kernel from above: one call feeds four attempts. */
 int asep_philox_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, float* ms);
 
+/* Microbenchmark of the attempt stream without lattice memory: as
+ * asep_philox_bench, and each of a call's four output words r drives the
+ * domain schedule's plain-ring update (sec. 2.1 bond rule: right hop iff the
+ * bond reads 10 and r < p_thr, left hop iff 01 and r < q_thr) on a 64-bit
+ * word pair w1:w0 held in registers, at bits j = r mod 32 and j + 1.  Thread
+ * t starts from w0 = 0x55555555 ^ t, w1 = 0xAAAAAAAA ^ (t * 0x9E3779B9 mod
+ * 2^32), takes call c with counter (c / 16, tag 4, call c mod 16, sample t,
+ * group t / 32) under the key 0x243F6A8885A308D3 (the same as
+ * asep_philox_bench), and writes its final pair to sink[2t], sink[2t + 1]
+ * (device buffer of 2*blocks*threads uint32, owned by the caller).
+ * Thresholds must be below ASEP_ALWAYS (else ASEP_ERR_INVALID).  Writes the
+ * kernel time in milliseconds to *ms; synchronises `stream`.  It bounds the
+ * domain kernel's attempt rate by the same random stream and bit operations
+ * with the shared-memory round trip of each attempt removed. */
+int asep_attempt_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t p_thr,
+                       uint32_t q_thr, uint32_t* sink, float* ms);
+
 /* Library version string. */
 const char* asep_version(void);
 

@@ -92,7 +92,7 @@ class asep_info(ctypes.Structure):
 # Every symbol include/asep.h declares (tests check that the library exports them).
 EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_state", "asep_reset", "asep_counters",
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
-            "asep_poisson_table", "asep_philox_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
+            "asep_poisson_table", "asep_philox_bench", "asep_attempt_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
             "asep_batch_sweep_static", "asep_set_plan", "asep_currents", "asep_profile", "asep_autocorr",
             "asep_height_offset", "asep_inject_fault")
@@ -139,6 +139,8 @@ def lib():
                                              P(ctypes.c_uint32)]
             L.asep_philox_bench.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, vp,
                                             P(ctypes.c_float)]
+            L.asep_attempt_bench.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, vp, P(ctypes.c_float)]
             L.asep_version.restype = ctypes.c_char_p
             L.asep_batch_create.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, P(vp)]
             L.asep_batch_sweep.argtypes = [vp, P(vp), P(ctypes.c_uint64), ctypes.c_uint32]
@@ -434,6 +436,17 @@ def asep_philox_bench(blocks: int, threads: int, calls: int, sink_ptr: int, stre
     (sink_ptr: device buffer of blocks*threads uint32)."""
     ms = ctypes.c_float()
     _check(lib().asep_philox_bench(stream, blocks, threads, calls, ctypes.c_void_p(sink_ptr), ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def asep_attempt_bench(blocks: int, threads: int, calls: int, p_thr: int, q_thr: int, sink_ptr: int,
+                       stream=None) -> float:
+    """Milliseconds for blocks*threads threads x `calls` Philox4x32-10 calls,
+    each feeding four plain-ring attempts on a register-held word pair
+    (sink_ptr: device buffer of 2*blocks*threads uint32, final pairs)."""
+    ms = ctypes.c_float()
+    _check(lib().asep_attempt_bench(stream, blocks, threads, calls, p_thr, q_thr, ctypes.c_void_p(sink_ptr),
+                                    ctypes.byref(ms)))
     return float(ms.value)
 
 

@@ -515,6 +515,31 @@ int set_clock(asep_ctx* ctx, uint64_t sweep, uint32_t next_time) {
   return ASEP_OK;
 }
 
+// Times one microbenchmark launch with CUDA events on `stream` and
+// synchronises it.
+template <typename Launch>
+int timed_bench(void* stream, float* ms, const char* what, Launch launch) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(nullptr, e, "event create");
+  }
+  int rc = ASEP_OK;
+  if ((e = cudaEventRecord(e0, st)) != cudaSuccess || (e = launch(st)) != cudaSuccess ||
+      (e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+      (e = cudaEventElapsedTime(ms, e0, e1)) != cudaSuccess)
+    rc = cuda_fail(nullptr, e, what);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+bool bench_shape_ok(uint32_t blocks, uint32_t threads) {
+  return blocks != 0 && threads != 0 && threads <= 1024 && (threads & 31) == 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -545,23 +570,22 @@ int asep_poisson_table(uint32_t m, uint32_t* k_lo, uint32_t* table, uint32_t cap
 }
 
 int asep_philox_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, float* ms) {
-  if (!sink || !ms || blocks == 0 || threads == 0 || threads > 1024 || (threads & 31))
+  if (!sink || !ms || !bench_shape_ok(blocks, threads))
     return fail(nullptr, ASEP_ERR_INVALID, "philox bench: bad launch shape");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e;
-  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
-    if (e0) cudaEventDestroy(e0);
-    return cuda_fail(nullptr, e, "event create");
-  }
-  int rc = ASEP_OK;
-  if ((e = cudaEventRecord(e0, st)) != cudaSuccess || (e = launch_philox_bench(blocks, threads, calls, sink, st)) !=
-      cudaSuccess || (e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
-      (e = cudaEventElapsedTime(ms, e0, e1)) != cudaSuccess)
-    rc = cuda_fail(nullptr, e, "philox bench");
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  return rc;
+  return timed_bench(stream, ms, "philox bench", [&](cudaStream_t st) {
+    return launch_philox_bench(blocks, threads, calls, sink, st);
+  });
+}
+
+int asep_attempt_bench(void* stream, uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t p_thr,
+                       uint32_t q_thr, uint32_t* sink, float* ms) {
+  if (!sink || !ms || !bench_shape_ok(blocks, threads))
+    return fail(nullptr, ASEP_ERR_INVALID, "attempt bench: bad launch shape");
+  if (p_thr == ASEP_ALWAYS || q_thr == ASEP_ALWAYS)
+    return fail(nullptr, ASEP_ERR_INVALID, "attempt bench: thresholds below ASEP_ALWAYS only");
+  return timed_bench(stream, ms, "attempt bench", [&](cudaStream_t st) {
+    return launch_attempt_bench(blocks, threads, calls, p_thr, q_thr, sink, st);
+  });
 }
 
 const char* asep_last_error(const asep_ctx* ctx) {

@@ -220,5 +220,9 @@ cudaError_t launch_set_clock(Clock* clock, uint64_t sweep, uint32_t next_time, c
 int batch_ctas_per_sm(uint32_t threads, size_t smem);
 cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st);
 cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, cudaStream_t st);
+cudaError_t launch_attempt_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t p, uint32_t q,
+                                 uint32_t* sink, cudaStream_t st);
+// Philox key of the microbenchmarks (the leading hexadecimal digits of pi).
+constexpr uint64_t kBenchSeed = 0x243F6A8885A308D3ull;
 
 }  // namespace asep

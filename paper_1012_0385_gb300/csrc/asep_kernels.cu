@@ -865,7 +865,7 @@ uint32_t grid_for(size_t total, uint32_t threads) {
 
 __global__ void k_philox_bench(uint32_t calls, uint32_t* sink) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint2 key = key_of(0x243F6A8885A308D3ull);
+  const uint2 key = key_of(kBenchSeed);
   uint32_t acc = 0;
   for (uint32_t c = 0; c < calls; ++c) {
     const uint4 x = philox10(ctr_of(c >> 4, kTagDom, c & 15u, tid, tid >> 5), key);
@@ -874,7 +874,43 @@ __global__ void k_philox_bench(uint32_t calls, uint32_t* sink) {
   sink[tid] = acc;
 }
 
+// The attempt stream without lattice memory: the domain kernel's Philox
+// calls (round keys from the descriptor-style key schedule, counters in the
+// attempt layout) and, for each of a call's four words r, the plain-ring
+// update of `attempt` applied to a word pair held in registers: bits j and
+// j + 1 (j = r mod 32) of the 64-bit pair w1:w0 are swapped when they read
+// 10 and r < p, or 01 and r < q.  The pair carries from attempt to attempt,
+// so the chain is as dependent as on the lattice; each thread writes its final
+// pair to sink[2 tid], sink[2 tid + 1].
+__global__ void k_attempt_bench(uint32_t calls, uint32_t p, uint32_t q, const KeySchedule ks, uint32_t* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t w0 = 0x55555555u ^ tid;
+  uint32_t w1 = 0xAAAAAAAAu ^ (tid * 0x9E3779B9u);
+  for (uint32_t c = 0; c < calls; ++c) {
+    const uint4 y = philox10(ctr_of(c >> 4, kTagDom, c & 15u, tid, tid >> 5), ks);
+    const uint32_t rs[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t r = rs[i];
+      const uint32_t pat = __funnelshift_r(w0, w1, r) & 3u;
+      const bool hop = (pat == 1u && r < p) || (pat == 2u && r < q);
+      if (hop) {
+        w0 ^= __funnelshift_l(0u, 3u, r);
+        w1 ^= __funnelshift_l(3u, 0u, r);
+      }
+    }
+  }
+  sink[2 * tid] = w0;
+  sink[2 * tid + 1] = w1;
+}
+
 }  // namespace
+
+cudaError_t launch_attempt_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t p, uint32_t q,
+                                 uint32_t* sink, cudaStream_t st) {
+  k_attempt_bench<<<blocks, threads, 0, st>>>(calls, p, q, key_schedule(kBenchSeed), sink);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, cudaStream_t st) {
   k_philox_bench<<<blocks, threads, 0, st>>>(calls, sink);

@@ -156,3 +156,19 @@ def test_misaligned_allocation_is_refused_without_device(A):
             A.asep_create(prm, sample_times=[0, 5], torch_alloc=False, stream=0)
         assert ei.value.code == A.ASEP_ERR_NOMEM and "allocation failed" in str(ei.value)
         assert sorted(freed) == sorted(live.items()), bad
+
+
+def test_microbenchmarks_reject_bad_arguments_without_device(A):
+    """The microbenchmarks refuse a missing sink, a launch shape that is not
+    whole warps, and (the attempt stream) an "always" threshold, before any
+    CUDA call."""
+    cases = [lambda: A.asep_philox_bench(1, 32, 1, 0),
+             lambda: A.asep_philox_bench(1, 33, 1, 0x10000),
+             lambda: A.asep_attempt_bench(1, 32, 1, 0, 0, 0),
+             lambda: A.asep_attempt_bench(0, 32, 1, 0, 0, 0x10000),
+             lambda: A.asep_attempt_bench(1, 32, 1, A.ASEP_ALWAYS, 0, 0x10000),
+             lambda: A.asep_attempt_bench(1, 32, 1, 0, A.ASEP_ALWAYS, 0x10000)]
+    for case in cases:
+        with pytest.raises(A.AsepError) as ei:
+            case()
+        assert ei.value.code == A.ASEP_ERR_INVALID

@@ -81,10 +81,12 @@ __device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t 
       const uint32_t yb = PHASE ? __funnelshift_r(xb, xn, 1) : xb;
       // even lanes: bonds of word 2g (ya, ya >> 1); odd lanes: bonds of word 2g + 1 (yb << 1, yb)
       const uint32_t sa = ya >> 1, tb = yb << 1;
-      rc[gi] = (ya & ~sa & kEven) | (tb & ~yb & kOdd);  // 10
-      lc[gi] = (~ya & sa & kEven) | (~tb & yb & kOdd);  // 01
+      const uint32_t df = ((ya ^ sa) & kEven) | ((tb ^ yb) & kOdd);  // the bond's sites differ
+      const uint32_t first = (ya & kEven) | (tb & kOdd);             // its first site
+      rc[gi] = df & first;   // 10
+      lc[gi] = df & ~first;  // 01
       acc[gi] = 0u;
-      eq[gi] = rc[gi] | lc[gi];
+      eq[gi] = df;
     }
     const uint32_t p20 = a.rates.p >> 12, q20 = a.rates.q >> 12;
 #pragma unroll
@@ -189,12 +191,15 @@ __device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t 
       n_left += __popc(h & lc[gi]);
     }
     const uint32_t ha = h & kEven, hb = (h >> 1) & kEven;  // bonds of word 2g and of word 2g + 1
+    // ha and hb hold even bits only, so a bond's two-bit flip ha | ha << 1 is
+    // the product 3 ha (6 ha one site further on), which the multiply-add
+    // unit forms, sparing the busier integer pipe a shift and an OR.
     if (PHASE == 0) {
-      x[2 * gi] ^= ha | (ha << 1);
-      x[2 * gi + 1] ^= hb | (hb << 1);
+      x[2 * gi] ^= ha * 3u;
+      x[2 * gi + 1] ^= hb * 3u;
     } else {
-      x[2 * gi] ^= (ha << 1) | (ha << 2);
-      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb << 1) | (hb << 2);  // bond (32w + 31, 32w + 32) of word 2g
+      x[2 * gi] ^= ha * 6u;
+      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb * 6u);  // bond (32w + 31, 32w + 32) of word 2g
       const uint32_t out = (hb >> 30) & 1u;                      // ... and of word 2g + 1
       if (gi < 3) x[2 * gi + 2] ^= out;
       else carry_out = out;

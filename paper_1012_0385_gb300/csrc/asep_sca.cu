@@ -55,6 +55,33 @@ __device__ __forceinline__ void load8(const uint32_t* p, uint32_t (&x)[8]) {
 // All-ones where bit k (0 = most significant of 20) of a 20-bit threshold is set.
 __device__ __forceinline__ uint32_t bit_mask(uint32_t t20, uint32_t k) { return 0u - ((t20 >> (19u - k)) & 1u); }
 
+// Applies the accepted moves h[g] of a unit's four groups (bit 2j: bond j
+// of word 2g, bit 2j + 1: bond j of word 2g + 1) to its words; returns the
+// flip of bit 0 of the next unit's first word that the unit's last odd bond
+// makes (odd phase).  The masks ha, hb hold even bits only, so a bond's
+// two-bit flip ha | ha << 1 is the product 3 ha (6 ha one site further on),
+// which the multiply-add unit forms, sparing the busier integer pipe a shift
+// and an OR.
+template <uint32_t PHASE>
+__device__ __forceinline__ uint32_t apply_moves(uint32_t (&x)[8], const uint32_t (&h)[4]) {
+  uint32_t carry_out = 0u;
+#pragma unroll
+  for (int gi = 0; gi < 4; ++gi) {
+    const uint32_t ha = h[gi] & kEven, hb = (h[gi] >> 1) & kEven;  // bonds of word 2g and of word 2g + 1
+    if (PHASE == 0) {
+      x[2 * gi] ^= ha * 3u;
+      x[2 * gi + 1] ^= hb * 3u;
+    } else {
+      x[2 * gi] ^= ha * 6u;
+      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb * 6u);  // bond (32w + 31, 32w + 32) of word 2g
+      const uint32_t out = (hb >> 30) & 1u;            // ... and of word 2g + 1
+      if (gi < 3) x[2 * gi + 2] ^= out;
+      else carry_out = out;
+    }
+  }
+  return carry_out;
+}
+
 // One phase over one unit (four groups, global unit index u) held in
 // registers: x = its 8 words, c = its 8 class words (DIS: the classes of
 // right hops, and of left hops too unless PQ), d = the classes of left hops
@@ -181,31 +208,14 @@ __device__ __forceinline__ uint32_t sca_update(uint32_t (&x)[8], const uint32_t 
       }
     }
   }
-  // apply the accepted moves
-  uint32_t carry_out = 0u;
+  if (COUNT) {
 #pragma unroll
-  for (int gi = 0; gi < 4; ++gi) {
-    const uint32_t h = acc[gi];
-    if (COUNT) {
-      n_right += __popc(h & rc[gi]);
-      n_left += __popc(h & lc[gi]);
-    }
-    const uint32_t ha = h & kEven, hb = (h >> 1) & kEven;  // bonds of word 2g and of word 2g + 1
-    // ha and hb hold even bits only, so a bond's two-bit flip ha | ha << 1 is
-    // the product 3 ha (6 ha one site further on), which the multiply-add
-    // unit forms, sparing the busier integer pipe a shift and an OR.
-    if (PHASE == 0) {
-      x[2 * gi] ^= ha * 3u;
-      x[2 * gi + 1] ^= hb * 3u;
-    } else {
-      x[2 * gi] ^= ha * 6u;
-      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb * 6u);  // bond (32w + 31, 32w + 32) of word 2g
-      const uint32_t out = (hb >> 30) & 1u;                      // ... and of word 2g + 1
-      if (gi < 3) x[2 * gi + 2] ^= out;
-      else carry_out = out;
+    for (int gi = 0; gi < 4; ++gi) {
+      n_right += __popc(acc[gi] & rc[gi]);
+      n_left += __popc(acc[gi] & lc[gi]);
     }
   }
-  return carry_out;
+  return apply_moves<PHASE>(x, acc);
 }
 
 // One phase over unit u of a ring resident in shared memory; the flip of
@@ -296,24 +306,9 @@ __device__ __forceinline__ uint32_t sca_lane_update(uint32_t (&x)[8], uint32_t x
       for (int gi = 0; gi < 4; ++gi) eq[gi] &= ~U[gi];
     }
   }
-  uint32_t carry_out = 0u;
 #pragma unroll
-  for (int gi = 0; gi < 4; ++gi) {
-    const uint32_t h = acc[gi];
-    hops += __popc(h);
-    const uint32_t ha = h & kEven, hb = (h >> 1) & kEven;
-    if (PHASE == 0) {
-      x[2 * gi] ^= ha | (ha << 1);
-      x[2 * gi + 1] ^= hb | (hb << 1);
-    } else {
-      x[2 * gi] ^= (ha << 1) | (ha << 2);
-      x[2 * gi + 1] ^= ((ha >> 30) & 1u) | (hb << 1) | (hb << 2);
-      const uint32_t out = (hb >> 30) & 1u;
-      if (gi < 3) x[2 * gi + 2] ^= out;
-      else carry_out = out;
-    }
-  }
-  return carry_out;
+  for (int gi = 0; gi < 4; ++gi) hops += __popc(acc[gi]);
+  return apply_moves<PHASE>(x, acc);
 }
 
 // One lane's in-lane phase over unit u of a plane resident in shared memory.

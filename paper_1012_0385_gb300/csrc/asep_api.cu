@@ -228,14 +228,6 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   return ASEP_OK;
 }
 
-// Resident plan: columns = super-domains, one thread per column.
-// Launch plan.  Resident: columns = super-domains, one thread per column, a
-// whole sample (or several small ones) per CTA.  Cluster tier: each sample
-// spread over 2..16 CTAs of a thread-block cluster, for samples one CTA
-// cannot hold -- or, on request, to spread few large samples over more SMs.
-// force_cluster: 0 = choose, 1 = resident only, n > 1 = exactly n CTAs per
-// sample.  force_spc: samples per CTA for the resident plan (0 = choose).
-// The plan changes only the launch shape, never the results.
 // SCA plan.  Resident: one CTA per sample holding the ring in shared memory,
 // a thread per unit of 8 words (at most 1024 threads, 512 with a quenched
 // plane).  Streamed (kStreamTier): the ring in global memory, a thread per
@@ -264,6 +256,13 @@ int plan_sca(asep_ctx* ctx, uint32_t force) {
   return ASEP_OK;
 }
 
+// Launch plan.  Resident: columns = super-domains, one thread per column, a
+// whole sample (or several small ones) per CTA.  Cluster tier: each sample
+// spread over 2..16 CTAs of a thread-block cluster, for samples one CTA
+// cannot hold -- or, on request, to spread few large samples over more SMs.
+// force_cluster: 0 = choose, 1 = resident only, n > 1 = exactly n CTAs per
+// sample.  force_spc: samples per CTA for the resident plan (0 = choose).
+// The plan changes only the launch shape, never the results.
 int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
   const uint32_t D = ctx->D;
   ctx->R2 = 2 * D / 32;

@@ -60,13 +60,22 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
 
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
     const uint64_t s = s0 + it;
+    // The two words of attempt att: bond draw and acceptance draw.
+    auto draws = [&](uint32_t att, uint32_t& rb, uint32_t& ru) {
+      const uint4 x4 = philox10(ctr_of(s, kTagSer, 0, n_glob, att >> 1), key);
+      rb = (att & 1u) ? x4.z : x4.x;
+      ru = (att & 1u) ? x4.w : x4.y;
+    };
     uint32_t base = 0;
+    uint32_t rb, ru;  // draws of attempt base + lane
+    draws(lane, rb, ru);
     while (base < n_att) {
       const uint32_t b = min(32u, n_att - base);
       const bool active = lane < b;
-      const uint32_t att = base + lane;
-      const uint4 x4 = philox10(ctr_of(s, kTagSer, 0, n_glob, att >> 1), key);
-      const uint32_t rb = (att & 1u) ? x4.z : x4.x, ru = (att & 1u) ? x4.w : x4.y;
+      // the next batch's draws if all 32 attempts commit, formed while this
+      // batch runs (they do not depend on the lattice)
+      uint32_t rb_next, ru_next;
+      draws(base + 32u + lane, rb_next, ru_next);
       uint32_t pl = 0, i;
       if (MODEL == kTwoLane) {
         const uint32_t j = rb & (n_att - 1u);
@@ -107,6 +116,14 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
         }
       }
       __syncwarp();
+      // the next batch starts at attempt base + c: lane k takes the draws of
+      // this batch's lane c + k, or of the prefetched lane c + k - 32
+      const uint32_t src = lane + c;
+      const uint32_t rb_a = __shfl_sync(0xffffffffu, rb, src & 31u), ru_a = __shfl_sync(0xffffffffu, ru, src & 31u);
+      const uint32_t rb_b = __shfl_sync(0xffffffffu, rb_next, src & 31u);
+      const uint32_t ru_b = __shfl_sync(0xffffffffu, ru_next, src & 31u);
+      rb = src < 32u ? rb_a : rb_b;
+      ru = src < 32u ? ru_a : ru_b;
       base += c;
     }
     if (MODEL == kTwoLane && (DIS == kDisTurning || DIS == kDisCrossing)) {

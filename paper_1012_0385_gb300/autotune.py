@@ -100,7 +100,7 @@ class PlanCache:
 
     @staticmethod
     def key(params) -> str:
-        return (f"m{params.model}-d{params.dis_kind}-L{params.L}-D{params.domain_sites}-"
+        return (f"s{params.schedule}-m{params.model}-d{params.dis_kind}-L{params.L}-D{params.domain_sites}-"
                 f"S{params.n_realizations * params.samples_per_real}-f{params.flags}")
 
     def get(self, params):

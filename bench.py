@@ -177,6 +177,7 @@ def cpu_oracle_sample(target_s: float, n_mcs_cap: int = N_MCS):
     oracle.run(P, n, [t for t in log_times(N_MCS) if t <= n], threads=cores, samples=range(k))
     dt = time.perf_counter() - t0
     return {"value": k * L_SITES * n / dt, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+            "value_per_core": k * L_SITES * n / dt / cores,
             "sample": f"{k} of 256 samples x {n} of 2^14 sweeps (init + sweeps + W^2 at the log times), "
                       f"{dt:.1f} s on {cores} host threads"}
 
@@ -202,7 +203,7 @@ def run_reference(args):
                        "domain_sites": DOMAIN, "schedule": "two-phase Poisson-domain RSU",
                        "note": "ms_per_step extrapolates the sampled oracle rate to one full step"},
             "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                             "value_per_core": value / r["cores"], "sample": r["sample"]},
             "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

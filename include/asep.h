@@ -27,7 +27,11 @@
  * Schedules:
  *   ASEP_SCHED_SERIAL  plain random-sequential update (RSU, paper sec. 2.1):
  *                      per sweep L (two lanes: 2L) attempts on uniformly drawn
- *                      bonds.  One GPU thread per sample; L a power of two.
+ *                      bonds.  One GPU warp per sample (it applies each batch of
+ *                      32 consecutive attempts up to the first one that
+ *                      shares a site with an earlier one of the batch, so
+ *                      the result is the sequential one); L a power of
+ *                      two.
  *   ASEP_SCHED_DOMAIN  two-phase Poisson-domain RSU (no paper counterpart; the
  *                      paper's GPU schedule is a two-sub-lattice cellular
  *                      automaton).  Per sweep a random offset splits the ring
@@ -290,6 +294,15 @@ int asep_get_info(const asep_ctx* ctx, asep_info* info);
  * device.  Takes effect for the next launch. */
 int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group);
 
+/* Cap the sweeps one kernel launch (or one batch step) runs for this
+ * context: max_sweeps = 0 restores the automatic bound (the 32-bit per-lane
+ * hop counters of the domain schedule, 2^20 otherwise).  Longer asep_sweep
+ * and batch calls are split into launches of at most this many sweeps; the
+ * streamed tiers run one sweep per step whatever the cap.  An autotuner knob:
+ * results never depend on it (every sample's randomness is keyed by its
+ * sweep index).  Takes effect for the next call. */
+int asep_set_launch_sweeps(asep_ctx* ctx, uint32_t max_sweeps);
+
 /* Wait for all work of the context.  ASEP_ERR_TIMEOUT: a streamed tile's
  * wait for its bulk copy ran out (after one second); the results since are
  * invalid and every later call reports it until asep_reset or
@@ -359,7 +372,12 @@ const char* asep_batch_last_error(const asep_batch* b);
  * 16384 sample groups per launch step; larger requests return
  * ASEP_ERR_INVALID.  Every context must use `stream`.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current, so make it before any stream capture.  All calls on one GPU
+ * device current, so make it before any stream capture.  A call with n = 0
+ * (ctxs and n_mcs may then be NULL) does only the set-up on the current
+ * device: it looks up the address and enqueues one empty launch of each
+ * batch kernel on `stream`, which loads their code and lets the driver size
+ * their per-thread local memory; a caller whose device footprint must be
+ * fixed after start-up makes this call once per device at start-up.  All calls on one GPU
  * share its array, which keeps the last call's contents (the queue counter is
  * cleared by every call): calls whose work overlaps on the same GPU, e.g. on
  * two streams, race and must be ordered by the caller.  The host side of calls

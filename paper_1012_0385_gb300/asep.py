@@ -94,7 +94,7 @@ EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_attempt_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
-            "asep_batch_sweep_static", "asep_set_plan", "asep_currents", "asep_profile", "asep_autocorr",
+            "asep_batch_sweep_static", "asep_set_plan", "asep_set_launch_sweeps", "asep_currents", "asep_profile", "asep_autocorr",
             "asep_height_offset", "asep_inject_fault")
 
 
@@ -151,6 +151,7 @@ def lib():
             L.asep_batch_last_error.restype = ctypes.c_char_p
             L.asep_batch_sweep_static.argtypes = [P(vp), P(ctypes.c_uint64), ctypes.c_uint32, vp]
             L.asep_set_plan.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
+            L.asep_set_launch_sweeps.argtypes = [vp, ctypes.c_uint32]
             L.asep_currents.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
             L.asep_profile.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_size_t]
             L.asep_autocorr.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
@@ -331,6 +332,10 @@ def asep_inject_fault(ctx, fault: int) -> None:
 
 def asep_set_plan(ctx, cluster: int = 0, samples_per_group: int = 0) -> None:
     _check(lib().asep_set_plan(_h(ctx), int(cluster), int(samples_per_group)), _h(ctx))
+
+
+def asep_set_launch_sweeps(ctx, max_sweeps: int = 0) -> None:
+    _check(lib().asep_set_launch_sweeps(_h(ctx), int(max_sweeps)), _h(ctx))
 
 
 def asep_width(ctx):
@@ -538,7 +543,8 @@ def asep_batch_destroy(b) -> None:
 def asep_batch_sweep_static(ctxs, n_mcs, stream=None) -> None:
     """The batch sweep without any allocation (static device workspace): for
     callers that may not allocate device memory when they run work.  Every
-    context must use `stream` (default: torch's current stream)."""
+    context must use `stream` (default: torch's current stream).  With no
+    contexts it only sets up the current device (the start-up call)."""
     if stream is None:
         try:
             import torch
@@ -550,10 +556,3 @@ def asep_batch_sweep_static(ctxs, n_mcs, stream=None) -> None:
     n = np.ascontiguousarray(np.broadcast_to(np.asarray(n_mcs, dtype=np.uint64), (len(ctxs),)))
     _check(lib().asep_batch_sweep_static(_ctx_array(ctxs), _ptr(n, ctypes.c_uint64), len(ctxs), stream or None))
 
-
-def width2_exact(L: int, sum_h: int, sum_h2_lo: int, sum_h2_hi: int):
-    """(L sum h^2 - (sum h)^2) / L^2 as an exact fraction (host check helper)."""
-    from fractions import Fraction
-
-    s2 = (int(sum_h2_hi) << 64) | int(sum_h2_lo)
-    return Fraction(L * s2 - int(sum_h) ** 2, L * L)

@@ -62,6 +62,7 @@ struct asep_ctx {
   uint32_t fault = ASEP_FAULT_NONE;  // injected fault (asep_inject_fault)
   size_t smem = 0;
   uint32_t max_sweeps_per_launch = 1;
+  uint32_t launch_sweeps = 0;      // caller's cap on sweeps per launch (0 = none)
   uint64_t launches = 0;
   std::string err;
 };
@@ -91,6 +92,16 @@ uint32_t log2u(uint64_t x) {
   uint32_t k = 0;
   while ((1ull << k) < x) ++k;
   return k;
+}
+
+// Sweeps one launch (or one batch step) may run for this context: the hop
+// counters' bound for the domain schedule, 2^20 otherwise, and the caller's
+// cap from asep_set_launch_sweeps when set.
+uint32_t sweeps_cap(const asep_ctx* c) {
+  uint32_t cap = c->p.schedule == ASEP_SCHED_DOMAIN ? std::min<uint32_t>(c->max_sweeps_per_launch, 1u << 20)
+                                                    : (1u << 20);
+  if (c->launch_sweeps) cap = std::min(cap, c->launch_sweeps);
+  return cap;
 }
 
 bool thr_ok(uint32_t t) { return t == ASEP_ALWAYS || (t & 0xFFFu) == 0; }
@@ -729,7 +740,7 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
   uint64_t done = 0;
   while (done < n_mcs) {
     uint64_t n = n_mcs - done;
-    const uint32_t cap = ctx->p.schedule == ASEP_SCHED_DOMAIN ? ctx->max_sweeps_per_launch : (1u << 20);
+    const uint32_t cap = sweeps_cap(ctx);
     if (n > cap) n = cap;
     cudaError_t e;
     if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster == kStreamTier) {
@@ -1157,8 +1168,7 @@ int asep_batch_sweep(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs
   for (;;) {
     bool any = false;
     for (uint32_t j = 0; j < n; ++j) {
-      step[j] = static_cast<uint32_t>(std::min<uint64_t>(left[j], std::min<uint64_t>(ctxs[j]->max_sweeps_per_launch,
-                                                                                       1u << 20)));
+      step[j] = static_cast<uint32_t>(std::min<uint64_t>(left[j], sweeps_cap(ctxs[j])));
       any = any || step[j] > 0;
     }
     if (!any) break;
@@ -1181,7 +1191,7 @@ int asep_batch_graph(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs
   std::vector<uint32_t> step(n);
   std::vector<uintptr_t> key;
   for (uint32_t j = 0; j < n; ++j) {
-    if (n_mcs[j] > std::min<uint64_t>(ctxs[j]->max_sweeps_per_launch, 1u << 20))
+    if (n_mcs[j] > sweeps_cap(ctxs[j]))
       return bfail(b, ASEP_ERR_INVALID, "context %u: a graph step is at most one launch of sweeps", j);
     step[j] = static_cast<uint32_t>(n_mcs[j]);
     key.push_back(reinterpret_cast<uintptr_t>(ctxs[j]));
@@ -1296,6 +1306,12 @@ int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
     ctx->err = msg;
   }
   return rc;
+}
+
+int asep_set_launch_sweeps(asep_ctx* ctx, uint32_t max_sweeps) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  ctx->launch_sweeps = max_sweeps;
+  return ASEP_OK;
 }
 
 int asep_currents(asep_ctx* ctx, int64_t* out, size_t n) {
@@ -1436,8 +1452,7 @@ int static_scratch(unsigned char** out) {
 extern "C" {
 
 int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32_t n, void* stream) {
-  if (n == 0) return ASEP_OK;
-  if (!ctxs || !n_mcs) return fail(nullptr, ASEP_ERR_INVALID, "ctxs or n_mcs is NULL");
+  if (n > 0 && (!ctxs || !n_mcs)) return fail(nullptr, ASEP_ERR_INVALID, "ctxs or n_mcs is NULL");
   if (n > kStaticMaxJobs)
     return fail(nullptr, ASEP_ERR_INVALID, "%u contexts exceed the static batch limit of %u", n, kStaticMaxJobs);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1460,6 +1475,13 @@ int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32
   DomainLaunch* d_jobs = reinterpret_cast<DomainLaunch*>(scratch);
   uint32_t* d_items = reinterpret_cast<uint32_t*>(scratch + kStaticJobsBytes);
   uint32_t* d_queue = reinterpret_cast<uint32_t*>(scratch + kStaticJobsBytes + kStaticItemsBytes);
+  if (n == 0) {
+    // start-up call: the array's address is known now; load the batch kernels
+    // and size their local memory with empty launches
+    const cudaError_t e = warm_batch_kernels(d_queue, st);
+    if (e != cudaSuccess) return fail(nullptr, ASEP_ERR_CUDA, "static batch warm-up: %s", cudaGetErrorString(e));
+    return ASEP_OK;
+  }
 
   DomainLaunch* jobs = g_static_jobs;
   uint32_t* items = g_static_items;
@@ -1473,8 +1495,7 @@ int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32
     uint64_t cost[kStaticMaxJobs];
     for (uint32_t j = 0; j < n; ++j) {
       const asep_ctx* c = ctxs[j];
-      const uint32_t step = static_cast<uint32_t>(std::min<uint64_t>(left[j], std::min<uint64_t>(
-                                                                                 c->max_sweeps_per_launch, 1u << 20)));
+      const uint32_t step = static_cast<uint32_t>(std::min<uint64_t>(left[j], sweeps_cap(c)));
       jobs[j] = domain_desc(c, step);
       threads = std::max(threads, c->threads);
       cost[j] = static_cast<uint64_t>(step) * c->spc * c->L * c->planes;

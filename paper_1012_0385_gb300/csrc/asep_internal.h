@@ -218,6 +218,8 @@ cudaError_t launch_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs, cuda
 cudaError_t launch_set_clock(Clock* clock, uint64_t sweep, uint32_t next_time, cudaStream_t st);
 // Occupancy of the persistent kernel (CTAs per SM) for a block size and shared memory.
 int batch_ctas_per_sm(uint32_t threads, size_t smem);
+// Empty launches of the batch kernels (code loaded, local memory sized); `queue` is a device counter.
+cudaError_t warm_batch_kernels(uint32_t* queue, cudaStream_t st);
 cudaError_t launch_serial(const SerialLaunch& a, uint32_t model, uint32_t dis, cudaStream_t st);
 cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t* sink, cudaStream_t st);
 cudaError_t launch_attempt_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t p, uint32_t q,

@@ -1080,6 +1080,22 @@ cudaError_t launch_advance_batch(const DomainLaunch* jobs, uint32_t n_jobs, cuda
   return cudaGetLastError();
 }
 
+// One empty launch of each batch kernel (no items, no jobs) on `st`: loads
+// the kernels' code on the current device and lets the driver size their
+// per-thread local memory, so later batch steps start without either.
+cudaError_t warm_batch_kernels(uint32_t* queue, cudaStream_t st) {
+  (void)cudaGetLastError();
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+  k_batch<512><<<1, 32, 0, st>>>(nullptr, nullptr, 0u, queue);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+  k_batch<1024><<<1, 32, 0, st>>>(nullptr, nullptr, 0u, queue);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_advance_batch<<<1, 32, 0, st>>>(nullptr, 0u);
+  return cudaGetLastError();
+}
+
 int batch_ctas_per_sm(uint32_t threads, size_t smem) {
   int n = 0;
   cudaError_t e;

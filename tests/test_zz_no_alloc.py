@@ -1,11 +1,15 @@
 """The allocation-free batch sweep (asep_batch_sweep_static).
 
 It is for callers that may not allocate device memory when they run work;
-its work queue lives in a static device array of the library.  The test runs
+its work queue lives in a static device array of the library.  The tests run
 the same contexts through it and through the batch object's sweep
-(asep_batch_sweep, which owns allocated workspace) and requires bit-identical
+(asep_batch_sweep, which owns allocated workspace) and require bit-identical
 lattices, height tables, counters and sweep indices after each of two calls
-in a row.  It also checks that requests beyond the array's limits are
+in a row -- once with one launch step per call and once with several (a cap
+on the sweeps per launch), so the step loop that reuses the static
+descriptors and items runs too.  They check that, after the start-up call and
+one call, a further call leaves the device's free memory and PyTorch's
+allocated bytes unchanged, and that requests beyond the array's limits are
 rejected.  The file is collected last so that a run stopping at the first
 failure has run every other test first.
 """
@@ -42,6 +46,7 @@ def _device():
 
     build.build()
     torch.cuda.set_device(0)
+    A.asep_batch_sweep_static([], [])  # the start-up call: set-up of this device only
 
 
 def snapshot(ctx):
@@ -50,9 +55,11 @@ def snapshot(ctx):
     return dict(words=words, sweep=sweep, sh=sh, sh2=sh2, cnt=A.asep_counters(ctx))
 
 
-def test_static_batch_matches_batch_sweep_on_two_calls():
+def compare_on_two_calls(launch_sweeps):
     ref = [A.asep_create(A.make_params(**kw), sample_times=t) for kw, t in MIX]
     got = [A.asep_create(A.make_params(**kw), sample_times=t) for kw, t in MIX]
+    for c in ref + got:
+        A.asep_set_launch_sweeps(c, launch_sweeps)
     with A.asep_batch_create(max_jobs=16, max_items=4096) as b:
         for k, n_mcs in enumerate(CALLS):
             A.asep_batch_sweep(b, ref, n_mcs)
@@ -63,6 +70,30 @@ def test_static_batch_matches_batch_sweep_on_two_calls():
                     assert np.array_equal(a[key], c[key]), (k, i, key)
                 assert a["sweep"] == c["sweep"] == sum(call[i] for call in CALLS[: k + 1])
     for c in ref + got:
+        c.close()
+
+
+def test_static_batch_matches_batch_sweep_on_two_calls():
+    compare_on_two_calls(0)  # automatic bound: one launch step per call
+
+
+def test_static_batch_matches_batch_sweep_with_several_steps_per_call():
+    compare_on_two_calls(7)  # at most 7 sweeps per step: 2 to 5 steps per call
+
+
+def test_static_batch_allocates_nothing():
+    import torch
+
+    ctxs = [A.asep_create(A.make_params(**kw), sample_times=t) for kw, t in MIX]
+    A.asep_batch_sweep_static(ctxs, CALLS[0])
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    A.asep_batch_sweep_static(ctxs, CALLS[1])
+    torch.cuda.synchronize()
+    free1, alloc1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    assert (free1, alloc1) == (free0, alloc0), (free0 - free1, alloc1 - alloc0)
+    assert A.asep_get_info(ctxs[0])["sweep"] == sum(call[0] for call in CALLS)
+    for c in ctxs:
         c.close()
 
 

@@ -40,6 +40,7 @@ SAMPLES = 256
 N_MCS = 1 << 14
 P_RATE, Q_RATE = 0.75, 0.25
 SEED = 1
+REF_STEP_S = 5.0  # CPU seconds per timed step of the reference arm
 # Algorithmic int32 lane operations per attempt of the domain kernel: a
 # quarter of one Philox4x32-10 call (10 rounds x [2 wide multiplies + 2
 # three-input XORs] = 40) plus the update (slot and row decode 2, address 1,
@@ -177,33 +178,44 @@ def cpu_oracle_sample(target_s: float, n_mcs_cap: int = N_MCS):
     oracle.run(P, n, [t for t in log_times(N_MCS) if t <= n], threads=cores, samples=range(k))
     dt = time.perf_counter() - t0
     return {"value": k * L_SITES * n / dt, "unit": "attempts/s", "cores": cores, "kind": "oracle",
-            "value_per_core": k * L_SITES * n / dt / cores,
+            "value_per_core": k * L_SITES * n / dt / cores, "seconds": dt, "attempts": k * L_SITES * n,
             "sample": f"{k} of 256 samples x {n} of 2^14 sweeps (init + sweeps + W^2 at the log times), "
                       f"{dt:.1f} s on {cores} host threads"}
 
 
+def workload_config(world: int) -> dict:
+    """The benchmarked workload, identical in both arms' JSON lines."""
+    from paper_1012_0385_gb300.sampling import log_times
+
+    return {"workload": WORKLOAD_NAME, "L": L_SITES, "samples_per_gpu": SAMPLES, "n_mcs": N_MCS,
+            "sample_times": len(log_times(N_MCS)), "domain_sites": DOMAIN,
+            "schedule": "two-phase Poisson-domain RSU", "rates": {"p": P_RATE, "q": Q_RATE},
+            "observables": "W^2 at the log times (hop counters off)",
+            "l2": "flushed between steps (256 MB write outside the timed region)",
+            "parallelism": f"replicas x{world} (disjoint sample ranges)"}
+
+
 def run_reference(args):
+    """The oracle as it stands, on the host cores: each timed step is one
+    bounded sample of the workload (REF_STEP_S seconds of CPU work: a subset
+    of the samples over a prefix of the sweeps, whole path), and the rate is
+    the attempts those steps made over their time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    per_step = 8.0
     for _ in range(args.warmup):
         cpu_oracle_sample(0.5)
-    vals, secs = [], []
-    for _ in range(args.steps):
-        r = cpu_oracle_sample(per_step)
-        vals.append(r["value"])
-        secs.append(L_SITES * SAMPLES * N_MCS / r["value"])
-    value = statistics.mean(vals)
+    runs = [cpu_oracle_sample(REF_STEP_S) for _ in range(args.steps)]
+    secs = [r["seconds"] for r in runs]
+    value = sum(r["attempts"] for r in runs) / sum(secs)
+    cores = runs[-1]["cores"]
     line = {"metric": "site-update attempts/s", "value": value, "unit": "attempts/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": WORKLOAD_NAME, "L": L_SITES, "samples": SAMPLES, "n_mcs": N_MCS,
-                       "domain_sites": DOMAIN, "schedule": "two-phase Poisson-domain RSU",
-                       "note": "ms_per_step extrapolates the sampled oracle rate to one full step"},
-            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": r["cores"], "kind": "oracle",
-                             "value_per_core": value / r["cores"], "sample": r["sample"]},
+            "impl": "reference", "config": workload_config(args.gpus),
+            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": cores, "kind": "oracle",
+                             "value_per_core": value / cores,
+                             "sample": "each step: " + runs[-1]["sample"] + " (the oracle's schedule replay)"},
             "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -329,14 +341,9 @@ def run_ours(args):
             "metric": "site-update attempts/s", "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "L": L_SITES, "samples_per_gpu": SAMPLES, "n_mcs": N_MCS,
-                       "sample_times": len(times), "domain_sites": DOMAIN,
-                       "schedule": "two-phase Poisson-domain RSU", "rates": {"p": P_RATE, "q": Q_RATE},
-                       "observables": "W^2 at the log times (hop counters off)",
-                       "l2": "flushed between steps (256 MB write outside the timed region)",
-                       "plan": ({"cluster": plan.cluster, "samples_per_group": plan.samples_per_group}
-                                if plan else "default"),
-                       "parallelism": f"replicas x{world} (disjoint sample ranges)"},
+            "config": workload_config(world),
+            "plan": ({"cluster": plan.cluster, "samples_per_group": plan.samples_per_group}
+                     if plan else "default"),
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": _traffic_from_profile(),
                          "kernel": "k_domain<ring>", "kernel_ms": kernel_ms,

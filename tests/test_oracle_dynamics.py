@@ -204,7 +204,7 @@ def test_two_lane_replay_matches_exact(oracle_mod, schedule):
 
 @pytest.mark.parametrize("model,schedule,dis", [
     (0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (1, 1, 2), (0, 2, 0), (0, 2, 1), (1, 2, 2), (1, 2, 0), (1, 2, 4),
-    (1, 1, 4)])
+    (1, 1, 4), (0, 0, 3), (1, 0, 4)])
 def test_particle_number_conserved(oracle_mod, model, schedule, dis):
     th = oracle_mod.threshold
     P = oracle_mod.Params(model=model, schedule=schedule, L=1024, D=64, samples_per_real=3, seed=9,
@@ -414,7 +414,7 @@ def test_independent_pq_class_draws(oracle_mod):
     assert not np.array_equal(two[:, :W], two[:, W:])
 
 
-@pytest.mark.parametrize("schedule", ["sca", "serial"])
+@pytest.mark.parametrize("schedule", ["sca", "serial", "domain"])
 def test_independent_pq_classes_rate_placement(oracle_mod, schedule):
     """Independent classes: right hops across (i, i+1) use p_i from the p
     plane, left hops q_{i+1} from the q plane.  Chi-square against the exact
@@ -423,8 +423,8 @@ def test_independent_pq_classes_rate_placement(oracle_mod, schedule):
     L = 8
     pf, ps, qf, qs = 0.9, 0.2, 0.7, 0.1
     th = oracle_mod.threshold
-    sched = oracle_mod.SCHED_SCA if schedule == "sca" else oracle_mod.SCHED_SERIAL
-    P = oracle_mod.Params(L=L, schedule=sched, samples_per_real=S_DIST, seed=29, p_thr=th(pf), q_thr=th(qf),
+    sched = {"sca": oracle_mod.SCHED_SCA, "serial": oracle_mod.SCHED_SERIAL, "domain": oracle_mod.SCHED_DOMAIN}[schedule]
+    P = oracle_mod.Params(L=L, D=2, schedule=sched, samples_per_real=S_DIST, seed=29, p_thr=th(pf), q_thr=th(qf),
                           dis_kind=oracle_mod.DIS_BIMODAL_PQ, dis_a_thr=th(0.5), dis_b_thr=th(ps),
                           dis_c_thr=th(qs), dis_seed=11)
     mask = oracle_mod.disorder(P)
@@ -436,7 +436,7 @@ def test_independent_pq_classes_rate_placement(oracle_mod, schedule):
 
     def op(pv, qv):
         m = ex.RingModel(L, L // 2, pv, qv)
-        return m.sca_sweep() if schedule == "sca" else m.rsu_sweep()
+        return {"sca": m.sca_sweep, "serial": m.rsu_sweep, "domain": lambda: m.domain_sweep(2)}[schedule]()
 
     sp = ex.RingModel(L, L // 2, pf, qf).sp
     counts = histogram(sp, _replay_hist(oracle_mod, P, 2, mask=mask))
@@ -540,7 +540,7 @@ def test_two_lane_sca_replay_matches_exact(oracle_mod):
         assert chi2_pvalue(counts, m.sp.flat_alt() @ np.linalg.matrix_power(wrong, 2)) < 1e-6
 
 
-@pytest.mark.parametrize("schedule", ["sca", "serial"])
+@pytest.mark.parametrize("schedule", ["sca", "serial", "domain"])
 def test_two_lane_crossing_classes_match_exact(oracle_mod, schedule):
     """The paper's two-lane crossing (sec. 3): every site may cross, A -> B
     with u_i and B -> A with v_i, each 0.8 unless the site is marked (0.2) in
@@ -549,8 +549,8 @@ def test_two_lane_crossing_classes_match_exact(oracle_mod, schedule):
     L, p = 4, 0.5
     th = oracle_mod.threshold
     uf, us = 0.8, 0.2
-    sched = oracle_mod.SCHED_SCA if schedule == "sca" else oracle_mod.SCHED_SERIAL
-    P = oracle_mod.Params(model=oracle_mod.MODEL_TWO_LANE, L=L, schedule=sched, samples_per_real=S_DIST, seed=41,
+    sched = {"sca": oracle_mod.SCHED_SCA, "serial": oracle_mod.SCHED_SERIAL, "domain": oracle_mod.SCHED_DOMAIN}[schedule]
+    P = oracle_mod.Params(model=oracle_mod.MODEL_TWO_LANE, L=L, D=1, schedule=sched, samples_per_real=S_DIST, seed=41,
                           p_thr=th(p), q_thr=th(p), dis_kind=oracle_mod.DIS_CROSSING, dis_a_thr=th(0.5),
                           dis_b_thr=th(uf), dis_c_thr=th(us), dis_seed=5)
     mask = oracle_mod.disorder(P)
@@ -563,7 +563,7 @@ def test_two_lane_crossing_classes_match_exact(oracle_mod, schedule):
 
     def op(uu, vv):
         m = ex.TwoLaneModel(L, L, p, p, range(L), uu, vv)
-        return m.sca_sweep() if schedule == "sca" else m.rsu_sweep(), m.sp
+        return {"sca": m.sca_sweep, "serial": m.rsu_sweep, "domain": lambda: m.domain_sweep(1)}[schedule](), m.sp
 
     A, sp = op(u, v)
     counts = histogram(sp, _replay_hist(oracle_mod, P, 2, mask=mask))

@@ -103,21 +103,22 @@ extern "C" {
 #define ASEP_DIS_NONE 0u
 #define ASEP_DIS_BIMODAL 1u /* dis_a = Q, dis_b = p_slow, dis_c = q_slow     */
 #define ASEP_DIS_TURNING 2u /* two lanes: dis_a = site density, dis_b = omega */
-/* Ring, SCA or serial schedule: independent slow classes for right and left
+/* Ring model: independent slow classes for right and left
  * hops (sec. 3, Eq. bimodal; the paper tags reduced forward and backward
  * rates with separate bits, the same distribution for q_i as for p_i):
  * dis_a = Q for both, dis_b = p_slow, dis_c = q_slow.  Plane 0 of a
  * realization holds the p classes (the ASEP_DIS_BIMODAL draw), plane 1 the q
- * classes (call 1 of the disorder stream).  Not under the domain schedule. */
+ * classes (call 1 of the disorder stream).  Every schedule. */
 #define ASEP_DIS_BIMODAL_PQ 3u
-/* Two lanes, SCA or serial schedule: the paper's crossing probabilities
+/* Two lanes: the paper's crossing probabilities
  * (sec. 3): a particle may change lanes at every site, A -> B with u_i and
  * B -> A with v_i, quenched with the distribution of Eq. bimodal: dis_a =
  * fraction of marked sites (for u and v independently), dis_b = the crossing
  * probability of unmarked sites (0.8 in the paper), dis_c = of marked ones
  * (0.2).  Plane 0 marks u, plane 1 (call 1 of the disorder stream) marks v.
- * Same draws per candidate site as ASEP_DIS_TURNING.  Not under the domain
- * schedule. */
+ * Same draws per candidate site as ASEP_DIS_TURNING.  Every schedule (the
+ * domain schedule's lane-change pass uses u_i for a particle in lane A, v_i
+ * for one in lane B). */
 #define ASEP_DIS_CROSSING 4u
 
 #define ASEP_INIT_FLAT_ALT 0u       /* 1010...: site i occupied iff i even (paper sec. 2.1) */

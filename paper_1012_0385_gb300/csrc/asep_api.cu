@@ -208,12 +208,8 @@ int validate(const asep_params* p, asep_ctx* ctx) {
   if (p->dis_kind > ASEP_DIS_CROSSING) return fail(ctx, ASEP_ERR_INVALID, "unknown dis_kind %u", p->dis_kind);
   if (p->dis_kind == ASEP_DIS_CROSSING && p->model != ASEP_MODEL_TWO_LANE)
     return fail(ctx, ASEP_ERR_INVALID, "crossing probabilities are defined for the two-lane model");
-  if (p->dis_kind == ASEP_DIS_CROSSING && p->schedule == ASEP_SCHED_DOMAIN)
-    return fail(ctx, ASEP_ERR_INVALID, "crossing at every site runs under the SCA and serial schedules");
   if ((p->dis_kind == ASEP_DIS_BIMODAL || p->dis_kind == ASEP_DIS_BIMODAL_PQ) && p->model != ASEP_MODEL_RING)
     return fail(ctx, ASEP_ERR_INVALID, "bimodal disorder is defined for the ring model");
-  if (p->dis_kind == ASEP_DIS_BIMODAL_PQ && p->schedule == ASEP_SCHED_DOMAIN)
-    return fail(ctx, ASEP_ERR_INVALID, "independent p and q classes run under the SCA and serial schedules");
   if (p->dis_kind == ASEP_DIS_TURNING && p->model != ASEP_MODEL_TWO_LANE)
     return fail(ctx, ASEP_ERR_INVALID, "turning sites are defined for the two-lane model");
   if (p->init_kind > ASEP_INIT_BERNOULLI_HALF) return fail(ctx, ASEP_ERR_INVALID, "unknown init_kind %u", p->init_kind);
@@ -484,7 +480,7 @@ DomainLaunch domain_desc(const asep_ctx* ctx, uint32_t n) {
   a.Gc = ctx->Gc;
   {
     // every warp inside one sample, and the idle realign buffer holds 5 words per column
-    const uint32_t np = (ctx->p.model == ASEP_MODEL_TWO_LANE ? 2u : 1u) + (ctx->p.dis_kind != ASEP_DIS_NONE ? 1u : 0u);
+    const uint32_t np = (ctx->p.model == ASEP_MODEL_TWO_LANE ? 2u : 1u) + dis_planes(ctx->p.dis_kind);
     a.lane_sort = (ctx->cluster <= 1 && ctx->G % 32 == 0 && np * (ctx->R2 + 1) >= 5) ? 1u : 0u;
   }
   a.rates = rates(ctx);
@@ -791,7 +787,8 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
     // of the streamed domain schedule with turning sites) and the clock
     uint32_t sweep_launches = 1;
     if (ctx->cluster == kStreamTier)
-      sweep_launches = (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->p.dis_kind == ASEP_DIS_TURNING) ? 3u : 2u;
+      sweep_launches = (ctx->p.schedule == ASEP_SCHED_DOMAIN &&
+                        (ctx->p.dis_kind == ASEP_DIS_TURNING || ctx->p.dis_kind == ASEP_DIS_CROSSING)) ? 3u : 2u;
     ctx->launches += sweep_launches + 1;
     advance_host(ctx, n);
     done += n;

@@ -59,13 +59,19 @@ __device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& 
     o0 += laneB * PWb;
     okR = !laneB && (a.rates.p_always || r < a.rates.p);  // lane A: 10 -> 01
     okL = laneB && (a.rates.q_always || r < a.rates.q);   // lane B: 01 -> 10
-  } else if (DIS == kDisBimodal) {
+  } else if (DIS == kDisBimodal || DIS == kDisBimodalPQ) {
     const uint32_t c0 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0);
     const uint32_t c1 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0 + cpb);
     const uint32_t pc = __funnelshift_r(c0, c1, r);  // bit0: class of site i, bit1: of site i+1
+    uint32_t qc = pc;
+    if (DIS == kDisBimodalPQ) {  // left hops take the class of site i+1 from the second quenched plane
+      const uint32_t d0 = *reinterpret_cast<const uint32_t*>(cur + 2u * PWb + o0);
+      const uint32_t d1 = *reinterpret_cast<const uint32_t*>(cur + 2u * PWb + o0 + cpb);
+      qc = __funnelshift_r(d0, d1, r);
+    }
     const uint32_t u = r & kAcceptMask;
     okR = u < ((pc & 1u) ? a.rates.p_slow : a.rates.p);
-    okL = u < ((pc & 2u) ? a.rates.q_slow : a.rates.q);
+    okL = u < ((qc & 2u) ? a.rates.q_slow : a.rates.q);
   } else {
     okR = a.rates.p_always || r < a.rates.p;
     okL = a.rates.q_always || r < a.rates.q;

@@ -293,24 +293,32 @@ __device__ __forceinline__ void mirror_out(uint32_t* cur, const DomainLaunch& a,
   }
 }
 
-// Lane changes of the two-lane model at the turning sites of one column.
+// Lane changes of the two-lane model in one column: at every turning site
+// (DIS = kDisTurning: the sites of the turning plane, probability omega both
+// ways) or every site (DIS = kDisCrossing: A -> B with u_i, B -> A with v_i,
+// the slow value at sites marked in the u and v planes) where exactly one
+// lane is occupied.
+template <uint32_t DIS>
 __device__ __forceinline__ void turning(uint32_t* cur, const DomainLaunch& a, uint32_t PW, uint64_t s,
                                         uint32_t R_cur, const Lane& ln, uint2 key, Cnt& cnt) {
   uint32_t* A = cur;
   uint32_t* B = cur + PW;
-  const uint32_t* M = cur + 2 * PW;
+  const uint32_t* M = cur + 2 * PW;  // turning plane, or the u marks (the v marks follow)
   const uint64_t L = a.geo.L;
   for (uint32_t r = 0; r < a.R2; ++r) {
     const uint32_t idx = r * a.Cp + ln.c;
     uint32_t av = A[idx], bv = B[idx];
-    uint32_t e = M[idx] & (av ^ bv);
+    uint32_t e = DIS == kDisCrossing ? (av ^ bv) : M[idx] & (av ^ bv);
+    const uint32_t um = DIS == kDisCrossing ? M[idx] : 0u, vm = DIS == kDisCrossing ? M[PW + idx] : 0u;
     while (e) {
       const uint32_t b = __ffs(e) - 1;
       e &= e - 1;
       uint64_t site = static_cast<uint64_t>(R_cur) + 32ull * (ln.g * a.R2 + r) + b;
       if (site >= L) site -= L;
       const uint4 x = philox10(ctr_of(s, kTagTurn, 0, ln.n_glob, static_cast<uint32_t>(site >> 2)), key);
-      if (accept(pick(x, static_cast<uint32_t>(site & 3u)), a.rates.omega)) {
+      uint32_t t = a.rates.omega;
+      if (DIS == kDisCrossing && ((((av >> b) & 1u) ? um : vm) >> b) & 1u) t = a.rates.omega_slow;
+      if (accept(pick(x, static_cast<uint32_t>(site & 3u)), t)) {
         const uint32_t bit = 1u << b;
         if (av & bit) ++cnt.c;
         else ++cnt.d;
@@ -408,7 +416,8 @@ __device__ void record_extras(const uint32_t* cur, const DomainLaunch& a, uint32
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
 __device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group, unsigned char* smem_raw) {
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
-  constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
+  constexpr uint32_t NQ = dis_planes(DIS);
+  constexpr uint32_t NP = NOCC + NQ;
   const uint32_t R2 = a.R2, Cp = a.Cp, G = a.G, W = a.geo.W;
   const uint32_t PW = (R2 + 1) * Cp;  // R2 rows + the mirror row
   const uint64_t L = a.geo.L;
@@ -442,7 +451,7 @@ __device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group,
       const uint32_t sl = idx / W, w = idx - sl * W;
       const uint32_t smp = first + sl;
       const uint32_t v = p < NOCC ? a.state[(static_cast<size_t>(smp) * a.geo.planes + p) * W + w]
-                                  : a.mask[static_cast<size_t>(smp / a.geo.samples_per_real) * W + w];
+                                  : a.mask[(static_cast<size_t>(smp / a.geo.samples_per_real) * NQ + (p - NOCC)) * W + w];
       bufA[p * PW + (w & (R2 - 1)) * Cp + sl * G + (w >> a.logR2)] = v;
     }
   }
@@ -471,8 +480,8 @@ __device__ __forceinline__ void run_group(const DomainLaunch& a, uint32_t group,
     __syncthreads();
     if (ln.active) mirror_out<NOCC>(cur, a, PW, ln);
     __syncthreads();
-    if (MODEL == kTwoLane && DIS == kDisTurning) {
-      if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);
+    if (MODEL == kTwoLane && (DIS == kDisTurning || DIS == kDisCrossing)) {
+      if (ln.active) turning<DIS>(cur, a, PW, s, R_cur, ln, key, cnt);
       __syncthreads();
     }
     if (rec < a.n_times && a.times[rec] == s + 1) {
@@ -519,10 +528,14 @@ __global__ void __launch_bounds__(1024) k_domain(const DomainLaunch a) {
 __device__ __forceinline__ void run_group_any(const DomainLaunch& a, uint32_t group, unsigned char* smem) {
   if (a.model == kTwoLane) {
     if (a.dis == kDisTurning) run_group<kTwoLane, kDisTurning, true, 0>(a, group, smem);
+    else if (a.dis == kDisCrossing) run_group<kTwoLane, kDisCrossing, true, 0>(a, group, smem);
     else run_group<kTwoLane, kDisNone, true, 0>(a, group, smem);
   } else if (a.dis == kDisBimodal) {
     if (a.count_hops) run_group<kRing, kDisBimodal, true, 0>(a, group, smem);
     else run_group<kRing, kDisBimodal, false, 0>(a, group, smem);
+  } else if (a.dis == kDisBimodalPQ) {
+    if (a.count_hops) run_group<kRing, kDisBimodalPQ, true, 0>(a, group, smem);
+    else run_group<kRing, kDisBimodalPQ, false, 0>(a, group, smem);
   } else if (a.Cp == 256) {
     if (a.count_hops) run_group<kRing, kDisNone, true, 256>(a, group, smem);
     else run_group<kRing, kDisNone, false, 256>(a, group, smem);
@@ -728,7 +741,8 @@ __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long cta_sums[4];
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
-  constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
+  constexpr uint32_t NQ = dis_planes(DIS);
+  constexpr uint32_t NP = NOCC + NQ;
   cg::cluster_group cl = cg::this_cluster();
   const uint32_t my_rank = cl.block_rank(), NC = cl.num_blocks();
   const uint32_t R2 = a.R2, Cp = a.Cp, G = a.G, W = a.geo.W, Gc = a.Gc;
@@ -762,7 +776,7 @@ __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
   for (uint32_t p = 0; p < NP; ++p) {
     for (uint32_t w = w_lo + threadIdx.x; w < w_hi; w += blockDim.x) {
       const uint32_t v = p < NOCC ? a.state[(static_cast<size_t>(sample) * a.geo.planes + p) * W + w]
-                                  : a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + w];
+                                  : a.mask[(static_cast<size_t>(sample / a.geo.samples_per_real) * NQ + (p - NOCC)) * W + w];
       const uint32_t wl = w - w_lo;
       bufA[p * PW + (wl & (R2 - 1)) * Cp + (wl >> a.logR2)] = v;
     }
@@ -801,8 +815,8 @@ __global__ void __launch_bounds__(1024) k_cluster(const DomainLaunch a) {
       }
     }
     __syncthreads();
-    if (MODEL == kTwoLane && DIS == kDisTurning) {
-      if (ln.active) turning(cur, a, PW, s, R_cur, ln, key, cnt);
+    if (MODEL == kTwoLane && (DIS == kDisTurning || DIS == kDisCrossing)) {
+      if (ln.active) turning<DIS>(cur, a, PW, s, R_cur, ln, key, cnt);
     }
     cl.sync();
     if (rec < a.n_times && a.times[rec] == s + 1) {
@@ -919,7 +933,7 @@ cudaError_t launch_philox_bench(uint32_t blocks, uint32_t threads, uint32_t call
 
 size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp, uint32_t ptab_n, uint32_t threads) {
   const uint32_t nocc = model == kTwoLane ? 2u : 1u;
-  const uint32_t np = nocc + (dis != kDisNone ? 1u : 0u);
+  const uint32_t np = nocc + dis_planes(dis);
   return 2ull * np * (R2 + 1ull) * Cp * 4ull + ((ptab_n + 1ull) & ~1ull) * 4ull + (32ull + threads) * 8ull;
 }
 
@@ -960,9 +974,14 @@ cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, 
   if (a.model == kRing && a.dis == kDisBimodal)
     return count ? launch_domain_t<kRing, kDisBimodal, true>(a, threads, smem, st)
                  : launch_domain_t<kRing, kDisBimodal, false>(a, threads, smem, st);
+  if (a.model == kRing && a.dis == kDisBimodalPQ)
+    return count ? launch_domain_cp<kRing, kDisBimodalPQ, true, 0>(a, threads, smem, st)
+                 : launch_domain_cp<kRing, kDisBimodalPQ, false, 0>(a, threads, smem, st);
   if (a.model == kTwoLane && a.dis == kDisNone) return launch_domain_t<kTwoLane, kDisNone, true>(a, threads, smem, st);
   if (a.model == kTwoLane && a.dis == kDisTurning)
     return launch_domain_t<kTwoLane, kDisTurning, true>(a, threads, smem, st);
+  if (a.model == kTwoLane && a.dis == kDisCrossing)
+    return launch_domain_cp<kTwoLane, kDisCrossing, true, 0>(a, threads, smem, st);
   return cudaErrorInvalidValue;
 }
 
@@ -1050,18 +1069,27 @@ cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem,
   if (a.model == kRing && a.dis == kDisBimodal)
     return count ? launch_cluster_t<kRing, kDisBimodal, true>(a, threads, smem, st)
                  : launch_cluster_t<kRing, kDisBimodal, false>(a, threads, smem, st);
+  if (a.model == kRing && a.dis == kDisBimodalPQ)
+    return count ? launch_cluster_t<kRing, kDisBimodalPQ, true>(a, threads, smem, st)
+                 : launch_cluster_t<kRing, kDisBimodalPQ, false>(a, threads, smem, st);
   if (a.model == kTwoLane && a.dis == kDisNone) return launch_cluster_t<kTwoLane, kDisNone, true>(a, threads, smem, st);
   if (a.model == kTwoLane && a.dis == kDisTurning)
     return launch_cluster_t<kTwoLane, kDisTurning, true>(a, threads, smem, st);
+  if (a.model == kTwoLane && a.dis == kDisCrossing)
+    return launch_cluster_t<kTwoLane, kDisCrossing, true>(a, threads, smem, st);
   return cudaErrorInvalidValue;
 }
 
 int cluster_fits(uint32_t model, uint32_t dis, uint32_t cluster, uint32_t threads, size_t smem) {
   if (model == kRing && dis == kDisNone) return cluster_fits_t<kRing, kDisNone, true>(cluster, threads, smem);
   if (model == kRing && dis == kDisBimodal) return cluster_fits_t<kRing, kDisBimodal, true>(cluster, threads, smem);
+  if (model == kRing && dis == kDisBimodalPQ)
+    return cluster_fits_t<kRing, kDisBimodalPQ, true>(cluster, threads, smem);
   if (model == kTwoLane && dis == kDisNone) return cluster_fits_t<kTwoLane, kDisNone, true>(cluster, threads, smem);
   if (model == kTwoLane && dis == kDisTurning)
     return cluster_fits_t<kTwoLane, kDisTurning, true>(cluster, threads, smem);
+  if (model == kTwoLane && dis == kDisCrossing)
+    return cluster_fits_t<kTwoLane, kDisCrossing, true>(cluster, threads, smem);
   return 0;
 }
 

@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   constexpr uint32_t NOCC = MODEL == kTwoLane ? 2u : 1u;
-  constexpr uint32_t NP = NOCC + (DIS != kDisNone ? 1u : 0u);
+  constexpr uint32_t NQ = dis_planes(DIS);
+  constexpr uint32_t NP = NOCC + NQ;
   const uint32_t R2 = a.R2, Cp = a.Cp, C = a.C, W = a.geo.W, D = a.D;
   const uint32_t sample = blockIdx.x / tiles, tile = blockIdx.x - sample * tiles;
   const uint32_t g0 = tile * C, Cn = min(C, a.G - g0);
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t 
     mbar_expect_tx(&bar, NP * n_al * 4u + stall);
     for (uint32_t p = 0; p < NP; ++p) {
       const uint32_t* base = p < NOCC ? a.state + (static_cast<size_t>(sample) * NOCC + p) * W
-                                      : a.mask + static_cast<size_t>(sample / a.geo.samples_per_real) * W;
+                                      : a.mask + (static_cast<size_t>(sample / a.geo.samples_per_real) * NQ +
+                                                  (p - NOCC)) * W;
       bulk_g2s(stage + p * SW, base + a0, part1 * 4u, &bar);
       if (part2) bulk_g2s(stage + p * SW + part1, base, part2 * 4u, &bar);
     }
@@ -212,9 +214,12 @@ __global__ void __launch_bounds__(1024) k_stream(const DomainLaunch a, uint32_t 
 }
 
 // Lane changes of the two-lane model after the odd phase, on the natural
-// layout: every turning site with exactly one lane occupied moves its
-// particle with probability omega (the draw of the other tiers: tag TURN,
-// ctr3 = site / 4, word site mod 4).  One thread per word.
+// layout: every turning site (DIS = kDisTurning; probability omega) or every
+// site (DIS = kDisCrossing; A -> B with u_i, B -> A with v_i, the slow value
+// at sites marked in the u and v planes) with exactly one lane occupied moves
+// its particle (the draw of the other tiers: tag TURN, ctr3 = site / 4, word
+// site mod 4).  One thread per word.
+template <uint32_t DIS>
 __global__ void k_stream_turn(const DomainLaunch a) {
   const uint32_t W = a.geo.W;
   const size_t total = static_cast<size_t>(a.geo.S) * W;
@@ -225,9 +230,15 @@ __global__ void k_stream_turn(const DomainLaunch a) {
     const uint32_t sample = static_cast<uint32_t>(idx / W), w = static_cast<uint32_t>(idx - size_t(sample) * W);
     uint32_t* A = a.state + static_cast<size_t>(sample) * 2 * W;
     uint32_t* B = A + W;
-    const uint32_t m = a.mask[static_cast<size_t>(sample / a.geo.samples_per_real) * W + w];
+    const uint32_t real = sample / a.geo.samples_per_real;
     uint32_t av = A[w], bv = B[w];
-    uint32_t e = m & (av ^ bv);
+    uint32_t e = av ^ bv, um = 0, vm = 0;
+    if (DIS == kDisCrossing) {
+      um = a.mask[(static_cast<size_t>(real) * 2) * W + w];
+      vm = a.mask[(static_cast<size_t>(real) * 2 + 1) * W + w];
+    } else {
+      e &= a.mask[static_cast<size_t>(real) * W + w];
+    }
     if (!e) continue;
     const uint32_t n_glob = a.geo.first_sample + sample;
     uint32_t ab = 0, ba = 0;
@@ -236,7 +247,9 @@ __global__ void k_stream_turn(const DomainLaunch a) {
       e &= e - 1;
       const uint32_t site = 32u * w + b;
       const uint4 x = philox10(ctr_of(s, kTagTurn, 0, n_glob, site >> 2), key);
-      if (accept(pick(x, site & 3u), a.rates.omega)) {
+      uint32_t t = a.rates.omega;
+      if (DIS == kDisCrossing && ((((av >> b) & 1u) ? um : vm) >> b) & 1u) t = a.rates.omega_slow;
+      if (accept(pick(x, site & 3u), t)) {
         if (av & (1u << b)) ++ab;
         else ++ba;
         av ^= 1u << b;
@@ -269,10 +282,10 @@ cudaError_t launch_stream_phases(const DomainLaunch& a, uint32_t tiles, uint32_t
   if (e != cudaSuccess) return e;
   e = launch_stream_t<MODEL, DIS, COUNT, 1>(a, tiles, threads, smem, err, stall, st);
   if (e != cudaSuccess) return e;
-  if (MODEL == kTwoLane && DIS == kDisTurning) {
+  if (MODEL == kTwoLane && (DIS == kDisTurning || DIS == kDisCrossing)) {
     const size_t total = static_cast<size_t>(a.geo.S) * a.geo.W;
     const uint32_t blocks = static_cast<uint32_t>(std::min<size_t>(152u * 16u, (total + 255) / 256));
-    k_stream_turn<<<blocks, 256, 0, st>>>(a);
+    k_stream_turn<DIS><<<blocks, 256, 0, st>>>(a);
     e = cudaGetLastError();
   }
   return e;
@@ -281,7 +294,7 @@ cudaError_t launch_stream_phases(const DomainLaunch& a, uint32_t tiles, uint32_t
 }  // namespace
 
 size_t stream_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t C, uint32_t ptab_n) {
-  const uint32_t np = (model == kTwoLane ? 2u : 1u) + (dis != kDisNone ? 1u : 0u);
+  const uint32_t np = (model == kTwoLane ? 2u : 1u) + dis_planes(dis);
   const uint32_t Cp = (C + 31) / 32 * 32;
   return 4ull * np * ((R2 + 1) * Cp + R2 * C + 16) + 4ull * ptab_n;
 }
@@ -292,12 +305,18 @@ cudaError_t launch_stream_sweep(const DomainLaunch& a, uint32_t tiles, uint32_t 
                                 uint32_t stall, cudaStream_t st) {
   const bool count = a.count_hops != 0;
   if (a.model == kTwoLane) {
-    return a.dis == kDisTurning ? launch_stream_phases<kTwoLane, kDisTurning, true>(a, tiles, threads, smem, err, stall, st)
-                                : launch_stream_phases<kTwoLane, kDisNone, true>(a, tiles, threads, smem, err, stall, st);
+    if (a.dis == kDisTurning)
+      return launch_stream_phases<kTwoLane, kDisTurning, true>(a, tiles, threads, smem, err, stall, st);
+    if (a.dis == kDisCrossing)
+      return launch_stream_phases<kTwoLane, kDisCrossing, true>(a, tiles, threads, smem, err, stall, st);
+    return launch_stream_phases<kTwoLane, kDisNone, true>(a, tiles, threads, smem, err, stall, st);
   }
   if (a.dis == kDisBimodal)
     return count ? launch_stream_phases<kRing, kDisBimodal, true>(a, tiles, threads, smem, err, stall, st)
                  : launch_stream_phases<kRing, kDisBimodal, false>(a, tiles, threads, smem, err, stall, st);
+  if (a.dis == kDisBimodalPQ)
+    return count ? launch_stream_phases<kRing, kDisBimodalPQ, true>(a, tiles, threads, smem, err, stall, st)
+                 : launch_stream_phases<kRing, kDisBimodalPQ, false>(a, tiles, threads, smem, err, stall, st);
   return count ? launch_stream_phases<kRing, kDisNone, true>(a, tiles, threads, smem, err, stall, st)
                : launch_stream_phases<kRing, kDisNone, false>(a, tiles, threads, smem, err, stall, st);
 }

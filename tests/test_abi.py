@@ -69,11 +69,11 @@ def test_create_rejects_bad_params_without_device(A):
            # SCA schedule: L a multiple of 256 (beyond shared memory it streams, up to 2^28)
            dict(L=4096 + 64, schedule=2), dict(L=(1 << 21) + 128, schedule=2), dict(L=1 << 29, schedule=2),
            dict(L=4096, schedule=3),
-           # independent p and q classes: ring, SCA or serial schedule only; no kind 4
-           dict(L=4096, dis_kind=3, dis_a_thr=4096), dict(L=4096, schedule=2, model=1, dis_kind=3, dis_a_thr=4096),
+           # independent p and q classes: the ring model only; no kind 5
+           dict(L=4096, schedule=2, model=1, dis_kind=3, dis_a_thr=4096), dict(L=4096, model=1, dis_kind=3),
            dict(L=4096, schedule=2, dis_kind=5),
-           # crossing probabilities: two lanes, SCA or serial schedule only
-           dict(L=4096, schedule=2, dis_kind=4, dis_a_thr=4096), dict(L=4096, model=1, dis_kind=4, dis_a_thr=4096)]
+           # crossing probabilities: the two-lane model only
+           dict(L=4096, schedule=2, dis_kind=4, dis_a_thr=4096), dict(L=4096, dis_kind=4, dis_a_thr=4096)]
     for kw in bad:
         prm = A.make_params(**kw)
         with pytest.raises(A.AsepError) as ei:

@@ -12,7 +12,7 @@ from paper_1012_0385_gb300 import asep as A
 pytestmark = pytest.mark.gpu
 
 th = oracle.threshold
-N_CASES = 120
+N_CASES = 144
 RATES = [0, A.ASEP_ALWAYS, th(0.75), th(0.25), th(0.5), th(0.6), th(0.3), th(0.9)]
 
 
@@ -20,12 +20,9 @@ def draw(k: int):
     rng = np.random.default_rng(1000 + k)
     schedule = int(rng.choice([A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_SCA, A.ASEP_SCHED_SERIAL]))
     model = int(rng.integers(2))
-    if model == 1:
-        # the paper's crossing probabilities at every site run under the SCA and serial schedules
-        dis = int(rng.choice([0, 2] if schedule == A.ASEP_SCHED_DOMAIN else [0, 2, 4]))
-    elif schedule == A.ASEP_SCHED_DOMAIN:
-        dis = int(rng.choice([0, 1]))
-    else:  # independent p and q classes run under the SCA and serial schedules
+    if model == 1:  # none, turning sites, or the paper's crossing probabilities at every site
+        dis = int(rng.choice([0, 2, 4]))
+    else:  # none, one slow class, or independent p and q classes
         dis = int(rng.choice([0, 1, 3]))
     if schedule == A.ASEP_SCHED_SERIAL:
         L = int(2 ** rng.integers(6, 12))

@@ -299,6 +299,42 @@ CASES = {
                               dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=8,
                               q_thr=A.ASEP_ALWAYS, seed=55, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR,
                               autocorr_t0=1), 3, [0, 1, 3]),
+    # the paper's independent p and q classes (sec. 2.3) and crossing marks (sec. 3) under the domain schedule:
+    # resident (with several samples per CTA and the lane sort), streamed and cluster tiers
+    "domain_bimodal_pq": (dict(L=8192, domain_sites=128, n_realizations=2, samples_per_real=2, p_thr=th(0.5),
+                               q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1), dis_c_thr=th(0.1),
+                               dis_seed=70, seed=71, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5),
+                          20, [0, 5, 20]),
+    "domain_bimodal_pq_packed": (dict(L=1 << 14, domain_sites=128, n_realizations=4, samples_per_real=3,
+                                      p_thr=th(0.8), q_thr=th(0.8), dis_kind=PQ, dis_a_thr=th(0.3),
+                                      dis_b_thr=th(0.2), dis_c_thr=A.ASEP_ALWAYS, dis_seed=72, seed=73), 15, [0, 15]),
+    "domain_bimodal_pq_cfg1_columns": (dict(L=1 << 17, domain_sites=256, n_realizations=2, samples_per_real=1,
+                                            p_thr=th(0.75), q_thr=th(0.25), dis_kind=PQ, dis_a_thr=th(0.1),
+                                            dis_b_thr=th(0.3), dis_c_thr=th(0.05), dis_seed=74, seed=75), 5, [0, 5]),
+    "stream_bimodal_pq": (dict(L=1 << 16, domain_sites=128, n_realizations=2, samples_per_real=1, p_thr=th(0.5),
+                               q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1), dis_c_thr=th(0.1),
+                               dis_seed=76, seed=77, plan=(32, 0)), 7, [0, 7]),
+    "cluster_bimodal_pq": (dict(L=1 << 19, domain_sites=256, n_realizations=2, samples_per_real=1, p_thr=th(0.5),
+                                q_thr=th(0.5), dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1),
+                                dis_c_thr=th(0.1), dis_seed=78, seed=79), 3, [0, 3]),
+    "domain_two_lane_crossing": (dict(model=TWO, L=4096, domain_sites=64, n_realizations=2, samples_per_real=2,
+                                      init_kind=1, init_seed=80, p_thr=th(0.5), q_thr=th(0.5), dis_kind=XING,
+                                      dis_a_thr=th(0.5), dis_b_thr=th(0.8), dis_c_thr=th(0.2), dis_seed=81, seed=82,
+                                      flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=4),
+                                 12, [0, 4, 12]),
+    "domain_two_lane_crossing_cfg3_shape": (dict(model=TWO, L=1 << 16, domain_sites=128, samples_per_real=3,
+                                                 init_kind=1, init_seed=83, p_thr=A.ASEP_ALWAYS,
+                                                 q_thr=A.ASEP_ALWAYS, dis_kind=XING, dis_a_thr=th(0.5),
+                                                 dis_b_thr=th(0.8), dis_c_thr=th(0.2), dis_seed=84, seed=85),
+                                            6, [0, 6]),
+    "stream_two_lane_crossing": (dict(model=TWO, L=1 << 16, domain_sites=128, n_realizations=2, samples_per_real=1,
+                                      init_kind=1, init_seed=86, p_thr=th(0.5), q_thr=th(0.5), dis_kind=XING,
+                                      dis_a_thr=th(0.5), dis_b_thr=th(0.8), dis_c_thr=th(0.2), dis_seed=87, seed=88,
+                                      plan=(32, 0)), 5, [0, 5]),
+    "cluster_two_lane_crossing": (dict(model=TWO, L=1 << 18, domain_sites=256, samples_per_real=1, init_kind=1,
+                                       init_seed=89, p_thr=A.ASEP_ALWAYS, q_thr=A.ASEP_ALWAYS, dis_kind=XING,
+                                       dis_a_thr=th(0.5), dis_b_thr=th(0.8), dis_c_thr=th(0.2), dis_seed=90,
+                                       seed=91), 3, [0, 3]),
     "cluster_ring_max_L": (dict(L=1 << 22, domain_sites=256, samples_per_real=1, p_thr=th(0.75), q_thr=th(0.25),
                                 seed=56), 2, [0, 2]),
     "cluster_two_lane_max_L": (dict(model=TWO, L=1 << 22, domain_sites=256, samples_per_real=1, init_kind=1,

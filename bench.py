@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -516,28 +518,37 @@ def other_workloads(tune: bool = True):
     return out
 
 
-def serving_comparison(capacity: float, n_jobs: int = 48, seed: int = 2026, load: float = 0.7):
-    """The served ensemble mix, scaled: Poisson arrivals of jobs drawn from
-    the four workload families with L log-uniform in [2^10, 2^22] (the mix's
-    full range; L above ~2^19 runs on thread-block clusters), 1-256 samples
-    and n_mcs log-uniform in [10, 10^4] (the mix's 10^3-10^6 divided by 100),
-    arrivals offering 70 % of the measured batched capacity.  The same trace
-    is replayed with continuous batching and with one launch per job; the
-    results are bit-identical between the two."""
+def serving_comparison(capacity: float, n_jobs: int = 500, seed: int = 2026, load: float = 0.4):
+    """The served ensemble mix (configuration 4) in a time-scaled reading:
+    Poisson arrivals of jobs drawn from the four workload families (plain
+    TASEP, ASEP growth, bimodal disorder, two lanes) with L log-uniform in
+    [2^10, 2^22] (the mix's full range; L above ~2^19 runs on thread-block
+    clusters), 1-256 samples and n_mcs log-uniform in [5, 5000] (the mix's
+    10^3-10^6 divided by 200, so that both modes finish in minutes),
+    arrivals offering 40 % of the headline kernel's rate (about 80 % of what
+    the batched server sustains on this mix: two-lane, disordered and
+    cluster-tier jobs run slower than the benchmarked ring).  The same trace
+    is replayed with continuous batching (admission by the library's device-
+    and shared-memory plan, up to 10^4 jobs in flight) and with one launch per
+    job; the results are bit-identical between the two."""
     from paper_1012_0385_gb300 import serve
 
     def trace():
         return serve.make_trace(n_jobs, seed=seed, rate_hz=1.0, L_range=(1 << 10, 1 << 22), samples_range=(1, 256),
-                                n_mcs_range=(10, 10_000), load=load, capacity=capacity)
+                                n_mcs_range=(5, 5000), load=load, capacity=capacity)
 
-    batched = serve.serve_batched(trace(), quantum_s=0.02)
-    plain = serve.serve_plain(trace())
-    rate = n_jobs / max(j.arrival for j in trace())
+    batched_jobs, plain_jobs = trace(), trace()
+    batched = serve.serve_batched(batched_jobs, quantum_s=0.02)
+    plain = serve.serve_plain(plain_jobs)
+    same = all(np.array_equal(a.result[k], b.result[k]) for a, b in zip(batched_jobs, plain_jobs)
+               for k in ("sum_h", "sum_h2", "counters"))
+    rate = n_jobs / max(j.arrival for j in batched_jobs)
     return {"trace": f"{n_jobs} jobs, Poisson ~{rate:.2f} Hz (offered load {load:g} of {capacity:.3g} attempts/s), "
                      "kinds tasep/asep/bimodal/two_lane, L log-uniform [2^10, 2^22], samples log-uniform [1, 256], "
-                     "n_mcs log-uniform [10, 10^4]",
-            "batched": batched, "plain": plain,
+                     "n_mcs log-uniform [5, 5000] (the configuration's [10^3, 10^6] / 200)",
+            "batched": batched, "plain": plain, "results_identical": bool(same),
             "throughput_ratio": batched["throughput_attempts_per_s"] / plain["throughput_attempts_per_s"],
+            "p50_ratio": batched["p50_latency_s"] / plain["p50_latency_s"],
             "p99_ratio": batched["p99_latency_s"] / plain["p99_latency_s"]}
 
 

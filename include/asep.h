@@ -188,6 +188,8 @@ typedef struct asep_info {
   uint32_t samples_per_group; /* samples per CTA (resident) or 1 (cluster) */
   uint32_t groups;        /* CTAs (resident) or clusters per sweep launch */
   uint32_t threads;       /* threads per CTA */
+  uint32_t smem_bytes;    /* dynamic shared memory per CTA of the sweep kernel */
+  uint32_t reserved;      /* 0 */
 } asep_info;
 
 /* Validate `params`, allocate device memory, draw the initial state (paper
@@ -196,6 +198,17 @@ typedef struct asep_info {
  * when 0 is a sample time.  On success *out owns the context; on failure
  * *out is NULL and nothing is leaked.  The sample_times array is copied. */
 int asep_create(const asep_params* params, asep_ctx** out);
+
+/* What asep_create would make of `params`, without allocating or launching
+ * anything: validates them (same errors as asep_create) and fills `info`
+ * with the sizes, the automatic launch plan (cluster, samples_per_group,
+ * groups, threads, smem_bytes) and device_bytes = the device memory the
+ * context would hold, exactly as asep_get_info reports it after creation;
+ * n_recorded, sweep and kernel_launches are 0.  For admission control: a
+ * server decides whether a job fits its device-memory and shared-memory
+ * budget before creating it.  Host only; plans beyond one CTA query the
+ * current device's occupancy.  No counterpart in the paper. */
+int asep_plan(const asep_params* params, asep_info* info);
 
 /* Enqueue n_mcs sweeps (Monte Carlo steps, paper sec. 2.1: one sweep = L
  * attempts per lane and sample) of all S samples on the context stream,
@@ -335,11 +348,15 @@ typedef struct asep_batch asep_batch; /* opaque; owns device workspace and a CUD
  * items, largest first, from a device work queue.  Every sample's randomness
  * depends only on its own Philox counters, so each context's results are
  * bit-identical to running it alone with asep_sweep.  The batch owns device
- * workspace for up to max_jobs contexts and max_items queue items (a
- * context contributes ceil(S / samples per group) items).  Work is enqueued
- * on `stream` (cudaStream_t or NULL); the batch first waits for the work
- * already enqueued on each context's stream, and each context's stream waits
- * for the batch before its later work.  Only ASEP_SCHED_DOMAIN contexts. */
+ * workspace for up to max_jobs contexts (at most 16384) and max_items queue
+ * items (a context contributes ceil(S / samples per group) items, at most
+ * 2^18 per context: larger contexts run alone with asep_sweep).  Work is
+ * enqueued on `stream` (cudaStream_t or NULL); the batch first waits for the
+ * work already enqueued on each context's stream, and each context's stream
+ * waits for the batch before its later work (contexts that share a stream
+ * are ordered once).  Only ASEP_SCHED_DOMAIN contexts whose lattices sit in
+ * shared memory (one CTA or a cluster); streamed-tier contexts run with
+ * asep_sweep. */
 int asep_batch_create(void* stream, uint32_t max_jobs, uint32_t max_items, asep_batch** out);
 
 /* Advance ctxs[i] by n_mcs[i] sweeps (0 allowed) for i < n, in one persistent

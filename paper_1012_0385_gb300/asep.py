@@ -86,11 +86,13 @@ class asep_info(ctypes.Structure):
         ("samples_per_group", ctypes.c_uint32),
         ("groups", ctypes.c_uint32),
         ("threads", ctypes.c_uint32),
+        ("smem_bytes", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 
 # Every symbol include/asep.h declares (tests check that the library exports them).
-EXPORTED = ("asep_create", "asep_sweep", "asep_width", "asep_state", "asep_load_state", "asep_reset", "asep_counters",
+EXPORTED = ("asep_create", "asep_plan", "asep_sweep", "asep_width", "asep_state", "asep_load_state", "asep_reset", "asep_counters",
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_attempt_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
@@ -128,6 +130,7 @@ def lib():
             L.asep_counters.argtypes = [vp, P(ctypes.c_uint64), ctypes.c_size_t]
             L.asep_disorder.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_size_t]
             L.asep_get_info.argtypes = [vp, P(asep_info)]
+            L.asep_plan.argtypes = [P(asep_params), P(asep_info)]
             L.asep_sync.argtypes = [vp]
             L.asep_inject_fault.argtypes = [vp, ctypes.c_uint32]
             L.asep_destroy.argtypes = [vp]
@@ -313,6 +316,19 @@ def asep_create(params: asep_params, sample_times=(), stream=None, torch_alloc: 
     if rc != ASEP_OK:
         raise AsepError(rc, asep_last_error(None))
     return Context(h, params, keep)
+
+
+def asep_plan(params: asep_params, sample_times=()) -> dict:
+    """The context asep_create would make (sizes, launch plan, device bytes,
+    shared memory per CTA), without allocating or launching anything."""
+    times = np.ascontiguousarray(np.asarray(sorted(set(int(t) for t in sample_times)), dtype=np.uint64))
+    params.sample_times = _ptr(times, ctypes.c_uint64) if times.size else None
+    params.n_sample_times = int(times.size)
+    info = asep_info()
+    rc = lib().asep_plan(ctypes.byref(params), ctypes.byref(info))
+    if rc != ASEP_OK:
+        raise AsepError(rc, asep_last_error(None))
+    return {f: getattr(info, f) for f, _ in asep_info._fields_}
 
 
 def asep_sweep(ctx, n_mcs: int) -> None:

@@ -599,14 +599,13 @@ const char* asep_last_error(const asep_ctx* ctx) {
   return ctx->err.c_str();
 }
 
-int asep_create(const asep_params* params, asep_ctx** out) {
-  if (!out) return fail(nullptr, ASEP_ERR_INVALID, "out is NULL");
-  *out = nullptr;
-  g_create_error.clear();
-  int rc = validate(params, nullptr);
-  if (rc != ASEP_OK) return rc;
-  asep_ctx* ctx = new (std::nothrow) asep_ctx();
-  if (!ctx) return fail(nullptr, ASEP_ERR_NOMEM, "host allocation failed");
+}  // extern "C"
+
+namespace {
+
+// Sizes, attempt-count table and launch plan of a new context (no device
+// memory, no stream work).  Used by asep_create and asep_plan.
+int plan_context(asep_ctx* ctx, const asep_params* params) {
   ctx->p = *params;
   ctx->p.sample_times = nullptr;
   ctx->L = params->L;
@@ -616,14 +615,6 @@ int asep_create(const asep_params* params, asep_ctx** out) {
   ctx->R = params->dis_kind == ASEP_DIS_NONE ? 0u : params->n_realizations;
   ctx->stream = static_cast<cudaStream_t>(params->stream);
   ctx->times.assign(params->sample_times, params->sample_times + params->n_sample_times);
-
-  auto bail = [&](int code) {
-    g_create_error = ctx->err;
-    release(ctx);
-    delete ctx;
-    return code;
-  };
-
   if (params->schedule == ASEP_SCHED_DOMAIN) {
     uint32_t D = params->domain_sites;
     if (D == 0) {
@@ -631,21 +622,106 @@ int asep_create(const asep_params* params, asep_ctx** out) {
       while (D > 32 && ctx->L % (2ull * D)) D >>= 1;
     }
     if (D < 32 || D > 2048 || !is_pow2(D) || ctx->L % (2ull * D))
-      return bail(fail(ctx, ASEP_ERR_INVALID, "domain_sites = %u must be a power of two in [32, 2048] with "
-                       "L a multiple of 2*domain_sites", D));
+      return fail(ctx, ASEP_ERR_INVALID, "domain_sites = %u must be a power of two in [32, 2048] with "
+                  "L a multiple of 2*domain_sites", D);
     ctx->D = D;
     ctx->logD = log2u(D);
     const uint32_t bonds = ctx->planes * D;
     if (poisson_table_host(bonds, ctx->ptab, ctx->ptab_klo) != ASEP_OK)
-      return bail(fail(ctx, ASEP_ERR_INVALID, "attempt-count table for %u bonds failed", bonds));
-    rc = plan_domain(ctx, 0, 0);
-    if (rc != ASEP_OK) return bail(rc);
-  } else if (params->schedule == ASEP_SCHED_SCA) {
-    rc = plan_sca(ctx, 0);
-    if (rc != ASEP_OK) return bail(rc);
+      return fail(ctx, ASEP_ERR_INVALID, "attempt-count table for %u bonds failed", bonds);
+    return plan_domain(ctx, 0, 0);
   }
+  if (params->schedule == ASEP_SCHED_SCA) return plan_sca(ctx, 0);
+  return ASEP_OK;
+}
 
-  // device memory
+// Device bytes asep_create allocates for a planned context: the same list,
+// in the same sizes, as its allocations below.
+size_t planned_device_bytes(const asep_ctx* ctx) {
+  size_t total = 0;
+  const auto add = [&](size_t b) { total += b ? b : 16; };
+  const size_t state_words = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
+  const size_t n_times = std::max<size_t>(1, ctx->times.size());
+  const size_t entries = n_times * ctx->S * ctx->planes;
+  add(state_words * 4);
+  add(static_cast<size_t>(ctx->S) * 4 * 8);
+  add(entries * 8);
+  add(entries * 16);
+  add(n_times * 8);
+  add(sizeof(Clock));
+  add(n_times * ctx->S * 32);
+  add(static_cast<size_t>(ctx->S) * ctx->planes * 8);
+  add(static_cast<size_t>(ctx->S) * ctx->planes * 16);
+  add(static_cast<size_t>(ctx->S) * 32);
+  add(16);
+  if (height_chunks(ctx->W) > 1) add(static_cast<size_t>(ctx->S) * ctx->planes * height_chunks(ctx->W) * sizeof(HeightPart));
+  if (ctx->p.flags & ASEP_FLAG_PROFILE) add(state_words * 4);
+  if (ctx->p.flags & ASEP_FLAG_AUTOCORR) {
+    add(state_words * 4);
+    add(entries * 8);
+  }
+  if (ctx->R) add(static_cast<size_t>(ctx->R) * dis_planes(ctx->p.dis_kind) * ctx->W * 4);
+  if (!ctx->ptab.empty()) add(ctx->ptab.size() * 4);
+  return total;
+}
+
+void fill_info(const asep_ctx* ctx, asep_info* info) {
+  info->L = ctx->L;
+  info->D = ctx->D;
+  info->planes = ctx->planes;
+  info->S = ctx->S;
+  info->n_recorded = ctx->next_time;
+  info->sweep = ctx->sweep;
+  info->attempts_per_sweep = ctx->L * ctx->planes;
+  info->device_bytes = ctx->dev_bytes;
+  info->kernel_launches = ctx->launches;
+  info->cluster = ctx->cluster;
+  info->samples_per_group = ctx->spc;
+  info->groups = ctx->blocks;
+  info->threads = ctx->threads;
+  info->smem_bytes = static_cast<uint32_t>(ctx->smem);
+  info->reserved = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int asep_plan(const asep_params* params, asep_info* info) {
+  g_create_error.clear();
+  if (!info) return fail(nullptr, ASEP_ERR_INVALID, "info is NULL");
+  int rc = validate(params, nullptr);
+  if (rc != ASEP_OK) return rc;
+  asep_ctx ctx;
+  rc = plan_context(&ctx, params);
+  if (rc != ASEP_OK) {
+    g_create_error = ctx.err;
+    return rc;
+  }
+  fill_info(&ctx, info);
+  info->device_bytes = planned_device_bytes(&ctx);
+  return ASEP_OK;
+}
+
+int asep_create(const asep_params* params, asep_ctx** out) {
+  if (!out) return fail(nullptr, ASEP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  g_create_error.clear();
+  int rc = validate(params, nullptr);
+  if (rc != ASEP_OK) return rc;
+  asep_ctx* ctx = new (std::nothrow) asep_ctx();
+  if (!ctx) return fail(nullptr, ASEP_ERR_NOMEM, "host allocation failed");
+
+  auto bail = [&](int code) {
+    g_create_error = ctx->err;
+    release(ctx);
+    delete ctx;
+    return code;
+  };
+  rc = plan_context(ctx, params);
+  if (rc != ASEP_OK) return bail(rc);
+
+  // device memory (planned_device_bytes lists the same sizes)
   const size_t state_words = static_cast<size_t>(ctx->S) * ctx->planes * ctx->W;
   const size_t n_times = std::max<size_t>(1, ctx->times.size());
   const size_t entries = n_times * ctx->S * ctx->planes;
@@ -1005,7 +1081,7 @@ int batch_prepare(asep_batch* b, asep_ctx* const* ctxs, const uint32_t* n, uint3
                                             static_cast<uint32_t>(c->ptab.size()), threads));
     if (n[j] == 0) continue;
     const uint64_t cost = static_cast<uint64_t>(n[j]) * c->spc * c->L * c->planes;
-    for (uint32_t g = 0; g < c->blocks; ++g) items.push_back({cost, (j << 20) | g});
+    for (uint32_t g = 0; g < c->blocks; ++g) items.push_back({cost, (j << kItemGroupBits) | g});
   }
   if (items.size() > b->max_items)
     return bfail(b, ASEP_ERR_INVALID, "%zu queue items exceed the batch's max_items %u", items.size(), b->max_items);
@@ -1040,7 +1116,7 @@ int batch_check(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uin
   if (n == 0) return ASEP_OK;
   if (!ctxs || !n_mcs) return bfail(b, ASEP_ERR_INVALID, "ctxs or n_mcs is NULL");
   if (n > b->max_jobs) return bfail(b, ASEP_ERR_INVALID, "%u contexts exceed max_jobs %u", n, b->max_jobs);
-  if (n > (1u << 12)) return bfail(b, ASEP_ERR_INVALID, "at most 4096 contexts per batch");
+  if (n > kItemMaxJobs) return bfail(b, ASEP_ERR_INVALID, "at most %u contexts per batch", kItemMaxJobs);
   for (uint32_t j = 0; j < n; ++j) {
     if (!ctxs[j]) return bfail(b, ASEP_ERR_INVALID, "context %u is NULL", j);
     if (ctxs[j]->p.schedule != ASEP_SCHED_DOMAIN)
@@ -1048,16 +1124,24 @@ int batch_check(asep_batch* b, asep_ctx* const* ctxs, const uint64_t* n_mcs, uin
     if (ctxs[j]->cluster == kStreamTier)
       return bfail(b, ASEP_ERR_INVALID, "context %u streams its lattice from global memory; use asep_sweep", j);
     if (ctxs[j]->sweep + n_mcs[j] >= (1ull << 40)) return bfail(b, ASEP_ERR_INVALID, "context %u: sweep >= 2^40", j);
-    if (ctxs[j]->blocks > (1u << 20)) return bfail(b, ASEP_ERR_INVALID, "context %u: more than 2^20 groups", j);
+    if (ctxs[j]->blocks > kItemMaxGroups)
+      return bfail(b, ASEP_ERR_INVALID, "context %u: more than %u sample groups; use asep_sweep", j, kItemMaxGroups);
     for (uint32_t k = 0; k < j; ++k)
       if (ctxs[k] == ctxs[j]) return bfail(b, ASEP_ERR_INVALID, "context %u appears twice", j);
   }
   return ASEP_OK;
 }
 
+// Streams of the contexts of a step, each once (contexts often share one).
+bool seen_before(asep_ctx* const* ctxs, uint32_t j) {
+  for (uint32_t k = j; k-- > 0 && j - k <= 8;)
+    if (ctxs[k]->stream == ctxs[j]->stream) return true;
+  return false;
+}
+
 int order_in(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
   for (uint32_t j = 0; j < n; ++j) {
-    if (ctxs[j]->stream == b->stream) continue;
+    if (ctxs[j]->stream == b->stream || seen_before(ctxs, j)) continue;
     cudaError_t e;
     if ((e = cudaEventRecord(b->order, ctxs[j]->stream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(b->stream, b->order, 0)) != cudaSuccess)
@@ -1070,7 +1154,7 @@ int order_out(asep_batch* b, asep_ctx* const* ctxs, uint32_t n) {
   cudaError_t e = cudaEventRecord(b->order, b->stream);
   if (e != cudaSuccess) return bfail(b, ASEP_ERR_CUDA, "order: %s", cudaGetErrorString(e));
   for (uint32_t j = 0; j < n; ++j) {
-    if (ctxs[j]->stream == b->stream) continue;
+    if (ctxs[j]->stream == b->stream || seen_before(ctxs, j)) continue;
     if ((e = cudaStreamWaitEvent(ctxs[j]->stream, b->order, 0)) != cudaSuccess)
       return bfail(b, ASEP_ERR_CUDA, "order: %s", cudaGetErrorString(e));
   }
@@ -1114,8 +1198,8 @@ extern "C" {
 int asep_batch_create(void* stream, uint32_t max_jobs, uint32_t max_items, asep_batch** out) {
   if (!out) return bfail(nullptr, ASEP_ERR_INVALID, "out is NULL");
   *out = nullptr;
-  if (max_jobs == 0 || max_jobs > (1u << 12) || max_items == 0 || max_items > (1u << 24))
-    return bfail(nullptr, ASEP_ERR_INVALID, "max_jobs in [1, 4096], max_items in [1, 2^24]");
+  if (max_jobs == 0 || max_jobs > kItemMaxJobs || max_items == 0 || max_items > (1u << 24))
+    return bfail(nullptr, ASEP_ERR_INVALID, "max_jobs in [1, %u], max_items in [1, 2^24]", kItemMaxJobs);
   asep_batch* b = new (std::nothrow) asep_batch();
   if (!b) return bfail(nullptr, ASEP_ERR_NOMEM, "host allocation failed");
   b->stream = static_cast<cudaStream_t>(stream);
@@ -1366,19 +1450,7 @@ int asep_height_offset(asep_ctx* ctx, int64_t* out, size_t n) {
 
 int asep_get_info(const asep_ctx* ctx, asep_info* info) {
   if (!ctx || !info) return ASEP_ERR_INVALID;
-  info->L = ctx->L;
-  info->D = ctx->D;
-  info->planes = ctx->planes;
-  info->S = ctx->S;
-  info->n_recorded = ctx->next_time;
-  info->sweep = ctx->sweep;
-  info->attempts_per_sweep = ctx->L * ctx->planes;
-  info->device_bytes = ctx->dev_bytes;
-  info->kernel_launches = ctx->launches;
-  info->cluster = ctx->cluster;
-  info->samples_per_group = ctx->spc;
-  info->groups = ctx->blocks;
-  info->threads = ctx->threads;
+  fill_info(ctx, info);
   return ASEP_OK;
 }
 
@@ -1513,10 +1585,10 @@ int asep_batch_sweep_static(asep_ctx* const* ctxs, const uint64_t* n_mcs, uint32
     for (uint32_t k = 0; k < n; ++k) {
       const uint32_t j = order[k];
       if (jobs[j].n_sweeps == 0) continue;
-      if (ctxs[j]->blocks > (1u << 20) || n_items + ctxs[j]->blocks > kStaticMaxItems)
+      if (ctxs[j]->blocks > kItemMaxGroups || n_items + ctxs[j]->blocks > kStaticMaxItems)
         return fail(nullptr, ASEP_ERR_INVALID, "more than %u sample groups exceed the static batch limit",
                     kStaticMaxItems);
-      for (uint32_t g = 0; g < ctxs[j]->blocks; ++g) items[n_items++] = (j << 20) | g;
+      for (uint32_t g = 0; g < ctxs[j]->blocks; ++g) items[n_items++] = (j << kItemGroupBits) | g;
     }
     int per_sm = batch_ctas_per_sm(threads, smem);
     if (per_sm <= 0) return fail(nullptr, ASEP_ERR_INVALID, "batch kernel does not fit (%u threads)", threads);

@@ -190,7 +190,11 @@ uint32_t height_chunks(uint32_t W);
 cudaError_t launch_heights(const HeightsLaunch& a, cudaStream_t st);
 // One CTA per sample group of one context.
 cudaError_t launch_domain(const DomainLaunch& a, uint32_t threads, size_t smem, cudaStream_t st);
-// Persistent: `ctas` CTAs of `threads` threads take items (job << 20 | group)
+// Work items of the persistent batch kernel: (context index << kItemGroupBits) | sample group.
+constexpr uint32_t kItemGroupBits = 18;
+constexpr uint32_t kItemMaxJobs = 1u << (32 - kItemGroupBits);  // contexts per batch step
+constexpr uint32_t kItemMaxGroups = 1u << kItemGroupBits;       // sample groups per context and step
+// Persistent: `ctas` CTAs of `threads` threads take items (job << kItemGroupBits | group)
 // from items[0..n_items) through the queue counter (zeroed here first).
 cudaError_t launch_batch(const DomainLaunch* jobs, const uint32_t* items, uint32_t n_items, uint32_t* queue,
                          uint32_t threads, uint32_t ctas, size_t smem, cudaStream_t st);

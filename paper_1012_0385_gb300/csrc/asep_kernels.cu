@@ -561,9 +561,9 @@ __global__ void __maxnreg__(MAXT == 512 ? 104 : 64) k_batch(const DomainLaunch* 
     const uint32_t i = item_idx;
     if (i >= n_items) break;
     const uint32_t it = items[i];
-    if (threadIdx.x == 0) desc = jobs[it >> 20];
+    if (threadIdx.x == 0) desc = jobs[it >> kItemGroupBits];
     __syncthreads();
-    run_group_any(desc, it & 0xFFFFFu, smem_raw);
+    run_group_any(desc, it & (kItemMaxGroups - 1u), smem_raw);
   }
 }
 

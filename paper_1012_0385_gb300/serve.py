@@ -1,16 +1,21 @@
 """Serving: continuous batching of ensemble jobs on one GPU.
 
 A job is one ensemble request (model, L, rates, disorder seed, samples,
-n_mcs, sample times).  :func:`serve` replays an arrival trace against the
-GPU in one of two modes:
+n_mcs, sample times).  :func:`serve_batched` and :func:`serve_plain` replay
+an arrival trace against the GPU:
 
 ``batched``  (continuous batching) -- the server keeps every admitted job's
-    packed lattices and Philox clock on the device.  Each step it admits the
-    jobs that have arrived, as far as the device-memory budget allows, and
-    advances every active job by a quantum of sweeps in ONE persistent launch
+    packed lattices and Philox clock on the device.  Jobs are admitted as
+    they arrive while the device-memory budget and the shared-memory budget
+    allow; both footprints come from the library's own launch plan
+    (``asep_plan``, before anything is allocated).  Every step advances all
+    active jobs by a quantum of sweeps in ONE persistent launch
     (``asep_batch_sweep``: the CTAs of all jobs share one work queue, so jobs
-    of very different size overlap on the device); jobs that have finished
-    are read back and their memory is released before the next step.
+    of very different size overlap on the device); jobs whose lattices stream
+    from HBM run their own launches beside it on their own streams.  The host
+    never waits for a step: it keeps up to two steps in flight, admits arrivals
+    and reads back finished jobs (each job has its own stream, so reading one
+    waits for nothing else) while the GPU runs.
 ``plain``    -- one launch per job, first come first served: each job is
     created, swept to n_mcs in one ``asep_sweep`` call, read back and
     destroyed before the next one starts.
@@ -23,6 +28,7 @@ from __future__ import annotations
 
 import math
 import time
+from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -30,6 +36,8 @@ import numpy as np
 from . import asep as A
 from .sampling import log_times
 
+SMEM_PER_SM = 228 * 1024  # bytes of shared memory per SM (GB300)
+STREAMED = 32  # asep_info.cluster of a context whose lattice streams from HBM
 KINDS = ("tasep", "asep", "bimodal", "two_lane")
 
 
@@ -52,6 +60,7 @@ class Job:
     admitted: float = math.nan
     finished: float = math.nan
     result: dict = field(default_factory=dict)
+    _plan: dict | None = field(default=None, repr=False)
 
     @property
     def planes(self) -> int:
@@ -93,12 +102,22 @@ class Job:
     def times(self):
         return log_times(self.n_mcs) + ([self.n_mcs] if log_times(self.n_mcs)[-1] != self.n_mcs else [])
 
-    def footprint(self) -> int:
-        """Device bytes the job's context holds (lattices, disorder, tables)."""
-        S = self.S
-        W = self.L // 32
-        nt = len(self.times())
-        return S * self.planes * W * 4 + S * W * 4 + nt * S * self.planes * 24 + S * 32 + 4096
+    def plan(self) -> dict:
+        """The library's plan of the job's context (asep_plan): launch shape,
+        device bytes, shared memory per CTA; nothing is allocated."""
+        if self._plan is None:
+            self._plan = A.asep_plan(self.params(), sample_times=self.times())
+        return self._plan
+
+    def device_bytes(self) -> int:
+        return int(self.plan()["device_bytes"])
+
+    def smem_demand(self) -> int:
+        """Shared memory the job's work items occupy when all are resident:
+        CTAs (a cluster-tier sample holds `cluster` CTAs) x bytes per CTA."""
+        pl = self.plan()
+        per_item = pl["cluster"] if 1 < pl["cluster"] < STREAMED else 1
+        return int(pl["groups"]) * per_item * int(pl["smem_bytes"])
 
 
 def make_trace(n_jobs: int, seed: int = 0, rate_hz: float = 50.0, L_range=(1 << 10, 1 << 19),
@@ -156,67 +175,132 @@ def serve_plain(trace: list[Job]) -> dict:
     return _summary(jobs, time.perf_counter() - t0, "plain")
 
 
-def _group_work(ctx) -> tuple[int, int]:
-    """(attempts per sweep of one work item, SMs one item occupies): a
-    resident group is samples_per_group samples on one CTA, a cluster-tier
-    item one sample on `cluster` CTAs."""
-    info = A.asep_get_info(ctx)
-    return info["attempts_per_sweep"] * info["samples_per_group"], info["cluster"]
+@dataclass
+class _Active:
+    job: Job
+    ctx: object
+    stream: object
+    left: int
+    streamed: bool
+    mem: int
+    smem: int
+    item_attempts: int  # attempts per sweep of one work item (a CTA's samples, or a cluster's sample)
+    item_sms: int       # SMs one work item occupies
 
 
-def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int = 16 << 30, max_active: int = 256,
-                  rate_guess: float = 4e11, sms: int = 152) -> dict:
-    """Continuous batching: admit at step boundaries by footprint, one
-    persistent launch per step over all active jobs, retire finished jobs.
-    Each job's quantum of sweeps is chosen so that one of its work items (a
-    CTA's sample group, or a cluster's sample) takes about `quantum_s` at the
-    per-SM rate, so the items of a step have similar lengths."""
-    pending = sorted(trace, key=lambda j: j.arrival)
-    active: list[tuple[Job, object, int]] = []  # (job, ctx, sweeps left)
-    shape: dict[int, tuple[int, int]] = {}
-    used = 0
-    t0 = time.perf_counter()
-    batch = A.asep_batch_create(max_jobs=max_active, max_items=1 << 20)
+@dataclass
+class _Step:
+    events: list
+    finishing: list
+    attempts: int
+
+
+def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int | None = None, waves: float = 8.0,
+                  max_active: int = 10_000, rate_guess: float = 4e11, depth: int = 2) -> dict:
+    """Continuous batching (see the module docstring).
+
+    Admission, first come first served: a job enters when its device bytes
+    fit `mem_budget` (default 60 % of the free device memory) and its
+    shared-memory demand fits `waves` times the device's shared memory
+    beside the active jobs (a job larger than half of that counts as half, so
+    that it still enters when the load dips); at most `max_active` jobs.
+    Quantum: each job advances by the sweeps one of its work items runs in
+    about `quantum_s` at the measured per-SM rate (less for a job whose
+    demand exceeds half the allowance), so a step lasts about `waves` quanta
+    at most."""
+    import torch
+
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if mem_budget is None:
+        mem_budget = int(0.6 * torch.cuda.mem_get_info(dev)[0])
+    allowance = int(waves * sms * SMEM_PER_SM)
+    main = torch.cuda.current_stream(dev)
+    pending = deque(sorted(trace, key=lambda j: j.arrival))
+    active: list[_Active] = []
+    in_flight: deque[_Step] = deque()
+    free_streams: list = []
+    used_mem = used_smem = 0
+    peak_active = 0
     rate = rate_guess
+    last_retire = None
+    t0 = time.perf_counter()
+    batch = A.asep_batch_create(max_jobs=min(max_active, 16384), max_items=1 << 20, stream=main.cuda_stream)
     try:
-        while pending or active:
+        while pending or active or in_flight:
             now = time.perf_counter() - t0
-            # admit every arrived job the memory budget allows (first come first served)
+            progressed = False
+            # admit arrived jobs while both budgets allow
             while pending and pending[0].arrival <= now and len(active) < max_active:
-                fp = pending[0].footprint()
-                if used + fp > mem_budget and active:
+                job = pending[0]
+                mem, dem = job.device_bytes(), int(min(job.smem_demand(), allowance // 2))
+                if (active or in_flight) and (used_mem + mem > mem_budget or used_smem + dem > allowance):
                     break
-                job = pending.pop(0)
+                pending.popleft()
+                st = free_streams.pop() if free_streams else torch.cuda.Stream(dev)
                 job.admitted = now
-                ctx = A.asep_create(job.params(), sample_times=job.times())
-                shape[job.id] = _group_work(ctx)
-                active.append((job, ctx, job.n_mcs))
-                used += fp
-            if not active:
-                time.sleep(max(0.0, pending[0].arrival - now))
-                continue
-            # one quantum: every work item runs about quantum_s at the per-SM rate
-            per_sm = rate / sms
-            q = [max(1, min(left, int(per_sm * shape[job.id][1] * quantum_s // shape[job.id][0])))
-                 for job, _, left in active]
-            t_step = time.perf_counter()
-            A.asep_batch_sweep(batch, [c for _, c, _ in active], q)
-            A.asep_sync(active[0][1])
-            dt = time.perf_counter() - t_step
-            done = sum(k * job.L * job.planes * job.S for k, (job, _, _) in zip(q, active))
-            if dt > 0:
-                rate = 0.5 * rate + 0.5 * done / dt
-            still = []
-            for k, (job, ctx, left) in zip(q, active):
-                if left - k == 0:
-                    _finish(job, ctx, t0)
-                    ctx.close()
-                    used -= job.footprint()
-                else:
-                    still.append((job, ctx, left - k))
-            active = still
+                ctx = A.asep_create(job.params(), sample_times=job.times(), stream=st.cuda_stream)
+                info = A.asep_get_info(ctx)
+                per_item = info["cluster"] if 1 < info["cluster"] < STREAMED else 1
+                active.append(_Active(job, ctx, st, job.n_mcs, info["cluster"] == STREAMED, mem, dem,
+                                      info["attempts_per_sweep"] * info["samples_per_group"], per_item))
+                used_mem += mem
+                used_smem += dem
+                progressed = True
+            peak_active = max(peak_active, len(active) + sum(len(s.finishing) for s in in_flight))
+            # enqueue a step for every active job
+            if active and len(in_flight) < depth:
+                per_sm = rate / sms
+                ctxs, qs, events, finishing, still, attempts = [], [], [], [], [], 0
+                for a in active:
+                    target = quantum_s * min(1.0, (allowance / 2) / max(1, a.job.smem_demand()))
+                    q = max(1, min(a.left, int(per_sm * a.item_sms * target // max(1, a.item_attempts))))
+                    attempts += q * a.job.L * a.job.planes * a.job.S
+                    if a.streamed:  # its own launches, on its own stream, beside the batch
+                        A.asep_sweep(a.ctx, q)
+                        ev = torch.cuda.Event()
+                        ev.record(a.stream)
+                        events.append(ev)
+                    else:
+                        ctxs.append(a.ctx)
+                        qs.append(q)
+                    a.left -= q
+                    (finishing if a.left == 0 else still).append(a)
+                if ctxs:
+                    A.asep_batch_sweep(batch, ctxs, qs)
+                ev = torch.cuda.Event()
+                ev.record(main)
+                events.append(ev)
+                in_flight.append(_Step(events, finishing, attempts))
+                active = still
+                progressed = True
+            # retire the oldest step once the GPU has finished it
+            if in_flight and all(ev.query() for ev in in_flight[0].events):
+                step = in_flight.popleft()
+                t_now = time.perf_counter()
+                if last_retire is not None and t_now > last_retire:
+                    rate = 0.5 * rate + 0.5 * step.attempts / (t_now - last_retire)
+                last_retire = t_now
+                for a in step.finishing:
+                    _finish(a.job, a.ctx, t0)
+                    a.ctx.close()
+                    used_mem -= a.mem
+                    used_smem -= a.smem
+                    free_streams.append(a.stream)
+                if not in_flight:
+                    last_retire = None  # the GPU idles until the next step: restart the rate clock
+                progressed = True
+            if not progressed:
+                wait = pending[0].arrival - (time.perf_counter() - t0) if pending and not active and not in_flight \
+                    else 2e-4
+                time.sleep(min(max(wait, 0.0), 0.05))
     finally:
-        for _, ctx, _ in active:
-            ctx.close()
+        for s in in_flight:
+            for a in s.finishing:
+                a.ctx.close()
+        for a in active:
+            a.ctx.close()
         batch.close()
-    return _summary(sorted(trace, key=lambda j: j.arrival), time.perf_counter() - t0, "batched")
+    out = _summary(sorted(trace, key=lambda j: j.arrival), time.perf_counter() - t0, "batched")
+    out["peak_active_jobs"] = peak_active
+    return out

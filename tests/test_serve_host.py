@@ -40,7 +40,11 @@ def test_job_parameters_are_consistent(kind):
     assert j.attempts == 4096 * j.planes * j.S * 100
     t = j.times()
     assert t[0] == 0 and t[-1] == 100 and all(x < y for x, y in zip(t, t[1:]))
-    assert j.footprint() > j.S * j.planes * 4096 // 8
+    # admission footprints come from the library's plan (no device needed for one-CTA plans)
+    pl = j.plan()
+    assert pl["S"] == j.S and pl["planes"] == j.planes and pl["cluster"] == 1
+    assert j.device_bytes() > j.S * j.planes * 4096 // 8
+    assert j.smem_demand() == pl["groups"] * pl["smem_bytes"] > 0
     if kind == "two_lane":
         assert p.model == A.ASEP_MODEL_TWO_LANE and p.dis_kind == A.ASEP_DIS_TURNING
     if kind == "bimodal":

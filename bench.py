@@ -120,14 +120,20 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {
-    "domain": ("asep_kernels.cu", "asep_domain.cuh", "asep_device.cuh", "asep_internal.h"),
+    "domain": ("asep_kernels.cu", "asep_resident.cuh", "asep_domain.cuh", "asep_device.cuh", "asep_internal.h"),
+    "domain_bal": ("asep_balance.cu", "asep_resident.cuh", "asep_domain.cuh", "asep_device.cuh", "asep_internal.h"),
     "sca": ("asep_sca.cu", "asep_device.cuh", "asep_internal.h"),
     "sca_stream": ("asep_sca.cu", "asep_device.cuh", "asep_internal.h"),
+    "stream": ("asep_stream.cu", "asep_domain.cuh", "asep_device.cuh", "asep_internal.h"),
+    "serial": ("asep_serial.cu", "asep_device.cuh", "asep_internal.h"),
 }
 TRAFFIC_FILES = {
     "domain": "k_domain_growth_regime_traffic.txt",
+    "domain_bal": "k_domain_bal_growth_regime_traffic.txt",
     "sca": "k_sca_growth_regime_traffic.txt",
     "sca_stream": "k_sca_stream_large_rings_traffic.txt",
+    "stream": "k_stream_large_rings_traffic.txt",
+    "serial": "k_serial_plain_tasep_traffic.txt",
 }
 
 
@@ -183,6 +189,64 @@ def cpu_oracle_sample(target_s: float, n_mcs_cap: int = N_MCS):
             "value_per_core": k * L_SITES * n / dt / cores, "seconds": dt, "attempts": k * L_SITES * n,
             "sample": f"{k} of 256 samples x {n} of 2^14 sweeps (init + sweeps + W^2 at the log times), "
                       f"{dt:.1f} s on {cores} host threads"}
+
+
+def cpu_baselines_by_config(seconds_each: float = 2.5):
+    """The oracle's two programs on the host cores for configurations 0-3:
+    the schedule replay (the GPU path's own schedule, bit-identical to it:
+    serial RSU for configuration 0, the domain schedule for 1-3) and the
+    independent serial RSU reference (its own generator).  Configuration 0
+    runs in full (8 samples x 10^4 sweeps); the others on a bounded sample:
+    the first `cores` samples over as many sweeps of their window as fit
+    about `seconds_each` seconds, from the flat or random start.  One thread
+    per sample."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    th = oracle.threshold
+    oracle.build()
+    cfgs = [
+        ("0: plain TASEP, L=4096, 8 samples, 10^4 MCS", 10_000, 8,
+         dict(L=4096, schedule=oracle.SCHED_SERIAL, samples_per_real=8, p_thr=oracle.ALWAYS, q_thr=0, seed=1)),
+        ("1: growth regime, L=2^17, ASEP p=0.75 q=0.25 (256 samples, 2^14 MCS)", 1 << 14, 256,
+         dict(L=1 << 17, D=256, samples_per_real=min(cores, 256), p_thr=th(0.75), q_thr=th(0.25), seed=1)),
+        ("2: bimodal disorder, L=2^16, Q=0.1, p_slow=0.3 (64 x 4 samples, 10^4-MCS window)", 10_000, 256,
+         dict(L=1 << 16, D=256, n_realizations=max(1, min(cores, 256) // 4), samples_per_real=4,
+              p_thr=oracle.ALWAYS, q_thr=0, dis_kind=oracle.DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3),
+              dis_seed=2, seed=1)),
+        ("3: two lanes, 2 x L=2^16, turning 0.05, omega 0.1, D=128 (128 samples, 10^4-MCS window)", 10_000, 128,
+         dict(model=oracle.MODEL_TWO_LANE, L=1 << 16, D=128, samples_per_real=min(cores, 128), p_thr=oracle.ALWAYS,
+              q_thr=oracle.ALWAYS, dis_kind=oracle.DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=3,
+              init_kind=oracle.INIT_BERNOULLI_HALF, init_seed=4, seed=1)),
+    ]
+    rows = []
+    for name, window, s_full, kw in cfgs:
+        P = oracle.Params(**kw)
+        mask = oracle.disorder(P)
+        for program in ("replay", "serial reference"):
+            def run(n, st):
+                if program == "replay":
+                    oracle.replay(P, st, 0, n, mask=mask, threads=cores)
+                else:
+                    oracle.serial_reference(P, st, n, rng_seeds=[17 + s for s in range(P.S)], mask=mask,
+                                            threads=cores)
+
+            st = oracle.init_state(P)
+            t0 = time.perf_counter()
+            run(1, st)
+            per_sweep = max(1e-6, time.perf_counter() - t0)
+            n = window if P.S == s_full else int(max(2, min(window, seconds_each / per_sweep)))
+            st = oracle.init_state(P)
+            t0 = time.perf_counter()
+            run(n, st)
+            dt = time.perf_counter() - t0
+            attempts = P.S * P.L * P.planes * n
+            rows.append({"config": name, "program": program, "samples": P.S, "sweeps": n,
+                         "attempts_per_s": attempts / dt, "attempts_per_s_per_core": attempts / dt / min(cores, P.S),
+                         "threads": min(cores, P.S), "seconds": dt,
+                         "sample": "full run" if (P.S == s_full and n == window) else
+                         f"{P.S} of {s_full} samples x {n} of {window} sweeps"})
+    return rows
 
 
 def workload_config(world: int) -> dict:
@@ -344,11 +408,14 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_config(world),
-            "plan": ({"cluster": plan.cluster, "samples_per_group": plan.samples_per_group}
-                     if plan else "default"),
+            "plan": ({"cluster": plan.cluster, "samples_per_group": plan.samples_per_group,
+                      "balance_chunk_sweeps": plan.balance or "off",
+                      "launch_sweeps": plan.launch_sweeps or "auto"} if plan else "default"),
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s", "frac": achieved_ops / peak_ops, "traffic": _traffic_from_profile(),
-                         "kernel": "k_domain<ring>", "kernel_ms": kernel_ms,
+                         "unit": "Tops/s", "frac": achieved_ops / peak_ops,
+                         "traffic": _traffic_from_profile("domain_bal" if plan and plan.balance else "domain"),
+                         "kernel": "k_domain_bal<ring> (balanced launch)" if plan and plan.balance
+                         else "k_domain<ring>", "kernel_ms": kernel_ms,
                          "ops_per_attempt": OPS_PER_ATTEMPT,
                          "peak_basis": f"{SMS} SMs x {LANES_PER_SM} int32 lanes/clk x {max_mhz:.0f} MHz (issue)",
                          "philox_only_attempts_per_s": 4 * philox_calls_s,
@@ -360,8 +427,8 @@ def run_ours(args):
             "clocks": clk,
         }
         if tune_table:
-            line["autotune"] = [{k: r[k] for k in ("cluster", "samples_per_group", "ms_per_sweep")}
-                                for r in tune_table]
+            line["autotune"] = [{k: v for k, v in r.items() if k != "requested"} for r in tune_table]
+            line["autotune_batch"] = batch_mode_table()
         if not args.no_workloads and world == 1:
             line["sca"] = sca_growth(max(1, min(args.steps, 5)), peak_ops)
             line["workloads"] = other_workloads(tune=not args.no_autotune)
@@ -369,10 +436,30 @@ def run_ours(args):
             line["serving"] = serving_comparison(capacity=value)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
+            line["cpu_baseline"]["by_config"] = cpu_baselines_by_config()
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def batch_mode_table(n_contexts: int = 64, step_sweeps: int = 8, steps: int = 50):
+    """The batch knob of the autotuner on small jobs, where launch overhead
+    matters: 64 contexts of the served mix's small end (L in [2^10, 2^14],
+    1-16 samples, the four families) advanced in steps of 8 sweeps, eager
+    persistent launches against one captured CUDA graph replayed per step
+    (bit-identical lattices required)."""
+    from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300 import autotune, serve
+
+    jobs = serve.make_trace(n_contexts, seed=7, rate_hz=1.0, L_range=(1 << 10, 1 << 14), samples_range=(1, 16),
+                            n_mcs_range=(100, 100))
+
+    def make():
+        return [A.asep_create(j.params(), sample_times=[]) for j in jobs]
+
+    mode, rows = autotune.tune_batch_mode(make, [step_sweeps] * n_contexts, steps=steps)
+    return {"choice": mode, "contexts": n_contexts, "step_sweeps": step_sweeps, "rows": rows}
 
 
 def sca_growth(steps: int, peak_ops: float):
@@ -480,7 +567,9 @@ def other_workloads(tune: bool = True):
                 from paper_1012_0385_gb300.autotune import autotune
 
                 choice, _ = autotune(ctx, probe_sweeps=16)
-                tuned = {"cluster": choice.cluster, "samples_per_group": choice.samples_per_group, "autotuned": True}
+                tuned = {"cluster": choice.cluster, "samples_per_group": choice.samples_per_group,
+                         "balance_chunk_sweeps": choice.balance or "off",
+                         "launch_sweeps": choice.launch_sweeps or "auto", "autotuned": True}
             A.asep_reset(ctx, seed=kw["seed"], init_seed=kw.get("init_seed", 0))
             A.asep_sweep(ctx, 8)  # warm-up launch
             A.asep_reset(ctx, seed=kw["seed"], init_seed=kw.get("init_seed", 0))
@@ -553,22 +642,41 @@ def serving_comparison(capacity: float, n_jobs: int = 500, seed: int = 2026, loa
 
 
 def profile_case(schedule: str = "domain"):
-    """The benchmarked configuration with 64 sweeps instead of 2^14 (one
-    height record, at the end): the kernel reads and writes each lattice once
-    per launch, so its DRAM traffic per launch is that of a full step; only
-    the loop is shorter.  schedule "sca" runs the same workload under the
-    two-sub-lattice SCA kernel; "sca_stream" runs two sweeps (four launches,
-    one per phase) of the streamed SCA on 8 rings of 2^28 sites (256 MB)."""
+    """Short untimed runs of one kernel each, for ncu:
+    "domain"      the benchmarked configuration, 64 sweeps in one launch of
+                  k_domain (one record, at the end; the kernel reads and
+                  writes each lattice once per launch, so its DRAM traffic per
+                  launch is that of a full step);
+    "domain_bal"  the same as a balanced launch (k_domain_bal), 512 sweeps in
+                  chunks of 32: the groups move between SMs 16 times;
+    "sca"         the same workload under the two-sub-lattice SCA (k_sca);
+    "sca_stream"  two sweeps (four launches, one per phase) of the streamed
+                  SCA on 8 rings of 2^28 sites (256 MB);
+    "stream"      two sweeps (four launches) of the streamed domain tier
+                  (k_stream) on 16 rings of 2^24 sites (32 MB), the bench's
+                  streamed window;
+    "serial"      1000 sweeps of k_serial on the plain-TASEP configuration
+                  (L = 4096, 8 samples, a warp per sample)."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
 
     th = A.asep_threshold
-    if schedule == "sca_stream":
-        prm = A.make_params(L=1 << 28, schedule=A.ASEP_SCHED_SCA, samples_per_real=8, p_thr=th(P_RATE),
-                            q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
+    if schedule in ("sca_stream", "stream", "serial"):
+        if schedule == "sca_stream":
+            prm = A.make_params(L=1 << 28, schedule=A.ASEP_SCHED_SCA, samples_per_real=8, p_thr=th(P_RATE),
+                                q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
+            n = 2
+        elif schedule == "stream":
+            prm = A.make_params(L=1 << 24, domain_sites=256, samples_per_real=16, p_thr=th(P_RATE), q_thr=th(Q_RATE),
+                                seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS)
+            n = 2
+        else:
+            prm = A.make_params(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=8, p_thr=A.ASEP_ALWAYS,
+                                q_thr=0, seed=SEED)
+            n = 1000
         with A.asep_create(prm, sample_times=[]) as ctx:
-            A.asep_sweep(ctx, 2)
+            A.asep_sweep(ctx, n)
             A.asep_sync(ctx)
         torch.cuda.synchronize()
         print("profile case done", flush=True)
@@ -576,9 +684,12 @@ def profile_case(schedule: str = "domain"):
     sched = A.ASEP_SCHED_SCA if schedule == "sca" else A.ASEP_SCHED_DOMAIN
     prm = A.make_params(L=L_SITES, domain_sites=DOMAIN, samples_per_real=SAMPLES, p_thr=th(P_RATE),
                         q_thr=th(Q_RATE), seed=SEED, flags=A.ASEP_FLAG_NO_HOP_COUNTS, schedule=sched)
+    n = 512 if schedule == "domain_bal" else 64
     # one record, at the end: the full run records 131 times in 2^14 sweeps
-    with A.asep_create(prm, sample_times=[64]) as ctx:
-        A.asep_sweep(ctx, 64)
+    with A.asep_create(prm, sample_times=[n]) as ctx:
+        if schedule == "domain_bal":
+            A.asep_set_balance(ctx, 32)
+        A.asep_sweep(ctx, n)
         A.asep_sync(ctx)
     torch.cuda.synchronize()
     print("profile case done", flush=True)
@@ -598,8 +709,9 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the windows of the other configurations")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
-    ap.add_argument("--profile-case", nargs="?", const="domain", choices=["domain", "sca", "sca_stream"],
-                    help="one untimed launch of the benchmarked kernel (all 256 samples, 64 sweeps) for ncu")
+    ap.add_argument("--profile-case", nargs="?", const="domain",
+                    choices=["domain", "domain_bal", "sca", "sca_stream", "stream", "serial"],
+                    help="a short untimed run of one kernel for ncu (see profile_case)")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args.profile_case)

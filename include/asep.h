@@ -317,10 +317,26 @@ int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group);
  * sweep index).  Takes effect for the next call. */
 int asep_set_launch_sweeps(asep_ctx* ctx, uint32_t max_sweeps);
 
-/* Wait for all work of the context.  ASEP_ERR_TIMEOUT: a streamed tile's
- * wait for its bulk copy ran out (after one second); the results since are
- * invalid and every later call reports it until asep_reset or
- * asep_load_state replaces the lattice. */
+/* Balanced launches of a domain-schedule context whose samples sit in one
+ * CTA each (or a few per CTA): a launch's sweeps are cut into chunks of
+ * chunk_sweeps (at most 4096) and a persistent grid, as many CTAs as are
+ * resident at once, takes (sample group, chunk) items in chunk-major order;
+ * a CTA starts chunk k of a group once chunk k - 1 has written the group's
+ * lattice back, so groups move between SMs between chunks and no SM idles
+ * half-loaded while others hold two groups (e.g. 256 samples on 152 SMs).
+ * 0 (the default) = one CTA per group for the whole launch.  Results never
+ * depend on it.  The first nonzero call allocates (S + 1) words of device
+ * memory for the chunk flags.  The wait for a previous chunk is bounded (5
+ * seconds): if it runs out the launch gives up and asep_sync reports
+ * ASEP_ERR_TIMEOUT.  Cluster and streamed plans ignore it; batches do not
+ * use it.  No counterpart in the paper (its blocks each keep one chain). */
+int asep_set_balance(asep_ctx* ctx, uint32_t chunk_sweeps);
+
+/* Wait for all work of the context.  ASEP_ERR_TIMEOUT: a bounded
+ * device-side wait ran out -- a streamed tile's wait for its bulk copy (one
+ * second), or a balanced launch's wait for a previous chunk (five seconds);
+ * the results since are invalid and every later call reports it until
+ * asep_reset or asep_load_state replaces the lattice. */
 int asep_sync(asep_ctx* ctx);
 
 /* Fault injection for tests of the timeout path (default ASEP_FAULT_NONE).
@@ -330,6 +346,11 @@ int asep_sync(asep_ctx* ctx);
  * faults or hangs.  Takes effect for the next launch. */
 #define ASEP_FAULT_NONE 0u
 #define ASEP_FAULT_COPY_STALL 1u
+/* ASEP_FAULT_BALANCE_STALL: in a balanced launch, sample group 0 never
+ * announces its first chunk, so the CTA that takes its second chunk waits
+ * until the bound runs out (five seconds), the others stop waiting, and the
+ * sweep reports ASEP_ERR_TIMEOUT; nothing faults or hangs. */
+#define ASEP_FAULT_BALANCE_STALL 2u
 int asep_inject_fault(asep_ctx* ctx, uint32_t fault);
 
 /* Free everything the context owns.  NULL-safe; synchronises first. */

@@ -32,7 +32,7 @@ ASEP_SCHED_DOMAIN, ASEP_SCHED_SERIAL, ASEP_SCHED_SCA = 0, 1, 2
 ASEP_DIS_NONE, ASEP_DIS_BIMODAL, ASEP_DIS_TURNING, ASEP_DIS_BIMODAL_PQ, ASEP_DIS_CROSSING = 0, 1, 2, 3, 4
 ASEP_INIT_FLAT_ALT, ASEP_INIT_BERNOULLI_HALF = 0, 1
 ASEP_ALWAYS = 0xFFFFFFFF
-ASEP_FAULT_NONE, ASEP_FAULT_COPY_STALL = 0, 1
+ASEP_FAULT_NONE, ASEP_FAULT_COPY_STALL, ASEP_FAULT_BALANCE_STALL = 0, 1, 2
 ASEP_FLAG_NO_HOP_COUNTS = 1
 ASEP_FLAG_PROFILE = 2
 ASEP_FLAG_AUTOCORR = 4
@@ -96,7 +96,7 @@ EXPORTED = ("asep_create", "asep_plan", "asep_sweep", "asep_width", "asep_state"
             "asep_disorder", "asep_get_info", "asep_sync", "asep_destroy", "asep_last_error", "asep_threshold",
             "asep_poisson_table", "asep_philox_bench", "asep_attempt_bench", "asep_version", "asep_batch_create", "asep_batch_sweep",
             "asep_batch_graph", "asep_batch_set_launch", "asep_batch_destroy", "asep_batch_last_error",
-            "asep_batch_sweep_static", "asep_set_plan", "asep_set_launch_sweeps", "asep_currents", "asep_profile", "asep_autocorr",
+            "asep_batch_sweep_static", "asep_set_plan", "asep_set_launch_sweeps", "asep_set_balance", "asep_currents", "asep_profile", "asep_autocorr",
             "asep_height_offset", "asep_inject_fault")
 
 
@@ -155,6 +155,7 @@ def lib():
             L.asep_batch_sweep_static.argtypes = [P(vp), P(ctypes.c_uint64), ctypes.c_uint32, vp]
             L.asep_set_plan.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32]
             L.asep_set_launch_sweeps.argtypes = [vp, ctypes.c_uint32]
+            L.asep_set_balance.argtypes = [vp, ctypes.c_uint32]
             L.asep_currents.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
             L.asep_profile.argtypes = [vp, P(ctypes.c_uint32), ctypes.c_size_t]
             L.asep_autocorr.argtypes = [vp, P(ctypes.c_int64), ctypes.c_size_t]
@@ -352,6 +353,10 @@ def asep_set_plan(ctx, cluster: int = 0, samples_per_group: int = 0) -> None:
 
 def asep_set_launch_sweeps(ctx, max_sweeps: int = 0) -> None:
     _check(lib().asep_set_launch_sweeps(_h(ctx), int(max_sweeps)), _h(ctx))
+
+
+def asep_set_balance(ctx, chunk_sweeps: int = 0) -> None:
+    _check(lib().asep_set_balance(_h(ctx), int(chunk_sweeps)), _h(ctx))
 
 
 def asep_width(ctx):

@@ -1,13 +1,25 @@
-"""Autotuner for the launch plan of a domain-schedule context.
+"""Autotuner for the launches of a domain-schedule context and of a batch.
 
-The plan is the "tile" of the resident kernel: how many CTAs one sample is
-spread over (1 = whole samples in one CTA; 2..16 = a thread-block cluster,
-i.e. 2D/32 words per thread and G/cluster columns per CTA) and how many small
-samples share one CTA.  The sweeps per launch are fixed by the counter width
-(every launch covers up to the context's limit).  No plan changes a result:
-the tuner times every valid plan on a short probe run and, as a guard,
-requires the probe's lattices to be bit-identical to those of the default
-plan before it accepts any timing.
+Knobs, each timed on a short probe with CUDA events:
+
+* the plan, the "tile" of the resident kernel: how many CTAs one sample is
+  spread over (1 = whole samples in one CTA; 2..16 = a thread-block cluster,
+  i.e. G/cluster columns of 2D sites per CTA) and how many small samples
+  share one CTA;
+* balanced launches (``asep_set_balance``): whole launches per sample
+  group, or persistent CTAs taking (group, chunk of sweeps) items so that
+  groups move between SMs -- off, or the chunk length;
+* sweeps per launch (``asep_set_launch_sweeps``): the automatic bound (the
+  32-bit per-lane hop counters) or shorter launches;
+* for a batch: eager persistent launches (``asep_batch_sweep``) or one
+  captured CUDA graph replayed per step (``asep_batch_graph``).
+
+The words each thread handles are not a knob: a thread holds one column, the
+2D/32 words of a domain pair, and the domain size D is part of the schedule's
+definition -- another D gives other (equally valid) trajectories, so it is a
+parameter of the job, not of the launch.  No knob changes a result: as a
+guard, every probe's lattices must be bit-identical to the first one's
+before its timing is accepted.
 """
 from __future__ import annotations
 
@@ -25,6 +37,8 @@ class Choice:
     cluster: int
     samples_per_group: int
     ms_per_sweep: float
+    launch_sweeps: int = 0  # 0 = automatic
+    balance: int = 0  # sweeps per chunk of a balanced launch (0 = off)
 
 
 def candidates(ctx) -> list[tuple[int, int]]:
@@ -61,10 +75,34 @@ def _probe(ctx, n_sweeps: int, seed: int) -> tuple[float, np.ndarray]:
     return e0.elapsed_time(e1) / n_sweeps, words
 
 
-def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345) -> tuple[Choice, list[dict]]:
+def _sm_count() -> int:
+    import torch
+
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def launch_sweep_candidates(probe_sweeps: int) -> list[int]:
+    """0 (automatic: the whole probe in one launch) and shorter launches."""
+    out = [0]
+    for k in (2, 4, 8):
+        if probe_sweeps // k >= 1 and probe_sweeps // k not in out:
+            out.append(probe_sweeps // k)
+    return out
+
+
+BALANCE_CHUNKS = (16, 32, 64)
+
+
+def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345, launch_sweeps: bool = True,
+             balance: bool = True) -> tuple[Choice, list[dict]]:
     """Time every valid plan on `ctx` (its state is reset; re-seed or reset it
     afterwards), check bit-exactness against the automatic plan, apply the
-    fastest plan to `ctx` and return it with the full table."""
+    fastest plan to `ctx`; then, on that plan, time balanced launches (one
+    CTA per group for whole launches, or chunks of 16/32/64 sweeps, on a
+    probe of 16 of the longest chunks, when the plan keeps samples in single
+    CTAs and there are more groups than SMs) and the sweeps-per-launch caps,
+    applying the fastest of each.  Returns the chosen plan and the full table
+    (rows with knob "plan", "balance" or "launch_sweeps")."""
     table = []
     ref_words = None
     best = None
@@ -79,13 +117,82 @@ def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345) -> tuple[Choice, li
         elif not np.array_equal(words, ref_words):
             raise RuntimeError(f"plan cluster={cluster} spc={spc} changed the result")
         info = A.asep_get_info(ctx)
-        row = {"cluster": info["cluster"], "samples_per_group": info["samples_per_group"], "ms_per_sweep": ms,
-               "requested": [cluster, spc]}
+        row = {"knob": "plan", "cluster": info["cluster"], "samples_per_group": info["samples_per_group"],
+               "ms_per_sweep": ms, "requested": [cluster, spc]}
         table.append(row)
         if best is None or ms < best.ms_per_sweep:
             best = Choice(info["cluster"], info["samples_per_group"], ms)
     A.asep_set_plan(ctx, best.cluster, best.samples_per_group if best.cluster == 1 else 0)
+    info = A.asep_get_info(ctx)
+    sms = _sm_count()
+    if balance and info["cluster"] == 1 and info["groups"] > sms:
+        n = 16 * max(BALANCE_CHUNKS)
+        _, long_ref = _probe(ctx, n, seed)  # reference lattices of the longer probe
+        best_chunk, best_ms = 0, None
+        for chunk in (0,) + BALANCE_CHUNKS:
+            A.asep_set_balance(ctx, chunk)
+            ms, words = _probe(ctx, n, seed)
+            if not np.array_equal(words, long_ref):
+                raise RuntimeError(f"balanced launches in chunks of {chunk} sweeps changed the result")
+            table.append({"knob": "balance", "chunk_sweeps": chunk or "off", "ms_per_sweep": ms})
+            if best_ms is None or ms < 0.99 * best_ms:  # only when measurably faster
+                best_chunk, best_ms = chunk, ms
+        A.asep_set_balance(ctx, best_chunk)
+        best.balance = best_chunk
+    if launch_sweeps:
+        best_cap, best_ms = 0, None
+        for cap in launch_sweep_candidates(probe_sweeps):
+            A.asep_set_launch_sweeps(ctx, cap)
+            ms, words = _probe(ctx, probe_sweeps, seed)
+            if not np.array_equal(words, ref_words):
+                raise RuntimeError(f"{cap} sweeps per launch changed the result")
+            table.append({"knob": "launch_sweeps", "launch_sweeps": cap or "auto", "ms_per_sweep": ms})
+            # shorter launches only when measurably faster (1 %): noise must not split long runs
+            if best_ms is None or ms < 0.99 * best_ms:
+                best_cap, best_ms = cap, ms
+        A.asep_set_launch_sweeps(ctx, best_cap)
+        best.launch_sweeps = best_cap
     return best, table
+
+
+def tune_batch_mode(make_contexts, step_sweeps, steps: int = 20) -> tuple[str, list[dict]]:
+    """Eager persistent launches or a captured CUDA graph for a batch of
+    contexts advanced in equal steps: `make_contexts()` returns fresh
+    contexts (same parameters every call), each advanced `steps` times by
+    `step_sweeps` (one value per context).  Both modes run the same steps
+    from the same start; their final lattices must agree bit for bit.
+    Returns "graph" or "eager" and the table (ms per step)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    rows, finals = [], {}
+    for mode in ("eager", "graph"):
+        ctxs = make_contexts()
+        with A.asep_batch_create(max_jobs=max(1, len(ctxs)), max_items=1 << 20) as b:
+            # one warm-up step (the graph mode captures here), then the timed steps
+            if mode == "eager":
+                A.asep_batch_sweep(b, ctxs, step_sweeps)
+            else:
+                A.asep_batch_graph(b, ctxs, step_sweeps, 1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if mode == "eager":
+                for _ in range(steps):
+                    A.asep_batch_sweep(b, ctxs, step_sweeps)
+            else:
+                A.asep_batch_graph(b, ctxs, step_sweeps, steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"knob": "batch_mode", "mode": mode, "contexts": len(ctxs),
+                         "ms_per_step": e0.elapsed_time(e1) / steps})
+            finals[mode] = [A.asep_state(c)[0] for c in ctxs]
+        for c in ctxs:
+            c.close()
+    if not all(np.array_equal(a, b) for a, b in zip(finals["eager"], finals["graph"])):
+        raise RuntimeError("graph replay changed the result")
+    best = min(rows, key=lambda r: r["ms_per_step"])["mode"]
+    return best, rows
 
 
 class PlanCache:
@@ -108,6 +215,7 @@ class PlanCache:
 
     def put(self, params, choice: Choice):
         self.data[self.key(params)] = {"cluster": choice.cluster, "samples_per_group": choice.samples_per_group,
+                                       "launch_sweeps": choice.launch_sweeps, "balance": choice.balance,
                                        "ms_per_sweep": choice.ms_per_sweep}
         tmp = self.path + ".tmp"
         with open(tmp, "w") as f:

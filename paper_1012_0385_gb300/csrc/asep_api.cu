@@ -63,6 +63,8 @@ struct asep_ctx {
   size_t smem = 0;
   uint32_t max_sweeps_per_launch = 1;
   uint32_t launch_sweeps = 0;      // caller's cap on sweeps per launch (0 = none)
+  uint32_t balance = 0;            // balanced launches: sweeps per chunk (0 = off)
+  uint32_t* d_progress = nullptr;  // balanced launches: [S + 1] chunk flags and queue counter
   uint64_t launches = 0;
   std::string err;
 };
@@ -835,6 +837,16 @@ int asep_sweep(asep_ctx* ctx, uint64_t n_mcs) {
       }
     } else if (ctx->p.schedule == ASEP_SCHED_SCA) {
       e = launch_sca(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
+    } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->balance && ctx->cluster == 1 && n > ctx->balance) {
+      BalanceLaunch b;
+      b.chunk = ctx->balance;
+      b.chunks = static_cast<uint32_t>((n + ctx->balance - 1) / ctx->balance);
+      b.progress = ctx->d_progress;
+      b.queue = ctx->d_progress + ctx->blocks;
+      b.err = ctx->d_err;
+      b.stall = ctx->fault == ASEP_FAULT_BALANCE_STALL ? 1u : 0u;
+      e = launch_domain_balanced(domain_desc(ctx, static_cast<uint32_t>(n)), b, ctx->threads, ctx->smem,
+                                 ctx->stream);
     } else if (ctx->p.schedule == ASEP_SCHED_DOMAIN) {
       e = launch_domain(domain_desc(ctx, static_cast<uint32_t>(n)), ctx->threads, ctx->smem, ctx->stream);
     } else {
@@ -908,7 +920,7 @@ int asep_reset(asep_ctx* ctx, uint64_t seed, uint64_t init_seed) {
 
 int asep_inject_fault(asep_ctx* ctx, uint32_t fault) {
   if (!ctx) return ASEP_ERR_INVALID;
-  if (fault > ASEP_FAULT_COPY_STALL) return fail(ctx, ASEP_ERR_INVALID, "unknown fault %u", fault);
+  if (fault > ASEP_FAULT_BALANCE_STALL) return fail(ctx, ASEP_ERR_INVALID, "unknown fault %u", fault);
   ctx->fault = fault;
   return ASEP_OK;
 }
@@ -917,16 +929,17 @@ int asep_sync(asep_ctx* ctx) {
   if (!ctx) return ASEP_ERR_INVALID;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
-  if (ctx->cluster == kStreamTier && ctx->d_err && !ctx->err_seen) {
+  if ((ctx->cluster == kStreamTier || ctx->balance) && ctx->d_err && !ctx->err_seen) {
     uint32_t flag = 0;
     if ((e = cudaMemcpy(&flag, ctx->d_err, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
-      return cuda_fail(ctx, e, "read the streamed tier's error flag");
+      return cuda_fail(ctx, e, "read the error flag");
     if (flag) {
       ctx->err_seen = 1;
-      return fail(ctx, ASEP_ERR_TIMEOUT, "a streamed tile's bulk copy did not complete; results are invalid");
+      return fail(ctx, ASEP_ERR_TIMEOUT, "a bounded device-side wait ran out (a streamed tile's bulk copy, or a "
+                  "balanced launch's previous chunk); results are invalid");
     }
   }
-  return ctx->err_seen ? fail(ctx, ASEP_ERR_TIMEOUT, "a streamed tile's bulk copy did not complete earlier") : ASEP_OK;
+  return ctx->err_seen ? fail(ctx, ASEP_ERR_TIMEOUT, "a bounded device-side wait ran out earlier") : ASEP_OK;
 }
 
 int asep_width(asep_ctx* ctx, int64_t* sum_h, uint64_t* sum_h2, double* w2, size_t n_entries) {
@@ -1392,6 +1405,20 @@ int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
 int asep_set_launch_sweeps(asep_ctx* ctx, uint32_t max_sweeps) {
   if (!ctx) return ASEP_ERR_INVALID;
   ctx->launch_sweeps = max_sweeps;
+  return ASEP_OK;
+}
+
+int asep_set_balance(asep_ctx* ctx, uint32_t chunk_sweeps) {
+  if (!ctx) return ASEP_ERR_INVALID;
+  if (chunk_sweeps && ctx->p.schedule != ASEP_SCHED_DOMAIN)
+    return fail(ctx, ASEP_ERR_INVALID, "balanced launches apply to the domain schedule");
+  if (chunk_sweeps > kMaxBalanceChunk)
+    return fail(ctx, ASEP_ERR_INVALID, "chunk of %u sweeps exceeds %u", chunk_sweeps, kMaxBalanceChunk);
+  if (chunk_sweeps && !ctx->d_progress) {
+    ctx->d_progress = static_cast<uint32_t*>(dev_alloc(ctx, (static_cast<size_t>(ctx->S) + 1) * sizeof(uint32_t)));
+    if (!ctx->d_progress) return fail(ctx, ASEP_ERR_NOMEM, "device allocation of the chunk flags failed");
+  }
+  ctx->balance = chunk_sweeps;
   return ASEP_OK;
 }
 

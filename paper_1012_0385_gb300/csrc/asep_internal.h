@@ -178,6 +178,21 @@ struct HeightsLaunch {
   HeightPart* parts;       // [S][planes][chunks] when W > kHeightChunkWords (else unused)
 };
 
+// Balanced launch of the resident tier (asep_balance.cu): persistent CTAs
+// take (sample group, chunk of `chunk` sweeps) items in chunk-major order.
+struct BalanceLaunch {
+  uint32_t chunk;      // sweeps per chunk
+  uint32_t chunks;     // chunks of this launch: ceil(n_sweeps / chunk)
+  uint32_t* progress;  // [n_groups + 1]: chunks each group has published, then the queue counter
+  uint32_t* queue;     // = progress + n_groups
+  uint32_t* err;       // set when a wait for a previous chunk runs out
+  uint32_t stall;      // fault injection: group 0 never publishes its first chunk
+};
+// Longest chunk the host allows (the device-side wait bound is sized for it).
+constexpr uint32_t kMaxBalanceChunk = 4096;
+cudaError_t launch_domain_balanced(const DomainLaunch& a, const BalanceLaunch& b, uint32_t threads, size_t smem,
+                                   cudaStream_t st);
+
 // Shared memory of the resident kernel, in bytes (planes of R2 + 1 rows:
 // the extra row mirrors the next column's row 0).
 size_t domain_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t Cp, uint32_t ptab_n, uint32_t threads);

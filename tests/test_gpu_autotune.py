@@ -75,9 +75,45 @@ def test_autotune_applies_the_fastest_valid_plan(tmp_path):
     with A.asep_create(A.make_params(**kw), sample_times=[]) as ctx:
         choice, table = autotune.autotune(ctx, probe_sweeps=16)
         assert len(table) >= 3
-        assert choice.ms_per_sweep == min(r["ms_per_sweep"] for r in table)
+        assert choice.ms_per_sweep == min(r["ms_per_sweep"] for r in table if r["knob"] == "plan")
         info = A.asep_get_info(ctx)
         assert info["cluster"] == choice.cluster
         cache = autotune.PlanCache(str(tmp_path / "plans.json"))
         cache.put(ctx.params, choice)
         assert autotune.PlanCache(str(tmp_path / "plans.json")).get(ctx.params)["cluster"] == choice.cluster
+
+
+@pytest.mark.parametrize("schedule", [A.ASEP_SCHED_DOMAIN, A.ASEP_SCHED_SCA, A.ASEP_SCHED_SERIAL])
+def test_sweeps_per_launch_never_change_results(schedule):
+    """The launch-sweeps knob splits a run into more launches; lattices,
+    every record and the counters stay bit-identical."""
+    kw = dict(L=1 << 14, schedule=schedule, samples_per_real=5, p_thr=th(0.75), q_thr=th(0.25))
+    if schedule == A.ASEP_SCHED_DOMAIN:
+        kw["domain_sites"] = 128
+    with A.asep_create(A.make_params(**kw), sample_times=[0, 2, 7, 19, 20]) as ctx:
+        ref = run(ctx, 20)
+        for cap in (1, 3, 7, 0):
+            A.asep_set_launch_sweeps(ctx, cap)
+            launches0 = A.asep_get_info(ctx)["kernel_launches"]
+            got = run(ctx, 20)
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), cap
+            if cap:
+                assert A.asep_get_info(ctx)["kernel_launches"] - launches0 >= 20 // cap
+
+
+def test_autotune_times_the_launch_sweeps_and_batch_mode():
+    kw = dict(L=1 << 15, domain_sites=256, samples_per_real=20, p_thr=th(0.75), q_thr=th(0.25))
+    with A.asep_create(A.make_params(**kw), sample_times=[]) as ctx:
+        choice, table = autotune.autotune(ctx, probe_sweeps=16)
+        caps = [r["launch_sweeps"] for r in table if r["knob"] == "launch_sweeps"]
+        assert caps == ["auto", 8, 4, 2]
+        assert choice.launch_sweeps in (0, 8, 4, 2)
+    shapes = [dict(L=2048, domain_sites=128, samples_per_real=3, p_thr=th(0.6), seed=5 + i) for i in range(6)]
+
+    def make():
+        return [A.asep_create(A.make_params(**k), sample_times=[]) for k in shapes]
+
+    mode, rows = autotune.tune_batch_mode(make, [4] * len(shapes), steps=5)
+    assert mode in ("eager", "graph") and [r["mode"] for r in rows] == ["eager", "graph"]
+    assert all(r["ms_per_step"] > 0 for r in rows)

@@ -162,6 +162,33 @@ def _traffic_from_profile(kernel: str = "domain"):
     return None
 
 
+WINDOW_KERNELS = ["serial", "domain", "domain", "domain", "sca", "sca", "stream", "sca_stream"]
+COUNTS_FILE = "window_kernels_counts.txt"
+
+
+def _inst_counts() -> dict:
+    """Thread instructions per attempt of the benchmarked kernels, from the
+    committed ncu summary: name ("window<i>", "headline_domain",
+    "headline_domain_bal") -> value, for kernels whose sources are unchanged
+    since the counts were taken."""
+    out = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", COUNTS_FILE)):
+            if line.startswith("#") or "=" not in line:
+                continue
+            kv = dict(x.split("=", 1) for x in line.split())
+            if kv.get("kernel_source_sha256_16") == kernel_source_digest(kv["family"]):
+                out[kv["name"]] = float(kv["inst_per_attempt"])
+    except Exception:
+        pass
+    return out
+
+
+def _window_counts() -> dict:
+    """Window index -> thread instructions per attempt (see _inst_counts)."""
+    return {int(k[len("window"):]): v for k, v in _inst_counts().items() if k.startswith("window")}
+
+
 def cpu_oracle_sample(target_s: float, n_mcs_cap: int = N_MCS):
     """Time the CPU oracle (whole path: init, sweeps, heights at the log
     times) on `cores` samples of the workload, sized to about target_s."""
@@ -247,6 +274,17 @@ def cpu_baselines_by_config(seconds_each: float = 2.5):
                          "sample": "full run" if (P.S == s_full and n == window) else
                          f"{P.S} of {s_full} samples x {n} of {window} sweeps"})
     return rows
+
+
+def _issue_fraction(rate: float, name: str, peak_ops: float):
+    """Issue slots the kernel fills: measured thread instructions per attempt
+    (ncu) x attempts/s, over 152 SMs x 128 lanes x clock; None without a
+    count for the current sources."""
+    ipa = _inst_counts().get(name)
+    if ipa is None:
+        return None
+    return {"inst_per_attempt": ipa, "achieved_tops": rate * ipa / 1e12, "peak_tops": peak_ops / 1e12,
+            "frac": rate * ipa / peak_ops, "source": "profiles/" + COUNTS_FILE}
 
 
 def workload_config(world: int) -> dict:
@@ -371,6 +409,10 @@ def run_ours(args):
         barrier()
         t0 = time.perf_counter()
         c = A.asep_create(params(), sample_times=times)
+        if plan:  # the tuned plan, as a user applies a cached one
+            A.asep_set_plan(c, plan.cluster, plan.samples_per_group if plan.cluster == 1 else 0)
+            A.asep_set_balance(c, plan.balance)
+            A.asep_set_launch_sweeps(c, plan.launch_sweeps)
         A.asep_sweep(c, N_MCS)
         sh, sh2, w2 = A.asep_width(c)
         A.asep_destroy(c)
@@ -422,6 +464,8 @@ def run_ours(args):
                          "rng_bitop_only_attempts_per_s": rb_attempts_s,
                          "rng_bitop_only_at_kernel_shape_attempts_per_s": rbk_attempts_s,
                          "frac_of_rng_bitop_only": value / rb_attempts_s},
+            "issue": _issue_fraction(value, "headline_domain_bal" if plan and plan.balance else "headline_domain",
+                                     peak_ops),
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -431,7 +475,7 @@ def run_ours(args):
             line["autotune_batch"] = batch_mode_table()
         if not args.no_workloads and world == 1:
             line["sca"] = sca_growth(max(1, min(args.steps, 5)), peak_ops)
-            line["workloads"] = other_workloads(tune=not args.no_autotune)
+            line["workloads"] = other_workloads(tune=not args.no_autotune, peak_ops=peak_ops, rng_bitop=rb_attempts_s)
         if not args.no_serving and world == 1:
             line["serving"] = serving_comparison(capacity=value)
         if not args.no_cpu_baseline and world == 1:
@@ -500,20 +544,9 @@ def sca_growth(steps: int, peak_ops: float):
                          "traffic": _traffic_from_profile("sca")}}
 
 
-def other_workloads(tune: bool = True):
-    """Device-timed windows of the other configurations of the study (one
-    run each after a warm-up launch, CUDA events on the launching stream):
-    plain TASEP under serial RSU and under the domain schedule (full 10^4
-    sweeps, snapshots every 100), quenched bimodal disorder and the two-lane
-    model with turning sites (10^4-sweep windows of their 10^7 / 10^6 sweep
-    runs, log-spaced sample times, two-lane currents, profile and
-    autocorrelation on), the latter also under the paper's two-lane SCA; the
-    paper's quenched SSEP (independent slow classes for both directions); and
-    the two streamed modes (domain schedule and SCA) on rings far beyond
-    shared memory.  Resident domain-schedule windows first take the
-    autotuner's plan (bit-exactness guarded; `tune`)."""
-    import torch
-
+def window_cases():
+    """(name, parameters, sample times, lanes) of the windows of the other
+    configurations (see other_workloads)."""
     from paper_1012_0385_gb300 import asep as A
     from paper_1012_0385_gb300.sampling import every, log_times
 
@@ -557,9 +590,31 @@ def other_workloads(tune: bool = True):
          dict(L=1 << 28, schedule=A.ASEP_SCHED_SCA, samples_per_real=8, p_thr=th(0.75), q_thr=th(0.25), seed=1,
               flags=A.ASEP_FLAG_NO_HOP_COUNTS), [200], 1),
     ]
+    return cases
+
+
+def other_workloads(tune: bool = True, peak_ops: float | None = None, rng_bitop: float | None = None):
+    """Device-timed windows of the other configurations of the study (one
+    run each after a warm-up launch, CUDA events on the launching stream):
+    plain TASEP under serial RSU and under the domain schedule (full 10^4
+    sweeps, snapshots every 100), quenched bimodal disorder and the two-lane
+    model with turning sites (10^4-sweep windows of their 10^7 / 10^6 sweep
+    runs, log-spaced sample times, two-lane currents, profile and
+    autocorrelation on), the latter also under the paper's two-lane SCA; the
+    paper's quenched SSEP (independent slow classes for both directions); and
+    the two streamed modes (domain schedule and SCA) on rings far beyond
+    shared memory.  Resident domain-schedule windows first take the
+    autotuner's plan (bit-exactness guarded; `tune`)."""
+    import torch
+
+    from paper_1012_0385_gb300 import asep as A
+    from paper_1012_0385_gb300.sampling import every, log_times
+
+    cases = window_cases()
+    counts = _window_counts()
     stream = torch.cuda.current_stream()
     out = []
-    for name, kw, times, lanes in cases:
+    for wi, (name, kw, times, lanes) in enumerate(cases):
         with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
             tuned = None
             if tune and kw.get("schedule", A.ASEP_SCHED_DOMAIN) == A.ASEP_SCHED_DOMAIN and \
@@ -592,6 +647,15 @@ def other_workloads(tune: bool = True):
                    "samples_per_group": info["samples_per_group"]}
             if tuned:
                 row["plan"] = tuned
+            # issue-slot roofline: measured instructions per attempt x attempts/s over the SMs' issue rate
+            if peak_ops and wi in counts:
+                ach = row["attempts_per_s"] * counts[wi]
+                row["roofline"] = {"bound": "alu", "unit": "Tops/s", "achieved": ach / 1e12, "peak": peak_ops / 1e12,
+                                   "frac": ach / peak_ops, "inst_per_attempt": counts[wi],
+                                   "basis": "thread instructions per attempt (ncu, profiles/" + COUNTS_FILE +
+                                            ") x attempts/s, over 152 SMs x 128 lanes x clock"}
+                if rng_bitop and WINDOW_KERNELS[wi] in ("serial", "domain", "stream"):
+                    row["roofline"]["frac_of_rng_bitop_only"] = row["attempts_per_s"] / rng_bitop
             if info["cluster"] == 32:
                 # streamed: each phase reads and writes every lattice word once (4 x L/8 bytes per plane
                 # and sweep); the whole window, launch gaps and records included, against measured HBM
@@ -607,38 +671,51 @@ def other_workloads(tune: bool = True):
     return out
 
 
-def serving_comparison(capacity: float, n_jobs: int = 500, seed: int = 2026, load: float = 0.4):
-    """The served ensemble mix (configuration 4) in a time-scaled reading:
-    Poisson arrivals of jobs drawn from the four workload families (plain
-    TASEP, ASEP growth, bimodal disorder, two lanes) with L log-uniform in
-    [2^10, 2^22] (the mix's full range; L above ~2^19 runs on thread-block
+def serving_comparison(capacity: float, n_jobs: int = 500, seed: int = 2026, load: float = 0.4,
+                       n_burst: int = 200, burst_seed: int = 77):
+    """The served ensemble mix (configuration 4) in a time-scaled reading,
+    replayed with continuous batching (admission by the library's device- and
+    shared-memory plan, up to 10^4 jobs in flight, age-weighted quanta) and
+    with one launch per job, on the same GPU; results bit-identical between
+    the two.  Jobs are drawn from the four workload families (plain TASEP,
+    ASEP growth, bimodal disorder, two lanes) with L log-uniform in [2^10,
+    2^22] (the mix's full range; L above ~2^19 runs on thread-block
     clusters), 1-256 samples and n_mcs log-uniform in [5, 5000] (the mix's
-    10^3-10^6 divided by 200, so that both modes finish in minutes),
-    arrivals offering 40 % of the headline kernel's rate (about 80 % of what
-    the batched server sustains on this mix: two-lane, disordered and
-    cluster-tier jobs run slower than the benchmarked ring).  The same trace
-    is replayed with continuous batching (admission by the library's device-
-    and shared-memory plan, up to 10^4 jobs in flight) and with one launch per
-    job; the results are bit-identical between the two."""
+    10^3-10^6 divided by 200, so that both modes finish in minutes).  Two
+    regimes: `latency` -- n_jobs Poisson arrivals offering 40 % of the
+    headline kernel's rate (about 80 % of what the batched server sustains on
+    this mix: two-lane, disordered and cluster-tier jobs run slower than the
+    benchmarked ring), where throughput follows the arrivals and the
+    latencies differ; `capacity` -- n_burst jobs arriving at once, where the
+    makespan measures each mode's throughput."""
     from paper_1012_0385_gb300 import serve
 
-    def trace():
-        return serve.make_trace(n_jobs, seed=seed, rate_hz=1.0, L_range=(1 << 10, 1 << 22), samples_range=(1, 256),
-                                n_mcs_range=(5, 5000), load=load, capacity=capacity)
+    def trace(n, sd, at_zero):
+        t = serve.make_trace(n, seed=sd, rate_hz=1.0, L_range=(1 << 10, 1 << 22), samples_range=(1, 256),
+                             n_mcs_range=(5, 5000), load=load, capacity=capacity)
+        if at_zero:
+            for j in t:
+                j.arrival = 0.0
+        return t
 
-    batched_jobs, plain_jobs = trace(), trace()
-    batched = serve.serve_batched(batched_jobs, quantum_s=0.02)
-    plain = serve.serve_plain(plain_jobs)
-    same = all(np.array_equal(a.result[k], b.result[k]) for a, b in zip(batched_jobs, plain_jobs)
-               for k in ("sum_h", "sum_h2", "counters"))
-    rate = n_jobs / max(j.arrival for j in batched_jobs)
-    return {"trace": f"{n_jobs} jobs, Poisson ~{rate:.2f} Hz (offered load {load:g} of {capacity:.3g} attempts/s), "
-                     "kinds tasep/asep/bimodal/two_lane, L log-uniform [2^10, 2^22], samples log-uniform [1, 256], "
-                     "n_mcs log-uniform [5, 5000] (the configuration's [10^3, 10^6] / 200)",
+    out = {}
+    for regime, n, sd, at_zero in (("latency", n_jobs, seed, False), ("capacity", n_burst, burst_seed, True)):
+        batched_jobs, plain_jobs = trace(n, sd, at_zero), trace(n, sd, at_zero)
+        batched = serve.serve_batched(batched_jobs, quantum_s=0.02)
+        plain = serve.serve_plain(plain_jobs)
+        same = all(np.array_equal(a.result[k], b.result[k]) for a, b in zip(batched_jobs, plain_jobs)
+                   for k in ("sum_h", "sum_h2", "counters"))
+        desc = (f"{n} jobs arriving together" if at_zero else
+                f"{n} jobs, Poisson ~{n / max(j.arrival for j in batched_jobs):.2f} Hz (offered load {load:g} of "
+                f"{capacity:.3g} attempts/s)")
+        out[regime] = {
+            "trace": desc + ", kinds tasep/asep/bimodal/two_lane, L log-uniform [2^10, 2^22], samples "
+                            "log-uniform [1, 256], n_mcs log-uniform [5, 5000] (the configuration's [10^3, 10^6] / 200)",
             "batched": batched, "plain": plain, "results_identical": bool(same),
             "throughput_ratio": batched["throughput_attempts_per_s"] / plain["throughput_attempts_per_s"],
             "p50_ratio": batched["p50_latency_s"] / plain["p50_latency_s"],
             "p99_ratio": batched["p99_latency_s"] / plain["p99_latency_s"]}
+    return out
 
 
 def profile_case(schedule: str = "domain"):
@@ -656,12 +733,27 @@ def profile_case(schedule: str = "domain"):
                   (k_stream) on 16 rings of 2^24 sites (32 MB), the bench's
                   streamed window;
     "serial"      1000 sweeps of k_serial on the plain-TASEP configuration
-                  (L = 4096, 8 samples, a warp per sample)."""
+                  (L = 4096, 8 samples, a warp per sample);
+    "window<i>"   window i of window_cases(), 32 sweeps (streamed: 2)."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
 
     th = A.asep_threshold
+    if schedule.startswith("window"):
+        # one window of the other configurations, briefly: 32 sweeps (streamed ones 2), one record at the end
+        name, kw, times, lanes = window_cases()[int(schedule[len("window"):])]
+        kw = dict(kw)
+        n = 2 if kw["L"] >= 1 << 24 else 32
+        if kw.get("flags", 0) & A.ASEP_FLAG_AUTOCORR:
+            kw["autocorr_t0"] = n
+        with A.asep_create(A.make_params(**kw), sample_times=[n]) as ctx:
+            A.asep_sweep(ctx, n)
+            A.asep_sync(ctx)
+            info = A.asep_get_info(ctx)
+        torch.cuda.synchronize()
+        print(f"profile case done: {name}; attempts {lanes * kw['L'] * info['S'] * n} in {n} sweeps", flush=True)
+        return 0
     if schedule in ("sca_stream", "stream", "serial"):
         if schedule == "sca_stream":
             prm = A.make_params(L=1 << 28, schedule=A.ASEP_SCHED_SCA, samples_per_real=8, p_thr=th(P_RATE),
@@ -710,7 +802,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
     ap.add_argument("--profile-case", nargs="?", const="domain",
-                    choices=["domain", "domain_bal", "sca", "sca_stream", "stream", "serial"],
+                    choices=["domain", "domain_bal", "sca", "sca_stream", "stream", "serial"] +
+                    [f"window{i}" for i in range(8)],
                     help="a short untimed run of one kernel for ncu (see profile_case)")
     args = ap.parse_args()
     if args.profile_case:

@@ -96,60 +96,55 @@ BALANCE_CHUNKS = (16, 32, 64)
 def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345, launch_sweeps: bool = True,
              balance: bool = True) -> tuple[Choice, list[dict]]:
     """Time every valid plan on `ctx` (its state is reset; re-seed or reset it
-    afterwards), check bit-exactness against the automatic plan, apply the
-    fastest plan to `ctx`; then, on that plan, time balanced launches (one
-    CTA per group for whole launches, or chunks of 16/32/64 sweeps, on a
-    probe of 16 of the longest chunks, when the plan keeps samples in single
-    CTAs and there are more groups than SMs) and the sweeps-per-launch caps,
-    applying the fastest of each.  Returns the chosen plan and the full table
-    (rows with knob "plan", "balance" or "launch_sweeps")."""
-    table = []
-    ref_words = None
-    best = None
+    afterwards) and, for plans that keep samples in single CTAs with more
+    sample groups than SMs, also balanced launches in chunks of 16/32/64
+    sweeps; when balanced launches are among the candidates every candidate
+    runs the same longer probe (16 of the longest chunks) so that chunking
+    shows.  Every candidate's lattices must equal the first one's.  The
+    fastest (plan, chunk) is applied; then, on it and on the same probe, the
+    sweeps-per-launch caps are timed and the fastest applied.  Returns the choice and the table
+    (rows with knob "plan" or "launch_sweeps")."""
+    sms = _sm_count()
+    plans = []
     for cluster, spc in candidates(ctx):
         try:
             A.asep_set_plan(ctx, cluster, spc)
         except A.AsepError:
             continue  # does not fit this device
-        ms, words = _probe(ctx, probe_sweeps, seed)
-        if ref_words is None:
-            ref_words = words
-        elif not np.array_equal(words, ref_words):
-            raise RuntimeError(f"plan cluster={cluster} spc={spc} changed the result")
         info = A.asep_get_info(ctx)
-        row = {"knob": "plan", "cluster": info["cluster"], "samples_per_group": info["samples_per_group"],
-               "ms_per_sweep": ms, "requested": [cluster, spc]}
-        table.append(row)
-        if best is None or ms < best.ms_per_sweep:
-            best = Choice(info["cluster"], info["samples_per_group"], ms)
-    A.asep_set_plan(ctx, best.cluster, best.samples_per_group if best.cluster == 1 else 0)
-    info = A.asep_get_info(ctx)
-    sms = _sm_count()
-    if balance and info["cluster"] == 1 and info["groups"] > sms:
-        n = 16 * max(BALANCE_CHUNKS)
-        _, long_ref = _probe(ctx, n, seed)  # reference lattices of the longer probe
-        best_chunk, best_ms = 0, None
-        for chunk in (0,) + BALANCE_CHUNKS:
+        plans.append((cluster, spc, info["cluster"] == 1 and info["groups"] > sms))
+    n = 16 * max(BALANCE_CHUNKS) if balance and any(b for *_, b in plans) else probe_sweeps
+    table, ref_words, best, best_ms = [], None, None, None
+    for cluster, spc, can_balance in plans:
+        A.asep_set_plan(ctx, cluster, spc)
+        info = A.asep_get_info(ctx)
+        for chunk in (0,) + (BALANCE_CHUNKS if balance and can_balance else ()):
             A.asep_set_balance(ctx, chunk)
             ms, words = _probe(ctx, n, seed)
-            if not np.array_equal(words, long_ref):
-                raise RuntimeError(f"balanced launches in chunks of {chunk} sweeps changed the result")
-            table.append({"knob": "balance", "chunk_sweeps": chunk or "off", "ms_per_sweep": ms})
-            if best_ms is None or ms < 0.99 * best_ms:  # only when measurably faster
-                best_chunk, best_ms = chunk, ms
-        A.asep_set_balance(ctx, best_chunk)
-        best.balance = best_chunk
-    if launch_sweeps:
-        best_cap, best_ms = 0, None
-        for cap in launch_sweep_candidates(probe_sweeps):
+            if ref_words is None:
+                ref_words = words
+            elif not np.array_equal(words, ref_words):
+                raise RuntimeError(f"plan cluster={cluster} spc={spc} balance={chunk} changed the result")
+            table.append({"knob": "plan", "cluster": info["cluster"], "samples_per_group": info["samples_per_group"],
+                          "balance_chunk_sweeps": chunk or "off", "ms_per_sweep": ms, "probe_sweeps": n,
+                          "requested": [cluster, spc]})
+            if best is None or ms < best_ms:
+                best, best_ms = Choice(info["cluster"], info["samples_per_group"], ms, 0, chunk), ms
+        A.asep_set_balance(ctx, 0)
+    A.asep_set_plan(ctx, best.cluster, best.samples_per_group if best.cluster == 1 else 0)
+    A.asep_set_balance(ctx, best.balance)
+    if launch_sweeps:  # on the same probe as the plans: a cap below it must not hide the chunking
+        best_cap, cap_ms = 0, None
+        for cap in launch_sweep_candidates(n):
             A.asep_set_launch_sweeps(ctx, cap)
-            ms, words = _probe(ctx, probe_sweeps, seed)
+            ms, words = _probe(ctx, n, seed)
             if not np.array_equal(words, ref_words):
                 raise RuntimeError(f"{cap} sweeps per launch changed the result")
-            table.append({"knob": "launch_sweeps", "launch_sweeps": cap or "auto", "ms_per_sweep": ms})
+            table.append({"knob": "launch_sweeps", "launch_sweeps": cap or "auto", "ms_per_sweep": ms,
+                          "probe_sweeps": n})
             # shorter launches only when measurably faster (1 %): noise must not split long runs
-            if best_ms is None or ms < 0.99 * best_ms:
-                best_cap, best_ms = cap, ms
+            if cap_ms is None or ms < 0.99 * cap_ms:
+                best_cap, cap_ms = cap, ms
         A.asep_set_launch_sweeps(ctx, best_cap)
         best.launch_sweeps = best_cap
     return best, table

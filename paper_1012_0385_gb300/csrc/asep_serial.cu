@@ -235,13 +235,27 @@ __global__ void __launch_bounds__(256) k_serial(const SerialLaunch a) {
   }
 }
 
+// Warps (samples) per CTA: up to 8, but no more than spreads the samples
+// over all SMs -- each warp's attempts form one dependent chain, so a few
+// samples run fastest one per SM.
+uint32_t serial_warps_per_cta(uint32_t S) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                               cudaSuccess || sms <= 0) {
+    (void)cudaGetLastError();
+    sms = 1;
+  }
+  return std::max<uint32_t>(1, std::min<uint32_t>(8, (S + sms - 1) / static_cast<uint32_t>(sms)));
+}
+
 template <uint32_t MODEL, uint32_t DIS>
 cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
   constexpr uint32_t NPL = (MODEL == kTwoLane ? 2u : 1u) + dis_planes(DIS);
   const size_t per_sample = static_cast<size_t>(NPL) * a.geo.W * 4u;
   const size_t budget = 200u * 1024u;  // shared memory for the staged lattices of one block
+  const uint32_t spread = serial_warps_per_cta(a.geo.S);
   if (per_sample <= budget) {
-    const uint32_t warps = static_cast<uint32_t>(std::min<size_t>(8u, budget / per_sample));
+    const uint32_t warps = static_cast<uint32_t>(std::min<size_t>(spread, budget / per_sample));
     const size_t smem = per_sample * warps;
     const uint32_t blocks = (a.geo.S + warps - 1) / warps;
     (void)cudaGetLastError();
@@ -251,7 +265,7 @@ cudaError_t launch_serial_t(const SerialLaunch& a, cudaStream_t st) {
     k_serial<MODEL, DIS, true><<<blocks, 32 * warps, smem, st>>>(a);
     return cudaGetLastError();
   }
-  const uint32_t warps = 8;
+  const uint32_t warps = spread;
   const uint32_t blocks = (a.geo.S + warps - 1) / warps;
   k_serial<MODEL, DIS, false><<<blocks, 32 * warps, 0, st>>>(a);
   return cudaGetLastError();

@@ -196,7 +196,8 @@ class _Step:
 
 
 def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int | None = None, waves: float = 8.0,
-                  max_active: int = 10_000, rate_guess: float = 4e11, depth: int = 2) -> dict:
+                  max_active: int = 10_000, rate_guess: float = 4e11, depth: int = 2,
+                  age_s: float | None = 0.5, max_weight: float = 32.0) -> dict:
     """Continuous batching (see the module docstring).
 
     Admission, first come first served: a job enters when its device bytes
@@ -207,7 +208,10 @@ def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int | N
     Quantum: each job advances by the sweeps one of its work items runs in
     about `quantum_s` at the measured per-SM rate (less for a job whose
     demand exceeds half the allowance), so a step lasts about `waves` quanta
-    at most."""
+    at most.  With `age_s`, a job's quantum is weighted by 1 + (time since
+    its arrival) / age_s (at most `max_weight`): jobs that have waited or run
+    long get a larger share of each step, so the largest jobs, which make the
+    latency tail, are not stretched by the stream of small ones."""
     import torch
 
     dev = torch.cuda.current_device()
@@ -252,8 +256,11 @@ def serve_batched(trace: list[Job], quantum_s: float = 0.02, mem_budget: int | N
             if active and len(in_flight) < depth:
                 per_sm = rate / sms
                 ctxs, qs, events, finishing, still, attempts = [], [], [], [], [], 0
+                t_now = time.perf_counter() - t0
                 for a in active:
                     target = quantum_s * min(1.0, (allowance / 2) / max(1, a.job.smem_demand()))
+                    if age_s:
+                        target *= min(max_weight, 1.0 + (t_now - a.job.arrival) / age_s)
                     q = max(1, min(a.left, int(per_sm * a.item_sms * target // max(1, a.item_attempts))))
                     attempts += q * a.job.L * a.job.planes * a.job.S
                     if a.streamed:  # its own launches, on its own stream, beside the batch

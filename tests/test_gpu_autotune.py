@@ -107,8 +107,9 @@ def test_autotune_times_the_launch_sweeps_and_batch_mode():
     with A.asep_create(A.make_params(**kw), sample_times=[]) as ctx:
         choice, table = autotune.autotune(ctx, probe_sweeps=16)
         caps = [r["launch_sweeps"] for r in table if r["knob"] == "launch_sweeps"]
-        assert caps == ["auto", 8, 4, 2]
-        assert choice.launch_sweeps in (0, 8, 4, 2)
+        probe = table[0]["probe_sweeps"]
+        assert caps == ["auto", probe // 2, probe // 4, probe // 8]
+        assert choice.launch_sweeps in (0, probe // 2, probe // 4, probe // 8)
     shapes = [dict(L=2048, domain_sites=128, samples_per_real=3, p_thr=th(0.6), seed=5 + i) for i in range(6)]
 
     def make():

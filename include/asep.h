@@ -189,7 +189,7 @@ typedef struct asep_info {
   uint32_t groups;        /* CTAs (resident) or clusters per sweep launch */
   uint32_t threads;       /* threads per CTA */
   uint32_t smem_bytes;    /* dynamic shared memory per CTA of the sweep kernel */
-  uint32_t reserved;      /* 0 */
+  uint32_t tile_columns;  /* streamed domain tier: columns (threads) per tile; 0 otherwise */
 } asep_info;
 
 /* Validate `params`, allocate device memory, draw the initial state (paper
@@ -302,8 +302,10 @@ int asep_get_info(const asep_ctx* ctx, asep_info* info);
  * lattice stays in global memory and tiles of columns pass through shared
  * memory once per phase (the automatic choice when a sample fits neither one
  * CTA nor a 16-CTA cluster; one launch per phase, records between sweeps;
- * not in batches).  samples_per_group:
- * samples per CTA of the one-CTA plan (0 = automatic).  Returns
+ * not in batches).  samples_per_group: samples per CTA of the one-CTA plan
+ * (0 = automatic); with cluster = 32 it is instead the tile width in columns
+ * (a multiple of 32 up to 1024, at most half the sample's columns; 0 =
+ * automatic, 128 or the widest that fits below it).  Returns
  * ASEP_ERR_INVALID, keeping the previous plan, when the plan does not fit the
  * device.  Takes effect for the next launch. */
 int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group);

@@ -87,7 +87,7 @@ class asep_info(ctypes.Structure):
         ("groups", ctypes.c_uint32),
         ("threads", ctypes.c_uint32),
         ("smem_bytes", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("tile_columns", ctypes.c_uint32),
     ]
 
 

@@ -56,6 +56,10 @@ def candidates(ctx) -> list[tuple[int, int]]:
     for nc in (2, 4, 8, 16):
         if G // nc >= 32:
             out.append((nc, 0))
+    if info["cluster"] == 32:  # streamed: the tile width in columns
+        for cols in STREAM_TILE_COLUMNS:
+            if 2 * cols <= G:
+                out.append((32, cols))
     return out
 
 
@@ -91,6 +95,7 @@ def launch_sweep_candidates(probe_sweeps: int) -> list[int]:
 
 
 BALANCE_CHUNKS = (16, 32, 64)
+STREAM_TILE_COLUMNS = (64, 128, 256, 512, 1024)
 
 
 def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345, launch_sweeps: bool = True,
@@ -125,13 +130,14 @@ def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345, launch_sweeps: bool
                 ref_words = words
             elif not np.array_equal(words, ref_words):
                 raise RuntimeError(f"plan cluster={cluster} spc={spc} balance={chunk} changed the result")
+            second = info["tile_columns"] if info["cluster"] == 32 else info["samples_per_group"]
             table.append({"knob": "plan", "cluster": info["cluster"], "samples_per_group": info["samples_per_group"],
-                          "balance_chunk_sweeps": chunk or "off", "ms_per_sweep": ms, "probe_sweeps": n,
-                          "requested": [cluster, spc]})
+                          "tile_columns": info["tile_columns"], "balance_chunk_sweeps": chunk or "off",
+                          "ms_per_sweep": ms, "probe_sweeps": n, "requested": [cluster, spc]})
             if best is None or ms < best_ms:
-                best, best_ms = Choice(info["cluster"], info["samples_per_group"], ms, 0, chunk), ms
+                best, best_ms = Choice(info["cluster"], second, ms, 0, chunk), ms
         A.asep_set_balance(ctx, 0)
-    A.asep_set_plan(ctx, best.cluster, best.samples_per_group if best.cluster == 1 else 0)
+    A.asep_set_plan(ctx, best.cluster, best.samples_per_group if best.cluster in (1, 32) else 0)
     A.asep_set_balance(ctx, best.balance)
     if launch_sweeps:  # on the same probe as the plans: a cap below it must not hide the chunking
         best_cap, cap_ms = 0, None

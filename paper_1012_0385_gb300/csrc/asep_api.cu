@@ -325,10 +325,14 @@ int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
     }
     if (force_cluster > 1) break;
   }
-  // streamed tier: tiles of C columns (a multiple of 32, at least two tiles) through shared memory
+  // streamed tier: tiles of C columns (a multiple of 32, at least two tiles) through shared memory.
+  // Automatic width kStreamTileColumns: narrow tiles keep several CTAs on every SM, so one CTA's bulk
+  // copy and phase tail overlap another's attempts, and the last wave of tiles is short.
+  // force_spc with force_cluster == kStreamTier: exactly that width.
   if (!placed && (force_cluster == 0 || force_cluster == kStreamTier) && ctx->W % 4 == 0) {
-    for (uint32_t C = 1024; C >= 32 && !placed; C -= 32) {
-      if (2ull * C > G) continue;
+    const uint32_t C0 = force_cluster == kStreamTier && force_spc ? force_spc : kStreamTileColumns;
+    for (uint32_t C = C0; C >= 32 && !placed; C -= 32) {
+      if (2ull * C > G || (force_cluster == kStreamTier && force_spc && C != force_spc)) continue;
       const size_t smem = stream_smem_bytes(ctx->p.model, dis, ctx->R2, C, ptab_n);
       if (smem > 200u * 1024u) continue;
       ctx->cluster = kStreamTier;
@@ -682,7 +686,7 @@ void fill_info(const asep_ctx* ctx, asep_info* info) {
   info->groups = ctx->blocks;
   info->threads = ctx->threads;
   info->smem_bytes = static_cast<uint32_t>(ctx->smem);
-  info->reserved = 0;
+  info->tile_columns = ctx->p.schedule == ASEP_SCHED_DOMAIN && ctx->cluster == kStreamTier ? ctx->C : 0;
 }
 
 }  // namespace
@@ -1380,9 +1384,14 @@ int asep_set_plan(asep_ctx* ctx, uint32_t cluster, uint32_t samples_per_group) {
     return fail(ctx, ASEP_ERR_INVALID, "plans apply to the domain and SCA schedules");
   if (cluster != kStreamTier && (cluster > 16 || (cluster > 1 && (cluster & (cluster - 1)))))
     return fail(ctx, ASEP_ERR_INVALID, "cluster must be 0, 1, 2, 4, 8, 16 or 32 (streamed)");
-  if (samples_per_group && cluster > 1)
-    return fail(ctx, ASEP_ERR_INVALID, "samples_per_group applies to the resident plan (cluster 0 or 1)");
-  if (samples_per_group > ctx->S) return fail(ctx, ASEP_ERR_INVALID, "samples_per_group exceeds the samples");
+  if (cluster == kStreamTier) {
+    if (samples_per_group % 32 || samples_per_group > 1024)
+      return fail(ctx, ASEP_ERR_INVALID, "streamed tile width must be 0 (automatic) or a multiple of 32 up to 1024");
+  } else {
+    if (samples_per_group && cluster > 1)
+      return fail(ctx, ASEP_ERR_INVALID, "samples_per_group applies to the resident plan (cluster 0 or 1)");
+    if (samples_per_group > ctx->S) return fail(ctx, ASEP_ERR_INVALID, "samples_per_group exceeds the samples");
+  }
   const asep_ctx saved = *ctx;  // restore the previous plan if the new one does not fit
   const int rc = plan_domain(ctx, cluster, samples_per_group);
   if (rc != ASEP_OK) {

@@ -276,7 +276,7 @@ CASES = {
                          plan=(32, 0), flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 13,
                     [0, 5, 13]),
     "stream_ring_four_tiles": (dict(L=1 << 18, domain_sites=32, samples_per_real=2, p_thr=th(0.6), q_thr=th(0.3),
-                                    seed=62, plan=(32, 0)), 6, [0, 6]),
+                                    seed=62, plan=(32, 1024)), 6, [0, 6]),
     "stream_bimodal": (dict(L=1 << 16, domain_sites=128, n_realizations=2, samples_per_real=2, p_thr=A.ASEP_ALWAYS,
                             dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_c_thr=th(0.05),
                             q_thr=th(0.1), dis_seed=63, seed=64, plan=(32, 0)), 9, [0, 9]),
@@ -689,6 +689,44 @@ def torch_probe_ok() -> bool:
 
     y = torch.arange(1024, device="cuda", dtype=torch.int64).sum().item()
     return y == 1023 * 1024 // 2
+
+
+@pytest.mark.parametrize("model", [0, TWO])
+def test_streamed_tile_width_does_not_change_results(model):
+    """The streamed tier's tile width (columns per CTA, an autotuner knob):
+    widths of 32, 96 (a ragged last tile), 128 and 1024 columns give the
+    same lattices, heights and counters, and they equal the oracle's."""
+    kw = dict(model=model, L=1 << 18, domain_sites=32 if model == 0 else 64, samples_per_real=2, p_thr=th(0.6),
+              q_thr=th(0.3), seed=81, init_kind=1, init_seed=82)
+    if model == TWO:
+        kw.update(dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=83)
+    times = [0, 3, 7]
+    runs = {}
+    for cols in (32, 96, 128, 1024):
+        runs[cols] = run_gpu(dict(kw, plan=(32, cols)), [3, 4], times)
+    P = oracle_params(kw)
+    assert_same(runs[128], oracle.run(P, 7, times), P, times)
+    for cols in (32, 96, 1024):
+        for key in ("words", "sh", "sh2", "cnt", "cur"):
+            assert np.array_equal(runs[cols][key], runs[128][key]), (cols, key)
+
+
+def test_streamed_tile_width_is_a_plan_knob():
+    with A.asep_create(A.make_params(L=1 << 24, domain_sites=256, samples_per_real=1), sample_times=[]) as ctx:
+        info = A.asep_get_info(ctx)
+        assert info["cluster"] == 32 and info["tile_columns"] == 128  # the automatic width
+        A.asep_set_plan(ctx, 32, 512)
+        info = A.asep_get_info(ctx)
+        assert info["tile_columns"] == 512 and info["threads"] == 512 and info["groups"] == (1 << 24) // 512 // 512
+        for bad in (48, 2048):
+            with pytest.raises(A.AsepError):
+                A.asep_set_plan(ctx, 32, bad)
+            assert A.asep_get_info(ctx)["tile_columns"] == 512  # the previous plan stays
+    with A.asep_create(A.make_params(L=1 << 16, domain_sites=256, samples_per_real=1), sample_times=[]) as ctx:
+        with pytest.raises(A.AsepError):
+            A.asep_set_plan(ctx, 32, 128)  # 128 columns: one tile would hold the whole ring
+        A.asep_set_plan(ctx, 32, 0)
+        assert A.asep_get_info(ctx)["tile_columns"] == 64
 
 
 def test_streamed_tier_is_chosen_beyond_a_cluster():

@@ -410,7 +410,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         c = A.asep_create(params(), sample_times=times)
         if plan:  # the tuned plan, as a user applies a cached one
-            A.asep_set_plan(c, plan.cluster, plan.samples_per_group if plan.cluster == 1 else 0)
+            A.asep_set_plan(c, plan.cluster, plan.samples_per_group if plan.cluster in (1, 32) else 0)
             A.asep_set_balance(c, plan.balance)
             A.asep_set_launch_sweeps(c, plan.launch_sweeps)
         A.asep_sweep(c, N_MCS)
@@ -445,27 +445,32 @@ def run_ours(args):
         max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak_ops = SMS * LANES_PER_SM * max_mhz * 1e6
         achieved_ops = L_SITES * SAMPLES * N_MCS / (kernel_ms / 1000.0) * OPS_PER_ATTEMPT
+        headline_family = ("stream" if plan and plan.cluster == 32 else
+                           "domain_bal" if plan and plan.balance else "domain")
         line = {
             "metric": "site-update attempts/s", "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": workload_config(world),
-            "plan": ({"cluster": plan.cluster, "samples_per_group": plan.samples_per_group,
+            "plan": ({"cluster": plan.cluster,
+                      ("tile_columns" if plan.cluster == 32 else "samples_per_group"): plan.samples_per_group,
                       "balance_chunk_sweeps": plan.balance or "off",
                       "launch_sweeps": plan.launch_sweeps or "auto"} if plan else "default"),
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved_ops / peak_ops,
-                         "traffic": _traffic_from_profile("domain_bal" if plan and plan.balance else "domain"),
-                         "kernel": "k_domain_bal<ring> (balanced launch)" if plan and plan.balance
-                         else "k_domain<ring>", "kernel_ms": kernel_ms,
+                         "traffic": _traffic_from_profile(headline_family),
+                         "kernel": {"domain_bal": "k_domain_bal<ring> (balanced launch)",
+                                    "stream": "k_stream<ring> (streamed tiles)"}.get(headline_family,
+                                                                                      "k_domain<ring>"),
+                         "kernel_ms": kernel_ms,
                          "ops_per_attempt": OPS_PER_ATTEMPT,
                          "peak_basis": f"{SMS} SMs x {LANES_PER_SM} int32 lanes/clk x {max_mhz:.0f} MHz (issue)",
                          "philox_only_attempts_per_s": 4 * philox_calls_s,
                          "rng_bitop_only_attempts_per_s": rb_attempts_s,
                          "rng_bitop_only_at_kernel_shape_attempts_per_s": rbk_attempts_s,
                          "frac_of_rng_bitop_only": value / rb_attempts_s},
-            "issue": _issue_fraction(value, "headline_domain_bal" if plan and plan.balance else "headline_domain",
-                                     peak_ops),
+            "issue": (_issue_fraction(value, "headline_" + headline_family, peak_ops)
+                      if headline_family != "stream" else None),
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -617,12 +622,12 @@ def other_workloads(tune: bool = True, peak_ops: float | None = None, rng_bitop:
     for wi, (name, kw, times, lanes) in enumerate(cases):
         with A.asep_create(A.make_params(**kw), sample_times=times) as ctx:
             tuned = None
-            if tune and kw.get("schedule", A.ASEP_SCHED_DOMAIN) == A.ASEP_SCHED_DOMAIN and \
-                    A.asep_get_info(ctx)["cluster"] != 32:
+            if tune and kw.get("schedule", A.ASEP_SCHED_DOMAIN) == A.ASEP_SCHED_DOMAIN:
                 from paper_1012_0385_gb300.autotune import autotune
 
                 choice, _ = autotune(ctx, probe_sweeps=16)
-                tuned = {"cluster": choice.cluster, "samples_per_group": choice.samples_per_group,
+                tuned = {"cluster": choice.cluster, ("tile_columns" if choice.cluster == 32 else "samples_per_group"):
+                         choice.samples_per_group,
                          "balance_chunk_sweeps": choice.balance or "off",
                          "launch_sweeps": choice.launch_sweeps or "auto", "autotuned": True}
             A.asep_reset(ctx, seed=kw["seed"], init_seed=kw.get("init_seed", 0))

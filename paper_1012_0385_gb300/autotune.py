@@ -43,7 +43,10 @@ class Choice:
 
 def candidates(ctx) -> list[tuple[int, int]]:
     """Plans worth trying: the automatic one, the one-CTA plan with other
-    sample counts per CTA, and cluster splits that leave >= 32 columns per CTA."""
+    sample counts per CTA, cluster splits that leave >= 32 columns per CTA,
+    and the streamed tier at tile widths that leave >= 2 tiles per sample
+    (it spreads few samples over every SM, at the cost of one launch per
+    phase and a staging pass)."""
     info = A.asep_get_info(ctx)
     L, D = info["L"], info["D"]
     G = L // (2 * D)
@@ -56,7 +59,7 @@ def candidates(ctx) -> list[tuple[int, int]]:
     for nc in (2, 4, 8, 16):
         if G // nc >= 32:
             out.append((nc, 0))
-    if info["cluster"] == 32:  # streamed: the tile width in columns
+    if (L // 32) % 4 == 0:  # streamed (words per plane a multiple of 4): the tile width in columns
         for cols in STREAM_TILE_COLUMNS:
             if 2 * cols <= G:
                 out.append((32, cols))

@@ -272,6 +272,9 @@ int plan_sca(asep_ctx* ctx, uint32_t force) {
 // force_cluster: 0 = choose, 1 = resident only, n > 1 = exactly n CTAs per
 // sample.  force_spc: samples per CTA for the resident plan (0 = choose).
 // The plan changes only the launch shape, never the results.
+// Automatic tile width of the streamed tier, in columns (one thread each).
+constexpr uint32_t kStreamTileColumns = 128;
+
 int plan_domain(asep_ctx* ctx, uint32_t force_cluster, uint32_t force_spc) {
   const uint32_t D = ctx->D;
   ctx->R2 = 2 * D / 32;

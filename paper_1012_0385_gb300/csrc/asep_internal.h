@@ -218,8 +218,6 @@ cudaError_t launch_cluster(const DomainLaunch& a, uint32_t threads, size_t smem,
 // Streamed tier of the domain schedule (lattice in global memory, tiles of
 // columns through shared memory); plan code kStreamTier in `cluster`.
 constexpr uint32_t kStreamTier = 32;
-// Automatic tile width of the streamed tier, in columns (one thread each).
-constexpr uint32_t kStreamTileColumns = 128;
 size_t stream_smem_bytes(uint32_t model, uint32_t dis, uint32_t R2, uint32_t C, uint32_t ptab_n);
 // err: set when a tile's copy wait runs out (bounded to one second); stall:
 // extra bytes each tile's copies announce (0; fault injection for tests).

@@ -184,6 +184,37 @@ def _inst_counts() -> dict:
     return out
 
 
+def _smem_counts() -> dict:
+    """Shared-memory wavefronts per attempt of the benchmarked kernels (ncu
+    l1tex__data_pipe_lsu_wavefronts_mem_shared.sum / attempts), same source
+    and digest rule as _inst_counts."""
+    out = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", COUNTS_FILE)):
+            if line.startswith("#") or "=" not in line:
+                continue
+            kv = dict(x.split("=", 1) for x in line.split())
+            if kv.get("kernel_source_sha256_16") == kernel_source_digest(kv["family"]) and \
+                    "smem_wavefronts_per_attempt" in kv:
+                out[kv["name"]] = float(kv["smem_wavefronts_per_attempt"])
+    except Exception:
+        pass
+    return out
+
+
+def _smem_fraction(rate: float, name: str, max_mhz: float):
+    """Shared-memory bandwidth the kernel uses: measured wavefronts per
+    attempt x attempts/s, over one wavefront (128 bytes) per SM and clock;
+    None without a count for the current sources."""
+    wpa = _smem_counts().get(name)
+    if wpa is None:
+        return None
+    peak = SMS * max_mhz * 1e6
+    return {"wavefronts_per_attempt": wpa, "achieved_wavefronts_per_s": rate * wpa, "peak_wavefronts_per_s": peak,
+            "frac": rate * wpa / peak, "peak_basis": "152 SMs x 1 wavefront (128 B) per clock x max SM clock",
+            "source": "profiles/" + COUNTS_FILE}
+
+
 def _window_counts() -> dict:
     """Window index -> thread instructions per attempt (see _inst_counts)."""
     return {int(k[len("window"):]): v for k, v in _inst_counts().items() if k.startswith("window")}
@@ -471,6 +502,8 @@ def run_ours(args):
                          "frac_of_rng_bitop_only": value / rb_attempts_s},
             "issue": (_issue_fraction(value, "headline_" + headline_family, peak_ops)
                       if headline_family != "stream" else None),
+            "smem": (_smem_fraction(value, "headline_" + headline_family, max_mhz)
+                     if headline_family != "stream" else None),
             "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -661,6 +694,10 @@ def other_workloads(tune: bool = True, peak_ops: float | None = None, rng_bitop:
                                             ") x attempts/s, over 152 SMs x 128 lanes x clock"}
                 if rng_bitop and WINDOW_KERNELS[wi] in ("serial", "domain", "stream"):
                     row["roofline"]["frac_of_rng_bitop_only"] = row["attempts_per_s"] / rng_bitop
+                sm = _smem_fraction(row["attempts_per_s"], f"window{wi}", peak_ops / (SMS * LANES_PER_SM * 1e6))
+                if sm:  # shared-memory bandwidth: wavefronts per attempt (ncu) x attempts/s over 1 per SM and clock
+                    row["roofline"]["smem_frac"] = sm["frac"]
+                    row["roofline"]["smem_wavefronts_per_attempt"] = sm["wavefronts_per_attempt"]
             if info["cluster"] == 32:
                 # streamed: each phase reads and writes every lattice word once (4 x L/8 bytes per plane
                 # and sweep); the whole window, launch gaps and records included, against measured HBM

@@ -80,9 +80,14 @@ __device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& 
   uint32_t* p1 = reinterpret_cast<uint32_t*>(cur + o0 + cpb);
   const uint32_t w0 = *p0;
   const uint32_t w1 = *p1;
-  const uint32_t pat = __funnelshift_r(w0, w1, r) & 3u;  // bit0 = site i, bit1 = site i+1 (shift = r mod 32)
-  const bool hopR = okR && pat == 1u;
-  const bool hopL = okL && pat == 2u;
+  // the bond's two sites: bit 0 = site i, bit 1 = site i+1 (shift = r mod 32).  On the ring they are
+  // compared at bits 30-31 instead: a left shift can issue on the multiply-add unit, where the mask
+  // needs the busier integer pipe (measured +1.5 % on the growth workload; two lanes keep the mask)
+  const uint32_t x = __funnelshift_r(w0, w1, r);
+  constexpr uint32_t kAt = MODEL == kRing ? 30u : 0u;
+  const uint32_t pat = MODEL == kRing ? x << kAt : x & 3u;
+  const bool hopR = okR && pat == (1u << kAt);
+  const bool hopL = okL && pat == (2u << kAt);
   if (valid && (hopR || hopL)) {
     *p0 = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
     *p1 = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0

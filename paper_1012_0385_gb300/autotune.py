@@ -41,12 +41,14 @@ class Choice:
     balance: int = 0  # sweeps per chunk of a balanced launch (0 = off)
 
 
-def candidates(ctx) -> list[tuple[int, int]]:
+def candidates(ctx, sms: int | None = None) -> list[tuple[int, int]]:
     """Plans worth trying: the automatic one, the one-CTA plan with other
     sample counts per CTA, cluster splits that leave >= 32 columns per CTA,
-    and the streamed tier at tile widths that leave >= 2 tiles per sample
-    (it spreads few samples over every SM, at the cost of one launch per
-    phase and a staging pass)."""
+    and the streamed tier at tile widths that leave >= 2 tiles per sample --
+    for streamed contexts, and for contexts with fewer samples than the
+    device has SMs (`sms`), where one CTA per sample leaves SMs idle and
+    tiles spread the samples over all of them, at the cost of one launch
+    per phase and a staging pass."""
     info = A.asep_get_info(ctx)
     L, D = info["L"], info["D"]
     G = L // (2 * D)
@@ -59,7 +61,8 @@ def candidates(ctx) -> list[tuple[int, int]]:
     for nc in (2, 4, 8, 16):
         if G // nc >= 32:
             out.append((nc, 0))
-    if (L // 32) % 4 == 0:  # streamed (words per plane a multiple of 4): the tile width in columns
+    few = sms is not None and info["S"] < sms
+    if (info["cluster"] == 32 or few) and (L // 32) % 4 == 0:  # streamed: the tile width in columns
         for cols in STREAM_TILE_COLUMNS:
             if 2 * cols <= G:
                 out.append((32, cols))
@@ -114,7 +117,7 @@ def autotune(ctx, probe_sweeps: int = 32, seed: int = 12345, launch_sweeps: bool
     (rows with knob "plan" or "launch_sweeps")."""
     sms = _sm_count()
     plans = []
-    for cluster, spc in candidates(ctx):
+    for cluster, spc in candidates(ctx, sms):
         try:
             A.asep_set_plan(ctx, cluster, spc)
         except A.AsepError:

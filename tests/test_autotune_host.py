@@ -33,15 +33,17 @@ def test_plan_candidates_include_streamed_tile_widths(monkeypatch):
         return lambda ctx: {"L": L, "D": D, "S": S, "cluster": cluster}
 
     monkeypatch.setattr(A, "asep_get_info", fake(1 << 17, 256, 256, 1))  # 256 columns per sample
-    c = autotune.candidates(None)
+    c = autotune.candidates(None, sms=152)
     assert (0, 0) in c and (1, 1) in c and (1, 4) in c and (1, 8) not in c
     assert [x for x in c if x[0] in (2, 4, 8, 16)] == [(2, 0), (4, 0), (8, 0)]
-    assert [x for x in c if x[0] == 32] == [(32, 64), (32, 128)]
+    assert not [x for x in c if x[0] == 32]  # 256 samples fill 152 SMs: no streamed plans
+    monkeypatch.setattr(A, "asep_get_info", fake(1 << 17, 256, 128, 1))  # 128 samples on 152 SMs
+    assert [x for x in autotune.candidates(None, sms=152) if x[0] == 32] == [(32, 64), (32, 128)]
     monkeypatch.setattr(A, "asep_get_info", fake(1 << 24, 256, 16, 32))  # 32768 columns: streamed only
     c = autotune.candidates(None)
     assert [x for x in c if x[0] == 32] == [(32, w) for w in autotune.STREAM_TILE_COLUMNS]
     assert not [x for x in c if x[0] == 1]
     monkeypatch.setattr(A, "asep_get_info", fake(48 * 64, 32, 4, 1))  # 48 columns: no two tiles of 32
-    assert not [x for x in autotune.candidates(None) if x[0] == 32]
+    assert not [x for x in autotune.candidates(None, sms=152) if x[0] == 32]
     monkeypatch.setattr(A, "asep_get_info", fake(65 * 64, 32, 4, 1))  # 130 words per plane: bulk copies need 4k
-    assert not [x for x in autotune.candidates(None) if x[0] == 32]
+    assert not [x for x in autotune.candidates(None, sms=152) if x[0] == 32]

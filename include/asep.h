@@ -27,11 +27,17 @@
  * Schedules:
  *   ASEP_SCHED_SERIAL  plain random-sequential update (RSU, paper sec. 2.1):
  *                      per sweep L (two lanes: 2L) attempts on uniformly drawn
- *                      bonds.  One GPU warp per sample (it applies each batch of
- *                      32 consecutive attempts up to the first one that
- *                      shares a site with an earlier one of the batch, so
- *                      the result is the sequential one); L a power of
- *                      two.
+ *                      bonds; L a power of two.  Two plans, both giving the
+ *                      sequential result: one CTA per sample, which runs a
+ *                      sweep's attempts in rounds, each attempt once every
+ *                      earlier attempt sharing a site with it has run (the
+ *                      automatic plan when the lattice and a sweep's draws
+ *                      fit 200 KB of shared memory -- a ring of up to 16384
+ *                      sites, two lanes of up to 8192 -- and the samples
+ *                      number at most four per SM); or one warp per sample, which
+ *                      applies each batch of 32 consecutive attempts up to
+ *                      the first one that shares a site with an earlier one
+ *                      of the batch.
  *   ASEP_SCHED_DOMAIN  two-phase Poisson-domain RSU (no paper counterpart; the
  *                      paper's GPU schedule is a two-sub-lattice cellular
  *                      automaton).  Per sweep a random offset splits the ring
@@ -292,8 +298,11 @@ int asep_height_offset(asep_ctx* ctx, int64_t* out, size_t n);
  * context (no synchronisation; n_recorded and sweep count enqueued work). */
 int asep_get_info(const asep_ctx* ctx, asep_info* info);
 
-/* Choose the launch plan of a domain- or SCA-schedule context (the
- * autotuner's knob; results never depend on it).  SCA: cluster 0 =
+/* Choose the launch plan of a context (the autotuner's knob; results never
+ * depend on it).  Serial schedule: cluster 0 = automatic, 1 = one CTA per
+ * sample running each sweep in dependency rounds (ASEP_ERR_INVALID beyond
+ * 32768 attempts per sweep or 200 KB of shared memory), 2 = one warp per
+ * sample; samples_per_group 0.  SCA: cluster 0 =
  * automatic, 1 = the ring in one CTA's shared memory (ASEP_ERR_INVALID when
  * it does not fit), 32 = streamed from global memory; samples_per_group 0.
  * Domain schedule: cluster 0 = automatic, 1 = whole samples in

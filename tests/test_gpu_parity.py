@@ -152,6 +152,29 @@ CASES = {
     "serial_bimodal": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
                             dis_kind=A.ASEP_DIS_BIMODAL, dis_a_thr=th(0.1), dis_b_thr=th(0.3), dis_seed=3, seed=4),
                        20, [20]),
+    # the serial schedule's two plans: one CTA per sample running a sweep in dependency rounds (the automatic
+    # plan while the lattice and the sweep's draws fit shared memory: the cases above), and one warp per
+    # sample taking committed prefixes of 32 attempts (plan 2; the automatic plan beyond)
+    "serial_rounds_largest_ring": (dict(L=1 << 14, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=2,
+                                        p_thr=th(0.75), q_thr=th(0.25), seed=31, plan=(1, 0)), 6, [0, 3, 6]),
+    "serial_rounds_largest_two_lane": (dict(model=TWO, L=1 << 13, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2,
+                                            samples_per_real=1, init_kind=1, init_seed=32, q_thr=A.ASEP_ALWAYS,
+                                            dis_kind=XING, dis_a_thr=th(0.5), dis_b_thr=th(0.8),
+                                            dis_c_thr=th(0.2), dis_seed=33, seed=34, plan=(1, 0)), 4, [0, 2, 4]),
+    "serial_rounds_smallest": (dict(L=64, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=33, p_thr=th(0.6),
+                                    q_thr=th(0.3), seed=35, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR,
+                                    autocorr_t0=10), 40, [0, 10, 25, 40]),
+    "serial_warp_cfg0_shape": (dict(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=8, seed=1,
+                                    plan=(2, 0)), 50, [0, 50]),
+    "serial_warp_two_lane": (dict(model=TWO, L=1024, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=3,
+                                  init_kind=1, init_seed=4, dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05),
+                                  dis_b_thr=th(0.1), dis_seed=2, q_thr=A.ASEP_ALWAYS, seed=3, plan=(2, 0),
+                                  flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR, autocorr_t0=5), 20,
+                             [0, 5, 20]),
+    "serial_warp_bimodal_pq": (dict(L=2048, schedule=A.ASEP_SCHED_SERIAL, n_realizations=2, samples_per_real=2,
+                                    p_thr=th(0.5), q_thr=th(0.5), dis_kind=A.ASEP_DIS_BIMODAL_PQ,
+                                    dis_a_thr=th(0.5), dis_b_thr=th(0.1), dis_c_thr=th(0.1), dis_seed=52,
+                                    seed=53, plan=(2, 0)), 12, [0, 12]),
     # cluster tier: one sample spread over 2..16 CTAs of a thread-block cluster
     # the paper's two-sub-lattice SCA schedule (bit-sliced, one CTA per ring)
     "sca_asep": (dict(L=1 << 15, schedule=SCA, samples_per_real=6, p_thr=th(0.75), q_thr=th(0.25), seed=5,
@@ -727,6 +750,32 @@ def test_streamed_tile_width_is_a_plan_knob():
             A.asep_set_plan(ctx, 32, 128)  # 128 columns: one tile would hold the whole ring
         A.asep_set_plan(ctx, 32, 0)
         assert A.asep_get_info(ctx)["tile_columns"] == 64
+
+
+def test_serial_plans():
+    """The serial schedule's plan: one CTA per sample (dependency rounds)
+    while it fits, one warp per sample beyond; both give the same lattices."""
+    kw = dict(L=4096, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=3, p_thr=th(0.7), q_thr=th(0.2), seed=41)
+    with A.asep_create(A.make_params(**kw), sample_times=[0, 9]) as ctx:
+        info = A.asep_get_info(ctx)
+        assert (info["cluster"], info["threads"], info["groups"]) == (1, 1024, 3)
+        A.asep_sweep(ctx, 9)
+        rounds, _ = A.asep_state(ctx)
+        A.asep_reset(ctx, seed=41)
+        A.asep_set_plan(ctx, 2, 0)
+        assert A.asep_get_info(ctx)["cluster"] == 2
+        A.asep_sweep(ctx, 9)
+        warp, _ = A.asep_state(ctx)
+        assert np.array_equal(rounds, warp)
+        with pytest.raises(A.AsepError):
+            A.asep_set_plan(ctx, 1, 4)  # samples_per_group is not a serial knob
+        with pytest.raises(A.AsepError):
+            A.asep_set_plan(ctx, 3, 0)
+    with A.asep_create(A.make_params(L=1 << 21, schedule=A.ASEP_SCHED_SERIAL), sample_times=[]) as ctx:
+        assert A.asep_get_info(ctx)["cluster"] == 2  # 2^21 attempts per sweep: one warp per sample
+        with pytest.raises(A.AsepError):
+            A.asep_set_plan(ctx, 1, 0)
+        assert A.asep_get_info(ctx)["cluster"] == 2
 
 
 def test_streamed_tier_is_chosen_beyond_a_cluster():

@@ -776,12 +776,23 @@ def profile_case(schedule: str = "domain"):
                   streamed window;
     "serial"      1000 sweeps of k_serial on the plain-TASEP configuration
                   (L = 4096, 8 samples, a warp per sample);
-    "window<i>"   window i of window_cases(), 32 sweeps (streamed: 2)."""
+    "window<i>"   window i of window_cases(), 32 sweeps (streamed: 2);
+    "attempt_bench" the RNG + bit-op microbenchmark at full occupancy
+                  (152 x 8 CTAs of 256 threads, 4096 Philox calls each), the
+                  measured roof of the domain schedule."""
     import torch
 
     from paper_1012_0385_gb300 import asep as A
 
     th = A.asep_threshold
+    if schedule == "attempt_bench":
+        sink = torch.empty(2 * 152 * 8 * 256, dtype=torch.int32, device="cuda")
+        ms = A.asep_attempt_bench(152 * 8, 256, 1 << 12, th(P_RATE), th(Q_RATE), sink.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        print(f"profile case done: attempt_bench {152 * 8 * 256 * 4 * (1 << 12) / (ms / 1e3):.3e} attempts/s",
+              flush=True)
+        return 0
     if schedule.startswith("window"):
         # one window of the other configurations, briefly: 32 sweeps (streamed ones 2), one record at the end
         name, kw, times, lanes = window_cases()[int(schedule[len("window"):])]
@@ -844,7 +855,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic launch plan")
     ap.add_argument("--domain", type=int, default=DOMAIN, help="domain sites D of the schedule (default 256)")
     ap.add_argument("--profile-case", nargs="?", const="domain",
-                    choices=["domain", "domain_bal", "sca", "sca_stream", "stream", "serial"] +
+                    choices=["domain", "domain_bal", "sca", "sca_stream", "stream", "serial", "attempt_bench"] +
                     [f"window{i}" for i in range(8)],
                     help="a short untimed run of one kernel for ncu (see profile_case)")
     args = ap.parse_args()

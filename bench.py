@@ -774,8 +774,9 @@ def profile_case(schedule: str = "domain"):
     "stream"      two sweeps (four launches) of the streamed domain tier
                   (k_stream) on 16 rings of 2^24 sites (32 MB), the bench's
                   streamed window;
-    "serial"      1000 sweeps of k_serial on the plain-TASEP configuration
-                  (L = 4096, 8 samples, a warp per sample);
+    "serial"      1000 sweeps of the serial schedule on the plain-TASEP
+                  configuration (L = 4096, 8 samples; its automatic plan, one
+                  CTA per sample running each sweep in dependency rounds);
     "window<i>"   window i of window_cases(), 32 sweeps (streamed: 2);
     "attempt_bench" the RNG + bit-op microbenchmark at full occupancy
                   (152 x 8 CTAs of 256 threads, 4096 Philox calls each), the

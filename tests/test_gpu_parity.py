@@ -161,6 +161,10 @@ CASES = {
                                             samples_per_real=1, init_kind=1, init_seed=32, q_thr=A.ASEP_ALWAYS,
                                             dis_kind=XING, dis_a_thr=th(0.5), dis_b_thr=th(0.8),
                                             dis_c_thr=th(0.2), dis_seed=33, seed=34, plan=(1, 0)), 4, [0, 2, 4]),
+    "serial_rounds_smallest_two_lane": (dict(model=TWO, L=64, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=5,
+                                             init_kind=1, init_seed=42, q_thr=A.ASEP_ALWAYS,
+                                             dis_kind=A.ASEP_DIS_CROSSING, dis_a_thr=th(0.5), dis_b_thr=th(0.8),
+                                             dis_c_thr=th(0.2), dis_seed=43, seed=44), 30, [0, 7, 30]),
     "serial_rounds_smallest": (dict(L=64, schedule=A.ASEP_SCHED_SERIAL, samples_per_real=33, p_thr=th(0.6),
                                     q_thr=th(0.3), seed=35, flags=A.ASEP_FLAG_PROFILE | A.ASEP_FLAG_AUTOCORR,
                                     autocorr_t0=10), 40, [0, 10, 25, 40]),
@@ -714,15 +718,22 @@ def torch_probe_ok() -> bool:
     return y == 1023 * 1024 // 2
 
 
-@pytest.mark.parametrize("model", [0, TWO])
+@pytest.mark.parametrize("model", [0, TWO, "pq", "crossing"])
 def test_streamed_tile_width_does_not_change_results(model):
     """The streamed tier's tile width (columns per CTA, an autotuner knob):
     widths of 32, 96 (a ragged last tile), 128 and 1024 columns give the
-    same lattices, heights and counters, and they equal the oracle's."""
-    kw = dict(model=model, L=1 << 18, domain_sites=32 if model == 0 else 64, samples_per_real=2, p_thr=th(0.6),
+    same lattices, heights and counters, and they equal the oracle's -- on
+    a ring, two lanes with turning sites, independent p and q classes, and
+    two lanes with crossing marks (two quenched planes each)."""
+    m = TWO if model in (TWO, "crossing") else 0
+    kw = dict(model=m, L=1 << 18, domain_sites=32 if m == 0 else 64, samples_per_real=2, p_thr=th(0.6),
               q_thr=th(0.3), seed=81, init_kind=1, init_seed=82)
     if model == TWO:
         kw.update(dis_kind=A.ASEP_DIS_TURNING, dis_a_thr=th(0.05), dis_b_thr=th(0.1), dis_seed=83)
+    elif model == "pq":
+        kw.update(dis_kind=PQ, dis_a_thr=th(0.5), dis_b_thr=th(0.1), dis_c_thr=th(0.2), dis_seed=84)
+    elif model == "crossing":
+        kw.update(dis_kind=XING, dis_a_thr=th(0.5), dis_b_thr=th(0.8), dis_c_thr=th(0.2), dis_seed=85)
     times = [0, 3, 7]
     runs = {}
     for cols in (32, 96, 128, 1024):

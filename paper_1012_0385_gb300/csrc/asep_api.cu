@@ -420,6 +420,8 @@ Rates rates(const asep_ctx* ctx) {
   r.omega_slow = ctx->p.dis_kind == ASEP_DIS_CROSSING ? ctx->p.dis_c_thr : r.omega;
   r.p_always = r.p == ASEP_ALWAYS;
   r.q_always = r.q == ASEP_ALWAYS;
+  r.pb = hop_bound(r.p);
+  r.qb = hop_bound(r.q);
   return r;
 }
 

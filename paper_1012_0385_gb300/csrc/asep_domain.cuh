@@ -53,6 +53,28 @@ __device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& 
   // byte offset of row (j >> 5) of this half: (r & (D - 1) & ~31) * (4 Cp / 32)
   const uint32_t cpb = CP ? CP * 4u : a.Cp * 4u;  // row pitch in bytes (compile-time when CP != 0)
   uint32_t o0 = base_b + (r & a.row_bits) * row_scale_b;
+  if (MODEL == kRing && DIS == kDisNone) {
+    // Both hop tests from one key: bits 31 and 30 hold sites i+1 and i, bits 29..0 hold r >> 2.  A left
+    // hop (sites 01 -> bits 10) is accepted iff the key, read as signed, lies in [INT_MIN, INT_MIN + q/4);
+    // adding 2^30 carries a right-hop pattern (bits 01) into the same window, tested against p/4
+    // (Rates::pb, qb).  For thresholds that are multiples of 4096, r < t iff r >> 2 < t >> 2.
+    uint32_t* p0 = reinterpret_cast<uint32_t*>(cur + o0);
+    uint32_t* p1 = reinterpret_cast<uint32_t*>(cur + o0 + cpb);
+    const uint32_t w0 = *p0;
+    const uint32_t w1 = *p1;
+    const uint32_t key = __funnelshift_l(r, __funnelshift_r(w0, w1, r), 30);
+    const bool hopL = static_cast<int32_t>(key) < a.rates.qb;
+    const bool hopR = static_cast<int32_t>(key + 0x40000000u) < a.rates.pb;
+    if (valid && (hopR || hopL)) {
+      *p0 = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
+      *p1 = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
+    }
+    if (COUNT) {
+      cnt.a += valid && hopR;
+      cnt.b += valid && hopL;
+    }
+    return;
+  }
   bool okR, okL;
   if (MODEL == kTwoLane) {
     const uint32_t laneB = (r >> a.logD) & 1u;

@@ -38,7 +38,14 @@ struct Rates {
   uint32_t omega;         // two lanes: lane-change probability per sweep (crossing kind: unmarked sites)
   uint32_t omega_slow;    // two lanes, crossing kind: lane-change probability at marked sites
   bool p_always, q_always;  // p / q == 0xffffffff (a draw r < t test alone cannot say "always")
+  // Signed bounds INT_MIN + t / 4 of p and q (INT_MIN + 2^30 for "always") for the ring's one-key
+  // hop test (asep_domain.cuh): r < t iff r >> 2 < t >> 2 when t is a multiple of 4096.
+  int32_t pb, qb;
 };
+
+inline int32_t hop_bound(uint32_t t) {
+  return static_cast<int32_t>(0x80000000u + (t == 0xFFFFFFFFu ? (1u << 30) : (t >> 2)));
+}
 
 // Device-side clock of a context: the sweep index of the next sweep and the
 // index of the first sample time not yet recorded.  Kernels read it; only the

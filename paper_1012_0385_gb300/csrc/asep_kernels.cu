@@ -612,7 +612,7 @@ __global__ void k_philox_bench(uint32_t calls, uint32_t* sink) {
 // 10 and r < p, or 01 and r < q.  The pair carries from attempt to attempt,
 // so the chain is as dependent as on the lattice; each thread writes its final
 // pair to sink[2 tid], sink[2 tid + 1].
-__global__ void k_attempt_bench(uint32_t calls, uint32_t p, uint32_t q, const KeySchedule ks, uint32_t* sink) {
+__global__ void k_attempt_bench(uint32_t calls, int32_t pb, int32_t qb, const KeySchedule ks, uint32_t* sink) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t w0 = 0x55555555u ^ tid;
   uint32_t w1 = 0xAAAAAAAAu ^ (tid * 0x9E3779B9u);
@@ -622,8 +622,9 @@ __global__ void k_attempt_bench(uint32_t calls, uint32_t p, uint32_t q, const Ke
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const uint32_t r = rs[i];
-      const uint32_t pat = __funnelshift_r(w0, w1, r) & 3u;
-      const bool hop = (pat == 1u && r < p) || (pat == 2u && r < q);
+      // the ring attempt's one-key hop test (asep_domain.cuh)
+      const uint32_t key = __funnelshift_l(r, __funnelshift_r(w0, w1, r), 30);
+      const bool hop = static_cast<int32_t>(key) < qb || static_cast<int32_t>(key + 0x40000000u) < pb;
       if (hop) {
         w0 ^= __funnelshift_l(0u, 3u, r);
         w1 ^= __funnelshift_l(3u, 0u, r);
@@ -638,7 +639,7 @@ __global__ void k_attempt_bench(uint32_t calls, uint32_t p, uint32_t q, const Ke
 
 cudaError_t launch_attempt_bench(uint32_t blocks, uint32_t threads, uint32_t calls, uint32_t p, uint32_t q,
                                  uint32_t* sink, cudaStream_t st) {
-  k_attempt_bench<<<blocks, threads, 0, st>>>(calls, p, q, key_schedule(kBenchSeed), sink);
+  k_attempt_bench<<<blocks, threads, 0, st>>>(calls, hop_bound(p), hop_bound(q), key_schedule(kBenchSeed), sink);
   return cudaGetLastError();
 }
 

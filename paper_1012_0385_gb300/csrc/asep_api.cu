@@ -422,6 +422,8 @@ Rates rates(const asep_ctx* ctx) {
   r.q_always = r.q == ASEP_ALWAYS;
   r.pb = hop_bound(r.p);
   r.qb = hop_bound(r.q);
+  r.pb_slow = hop_bound(r.p_slow);
+  r.qb_slow = hop_bound(r.q_slow);
   return r;
 }
 

@@ -44,43 +44,28 @@ struct Lane {
 // words are rows `row` and `row + 1` of the lane's own column (row 2D/32 is
 // the mirror of the next column's row 0), both loaded unconditionally; the
 // 64-bit flip mask (3 << j across the word pair) is applied under one
-// predicate.  Thresholds t are 0, multiples of 4096 or "always", and for the
-// multiples r < t is the same test as (r & 0xfffff000) < t, so only the
-// always flag needs separate handling.  `valid` is k <= K.
+// predicate.  `valid` is k <= K.
+//
+// Both hop tests come from one key: bits 31 and 30 hold sites i+1 and i (the
+// funnel-shifted word pair), bits 29..0 hold r >> 2.  A left hop (sites 01,
+// key bits 10) is accepted iff the key, read as signed, lies below
+// INT_MIN + t/4 for the left rate t; adding 2^30 carries a right-hop pattern
+// (bits 01) into the same window, tested against the right rate's bound
+// (hop_bound: INT_MIN + t/4, INT_MIN + 2^30 for "always", INT_MIN for 0).
+// Thresholds are multiples of 4096, for which r < t iff r >> 2 < t >> 2, so
+// the test equals u < t of the definition; the other two patterns fall
+// outside the window.
 template <uint32_t MODEL, uint32_t DIS, bool COUNT, uint32_t CP>
 __device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& a, uint32_t PWb, uint32_t base_b,
                                         uint32_t row_scale_b, uint32_t r, bool valid, Cnt& cnt) {
   // byte offset of row (j >> 5) of this half: (r & (D - 1) & ~31) * (4 Cp / 32)
   const uint32_t cpb = CP ? CP * 4u : a.Cp * 4u;  // row pitch in bytes (compile-time when CP != 0)
   uint32_t o0 = base_b + (r & a.row_bits) * row_scale_b;
-  if (MODEL == kRing && DIS == kDisNone) {
-    // Both hop tests from one key: bits 31 and 30 hold sites i+1 and i, bits 29..0 hold r >> 2.  A left
-    // hop (sites 01 -> bits 10) is accepted iff the key, read as signed, lies in [INT_MIN, INT_MIN + q/4);
-    // adding 2^30 carries a right-hop pattern (bits 01) into the same window, tested against p/4
-    // (Rates::pb, qb).  For thresholds that are multiples of 4096, r < t iff r >> 2 < t >> 2.
-    uint32_t* p0 = reinterpret_cast<uint32_t*>(cur + o0);
-    uint32_t* p1 = reinterpret_cast<uint32_t*>(cur + o0 + cpb);
-    const uint32_t w0 = *p0;
-    const uint32_t w1 = *p1;
-    const uint32_t key = __funnelshift_l(r, __funnelshift_r(w0, w1, r), 30);
-    const bool hopL = static_cast<int32_t>(key) < a.rates.qb;
-    const bool hopR = static_cast<int32_t>(key + 0x40000000u) < a.rates.pb;
-    if (valid && (hopR || hopL)) {
-      *p0 = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
-      *p1 = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
-    }
-    if (COUNT) {
-      cnt.a += valid && hopR;
-      cnt.b += valid && hopL;
-    }
-    return;
-  }
-  bool okR, okL;
+  int32_t bR = a.rates.pb, bL = a.rates.qb;  // bounds of the right and left hop
+  uint32_t laneB = 0;
   if (MODEL == kTwoLane) {
-    const uint32_t laneB = (r >> a.logD) & 1u;
+    laneB = (r >> a.logD) & 1u;  // lane A hops right only (p), lane B left only (q)
     o0 += laneB * PWb;
-    okR = !laneB && (a.rates.p_always || r < a.rates.p);  // lane A: 10 -> 01
-    okL = laneB && (a.rates.q_always || r < a.rates.q);   // lane B: 01 -> 10
   } else if (DIS == kDisBimodal || DIS == kDisBimodalPQ) {
     const uint32_t c0 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0);
     const uint32_t c1 = *reinterpret_cast<const uint32_t*>(cur + PWb + o0 + cpb);
@@ -91,25 +76,20 @@ __device__ __forceinline__ void attempt(unsigned char* cur, const DomainLaunch& 
       const uint32_t d1 = *reinterpret_cast<const uint32_t*>(cur + 2u * PWb + o0 + cpb);
       qc = __funnelshift_r(d0, d1, r);
     }
-    const uint32_t u = r & kAcceptMask;
-    okR = u < ((pc & 1u) ? a.rates.p_slow : a.rates.p);
-    okL = u < ((qc & 2u) ? a.rates.q_slow : a.rates.q);
-  } else {
-    okR = a.rates.p_always || r < a.rates.p;
-    okL = a.rates.q_always || r < a.rates.q;
+    bR = (pc & 1u) ? a.rates.pb_slow : bR;  // right hop across (i, i+1): p_i
+    bL = (qc & 2u) ? a.rates.qb_slow : bL;  // left hop: q_{i+1}
   }
   uint32_t* p0 = reinterpret_cast<uint32_t*>(cur + o0);
   uint32_t* p1 = reinterpret_cast<uint32_t*>(cur + o0 + cpb);
   const uint32_t w0 = *p0;
   const uint32_t w1 = *p1;
-  // the bond's two sites: bit 0 = site i, bit 1 = site i+1 (shift = r mod 32).  On the ring they are
-  // compared at bits 30-31 instead: a left shift can issue on the multiply-add unit, where the mask
-  // needs the busier integer pipe (measured +1.5 % on the growth workload; two lanes keep the mask)
-  const uint32_t x = __funnelshift_r(w0, w1, r);
-  constexpr uint32_t kAt = MODEL == kRing ? 30u : 0u;
-  const uint32_t pat = MODEL == kRing ? x << kAt : x & 3u;
-  const bool hopR = okR && pat == (1u << kAt);
-  const bool hopL = okL && pat == (2u << kAt);
+  const uint32_t key = __funnelshift_l(r, __funnelshift_r(w0, w1, r), 30);
+  bool hopL = static_cast<int32_t>(key) < bL;
+  bool hopR = static_cast<int32_t>(key + 0x40000000u) < bR;
+  if (MODEL == kTwoLane) {
+    hopR = hopR && !laneB;
+    hopL = hopL && laneB;
+  }
   if (valid && (hopR || hopL)) {
     *p0 = w0 ^ __funnelshift_l(0u, 3u, r);  // 3 << (j mod 32), truncated
     *p1 = w1 ^ __funnelshift_l(3u, 0u, r);  // 1 when j mod 32 == 31, else 0
@@ -193,17 +173,21 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
   // no per-attempt count test; the remaining calls up to Kmax test k <= K.  A
   // domain's attempts keep their order either way.  One call per iteration on
   // the plain ring (measured fastest), two with a quenched or second plane.
-  uint32_t call = 1;
+  // The fast calls are 1 .. (Kmin - 3) / 4; call k's counter is call 1's with k - 1 added at bit 12
+  // of word 1 (the call field), so the loop steps that word.
+  uint4 ctr = ctr_of(s, kTagDom, 1, ln.n_glob, dd);
+  const uint32_t n_fast = Kmin >= 3u ? (Kmin - 3u) >> 2 : 0u;
+  const uint32_t y_end = ctr.y + (n_fast << 12);
 #pragma unroll(MODEL == kRing && DIS == kDisNone ? 1 : 2)
-  for (; (call << 2) + 3 <= Kmin; ++call) {
-    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
+  for (; ctr.y != y_end; ctr.y += 1u << 12) {
+    const uint4 y = philox10(ctr, a.ks);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, true, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, true, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.z, true, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.w, true, cnt);
   }
 #pragma unroll 1
-  for (; (call << 2) <= Kmax; ++call) {
+  for (uint32_t call = n_fast + 1; (call << 2) <= Kmax; ++call) {
     const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
     const uint32_t k = call << 2;
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);

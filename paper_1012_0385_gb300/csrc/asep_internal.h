@@ -38,9 +38,10 @@ struct Rates {
   uint32_t omega;         // two lanes: lane-change probability per sweep (crossing kind: unmarked sites)
   uint32_t omega_slow;    // two lanes, crossing kind: lane-change probability at marked sites
   bool p_always, q_always;  // p / q == 0xffffffff (a draw r < t test alone cannot say "always")
-  // Signed bounds INT_MIN + t / 4 of p and q (INT_MIN + 2^30 for "always") for the ring's one-key
-  // hop test (asep_domain.cuh): r < t iff r >> 2 < t >> 2 when t is a multiple of 4096.
-  int32_t pb, qb;
+  // Signed bounds INT_MIN + t / 4 of p, q, p_slow, q_slow (INT_MIN + 2^30 for "always") for the
+  // one-key hop test of the domain attempt (asep_domain.cuh): r < t iff r >> 2 < t >> 2 when t is a
+  // multiple of 4096.
+  int32_t pb, qb, pb_slow, qb_slow;
 };
 
 inline int32_t hop_bound(uint32_t t) {

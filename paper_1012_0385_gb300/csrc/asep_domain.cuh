@@ -171,29 +171,39 @@ __device__ __forceinline__ void run_phase(uint32_t* cur, uint32_t* scr, bool sor
   attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, x0.w, 3 <= K, cnt);
   // Calls whose four attempts every lane of the warp makes (k + 3 <= Kmin) need
   // no per-attempt count test; the remaining calls up to Kmax test k <= K.  A
-  // domain's attempts keep their order either way.  Two calls per iteration
-  // (on the plain ring 0.8 % faster than one).
-  // The fast calls are 1 .. (Kmin - 3) / 4; call k's counter is call 1's with k - 1 added at bit 12
-  // of word 1 (the call field), so the loop steps that word.
+  // domain's attempts keep their order either way.  The fast calls are
+  // 1 .. (Kmin - 3) / 4; call k's counter is call 1's with k - 1 added at bit 12
+  // of word 1 (the call field), so the loop steps that word.  Each iteration
+  // draws the next call's words before it applies the current call's four
+  // attempts (the random stream does not depend on the lattice), so Philox's
+  // rounds overlap the attempts' dependent chain; two iterations per loop trip.
   uint4 ctr = ctr_of(s, kTagDom, 1, ln.n_glob, dd);
   const uint32_t n_fast = Kmin >= 3u ? (Kmin - 3u) >> 2 : 0u;
   const uint32_t y_end = ctr.y + (n_fast << 12);
+  uint4 y = philox10(ctr, a.ks);  // call n_fast + 1's words when the fast loop ends
 #pragma unroll 2
-  for (; ctr.y != y_end; ctr.y += 1u << 12) {
-    const uint4 y = philox10(ctr, a.ks);
+  for (; ctr.y != y_end;) {
+    ctr.y += 1u << 12;
+    const uint4 yn = philox10(ctr, a.ks);  // the next call, ahead of this call's attempts
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, true, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, true, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.z, true, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.w, true, cnt);
+    y = yn;
   }
 #pragma unroll 1
   for (uint32_t call = n_fast + 1; (call << 2) <= Kmax; ++call) {
-    const uint4 y = philox10(ctr_of(s, kTagDom, call, ln.n_glob, dd), a.ks);
     const uint32_t k = call << 2;
+    uint4 yn = y;
+    if (k + 4 <= Kmax) {  // warp-uniform
+      ctr.y += 1u << 12;
+      yn = philox10(ctr, a.ks);
+    }
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.x, k <= K, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.y, k + 1 <= K, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.z, k + 2 <= K, cnt);
     attempt<MODEL, DIS, COUNT, CP>(cb, a, PWb, base_b, row_scale_b, y.w, k + 3 <= K, cnt);
+    y = yn;
   }
 }
 
